@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused RLBM stream-collide step on GB300.
+
+Metric: GLUPS (10^9 lattice-node updates per second) of the stream-collide
+step, and its fraction of the measured HBM bandwidth.  Default workload:
+1024 x 1024 periodic lattice, FP32 populations, tau = 0.52, stirring force on
+the shell 4 <= |k| <= 6 (amplitude 1e-5, redrawn every 100 steps), started
+at rest -- the paper's stirred-turbulence runs (Sec. 5) at N = 1024.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the lattice's stream; between timed steps a 256 MB buffer (larger than
+the 129 MB L2) is rewritten on the same stream so each step starts with a
+cold L2.  Multi-GPU (torchrun): each rank advances its own independent
+replica (no data exchange; weak scaling); value = sum over ranks, time =
+max over ranks.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16", "f16"])
+    ap.add_argument("--landau", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "staged"])
+    ap.add_argument("--n", type=int, default=0, help="override lattice side (default: the workload's)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-form table, e2e and CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_for(args):
+    w = workloads.STIRRED_1024
+    n = args.n or w.nx
+    return w, n
+
+
+def forcing_of(w):
+    return dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw)
+
+
+def time_steps(torch, lat, steps, flush):
+    """Per-step CUDA-event timing on the lattice stream with an L2 flush in between."""
+    stream = lat._torch_stream
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            flush.fill_(1.0)
+            a.record(stream)
+            lat.step(1)
+            b.record(stream)
+            evs.append((a, b))
+    stream.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in evs])  # ms
+
+
+def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, init=None):
+    lat = rl.Lattice(n, n, w.tau, dtype=form, landau=landau, kernel=kernel, forcing=forcing_of(w))
+    if init is not None:
+        lat.init_fields(*init)
+    else:
+        lat.init_fields()
+    lat.step(warmup)
+    lat.synchronize()
+    ms = time_steps(torch, lat, steps, flush)
+    info = lat.info()
+    # steps that started a forcing epoch also carry the force re-synthesis
+    redraw = w.redraw
+    first = warmup
+    is_epoch = np.array([((first + i) % redraw) == 0 for i in range(steps)])
+    kernel_ms = ms[~is_epoch].mean() if (~is_epoch).any() else ms.mean()
+    lat.close()
+    return ms, kernel_ms, info, int(is_epoch.sum())
+
+
+def parity_error(rl, oracle, form, landau):
+    """Max relative error vs the FP64 oracle after 100 forced steps on a
+    128 x 128 lattice started from seeded smooth fields (the parity bar)."""
+    n, nsteps = 128, 100
+    w = workloads.STIRRED_1024
+    fields = workloads.random_smooth(n, n, seed=2024, deps=0.02, vmax=0.02)
+    fz = dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp * 10, seed=w.seed, redraw_period=w.redraw // 2)
+    lat = rl.Lattice(n, n, w.tau, dtype=form, landau=landau, forcing=fz)
+    lat.init_fields(*fields)
+    lat.step(nsteps)
+    e_g, vx_g, vy_g, _ = lat.moments()
+    lat.close()
+    f = oracle.init(n, n, *fields)
+    oracle.run(f, w.tau, nsteps, kmin=fz["kmin"], kmax=fz["kmax"], amp=fz["amp"], seed=fz["seed"],
+               redraw=fz["redraw_period"])
+    e_o, vx_o, vy_o = oracle.fields(f)
+    err_e = float(np.max(np.abs(e_g - e_o)) / np.max(np.abs(e_o)))
+    vn = max(np.max(np.abs(vx_o)), np.max(np.abs(vy_o)))
+    err_v = float(max(np.max(np.abs(vx_g - vx_o)), np.max(np.abs(vy_g - vy_o))) / vn)
+    return {"eps": err_e, "v": err_v, "case": "128x128, 100 forced steps from seeded smooth fields"}
+
+
+def cpu_oracle_glups(oracle, w, n, budget_s):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload:
+    the full n x n lattice if a step fits the budget, else a band of rows
+    (same shape per node); returns (GLUPS, description, threads)."""
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    rows = n
+    f = oracle.init(n, rows)
+    tmp_steps = 1
+    t0 = time.perf_counter()
+    oracle.run(f, w.tau, tmp_steps, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+    one = time.perf_counter() - t0
+    nsteps = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(f, w.tau, nsteps, step0=tmp_steps, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed,
+               redraw=w.redraw)
+    dt = time.perf_counter() - t0
+    glups = n * rows * nsteps / dt / 1e9
+    return glups, "%dx%d lattice, %d forced steps (FP64 oracle, OpenMP)" % (n, rows, nsteps), threads
+
+
+def e2e_glups(rl, w, n, form, landau, reps=3, steps_per_call=100):
+    """Through the public API with host buffers: upload the initial fields
+    from host memory, advance steps_per_call steps, read the fields back."""
+    eps, vx, vy = workloads.random_smooth(n, n, seed=5, deps=0.01, vmax=0.01)
+    lat = rl.Lattice(n, n, w.tau, dtype=form, landau=landau, forcing=forcing_of(w))
+    lat.init_fields(eps, vx, vy)
+    lat.step(steps_per_call)
+    lat.moments()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        lat.init_fields(eps, vx, vy)
+        lat.step(steps_per_call)
+        out = lat.moments()
+        times.append(time.perf_counter() - t0)
+    lat.close()
+    dt = float(np.median(times))
+    h2d = 3 * n * n * 8
+    d2h = 3 * n * n * 8 + 3 * 8
+    del out
+    return {"value": n * n * steps_per_call / dt / 1e9, "unit": "GLUPS",
+            "h2d_bytes_per_step": h2d / steps_per_call, "d2h_bytes_per_step": d2h / steps_per_call,
+            "steps_per_call": steps_per_call}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w, n = workload_for(args)
+    total_steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    oracle.set_threads(os.cpu_count() or 1)
+    # bounded sample: the full lattice, steps scaled so the run ends in minutes
+    f = oracle.init(n, n)
+    t0 = time.perf_counter()
+    oracle.run(f, w.tau, 1, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+    one = time.perf_counter() - t0
+    per_step_budget = 60.0 / max(1, total_steps + warm)
+    nsub = max(1, int(per_step_budget / max(one, 1e-6)))
+    nsub = min(nsub, 50)
+    for _ in range(min(warm, 3)):
+        oracle.run(f, w.tau, 1, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+    t0 = time.perf_counter()
+    steps_done = 0
+    for _ in range(total_steps):
+        oracle.run(f, w.tau, nsub, step0=steps_done, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed,
+                   redraw=w.redraw)
+        steps_done += nsub
+        if time.perf_counter() - t0 > 150:
+            break
+    dt = time.perf_counter() - t0
+    glups = n * n * steps_done / dt / 1e9
+    line = {"impl": "reference", "metric": "GLUPS of the fused stream-collide step", "value": glups, "unit": "GLUPS",
+            "n_gpus": args.gpus, "steps": total_steps, "warmup": args.warmup,
+            "ms_per_step": dt / steps_done * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "nx": n, "ny": n, "form": "f64 CPU oracle", "tau": w.tau},
+            "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "%dx%d lattice, %d forced steps" % (n, n, steps_done)},
+            "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+        __graft_entry__.build()
+    import paper_2101_06187_gb300 as rl
+
+    w, n = workload_for(args)
+    K, W = args.steps, max(3, args.warmup)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    dev_index = torch.cuda.current_device()
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = int(phys[dev_index]) if phys and phys[0].isdigit() and dev_index < len(phys) else dev_index
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(smi_index) as clocks:
+        ms, kernel_ms, info, n_epoch = measure_form(torch, rl, w, n, args.form, args.landau, args.kernel, K, W, flush)
+    torch.cuda.synchronize()
+    step_ms = float(ms.mean())
+    total_s = float(ms.sum()) / 1e3
+    nodes = n * n
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        torch.distributed.barrier()
+    glups_total = world * nodes * K / total_s / 1e9
+
+    hbm_peak, peak_kind = load_peaks()
+    bpn = int(info["bytes_per_node"])
+    achieved = bpn * nodes / (kernel_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as fh:
+                tj = json.load(fh)
+            key = "%s_%s_%s_%d" % (args.form, args.landau, info["kernel"], n)
+            import hashlib
+            src = os.path.join(ROOT, "paper_2101_06187_gb300", "csrc")
+            hsh = hashlib.sha256()
+            for fn in sorted(os.listdir(src)):
+                if fn.endswith((".cu", ".cuh", ".h")):
+                    hsh.update(open(os.path.join(src, fn), "rb").read())
+            ent = tj.get(key)
+            if ent and ent.get("source_sha256") == hsh.hexdigest():
+                traffic = ent["bytes_per_launch"]
+        except (OSError, ValueError, KeyError):
+            traffic = None
+
+    line = {
+        "metric": "GLUPS of the fused stream-collide step (and fraction of HBM peak)",
+        "value": glups_total, "unit": "GLUPS", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.form != "f64" else "f64", "data": "synthetic",
+        "config": {"workload": w.name, "nx": n, "ny": n, "form": args.form, "landau": args.landau,
+                   "kernel": ["auto", "gather", "staged"][info["kernel"]], "tau": w.tau,
+                   "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm" if args.form != "f64" else "alu", "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "bytes_per_node": bpn,
+                     "kernel_ms": kernel_ms, "epoch_steps_in_timed_region": n_epoch},
+        "clocks": clocks.summary(),
+        "gpu_launches": int(K + 2 * n_epoch),
+    }
+
+    if rank == 0 and not args.no_extras:
+        import oracle
+        oracle.build()
+        oracle.set_threads(os.cpu_count() or 1)
+        forms = {}
+        for form, landau in (("f32", "fp64"), ("f32", "fp32"), ("f64", "fp64"), ("bf16", "fp64"), ("f16", "fp64")):
+            if form == args.form and landau == args.landau:
+                g = glups_total / world
+                km = kernel_ms
+                bp = bpn
+            else:
+                msf, km, inf, _ = measure_form(torch, rl, w, n, form, landau, args.kernel, min(K, 100), 5, flush)
+                g = nodes * len(msf) / (msf.sum() / 1e3) / 1e9
+                bp = int(inf["bytes_per_node"])
+            err = parity_error(rl, oracle, form, landau)
+            forms["%s/landau-%s" % (form, landau)] = {
+                "glups": g, "hbm_gbs": bp * nodes / (km / 1e3) / 1e9,
+                "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak, "bytes_per_node": bp,
+                "max_rel_err_vs_oracle": err}
+        line["forms"] = forms
+        line["e2e"] = e2e_glups(rl, w, n, args.form, args.landau)
+        g, desc, th = cpu_oracle_glups(oracle, w, n, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": g, "unit": "GLUPS", "cores": th, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

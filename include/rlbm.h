@@ -1,0 +1,208 @@
+/*
+ * rlbm.h -- C ABI of the GB300 relativistic lattice Boltzmann (RLBM)
+ * stream-collide library.
+ *
+ * The library advances a massless (ultra-relativistic) fluid on a periodic
+ * 2D lattice with the method of Watson, "Two Dimensional Turbulence in a
+ * Massless Fluid with a Relativistic Lattice Boltzmann Model"
+ * (arXiv:2101.06187):
+ *   - velocity space: the spherical "D3Q27" momentum node with one lattice
+ *     node in z (Sec. 5), i.e. the 26 unit directions of the spherical
+ *     degree-7 rule (faces 1/21, edges 4/105, corners 9/280); on a one-layer
+ *     lattice the z-mirror pairs stream and collide alike, so the library
+ *     stores 17 in-plane classes (their sums);
+ *   - one step (Sec. 3.3, loop (b)-(e)): pull-streaming with linear
+ *     interpolation from x - v_i (Sec. 3.2), moments T^{mu nu}
+ *     (Eq. energyMomentumIntegral), the Landau-Lifshitz frame (eps, u^mu)
+ *     (the eigenvalue problem closing Sec. 3.2), the truncated Juttner
+ *     equilibrium (Eqs. rel_pdf_exp, rel_pdf_exp_coef, stressEnergyT with
+ *     P = eps/3), Anderson-Witting relaxation (Eq. boltzmanneq_rel), and the
+ *     projected driving term (Eq. forceTerm, App. B);
+ *   - the stirring force of Sec. 5: random modes on a wavenumber shell,
+ *     zero mean, redrawn every `redraw_period` steps.
+ * Lattice units: Delta x = Delta t = 1; tau is the relaxation time in steps.
+ * Signature (-,+,+,+).
+ *
+ * Conventions for every call:
+ *   - Every call returns an rlbm_status.  After a CUDA error the handle's
+ *     status is sticky: later calls return RLBM_ERR_CUDA until destroy.
+ *     rlbm_last_error() gives a one-line message.
+ *   - Host arrays are FP64, row-major (y, x), nx*ny elements, owned by the
+ *     caller; device state is owned by the handle.
+ *   - "Async" calls are ordered on the handle's CUDA stream and return
+ *     before the GPU finishes; calls with host outputs synchronise it.
+ *   - A handle is not thread-safe; use one handle per thread.
+ */
+#ifndef RLBM_H
+#define RLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RLBM_API __attribute__((visibility("default")))
+#else
+#define RLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlbm rlbm_t;
+
+typedef enum {
+    RLBM_OK = 0,
+    RLBM_ERR_ARG = 1,      /* invalid argument (size, tau, forcing band, NULL handle ...) */
+    RLBM_ERR_ALLOC = 2,    /* device allocation failed */
+    RLBM_ERR_CUDA = 3,     /* a CUDA call or kernel failed (sticky) */
+    RLBM_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    RLBM_ERR_NAN = 5,      /* a non-finite or non-physical (|v| >= 1, eps <= 0) state was found */
+    RLBM_ERR_STATE = 6     /* call not valid in the handle's current state */
+} rlbm_status;
+
+/* Velocity stencil.  Only the paper's node exists: the 26-direction
+ * spherical rule on a one-layer (2D) lattice, stored as 17 in-plane classes;
+ * sound speed c_s^2 = 1/3 (P = eps/3). */
+typedef enum { RLBM_STENCIL_SPH26_SLAB = 0 } rlbm_stencil;
+
+/* Storage form of the populations.  All forms store the scaled deviation
+ * q_c = (f_c - W_c eps0) / (W_c s) of each class from the rest equilibrium.
+ * F64: FP64 storage and arithmetic.  F32: FP32 storage and arithmetic.
+ * BF16 / F16: 16-bit storage, FP32 arithmetic. */
+typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16 = 2, RLBM_F16 = 3 } rlbm_dtype;
+
+/* Precision of the per-node Landau-frame solve for the F32/16-bit forms
+ * (the F64 form always solves in FP64). */
+typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
+
+/* Kernel variant of the fused step (RLBM_KERNEL_AUTO picks the fastest
+ * available for the form and lattice). */
+typedef enum { RLBM_KERNEL_AUTO = 0, RLBM_KERNEL_GATHER = 1, RLBM_KERNEL_STAGED = 2 } rlbm_kernel;
+
+/* Stirring force (Sec. 5).  Modes are the integer wavevectors k with
+ * kmin <= |k| <= kmax (k = 0 excluded), one per Hermitian pair (ky > 0, or
+ * ky = 0 and kx > 0), enumerated ky = 0..kmax, kx = -kmax..kmax.  In epoch e
+ * = step / redraw_period, mode m draws Philox4x32-10 with counter
+ * {e, m, 0, 0} (magnitude r*amp, phase) and {e, m, 1, 0} (direction), key
+ * {seed & 0xffffffff, seed >> 32}; each word pair (a, b) becomes the double
+ * (a * 2^21 + (b >> 11)) * 2^-53.  The force is
+ *   F(x) = sum_m 2 r_m amp (cos th_m, sin th_m) cos(2 pi (kx x/nx + ky y/ny) + ph_m).
+ * amp = 0 (or kmax = 0) disables forcing. */
+typedef struct {
+    int kmin;
+    int kmax;
+    double amp;
+    uint64_t seed;
+    int redraw_period; /* steps per epoch, >= 1 */
+} rlbm_forcing;
+
+/* Device allocator hooks.  alloc returns a device pointer of at least
+ * `bytes` (aligned to 256 bytes) or NULL; free releases it.  NULL alloc
+ * means cudaMalloc / cudaFree. */
+typedef void *(*rlbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*rlbm_free_fn)(void *ptr, size_t bytes, void *ctx);
+
+typedef struct {
+    int dtype;            /* rlbm_dtype (default RLBM_F32) */
+    int landau;           /* rlbm_landau (default RLBM_LANDAU_FP64) */
+    int kernel;           /* rlbm_kernel (default RLBM_KERNEL_AUTO) */
+    int use_graphs;       /* 1: replay the step loop as CUDA graphs (default 1) */
+    double eps0;          /* reference energy density of the deviation (default 1) */
+    double scale;         /* s of the deviation; 0 = default: 1 (F64/F32), 2^-6 (16-bit) */
+    void *stream;         /* cudaStream_t the handle works on; NULL = legacy default stream */
+    int device;           /* CUDA device ordinal; -1 = current device (default) */
+    rlbm_alloc_fn alloc;  /* optional device allocator */
+    rlbm_free_fn free;
+    void *alloc_ctx;
+} rlbm_opts;
+
+typedef struct {
+    int nx, ny, pitch;        /* lattice and row pitch (elements) of the device arrays */
+    int nclasses;             /* 17 stored in-plane classes */
+    int dtype;                /* rlbm_dtype */
+    int kernel;               /* rlbm_kernel actually used */
+    int nmodes;               /* forcing modes (0 = unforced) */
+    int64_t step;             /* steps taken since init */
+    double tau, eps0, scale;
+    size_t bytes_per_node;    /* algorithmic HBM bytes per lattice update */
+    size_t device_bytes;      /* device memory held by the handle */
+    const void *populations;  /* device pointer of the current state, [17][ny][pitch] of the storage type */
+} rlbm_info_t;
+
+/* Fill *opts with the defaults listed above. */
+RLBM_API void rlbm_opts_default(rlbm_opts *opts);
+
+/* Create a lattice of nx x ny nodes (nx, ny >= 4) with relaxation time
+ * tau > 1/2 (Eq. boltzmanneq_rel; eta = tau (eps + P)/5, Sec. 3.1) and
+ * optional forcing (NULL = none; needs kmax < min(nx, ny)/2, amp >= 0,
+ * 1 <= kmin <= kmax).  opts may be NULL (defaults).  The state starts as the
+ * "flat" equilibrium eps = eps0, v = 0 (Sec. 5) at step 0.  Allocates all
+ * device memory here; the step loop allocates nothing.
+ * Errors: RLBM_ERR_ARG (bad size, tau, forcing, opts), RLBM_ERR_ALLOC,
+ * RLBM_ERR_CUDA.  *out is NULL on error. */
+RLBM_API rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const rlbm_forcing *forcing,
+                        const rlbm_opts *opts, rlbm_t **out);
+
+/* Initialise with f = f_eq(eps, v) (step (a) of Sec. 3.3) from host FP64
+ * fields eps (> 0) and 3-velocity vx, vy (|v| < 1), nx*ny each, row-major;
+ * any NULL means eps = eps0 resp. v = 0.  Resets the step counter to 0.
+ * Copies the fields through pinned staging (synchronous). */
+RLBM_API rlbm_status rlbm_init_fields(rlbm_t *h, const double *eps, const double *vx, const double *vy);
+
+/* Same, from device FP64 arrays (async on the handle's stream). */
+RLBM_API rlbm_status rlbm_init_fields_device(rlbm_t *h, const double *d_eps, const double *d_vx, const double *d_vy);
+
+/* Advance n >= 0 steps (async).  Each step: stream + collide + force, one
+ * fused kernel; the force field is re-synthesised at each epoch start. */
+RLBM_API rlbm_status rlbm_step(rlbm_t *h, int n);
+
+/* Macroscopic fields seen by the next collision (post-stream moments and
+ * Landau frame): eps and the 3-velocity v = u^i/u^0, nx*ny FP64 each on the
+ * host (any may be NULL), and totals[3] = sum over nodes of (T^00, T^0x,
+ * T^0y) in FP64 (may be NULL).  Synchronises.  Returns RLBM_ERR_NAN if any
+ * node's solve failed (output entries of such nodes are NaN). */
+RLBM_API rlbm_status rlbm_moments(rlbm_t *h, double *eps, double *vx, double *vy, double totals[3]);
+
+/* Same into device FP64 buffers (nx*ny each; any may be NULL) and device
+ * totals[3]; async, no NaN check. */
+RLBM_API rlbm_status rlbm_moments_device(rlbm_t *h, double *d_eps, double *d_vx, double *d_vy, double *d_totals);
+
+/* Energy spectrum E(n), n = 0..nshells-1 (Sec. 4): v_hat(k) = (1/(nx ny))
+ * sum_x v(x) e^{-2 pi i (kx x/nx + ky y/ny)} of the 3-velocity field of
+ * rlbm_moments, shell n = {k : |k| in [n - 1/2, n + 1/2)} with signed
+ * integer wavenumbers, E(n) = 1/2 sum_shell |v_hat_x|^2 + |v_hat_y|^2.
+ * Ek is a host array of nshells doubles.  Synchronises. */
+RLBM_API rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek);
+
+/* Decoded populations f_c = W_c (eps0 + s q_c) of the 17 stored classes,
+ * host FP64 [17][ny][nx] (class order: rest; (1,0),(-1,0),(0,1),(0,-1);
+ * (a,0),(-a,0),(0,a),(0,-a); (a,a),(-a,a),(a,-a),(-a,-a);
+ * (b,b),(-b,b),(b,-b),(-b,-b); a = 1/sqrt2, b = 1/sqrt3).  Synchronises. */
+RLBM_API rlbm_status rlbm_get_populations(rlbm_t *h, double *f);
+
+/* Set the post-collision state from host FP64 populations in that layout
+ * (encoded to the storage form; synchronous). */
+RLBM_API rlbm_status rlbm_set_populations(rlbm_t *h, const double *f);
+
+/* Force field of the current epoch (the one the next step uses), host FP64
+ * nx*ny each.  Synchronises. */
+RLBM_API rlbm_status rlbm_get_force(rlbm_t *h, double *Fx, double *Fy);
+
+RLBM_API rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info);
+
+/* Wait for all work queued on the handle's stream. */
+RLBM_API rlbm_status rlbm_synchronize(rlbm_t *h);
+
+/* Copy the handle's last error message (NUL-terminated, truncated to len). */
+RLBM_API rlbm_status rlbm_last_error(rlbm_t *h, char *buf, size_t len);
+
+/* Release the handle and its device memory (NULL-safe; synchronises). */
+RLBM_API void rlbm_destroy(rlbm_t *h);
+
+RLBM_API const char *rlbm_status_string(rlbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLBM_H */

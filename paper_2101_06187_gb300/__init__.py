@@ -1,0 +1,380 @@
+"""GB300 relativistic lattice Boltzmann (RLBM) stream-collide library.
+
+Thin ctypes binding of the C ABI in ``include/rlbm.h`` (``librlbm.so``, built
+from ``csrc/`` by ``build.py``).  Every step of the method runs in the CUDA
+kernels of that library; this module only marshals arguments.  PyTorch is
+used, when present, for device memory (the caching allocator) and streams.
+
+The functions ``rlbm_create``, ``rlbm_init_fields``, ``rlbm_step``,
+``rlbm_moments``, ``rlbm_energy_spectrum``, ``rlbm_destroy`` ... carry the
+names of the C entry points; ``Lattice`` bundles them as methods.
+
+There is no CPU fallback: if the CUDA library is missing or fails to load,
+every call raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librlbm.so")
+
+RLBM_OK, RLBM_ERR_ARG, RLBM_ERR_ALLOC, RLBM_ERR_CUDA, RLBM_ERR_TIMEOUT, RLBM_ERR_NAN, RLBM_ERR_STATE = range(7)
+RLBM_STENCIL_SPH26_SLAB = 0
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+LANDAU = {"fp64": 0, "fp32": 1}
+KERNELS = {"auto": 0, "gather": 1, "staged": 2}
+NCLASSES = 17
+
+# Symbols declared in include/rlbm.h (checked by the ABI test).
+EXPORTS = (
+    "rlbm_opts_default", "rlbm_create", "rlbm_init_fields", "rlbm_init_fields_device", "rlbm_step", "rlbm_moments",
+    "rlbm_moments_device", "rlbm_energy_spectrum", "rlbm_get_populations", "rlbm_set_populations", "rlbm_get_force",
+    "rlbm_get_info", "rlbm_synchronize", "rlbm_last_error", "rlbm_destroy", "rlbm_status_string",
+)
+
+
+class RLBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+class Forcing(ctypes.Structure):
+    _fields_ = [("kmin", ctypes.c_int), ("kmax", ctypes.c_int), ("amp", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("redraw_period", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("landau", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("eps0", ctypes.c_double), ("scale", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_int), ("nclasses", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("kernel", ctypes.c_int), ("nmodes", ctypes.c_int),
+                ("step", ctypes.c_int64), ("tau", ctypes.c_double), ("eps0", ctypes.c_double),
+                ("scale", ctypes.c_double), ("bytes_per_node", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
+                ("populations", ctypes.c_void_p)]
+
+
+_lib_lock = threading.Lock()
+_lib_handle = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def _load():
+    global _lib_handle
+    with _lib_lock:
+        if _lib_handle is not None:
+            return _lib_handle
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is not built; run paper_2101_06187_gb300.build.build()" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        h = ctypes.c_void_p
+        lib.rlbm_opts_default.argtypes = [ctypes.POINTER(Opts)]
+        lib.rlbm_opts_default.restype = None
+        lib.rlbm_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Forcing),
+                                    ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]
+        lib.rlbm_init_fields.argtypes = [h, _dp, _dp, _dp]
+        lib.rlbm_init_fields_device.argtypes = [h, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.rlbm_step.argtypes = [h, ctypes.c_int]
+        lib.rlbm_moments.argtypes = [h, _dp, _dp, _dp, _dp]
+        lib.rlbm_moments_device.argtypes = [h, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.rlbm_energy_spectrum.argtypes = [h, ctypes.c_int, _dp]
+        lib.rlbm_get_populations.argtypes = [h, _dp]
+        lib.rlbm_set_populations.argtypes = [h, _dp]
+        lib.rlbm_get_force.argtypes = [h, _dp, _dp]
+        lib.rlbm_get_info.argtypes = [h, ctypes.POINTER(Info)]
+        lib.rlbm_synchronize.argtypes = [h]
+        lib.rlbm_last_error.argtypes = [h, ctypes.c_char_p, ctypes.c_size_t]
+        lib.rlbm_destroy.argtypes = [h]
+        lib.rlbm_destroy.restype = None
+        lib.rlbm_status_string.argtypes = [ctypes.c_int]
+        lib.rlbm_status_string.restype = ctypes.c_char_p
+        for name in ("rlbm_create", "rlbm_init_fields", "rlbm_init_fields_device", "rlbm_step", "rlbm_moments",
+                     "rlbm_moments_device", "rlbm_energy_spectrum", "rlbm_get_populations", "rlbm_set_populations",
+                     "rlbm_get_force", "rlbm_get_info", "rlbm_synchronize", "rlbm_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib_handle = lib
+        return lib
+
+
+def library():
+    """The loaded ctypes library (raises if it is not built)."""
+    return _load()
+
+
+def _check(h, st: int, what: str):
+    if st == RLBM_OK:
+        return
+    lib = _load()
+    msg = lib.rlbm_status_string(st).decode()
+    if h:
+        buf = ctypes.create_string_buffer(512)
+        lib.rlbm_last_error(h, buf, 512)
+        if buf.value:
+            msg += ": " + buf.value.decode()
+    raise RLBMError(st, "%s failed: %s" % (what, msg))
+
+
+def _f64(a, n) -> Optional[np.ndarray]:
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if a.size != n:
+        raise ValueError("expected %d elements, got %d" % (n, a.size))
+    return a
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+# ------------------------------------------------------------------ torch plumbing
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, handed to the library
+    through its allocator hooks."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+
+        def _alloc(nbytes, _ctx):
+            try:
+                return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+            except Exception:  # noqa: BLE001 - reported to C as NULL
+                return None
+
+        def _free(ptr, _nbytes, _ctx):
+            try:
+                self.torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:  # noqa: BLE001
+                pass
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+# ------------------------------------------------------------------ C-named entry points
+def rlbm_opts_default() -> Opts:
+    o = Opts()
+    _load().rlbm_opts_default(ctypes.byref(o))
+    return o
+
+
+def rlbm_create(nx: int, ny: int, stencil: int, tau: float, forcing: Optional[Forcing], opts: Optional[Opts]):
+    lib = _load()
+    out = ctypes.c_void_p()
+    st = lib.rlbm_create(int(nx), int(ny), int(stencil), float(tau), ctypes.byref(forcing) if forcing else None,
+                         ctypes.byref(opts) if opts else None, ctypes.byref(out))
+    _check(None, st, "rlbm_create")
+    return out
+
+
+def rlbm_init_fields(h, eps=None, vx=None, vy=None, n=None):
+    lib = _load()
+    st = lib.rlbm_init_fields(h, _p(eps), _p(vx), _p(vy))
+    _check(h, st, "rlbm_init_fields")
+
+
+def rlbm_init_fields_device(h, d_eps: int = 0, d_vx: int = 0, d_vy: int = 0):
+    _check(h, _load().rlbm_init_fields_device(h, d_eps or None, d_vx or None, d_vy or None),
+           "rlbm_init_fields_device")
+
+
+def rlbm_step(h, n: int):
+    _check(h, _load().rlbm_step(h, int(n)), "rlbm_step")
+
+
+def rlbm_moments(h, eps, vx, vy, totals):
+    st = _load().rlbm_moments(h, _p(eps), _p(vx), _p(vy), _p(totals))
+    _check(h, st, "rlbm_moments")
+
+
+def rlbm_moments_device(h, d_eps: int = 0, d_vx: int = 0, d_vy: int = 0, d_totals: int = 0):
+    st = _load().rlbm_moments_device(h, d_eps or None, d_vx or None, d_vy or None, d_totals or None)
+    _check(h, st, "rlbm_moments_device")
+
+
+def rlbm_energy_spectrum(h, nshells: int, Ek):
+    _check(h, _load().rlbm_energy_spectrum(h, int(nshells), _p(Ek)), "rlbm_energy_spectrum")
+
+
+def rlbm_get_populations(h, f):
+    _check(h, _load().rlbm_get_populations(h, _p(f)), "rlbm_get_populations")
+
+
+def rlbm_set_populations(h, f):
+    _check(h, _load().rlbm_set_populations(h, _p(f)), "rlbm_set_populations")
+
+
+def rlbm_get_force(h, Fx, Fy):
+    _check(h, _load().rlbm_get_force(h, _p(Fx), _p(Fy)), "rlbm_get_force")
+
+
+def rlbm_get_info(h) -> Info:
+    info = Info()
+    _check(h, _load().rlbm_get_info(h, ctypes.byref(info)), "rlbm_get_info")
+    return info
+
+
+def rlbm_synchronize(h):
+    _check(h, _load().rlbm_synchronize(h), "rlbm_synchronize")
+
+
+def rlbm_last_error(h) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _load().rlbm_last_error(h, buf, 512)
+    return buf.value.decode()
+
+
+def rlbm_status_string(status: int) -> str:
+    return _load().rlbm_status_string(int(status)).decode()
+
+
+def rlbm_destroy(h):
+    if h:
+        _load().rlbm_destroy(h)
+
+
+# ------------------------------------------------------------------ convenience class
+class Lattice:
+    """One periodic nx x ny RLBM lattice on a GPU.
+
+    dtype: "f64" | "f32" | "bf16" | "f16" (storage form); landau: "fp64" |
+    "fp32" (precision of the Landau solve in the 32/16-bit forms); forcing:
+    None or dict(kmin, kmax, amp, seed, redraw_period); allocator: "torch"
+    (PyTorch caching allocator) or "cuda" (cudaMalloc inside the library);
+    stream: a torch.cuda.Stream, an int cudaStream_t, or None (a new torch
+    stream for this lattice).
+    """
+
+    def __init__(self, nx: int, ny: int, tau: float, *, dtype: str = "f32", landau: str = "fp64",
+                 forcing: Optional[dict] = None, eps0: float = 1.0, scale: float = 0.0, kernel: str = "auto",
+                 use_graphs: bool = True, allocator: str = "torch", stream=None, device: Optional[int] = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the RLBM library runs on the GPU only")
+        self.nx, self.ny, self.tau = int(nx), int(ny), float(tau)
+        self._h = None
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = dev
+        if stream is None:
+            self._torch_stream = torch.cuda.Stream(device=dev)
+            s = self._torch_stream.cuda_stream
+        elif isinstance(stream, int):
+            self._torch_stream = None
+            s = stream
+        else:
+            self._torch_stream = stream
+            s = stream.cuda_stream
+        self.stream_handle = s
+        o = rlbm_opts_default()
+        o.dtype = DTYPES[dtype]
+        o.landau = LANDAU[landau]
+        o.kernel = KERNELS[kernel]
+        o.use_graphs = 1 if use_graphs else 0
+        o.eps0 = float(eps0)
+        o.scale = float(scale)
+        o.stream = s
+        o.device = dev
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(dev, s)
+            o.alloc = self._alloc.alloc
+            o.free = self._alloc.free
+        f = None
+        if forcing:
+            f = Forcing(int(forcing.get("kmin", 0)), int(forcing.get("kmax", 0)), float(forcing.get("amp", 0.0)),
+                        int(forcing.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF, int(forcing.get("redraw_period", 100)))
+        self.dtype = dtype
+        self._h = rlbm_create(self.nx, self.ny, RLBM_STENCIL_SPH26_SLAB, self.tau, f, o)
+
+    # -- life cycle
+    def close(self):
+        if self._h:
+            rlbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("lattice is closed")
+        return self._h
+
+    # -- calls
+    def init_fields(self, eps=None, vx=None, vy=None):
+        n = self.nx * self.ny
+        rlbm_init_fields(self.handle, _f64(eps, n), _f64(vx, n), _f64(vy, n))
+
+    def init_fields_device(self, eps=None, vx=None, vy=None):
+        ptr = lambda t: 0 if t is None else int(t.data_ptr())
+        rlbm_init_fields_device(self.handle, ptr(eps), ptr(vx), ptr(vy))
+
+    def step(self, n: int = 1):
+        rlbm_step(self.handle, n)
+
+    def moments(self):
+        """(eps, vx, vy, totals): (ny, nx) FP64 fields and totals[3]."""
+        eps = np.empty((self.ny, self.nx))
+        vx = np.empty((self.ny, self.nx))
+        vy = np.empty((self.ny, self.nx))
+        tot = np.empty(3)
+        rlbm_moments(self.handle, eps, vx, vy, tot)
+        return eps, vx, vy, tot
+
+    def moments_device(self, eps=None, vx=None, vy=None, totals=None):
+        ptr = lambda t: 0 if t is None else int(t.data_ptr())
+        rlbm_moments_device(self.handle, ptr(eps), ptr(vx), ptr(vy), ptr(totals))
+
+    def energy_spectrum(self, nshells: int) -> np.ndarray:
+        E = np.empty(int(nshells))
+        rlbm_energy_spectrum(self.handle, nshells, E)
+        return E
+
+    def populations(self) -> np.ndarray:
+        f = np.empty((NCLASSES, self.ny, self.nx))
+        rlbm_get_populations(self.handle, f)
+        return f
+
+    def set_populations(self, f):
+        rlbm_set_populations(self.handle, _f64(f, NCLASSES * self.nx * self.ny))
+
+    def force(self):
+        Fx = np.empty((self.ny, self.nx))
+        Fy = np.empty((self.ny, self.nx))
+        rlbm_get_force(self.handle, Fx, Fy)
+        return Fx, Fy
+
+    def info(self) -> dict:
+        i = rlbm_get_info(self.handle)
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def synchronize(self):
+        rlbm_synchronize(self.handle)

@@ -1,0 +1,421 @@
+// k_aux.cu -- kernels off the per-step path: initialisation (step (a) of
+// Sec. 3.3), the global conservation reduction, the stirring-force draw and
+// synthesis (Sec. 5), population encode/decode, and the energy spectrum
+// (Sec. 4).
+#include <math.h>
+
+#include "rlbm_internal.h"
+
+namespace rlbk {
+
+size_t storage_bytes(int dtype) { return dtype == RLBM_F64 ? 8 : dtype == RLBM_F32 ? 4 : 2; }
+size_t compute_bytes(int dtype) { return dtype == RLBM_F64 ? 8 : 4; }
+
+template <typename TS>
+__device__ __forceinline__ double load_any(const TS *p) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) return (double)__bfloat162float(*p);
+    else if constexpr (std::is_same<TS, __half>::value) return (double)__half2float(*p);
+    else return (double)*p;
+}
+
+template <typename TS>
+__device__ __forceinline__ TS store_any(double x) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) return __float2bfloat16_rn((float)x);
+    else if constexpr (std::is_same<TS, __half>::value) return __float2half_rn((float)x);
+    else return (TS)x;
+}
+
+#define RLBM_DISPATCH_STORAGE(dtype, TS, ...)            \
+    switch (dtype) {                                       \
+    case RLBM_F64: { using TS = double; __VA_ARGS__; break; }        \
+    case RLBM_F32: { using TS = float; __VA_ARGS__; break; }         \
+    case RLBM_BF16: { using TS = __nv_bfloat16; __VA_ARGS__; break; } \
+    default: { using TS = __half; __VA_ARGS__; break; }              \
+    }
+
+// ---------------------------------------------------------------- initialisation
+// f_c = f_eq,c(eps, v) in deviation form (see collide_node):
+// q_c = [eps - eps0 + eps gamma^2 (4 xi + 10 xi^2 - 2 |v|^2)] / s, xi = c . v.
+template <typename TS>
+__global__ void k_init(TS *q, StepParams p, const double *eps, const double *vx, const double *vy) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long i = (long long)y * p.nx + x;
+    const double e = eps ? eps[i] : p.eps0;
+    const double a = vx ? vx[i] : 0.0, b = vy ? vy[i] : 0.0;
+    const double v2 = a * a + b * b;
+    const double g2 = 1.0 / (1.0 - v2);
+    const long long n = (long long)y * p.pitch + x;
+    static_for<0, NC>([&](auto C) {
+        constexpr int c = decltype(C)::value;
+        const double xi = cls_cx(c) * a + cls_cy(c) * b;
+        const double qc = ((e - p.eps0) + e * g2 * (4.0 * xi + 10.0 * xi * xi - 2.0 * v2)) / p.scale;
+        q[(long long)c * p.plane + n] = store_any<TS>(qc);
+    });
+}
+
+cudaError_t launch_init(int dtype, void *q, const StepParams &p, const double *eps, const double *vx,
+                        const double *vy, cudaStream_t s) {
+    dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+    RLBM_DISPATCH_STORAGE(dtype, TS, k_init<TS><<<g, b, 0, s>>>(static_cast<TS *>(q), p, eps, vx, vy));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- conservation totals
+// Fixed-order FP64 reduction of the per-block partials: thread t sums
+// partials t, t+256, ..., then a tree over the 256 threads.
+__global__ void k_reduce_partials(const double *partials, int nblocks, double base_E, double *totals) {
+    __shared__ double red[3][256];
+    const int t = threadIdx.x;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = t; i < nblocks; i += 256) {
+        a += partials[3 * i + 0];
+        b += partials[3 * i + 1];
+        c += partials[3 * i + 2];
+    }
+    red[0][t] = a;
+    red[1][t] = b;
+    red[2][t] = c;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) {
+            red[0][t] += red[0][t + h];
+            red[1][t] += red[1][t + h];
+            red[2][t] += red[2][t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        totals[0] = base_E + red[0][0];
+        totals[1] = red[1][0];
+        totals[2] = red[2][0];
+    }
+}
+
+cudaError_t launch_reduce_partials(const double *partials, int nblocks, double base_E, double *totals,
+                                   cudaStream_t s) {
+    k_reduce_partials<<<1, 256, 0, s>>>(partials, nblocks, base_E, totals);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- stirring force
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the
+// published definition: per round two 32x32->64-bit products with the
+// multipliers 0xD2511F53 and 0xCD9E8D57, words recombined as
+// (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), key bumped by the Weyl
+// increments 0x9E3779B9 and 0xBB67AE85 after each round.
+struct U4 {
+    unsigned int w[4];
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 ctr, unsigned int k0, unsigned int k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned int lo0 = 0xD2511F53u * ctr.w[0];
+        const unsigned int hi0 = __umulhi(0xD2511F53u, ctr.w[0]);
+        const unsigned int lo1 = 0xCD9E8D57u * ctr.w[2];
+        const unsigned int hi1 = __umulhi(0xCD9E8D57u, ctr.w[2]);
+        U4 n;
+        n.w[0] = hi1 ^ ctr.w[1] ^ k0;
+        n.w[1] = lo1;
+        n.w[2] = hi0 ^ ctr.w[3] ^ k1;
+        n.w[3] = lo0;
+        ctr = n;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return ctr;
+}
+
+__device__ __forceinline__ double u01_53(unsigned int a, unsigned int b) {
+    const unsigned long long m = ((unsigned long long)a << 21) | (unsigned long long)(b >> 11);
+    return (double)m * (1.0 / 9007199254740992.0);
+}
+
+__global__ void k_draw_modes(Mode *modes, int nmodes, double amp, unsigned long long seed,
+                             unsigned long long epoch) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nmodes) return;
+    const unsigned int k0 = (unsigned int)(seed & 0xffffffffull), k1 = (unsigned int)(seed >> 32);
+    U4 c0 = {{(unsigned int)epoch, (unsigned int)m, 0u, 0u}};
+    U4 c1 = {{(unsigned int)epoch, (unsigned int)m, 1u, 0u}};
+    const U4 o0 = philox4x32_10(c0, k0, k1);
+    const U4 o1 = philox4x32_10(c1, k0, k1);
+    const double r = amp * u01_53(o0.w[0], o0.w[1]);
+    const double ph = 2.0 * M_PI * u01_53(o0.w[2], o0.w[3]);
+    const double th = 2.0 * M_PI * u01_53(o1.w[0], o1.w[1]);
+    double sph, cph, sth, cth;
+    sincos(ph, &sph, &cph);
+    sincos(th, &sth, &cth);
+    Mode md = modes[m];
+    md.ax = 2.0 * r * cth * cph;
+    md.bx = 2.0 * r * cth * sph;
+    md.ay = 2.0 * r * sth * cph;
+    md.by = 2.0 * r * sth * sph;
+    modes[m] = md;
+}
+
+cudaError_t launch_draw_modes(Mode *modes, int nmodes, double amp, unsigned long long seed,
+                              unsigned long long epoch, cudaStream_t s) {
+    if (nmodes <= 0) return cudaSuccess;
+    k_draw_modes<<<(nmodes + 127) / 128, 128, 0, s>>>(modes, nmodes, amp, seed, epoch);
+    return cudaGetLastError();
+}
+
+template <typename TC>
+struct C2 {
+    TC c, s;
+};
+
+// tw[j] = (cos, sin)(2 pi j / n), j < n.
+template <typename TC>
+__global__ void k_twiddles(C2<TC> *tw, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double sv, cv;
+    sincospi(2.0 * (double)j / (double)n, &sv, &cv);
+    tw[j].c = (TC)cv;
+    tw[j].s = (TC)sv;
+}
+
+cudaError_t launch_twiddles(int dtype, void *tw, int n, cudaStream_t s) {
+    if (dtype == RLBM_F64)
+        k_twiddles<double><<<(n + 255) / 256, 256, 0, s>>>(static_cast<C2<double> *>(tw), n);
+    else
+        k_twiddles<float><<<(n + 255) / 256, 256, 0, s>>>(static_cast<C2<float> *>(tw), n);
+    return cudaGetLastError();
+}
+
+// F(x) = sum_m [a cos psi - b sin psi], psi = 2 pi (kx x/nx + ky y/ny) with
+// e^{i psi} = tw_x[(kx x) mod nx] * tw_y[(ky y) mod ny] (integer phase
+// reduction keeps the argument exact at any lattice size).
+template <typename TC>
+__global__ void k_synth_force(TC *F, const Mode *__restrict__ modes, int nmodes, const C2<TC> *__restrict__ twx,
+                              const C2<TC> *__restrict__ twy, StepParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    TC fx = 0, fy = 0;
+    for (int m = 0; m < nmodes; ++m) {
+        const Mode md = modes[m];
+        const long long kxm = ((long long)md.kx % p.nx + p.nx) % p.nx;
+        const long long kym = ((long long)md.ky % p.ny + p.ny) % p.ny;
+        const C2<TC> a = twx[(kxm * x) % p.nx];
+        const C2<TC> b = twy[(kym * y) % p.ny];
+        const TC cpsi = a.c * b.c - a.s * b.s;
+        const TC spsi = a.s * b.c + a.c * b.s;
+        fx += (TC)md.ax * cpsi - (TC)md.bx * spsi;
+        fy += (TC)md.ay * cpsi - (TC)md.by * spsi;
+    }
+    const long long n = (long long)y * p.pitch + x;
+    F[n] = fx;
+    F[p.plane + n] = fy;
+}
+
+cudaError_t launch_synth_force(int dtype, void *F, const Mode *modes, int nmodes, const void *twx, const void *twy,
+                               const StepParams &p, cudaStream_t s) {
+    dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+    if (dtype == RLBM_F64)
+        k_synth_force<double><<<g, b, 0, s>>>(static_cast<double *>(F), modes, nmodes,
+                                              static_cast<const C2<double> *>(twx),
+                                              static_cast<const C2<double> *>(twy), p);
+    else
+        k_synth_force<float><<<g, b, 0, s>>>(static_cast<float *>(F), modes, nmodes,
+                                             static_cast<const C2<float> *>(twx),
+                                             static_cast<const C2<float> *>(twy), p);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- population encode / decode
+template <typename TS>
+__global__ void k_decode_class(const TS *q, int c, StepParams p, double W, double *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const double qc = load_any<TS>(q + (long long)c * p.plane + (long long)y * p.pitch + x);
+    out[(long long)y * p.nx + x] = W * (p.eps0 + p.scale * qc);
+}
+
+template <typename TS>
+__global__ void k_encode_class(TS *q, int c, StepParams p, double W, const double *in) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const double f = in[(long long)y * p.nx + x];
+    q[(long long)c * p.plane + (long long)y * p.pitch + x] = store_any<TS>((f / W - p.eps0) / p.scale);
+}
+
+static double class_weight(int c) {
+    return c == 0 ? 2.0 / 21.0 : c <= 4 ? 1.0 / 21.0 : c <= 8 ? 8.0 / 105.0 : c <= 12 ? 4.0 / 105.0 : 9.0 / 140.0;
+}
+
+cudaError_t launch_decode_class(int dtype, const void *q, int c, const StepParams &p, double *out, cudaStream_t s) {
+    dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+    const double W = class_weight(c);
+    RLBM_DISPATCH_STORAGE(dtype, TS, k_decode_class<TS><<<g, b, 0, s>>>(static_cast<const TS *>(q), c, p, W, out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_class(int dtype, void *q, int c, const StepParams &p, const double *in, cudaStream_t s) {
+    dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+    const double W = class_weight(c);
+    RLBM_DISPATCH_STORAGE(dtype, TS, k_encode_class<TS><<<g, b, 0, s>>>(static_cast<TS *>(q), c, p, W, in));
+    return cudaGetLastError();
+}
+
+template <typename TC>
+__global__ void k_force_to_f64(const TC *F, int comp, StepParams p, double *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    out[(long long)y * p.nx + x] = (double)F[comp * p.plane + (long long)y * p.pitch + x];
+}
+
+cudaError_t launch_force_to_f64(int dtype, const void *F, int comp, const StepParams &p, double *out,
+                                cudaStream_t s) {
+    dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+    if (dtype == RLBM_F64)
+        k_force_to_f64<double><<<g, b, 0, s>>>(static_cast<const double *>(F), comp, p, out);
+    else
+        k_force_to_f64<float><<<g, b, 0, s>>>(static_cast<const float *>(F), comp, p, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- energy spectrum
+// z = v_x + i v_y is transformed once (2D DFT, FP64); since every shell is
+// symmetric under k -> -k, sum_shell |X|^2 + |Y|^2 = sum_shell |Z|^2 with
+// X, Y the transforms of v_x, v_y, so E(n) = 1/2 sum_shell |Z|^2 / (nx ny)^2.
+// Lines of length 2^m <= 8192 use an in-shared-memory radix-2 FFT; other
+// lengths a direct DFT with an integer-reduced twiddle index.
+struct Z2 {
+    double re, im;
+};
+
+__device__ __forceinline__ Z2 zmul(Z2 a, Z2 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// Forward twiddles w[k] = exp(-2 pi i k / n), k < n.
+__global__ void k_dft_twiddles(Z2 *w, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)n, &s, &c);
+    w[k] = {c, -s};
+}
+
+__global__ void k_pack_z(const double *vx, const double *vy, Z2 *z, long long count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) z[i] = {vx[i], vy[i]};
+}
+
+// One line per block: elements line*ls + j*es, j < n.
+__global__ void k_fft_lines(Z2 *data, int n, int log2n, long long es, long long ls, const Z2 *__restrict__ w) {
+    extern __shared__ Z2 sh[];
+    Z2 *base = data + (long long)blockIdx.x * ls;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int r = (int)(__brev((unsigned int)j) >> (32 - log2n));
+        sh[r] = base[(long long)j * es];
+    }
+    __syncthreads();
+    for (int h = 1; h < n; h <<= 1) {
+        const int stride = n / (2 * h);
+        for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+            const int k = i % h;
+            const int pos = (i / h) * 2 * h + k;
+            const Z2 a = sh[pos];
+            const Z2 b = zmul(sh[pos + h], w[k * stride]);
+            sh[pos] = {a.re + b.re, a.im + b.im};
+            sh[pos + h] = {a.re - b.re, a.im - b.im};
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) base[(long long)j * es] = sh[j];
+}
+
+__global__ void k_dft_lines(Z2 *data, int n, long long es, long long ls, const Z2 *__restrict__ w) {
+    extern __shared__ Z2 sh[];
+    Z2 *base = data + (long long)blockIdx.x * ls;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) sh[j] = base[(long long)j * es];
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        Z2 acc = {0.0, 0.0};
+        long long idx = 0;
+        for (int j = 0; j < n; ++j) {
+            const Z2 t = zmul(sh[j], w[idx]);
+            acc.re += t.re;
+            acc.im += t.im;
+            idx += k;
+            if (idx >= n) idx -= n;
+        }
+        base[(long long)k * es] = acc;  // reads come from sh only
+    }
+}
+
+__global__ void k_shell_bin(const Z2 *z, int nx, int ny, int nshells, double *Ek) {
+    extern __shared__ double hist[];
+    for (int i = threadIdx.x; i < nshells; i += blockDim.x) hist[i] = 0.0;
+    __syncthreads();
+    const long long count = (long long)nx * ny;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int jy = (int)(i / nx), jx = (int)(i % nx);
+        const double kx = (jx < (nx + 1) / 2) ? jx : jx - nx;
+        const double ky = (jy < (ny + 1) / 2) ? jy : jy - ny;
+        const int sh = (int)floor(sqrt(kx * kx + ky * ky) + 0.5);
+        if (sh < nshells) atomicAdd(&hist[sh], z[i].re * z[i].re + z[i].im * z[i].im);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nshells; i += blockDim.x)
+        if (hist[i] != 0.0) atomicAdd(&Ek[i], hist[i]);
+}
+
+__global__ void k_scale(double *a, int n, double f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] *= f;
+}
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+static int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+size_t spectrum_work_doubles(int nx, int ny) { return 2 * ((size_t)nx * ny + (size_t)nx + (size_t)ny); }
+
+static cudaError_t transform_lines(Z2 *z, int n, int lines, long long es, long long ls, Z2 *w, cudaStream_t s) {
+    const size_t smem = (size_t)n * sizeof(Z2);
+    k_dft_twiddles<<<(n + 255) / 256, 256, 0, s>>>(w, n);
+    cudaError_t e;
+    if (is_pow2(n)) {
+        e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_fft_lines<<<lines, 512, smem, s>>>(z, n, ilog2(n), es, ls, w);
+    } else {
+        e = cudaFuncSetAttribute(k_dft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_dft_lines<<<lines, 256, smem, s>>>(z, n, es, ls, w);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum(const double *vx, const double *vy, int nx, int ny, int nshells, double *work,
+                            double *Ek, cudaStream_t s) {
+    Z2 *z = reinterpret_cast<Z2 *>(work);
+    Z2 *wx = z + (size_t)nx * ny;
+    Z2 *wy = wx + nx;
+    const long long count = (long long)nx * ny;
+    k_pack_z<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(vx, vy, z, count);
+    cudaError_t e = transform_lines(z, nx, ny, 1, nx, wx, s);  // rows
+    if (e != cudaSuccess) return e;
+    e = transform_lines(z, ny, nx, nx, 1, wy, s);  // columns
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(Ek, 0, sizeof(double) * nshells, s);
+    if (e != cudaSuccess) return e;
+    k_shell_bin<<<304, 256, sizeof(double) * nshells, s>>>(z, nx, ny, nshells, Ek);
+    const double f = 0.5 / ((double)count * (double)count);
+    k_scale<<<(nshells + 255) / 256, 256, 0, s>>>(Ek, nshells, f);
+    return cudaGetLastError();
+}
+
+}  // namespace rlbk

@@ -1,0 +1,34 @@
+// k_launch.cuh -- launch helpers instantiated once per storage form (one
+// translation unit each, so the forms compile in parallel).
+#pragma once
+
+#include "k_step_gather.cuh"
+#include "rlbm_internal.h"
+
+namespace rlbk {
+
+inline dim3 gather_block() { return dim3(32, 8, 1); }
+inline dim3 gather_grid(const StepParams &p) { return dim3((p.nx + 31) / 32, (p.ny + 7) / 8, 1); }
+
+template <typename TS, typename TC, typename TL>
+cudaError_t launch_step_t(int /*kernel*/, bool forced, const void *qin, void *qout, const void *F,
+                          const StepParams &p, cudaStream_t s) {
+    const TS *in = static_cast<const TS *>(qin);
+    TS *out = static_cast<TS *>(qout);
+    const TC *f = static_cast<const TC *>(F);
+    if (forced)
+        k_step_gather<TS, TC, TL, true><<<gather_grid(p), gather_block(), 0, s>>>(in, out, f, p);
+    else
+        k_step_gather<TS, TC, TL, false><<<gather_grid(p), gather_block(), 0, s>>>(in, out, f, p);
+    return cudaGetLastError();
+}
+
+template <typename TS, typename TC, typename TL>
+cudaError_t launch_moments_t(const void *qin, const StepParams &p, double *eps, double *vx, double *vy,
+                             double *partials, int *bad, cudaStream_t s) {
+    k_moments<TS, TC, TL><<<gather_grid(p), gather_block(), 0, s>>>(static_cast<const TS *>(qin), p, eps, vx, vy,
+                                                                    partials, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace rlbk

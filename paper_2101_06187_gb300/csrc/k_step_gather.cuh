@@ -1,0 +1,127 @@
+// k_step_gather.cuh -- fused stream + collide + force step, one node per
+// thread, gathering the streamed populations straight from global memory
+// (the 3x3 neighbourhood rows are re-read through L1/L2; HBM sees each
+// stored value about once).  Also the moments kernel, which runs the same
+// gather + moments + Landau solve without writing populations back.
+#pragma once
+
+#include "rlbm_device.cuh"
+
+namespace rlbk {
+
+// Gather class c at node (x, y) by bilinear pull interpolation (Sec. 3.2).
+// rows[k] / cols[k], k = 0, 1, 2, are the periodic neighbours y-1, y, y+1
+// (x-1, x, x+1); class offsets lie in {-1, 0, +1} (CFL 1).
+template <int c, typename TS, typename TC>
+__device__ __forceinline__ TC gather_class(const TS *__restrict__ plane, const long long (&rowoff)[3],
+                                           const int (&cols)[3]) {
+    constexpr int ox = cls_ox(c), oy = cls_oy(c);
+    constexpr double tx = cls_tx(c), ty = cls_ty(c);
+    const TS *r0 = plane + rowoff[oy + 1];
+    TC v = (TC)((1.0 - tx) * (1.0 - ty)) * load_q<TS, TC>(r0 + cols[ox + 1]);
+    if constexpr (tx != 0.0) v += (TC)(tx * (1.0 - ty)) * load_q<TS, TC>(r0 + cols[ox + 2]);
+    if constexpr (ty != 0.0) {
+        const TS *r1 = plane + rowoff[oy + 2];
+        v += (TC)((1.0 - tx) * ty) * load_q<TS, TC>(r1 + cols[ox + 1]);
+        if constexpr (tx != 0.0) v += (TC)(tx * ty) * load_q<TS, TC>(r1 + cols[ox + 2]);
+    }
+    return v;
+}
+
+template <typename TS, typename TC>
+__device__ __forceinline__ void gather_node(const TS *__restrict__ qin, const StepParams &p, int x, int y,
+                                            TC (&q)[NC]) {
+    const int ym = (y == 0) ? p.ny - 1 : y - 1;
+    const int yp = (y == p.ny - 1) ? 0 : y + 1;
+    const int xm = (x == 0) ? p.nx - 1 : x - 1;
+    const int xp = (x == p.nx - 1) ? 0 : x + 1;
+    const long long rowoff[3] = {(long long)ym * p.pitch, (long long)y * p.pitch, (long long)yp * p.pitch};
+    const int cols[3] = {xm, x, xp};
+    static_for<0, NC>([&](auto C) {
+        constexpr int c = decltype(C)::value;
+        q[c] = gather_class<c, TS, TC>(qin + (long long)c * p.plane, rowoff, cols);
+    });
+}
+
+template <typename TS, typename TC, typename TL, bool FORCED>
+__global__ void __launch_bounds__(256) k_step_gather(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                                     const TC *__restrict__ F, StepParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    TC q[NC];
+    gather_node<TS, TC>(qin, p, x, y, q);
+    const long long n = (long long)y * p.pitch + x;
+    TC Fx = 0, Fy = 0;
+    if constexpr (FORCED) {
+        Fx = __ldg(F + n);
+        Fy = __ldg(F + p.plane + n);
+    }
+    collide_node<TC, TL, FORCED>(q, Fx, Fy, p);
+    static_for<0, NC>([&](auto C) {
+        constexpr int c = decltype(C)::value;
+        qout[(long long)c * p.plane + n] = to_storage<TS, TC>(q[c]);
+    });
+}
+
+// Moments of the state the next collision sees: eps, v (FP64, compact
+// nx*ny), and per-block FP64 partial sums of (T^00, T^0x, T^0y) for the
+// global conservation totals (warp shuffles, then one partial per block in
+// `partials`, reduced in a fixed order by k_reduce_partials).
+template <typename TS, typename TC, typename TL>
+__global__ void __launch_bounds__(256) k_moments(const TS *__restrict__ qin, StepParams p, double *__restrict__ eps,
+                                                 double *__restrict__ vx, double *__restrict__ vy,
+                                                 double *__restrict__ partials, int *__restrict__ bad) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    double sE = 0.0, sMx = 0.0, sMy = 0.0;
+    if (x < p.nx && y < p.ny) {
+        TC q[NC];
+        gather_node<TS, TC>(qin, p, x, y, q);
+        const NodeMoments<TC> m = node_moments<TC>(q, (TC)p.scale);
+        const Frame<TL> fr = landau_solve<TL>((TL)p.eps0, (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
+                                              (TL)m.dSyy);
+        const long long n = (long long)y * p.nx + x;
+        const bool ok = (fr.v2 < (TL)1) && (fr.eps > (TL)0) && isfinite((double)fr.eps);
+        if (!ok) atomicAdd(bad, 1);
+        if (eps) eps[n] = ok ? (double)fr.eps : __longlong_as_double(0x7ff8000000000000LL);
+        if (vx) vx[n] = ok ? (double)fr.vx : __longlong_as_double(0x7ff8000000000000LL);
+        if (vy) vy[n] = ok ? (double)fr.vy : __longlong_as_double(0x7ff8000000000000LL);
+        sE = (double)m.dE;  // eps0 * nodes is added on the host side of the reduction
+        sMx = (double)m.Mx;
+        sMy = (double)m.My;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sE += __shfl_down_sync(0xffffffffu, sE, o);
+        sMx += __shfl_down_sync(0xffffffffu, sMx, o);
+        sMy += __shfl_down_sync(0xffffffffu, sMy, o);
+    }
+    __shared__ double red[3][32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) {
+        red[0][warp] = sE;
+        red[1][warp] = sMx;
+        red[2][warp] = sMy;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+        double a = lane < nw ? red[0][lane] : 0.0;
+        double b = lane < nw ? red[1][lane] : 0.0;
+        double c = lane < nw ? red[2][lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) {
+            const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+            partials[3 * blk + 0] = a;
+            partials[3 * blk + 1] = b;
+            partials[3 * blk + 2] = c;
+        }
+    }
+}
+
+}  // namespace rlbk

@@ -1,0 +1,540 @@
+// rlbm_api.cu -- the extern "C" boundary declared in include/rlbm.h: handle
+// life cycle, device memory, the step loop (direct launches or CUDA-graph
+// replay), diagnostics.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rlbm_internal.h"
+
+namespace rlbk {
+
+cudaError_t launch_step_f64(int kernel, int landau, bool forced, const void *qin, void *qout, const void *F,
+                            const StepParams &p, cudaStream_t s);
+cudaError_t launch_step_f32(int kernel, int landau, bool forced, const void *qin, void *qout, const void *F,
+                            const StepParams &p, cudaStream_t s);
+cudaError_t launch_step_h16(int dtype, int kernel, int landau, bool forced, const void *qin, void *qout,
+                            const void *F, const StepParams &p, cudaStream_t s);
+cudaError_t launch_moments_f64(int landau, const void *qin, const StepParams &p, double *eps, double *vx,
+                               double *vy, double *partials, int *bad, cudaStream_t s);
+cudaError_t launch_moments_f32(int landau, const void *qin, const StepParams &p, double *eps, double *vx,
+                               double *vy, double *partials, int *bad, cudaStream_t s);
+cudaError_t launch_moments_h16(int dtype, int landau, const void *qin, const StepParams &p, double *eps,
+                               double *vx, double *vy, double *partials, int *bad, cudaStream_t s);
+
+cudaError_t launch_step(int dtype, int landau, int kernel, bool forced, const void *qin, void *qout, const void *F,
+                        const StepParams &p, cudaStream_t s) {
+    switch (dtype) {
+    case RLBM_F64: return launch_step_f64(kernel, landau, forced, qin, qout, F, p, s);
+    case RLBM_F32: return launch_step_f32(kernel, landau, forced, qin, qout, F, p, s);
+    default: return launch_step_h16(dtype, kernel, landau, forced, qin, qout, F, p, s);
+    }
+}
+
+cudaError_t launch_moments(int dtype, int landau, const void *qin, const StepParams &p, double *eps, double *vx,
+                           double *vy, double *partials, int *bad, cudaStream_t s) {
+    switch (dtype) {
+    case RLBM_F64: return launch_moments_f64(landau, qin, p, eps, vx, vy, partials, bad, s);
+    case RLBM_F32: return launch_moments_f32(landau, qin, p, eps, vx, vy, partials, bad, s);
+    default: return launch_moments_h16(dtype, landau, qin, p, eps, vx, vy, partials, bad, s);
+    }
+}
+
+int moments_blocks(const StepParams &p) { return ((p.nx + 31) / 32) * ((p.ny + 7) / 8); }
+
+}  // namespace rlbk
+
+using namespace rlbk;
+
+// ---------------------------------------------------------------- helpers
+static rlbm_status fail(rlbm_t *h, rlbm_status st, const char *fmt, ...) {
+    if (!h) return st;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->msg = buf;
+    if (st == RLBM_ERR_CUDA || st == RLBM_ERR_TIMEOUT) h->status = st;  // sticky
+    return st;
+}
+
+#define CUDA_TRY(h, call)                                                                                 \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return fail(h, RLBM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                           \
+    } while (0)
+
+#define CHECK_HANDLE(h)                                  \
+    do {                                                 \
+        if (!(h)) return RLBM_ERR_ARG;                   \
+        if ((h)->status != RLBM_OK) return (h)->status;  \
+        if (cudaSetDevice((h)->device) != cudaSuccess) return fail(h, RLBM_ERR_CUDA, "cudaSetDevice failed"); \
+    } while (0)
+
+static void *dev_alloc(rlbm_t *h, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (h->opts.alloc) {
+        p = h->opts.alloc(bytes, h->opts.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) h->device_bytes += bytes;
+    return p;
+}
+
+static void dev_free(rlbm_t *h, void *p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    if (h->opts.alloc) {
+        if (h->opts.free) h->opts.free(p, bytes, h->opts.alloc_ctx);
+    } else {
+        cudaFree(p);
+    }
+}
+
+static StepParams params_of(const rlbm_t *h) {
+    StepParams p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.pitch = h->pitch;
+    p.plane = (long long)h->ny * h->pitch;
+    p.inv_tau = 1.0 / h->tau;
+    p.eps0 = h->opts.eps0;
+    p.scale = h->opts.scale;
+    p.err = nullptr;
+    return p;
+}
+
+static size_t q_bytes(const rlbm_t *h) { return (size_t)NC * h->ny * h->pitch * storage_bytes(h->opts.dtype); }
+static size_t F_bytes(const rlbm_t *h) { return (size_t)2 * h->ny * h->pitch * compute_bytes(h->opts.dtype); }
+static size_t tw_bytes(const rlbm_t *h, int n) { return (size_t)n * 2 * compute_bytes(h->opts.dtype); }
+static size_t fields_bytes(const rlbm_t *h) { return (size_t)3 * h->nx * h->ny * sizeof(double); }
+static size_t partials_bytes(const rlbm_t *h) { return (size_t)3 * moments_blocks(params_of(h)) * sizeof(double); }
+
+static int enumerate_modes(int kmin, int kmax, std::vector<Mode> *out) {
+    int m = 0;
+    for (int ky = 0; ky <= kmax; ++ky)
+        for (int kx = -kmax; kx <= kmax; ++kx) {
+            if (ky == 0 && kx <= 0) continue;
+            const int k2 = kx * kx + ky * ky;
+            if (k2 < kmin * kmin || k2 > kmax * kmax) continue;
+            if (out) out->push_back(Mode{kx, ky, 0.0, 0.0, 0.0, 0.0});
+            ++m;
+        }
+    return m;
+}
+
+// Make F hold the force of the epoch containing step `step`.
+static rlbm_status ensure_force(rlbm_t *h) {
+    if (!h->forced) return RLBM_OK;
+    const long long e = h->step / h->forcing.redraw_period;
+    if (e == h->force_epoch) return RLBM_OK;
+    const StepParams p = params_of(h);
+    CUDA_TRY(h, launch_draw_modes(h->modes, h->nmodes, h->forcing.amp, (unsigned long long)h->forcing.seed,
+                                  (unsigned long long)e, h->stream));
+    CUDA_TRY(h, launch_synth_force(h->opts.dtype, h->F, h->modes, h->nmodes, h->twx, h->twy, p, h->stream));
+    h->force_epoch = e;
+    return RLBM_OK;
+}
+
+static rlbm_status launch_steps(rlbm_t *h, int n) {
+    const StepParams p = params_of(h);
+    for (int i = 0; i < n; ++i) {
+        CUDA_TRY(h, launch_step(h->opts.dtype, h->opts.landau, h->kernel, h->forced, h->q[h->cur], h->q[h->cur ^ 1],
+                                h->F, p, h->stream));
+        h->cur ^= 1;
+    }
+    return RLBM_OK;
+}
+
+// Run `n` steps inside one epoch: replay a captured graph of n steps (n
+// even, so the ping-pong parity returns to where it started), or launch.
+static rlbm_status run_chunk(rlbm_t *h, int n) {
+    const bool graphs = h->opts.use_graphs && h->stream != nullptr && n >= 2;
+    if (!graphs) return launch_steps(h, n);
+    const int even = n & ~1;
+    auto key = std::make_pair(even, h->cur);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        const int cur0 = h->cur;
+        CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        rlbm_status st = launch_steps(h, even);
+        cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+        h->cur = cur0;
+        if (st != RLBM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ec != cudaSuccess) return fail(h, RLBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+        ec = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ec != cudaSuccess) return fail(h, RLBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+        it = h->graphs.emplace(key, ge).first;
+    }
+    CUDA_TRY(h, cudaGraphLaunch(it->second, h->stream));
+    if (even != n) return launch_steps(h, 1);
+    return RLBM_OK;
+}
+
+extern "C" {
+
+const char *rlbm_status_string(rlbm_status s) {
+    switch (s) {
+    case RLBM_OK: return "ok";
+    case RLBM_ERR_ARG: return "invalid argument";
+    case RLBM_ERR_ALLOC: return "device allocation failed";
+    case RLBM_ERR_CUDA: return "CUDA error";
+    case RLBM_ERR_TIMEOUT: return "device wait timed out";
+    case RLBM_ERR_NAN: return "non-finite or non-physical state";
+    case RLBM_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+void rlbm_opts_default(rlbm_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->dtype = RLBM_F32;
+    o->landau = RLBM_LANDAU_FP64;
+    o->kernel = RLBM_KERNEL_AUTO;
+    o->use_graphs = 1;
+    o->eps0 = 1.0;
+    o->scale = 0.0;
+    o->stream = nullptr;
+    o->device = -1;
+}
+
+void rlbm_destroy(rlbm_t *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    dev_free(h, h->q[0], q_bytes(h));
+    dev_free(h, h->q[1], q_bytes(h));
+    if (h->F) dev_free(h, h->F, F_bytes(h));
+    if (h->twx) dev_free(h, h->twx, tw_bytes(h, h->nx));
+    if (h->twy) dev_free(h, h->twy, tw_bytes(h, h->ny));
+    if (h->modes) dev_free(h, h->modes, sizeof(Mode) * h->nmodes);
+    dev_free(h, h->fields, fields_bytes(h));
+    dev_free(h, h->partials, partials_bytes(h));
+    dev_free(h, h->totals, 4 * sizeof(double));
+    dev_free(h, h->bad, sizeof(int) * 4);
+    if (h->spec_work) dev_free(h, h->spec_work, h->spec_work_bytes);
+    if (h->host_pinned) cudaFreeHost(h->host_pinned);
+    delete h;
+}
+
+rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const rlbm_forcing *forcing,
+                        const rlbm_opts *opts, rlbm_t **out) {
+    if (!out) return RLBM_ERR_ARG;
+    *out = nullptr;
+    if (stencil != RLBM_STENCIL_SPH26_SLAB) return RLBM_ERR_ARG;
+    if (nx < 4 || ny < 4 || (long long)nx * ny > (1ll << 31)) return RLBM_ERR_ARG;
+    if (!(tau > 0.5) || !isfinite(tau)) return RLBM_ERR_ARG;
+    rlbm_opts o;
+    rlbm_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
+    if (o.landau != RLBM_LANDAU_FP64 && o.landau != RLBM_LANDAU_FP32) return RLBM_ERR_ARG;
+    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_STAGED) return RLBM_ERR_ARG;
+    if (o.eps0 == 0.0) o.eps0 = 1.0;
+    if (!(o.eps0 > 0.0) || !isfinite(o.eps0)) return RLBM_ERR_ARG;
+    if (o.scale == 0.0) o.scale = (o.dtype == RLBM_BF16 || o.dtype == RLBM_F16) ? 1.0 / 64.0 : 1.0;
+    if (!(o.scale > 0.0) || !isfinite(o.scale)) return RLBM_ERR_ARG;
+    if (o.alloc && !o.free) return RLBM_ERR_ARG;
+    if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
+
+    rlbm_forcing fz{};
+    bool forced = false;
+    if (forcing) {
+        fz = *forcing;
+        if (!(fz.amp >= 0.0) || !isfinite(fz.amp)) return RLBM_ERR_ARG;
+        if (fz.amp > 0.0 && fz.kmax > 0) {
+            if (fz.kmin < 1 || fz.kmin > fz.kmax || 2 * fz.kmax >= std::min(nx, ny)) return RLBM_ERR_ARG;
+            if (fz.redraw_period < 1) return RLBM_ERR_ARG;
+            forced = true;
+        }
+    }
+
+    rlbm_t *h = new rlbm_t();
+    h->nx = nx;
+    h->ny = ny;
+    h->pitch = (nx + 31) & ~31;
+    h->tau = tau;
+    h->opts = o;
+    h->forcing = fz;
+    h->forced = forced;
+    h->kernel = RLBM_KERNEL_GATHER;
+    if (o.device >= 0) {
+        if (cudaSetDevice(o.device) != cudaSuccess) {
+            delete h;
+            return RLBM_ERR_ARG;
+        }
+        h->device = o.device;
+    } else if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return RLBM_ERR_CUDA;
+    }
+    h->stream = static_cast<cudaStream_t>(o.stream);
+
+    std::vector<Mode> modes;
+    if (forced) h->nmodes = enumerate_modes(fz.kmin, fz.kmax, &modes);
+
+    h->q[0] = dev_alloc(h, q_bytes(h));
+    h->q[1] = dev_alloc(h, q_bytes(h));
+    h->fields = static_cast<double *>(dev_alloc(h, fields_bytes(h)));
+    h->partials = static_cast<double *>(dev_alloc(h, partials_bytes(h)));
+    h->totals = static_cast<double *>(dev_alloc(h, 4 * sizeof(double)));
+    h->bad = static_cast<int *>(dev_alloc(h, sizeof(int) * 4));
+    bool ok = h->q[0] && h->q[1] && h->fields && h->partials && h->totals && h->bad;
+    if (forced) {
+        h->F = dev_alloc(h, F_bytes(h));
+        h->twx = dev_alloc(h, tw_bytes(h, nx));
+        h->twy = dev_alloc(h, tw_bytes(h, ny));
+        h->modes = static_cast<Mode *>(dev_alloc(h, sizeof(Mode) * h->nmodes));
+        ok = ok && h->F && h->twx && h->twy && h->modes;
+    }
+    if (!ok || cudaMallocHost(&h->host_pinned, fields_bytes(h)) != cudaSuccess) {
+        cudaGetLastError();
+        h->host_pinned = nullptr;
+        rlbm_destroy(h);
+        return RLBM_ERR_ALLOC;
+    }
+    rlbm_status st = RLBM_OK;
+    if (forced) {
+        cudaError_t e = cudaMemcpyAsync(h->modes, modes.data(), sizeof(Mode) * h->nmodes, cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twx, nx, h->stream);
+        if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twy, ny, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = RLBM_ERR_CUDA;
+    }
+    if (st == RLBM_OK) st = rlbm_init_fields_device(h, nullptr, nullptr, nullptr);
+    if (st == RLBM_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = RLBM_ERR_CUDA;
+    if (st != RLBM_OK) {
+        rlbm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_init_fields_device(rlbm_t *h, const double *d_eps, const double *d_vx, const double *d_vy) {
+    CHECK_HANDLE(h);
+    CUDA_TRY(h, launch_init(h->opts.dtype, h->q[0], params_of(h), d_eps, d_vx, d_vy, h->stream));
+    h->cur = 0;
+    h->step = 0;
+    h->force_epoch = -1;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_init_fields(rlbm_t *h, const double *eps, const double *vx, const double *vy) {
+    CHECK_HANDLE(h);
+    const size_t n = (size_t)h->nx * h->ny;
+    const double *src[3] = {eps, vx, vy};
+    for (int k = 0; k < 3; ++k) {
+        if (!src[k]) continue;
+        for (size_t i = 0; i < n; ++i) {
+            const double a = src[k][i];
+            if (!isfinite(a) || (k == 0 && !(a > 0.0))) return fail(h, RLBM_ERR_ARG, "invalid initial field");
+        }
+    }
+    if (vx || vy)
+        for (size_t i = 0; i < n; ++i) {
+            const double a = vx ? vx[i] : 0.0, b = vy ? vy[i] : 0.0;
+            if (!(a * a + b * b < 1.0)) return fail(h, RLBM_ERR_ARG, "|v| >= 1 in initial field");
+        }
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    double *dptr[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k) {
+        if (!src[k]) continue;
+        memcpy(h->host_pinned + k * n, src[k], n * sizeof(double));
+        dptr[k] = h->fields + k * n;
+        CUDA_TRY(h, cudaMemcpyAsync(dptr[k], h->host_pinned + k * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream));
+    }
+    rlbm_status st = rlbm_init_fields_device(h, dptr[0], dptr[1], dptr[2]);
+    if (st != RLBM_OK) return st;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_step(rlbm_t *h, int n) {
+    CHECK_HANDLE(h);
+    if (n < 0) return fail(h, RLBM_ERR_ARG, "negative step count");
+    while (n > 0) {
+        int chunk = n;
+        if (h->forced) {
+            rlbm_status st = ensure_force(h);
+            if (st != RLBM_OK) return st;
+            const int left = h->forcing.redraw_period - (int)(h->step % h->forcing.redraw_period);
+            chunk = std::min(n, left);
+        }
+        rlbm_status st = run_chunk(h, chunk);
+        if (st != RLBM_OK) return st;
+        h->step += chunk;
+        n -= chunk;
+    }
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_moments_device(rlbm_t *h, double *d_eps, double *d_vx, double *d_vy, double *d_totals) {
+    CHECK_HANDLE(h);
+    const StepParams p = params_of(h);
+    CUDA_TRY(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+    CUDA_TRY(h, launch_moments(h->opts.dtype, h->opts.landau, h->q[h->cur], p, d_eps, d_vx, d_vy, h->partials, h->bad,
+                               h->stream));
+    if (d_totals)
+        CUDA_TRY(h, launch_reduce_partials(h->partials, moments_blocks(p), h->opts.eps0 * (double)h->nx * h->ny,
+                                           d_totals, h->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_moments(rlbm_t *h, double *eps, double *vx, double *vy, double totals[3]) {
+    CHECK_HANDLE(h);
+    const size_t n = (size_t)h->nx * h->ny;
+    rlbm_status st = rlbm_moments_device(h, eps ? h->fields : nullptr, vx ? h->fields + n : nullptr,
+                                         vy ? h->fields + 2 * n : nullptr, totals ? h->totals : nullptr);
+    if (st != RLBM_OK) return st;
+    double *dst[3] = {eps, vx, vy};
+    for (int k = 0; k < 3; ++k)
+        if (dst[k])
+            CUDA_TRY(h, cudaMemcpyAsync(h->host_pinned + k * n, h->fields + k * n, n * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream));
+    double tot[3];
+    int bad = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (totals) CUDA_TRY(h, cudaMemcpyAsync(tot, h->totals, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 3; ++k)
+        if (dst[k]) memcpy(dst[k], h->host_pinned + k * n, n * sizeof(double));
+    if (totals)
+        for (int k = 0; k < 3; ++k) totals[k] = tot[k];
+    if (bad) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", bad);
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
+    CHECK_HANDLE(h);
+    if (nshells < 1 || nshells > 4096 || !Ek) return fail(h, RLBM_ERR_ARG, "nshells must be in [1, 4096]");
+    const int big = std::max(h->nx, h->ny);
+    if (big > 8192) return fail(h, RLBM_ERR_ARG, "spectrum supports lattice sides up to 8192");
+    const size_t need = spectrum_work_doubles(h->nx, h->ny) * sizeof(double) + 4096 * sizeof(double);
+    if (!h->spec_work) {
+        h->spec_work = static_cast<double *>(dev_alloc(h, need));
+        if (!h->spec_work) return fail(h, RLBM_ERR_ALLOC, "spectrum work area");
+        h->spec_work_bytes = need;
+    }
+    const size_t n = (size_t)h->nx * h->ny;
+    rlbm_status st = rlbm_moments_device(h, nullptr, h->fields + n, h->fields + 2 * n, nullptr);
+    if (st != RLBM_OK) return st;
+    double *dEk = h->spec_work + spectrum_work_doubles(h->nx, h->ny);
+    CUDA_TRY(h, launch_spectrum(h->fields + n, h->fields + 2 * n, h->nx, h->ny, nshells, h->spec_work, dEk,
+                                h->stream));
+    int bad = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->host_pinned, dEk, nshells * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    memcpy(Ek, h->host_pinned, nshells * sizeof(double));
+    if (bad) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", bad);
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_get_populations(rlbm_t *h, double *f) {
+    CHECK_HANDLE(h);
+    if (!f) return RLBM_ERR_ARG;
+    const size_t n = (size_t)h->nx * h->ny;
+    const StepParams p = params_of(h);
+    for (int c = 0; c < NC; ++c) {
+        CUDA_TRY(h, launch_decode_class(h->opts.dtype, h->q[h->cur], c, p, h->fields, h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(h->host_pinned, h->fields, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        memcpy(f + c * n, h->host_pinned, n * sizeof(double));
+    }
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_set_populations(rlbm_t *h, const double *f) {
+    CHECK_HANDLE(h);
+    if (!f) return RLBM_ERR_ARG;
+    const size_t n = (size_t)h->nx * h->ny;
+    const StepParams p = params_of(h);
+    for (int c = 0; c < NC; ++c) {
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        memcpy(h->host_pinned, f + c * n, n * sizeof(double));
+        CUDA_TRY(h, cudaMemcpyAsync(h->fields, h->host_pinned, n * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream));
+        CUDA_TRY(h, launch_encode_class(h->opts.dtype, h->q[h->cur], c, p, h->fields, h->stream));
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_get_force(rlbm_t *h, double *Fx, double *Fy) {
+    CHECK_HANDLE(h);
+    const size_t n = (size_t)h->nx * h->ny;
+    if (!h->forced) {
+        if (Fx) memset(Fx, 0, n * sizeof(double));
+        if (Fy) memset(Fy, 0, n * sizeof(double));
+        return RLBM_OK;
+    }
+    rlbm_status st = ensure_force(h);
+    if (st != RLBM_OK) return st;
+    const StepParams p = params_of(h);
+    double *dst[2] = {Fx, Fy};
+    for (int k = 0; k < 2; ++k) {
+        if (!dst[k]) continue;
+        CUDA_TRY(h, launch_force_to_f64(h->opts.dtype, h->F, k, p, h->fields, h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(h->host_pinned, h->fields, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        memcpy(dst[k], h->host_pinned, n * sizeof(double));
+    }
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
+    if (!h || !info) return RLBM_ERR_ARG;
+    info->nx = h->nx;
+    info->ny = h->ny;
+    info->pitch = h->pitch;
+    info->nclasses = NC;
+    info->dtype = h->opts.dtype;
+    info->kernel = h->kernel;
+    info->nmodes = h->forced ? h->nmodes : 0;
+    info->step = h->step;
+    info->tau = h->tau;
+    info->eps0 = h->opts.eps0;
+    info->scale = h->opts.scale;
+    info->bytes_per_node = (size_t)2 * NC * storage_bytes(h->opts.dtype) + (h->forced ? 2 * compute_bytes(h->opts.dtype) : 0);
+    info->device_bytes = h->device_bytes;
+    info->populations = h->q[h->cur];
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_synchronize(rlbm_t *h) {
+    CHECK_HANDLE(h);
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_last_error(rlbm_t *h, char *buf, size_t len) {
+    if (!h || !buf || len == 0) return RLBM_ERR_ARG;
+    snprintf(buf, len, "%s", h->msg.c_str());
+    return RLBM_OK;
+}
+
+}  // extern "C"

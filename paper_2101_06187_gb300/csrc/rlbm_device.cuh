@@ -1,0 +1,272 @@
+// rlbm_device.cuh -- per-node arithmetic of the RLBM stream-collide step
+// (Watson, arXiv:2101.06187), shared by the fused step kernels and the
+// moments kernel.
+//
+// Stored state: 17 in-plane classes c of the 26-direction spherical node
+// (Sec. 5, "spherical D3Q27" with one lattice node in z).  A class merges
+// the z-mirror pair (v_x, v_y, +v_z) / (v_x, v_y, -v_z): on a one-layer
+// periodic lattice both stream by (v_x, v_y) and collide alike, so only
+// their sum f_c is evolved.  Each class is stored as the scaled deviation
+//     q_c = (f_c - W_c eps0) / (W_c s)
+// from the rest equilibrium, which keeps the low-order digits that FP32 and
+// 16-bit storage would otherwise lose to the constant W_c eps0.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace rlbk {
+
+constexpr int NC = 17;
+
+// 1/sqrt(2) and 1/sqrt(3): in-plane components of the edge and corner directions.
+constexpr double kA = 0.70710678118654752440084436210484904;
+constexpr double kB = 0.57735026918962576450914878050195746;
+
+// Class table (in-plane velocity, merged weight W_c, v_z^2 of the class).
+// Rest (0,0,+-1): W = 2 * 1/21.  Axis faces: 1/21.  (a,0)-type edges with a
+// z component: 2 * 4/105.  In-plane diagonal edges: 4/105.  Corners:
+// 2 * 9/280.  Sum of W = 1.
+__host__ __device__ constexpr double cls_cx(int c) {
+    return c == 1 ? 1.0 : c == 2 ? -1.0 : c == 5 ? kA : c == 6 ? -kA : c == 9 ? kA : c == 10 ? -kA
+         : c == 11 ? kA : c == 12 ? -kA : c == 13 ? kB : c == 14 ? -kB : c == 15 ? kB : c == 16 ? -kB : 0.0;
+}
+__host__ __device__ constexpr double cls_cy(int c) {
+    return c == 3 ? 1.0 : c == 4 ? -1.0 : c == 7 ? kA : c == 8 ? -kA : c == 9 ? kA : c == 10 ? kA
+         : c == 11 ? -kA : c == 12 ? -kA : c == 13 ? kB : c == 14 ? kB : c == 15 ? -kB : c == 16 ? -kB : 0.0;
+}
+__host__ __device__ constexpr double cls_w(int c) {
+    return c == 0 ? 2.0 / 21.0 : c <= 4 ? 1.0 / 21.0 : c <= 8 ? 8.0 / 105.0 : c <= 12 ? 4.0 / 105.0 : 9.0 / 140.0;
+}
+__host__ __device__ constexpr double cls_vz2(int c) {
+    return c == 0 ? 1.0 : c <= 4 ? 0.0 : c <= 8 ? 0.5 : c <= 12 ? 0.0 : 1.0 / 3.0;
+}
+
+// Pull streaming with linear interpolation (Sec. 3.2): the class-c value at
+// node x is the bilinear interpolation of the post-collision field at the
+// off-lattice point x - c.  Source corner offset o = floor(-c) and
+// fractional part t = -c - o, per axis; both depend only on the class.
+__host__ __device__ constexpr int floor_int(double x) {
+    return (x >= 0.0) ? (int)x : ((double)(int)x == x ? (int)x : (int)x - 1);
+}
+__host__ __device__ constexpr int cls_ox(int c) { return floor_int(-cls_cx(c)); }
+__host__ __device__ constexpr int cls_oy(int c) { return floor_int(-cls_cy(c)); }
+__host__ __device__ constexpr double cls_tx(int c) { return -cls_cx(c) - (double)cls_ox(c); }
+__host__ __device__ constexpr double cls_ty(int c) { return -cls_cy(c) - (double)cls_oy(c); }
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+// ---------------------------------------------------------------- storage conversion
+template <typename TS, typename TC>
+__device__ __forceinline__ TC load_q(const TS *p) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
+        return (TC)__bfloat162float(__ldg(p));
+    } else if constexpr (std::is_same<TS, __half>::value) {
+        return (TC)__half2float(__ldg(p));
+    } else {
+        return (TC)__ldg(p);
+    }
+}
+
+template <typename TS, typename TC>
+__device__ __forceinline__ TS to_storage(TC x) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
+        return __float2bfloat16_rn((float)x);
+    } else if constexpr (std::is_same<TS, __half>::value) {
+        return __float2half_rn((float)x);
+    } else {
+        return (TS)x;
+    }
+}
+
+// ---------------------------------------------------------------- parameters
+struct StepParams {
+    int nx, ny, pitch;
+    long long plane;  // elements per class plane = ny * pitch
+    double inv_tau;   // 1/tau (Delta t = 1)
+    double eps0;      // reference energy density of the deviation
+    double scale;     // s
+    int *err;         // device error word (bounded-wait / failure reporting)
+};
+
+// Moments of the post-stream node (deviation form), Eq. energyMomentumIntegral
+// discretised: with f_c = W_c (eps0 + s q_c),
+//   E = eps0 + dE, dE = s sum W q;  M^a = s sum W q c^a;
+//   S^ab = eps0 delta^ab / 3 + dS^ab, dS^ab = s sum W q c^a c^b (in-plane);
+//   Q^abc = s sum W q c^a c^b c^c (in-plane); Q^azz = M^a - Q^axx - Q^ayy.
+template <typename TC>
+struct NodeMoments {
+    TC dE, Mx, My, dSxx, dSxy, dSyy, Qxxx, Qxxy, Qxyy, Qyyy;
+};
+
+template <typename TC>
+__device__ __forceinline__ NodeMoments<TC> node_moments(const TC (&q)[NC], TC s) {
+    NodeMoments<TC> m;
+    TC e = 0, mx = 0, my = 0, sxx = 0, sxy = 0, syy = 0, qxxx = 0, qxxy = 0, qxyy = 0, qyyy = 0;
+    static_for<0, NC>([&](auto C) {
+        constexpr int c = decltype(C)::value;
+        constexpr double w = cls_w(c), cx = cls_cx(c), cy = cls_cy(c);
+        const TC wq = (TC)w * q[c];
+        e += wq;
+        if constexpr (cx != 0.0) mx += (TC)cx * wq;
+        if constexpr (cy != 0.0) my += (TC)cy * wq;
+        if constexpr (cx != 0.0) sxx += (TC)(cx * cx) * wq;
+        if constexpr (cx != 0.0 && cy != 0.0) sxy += (TC)(cx * cy) * wq;
+        if constexpr (cy != 0.0) syy += (TC)(cy * cy) * wq;
+        if constexpr (cx != 0.0) qxxx += (TC)(cx * cx * cx) * wq;
+        if constexpr (cx != 0.0 && cy != 0.0) qxxy += (TC)(cx * cx * cy) * wq;
+        if constexpr (cx != 0.0 && cy != 0.0) qxyy += (TC)(cx * cy * cy) * wq;
+        if constexpr (cy != 0.0) qyyy += (TC)(cy * cy * cy) * wq;
+    });
+    m.dE = s * e;
+    m.Mx = s * mx;
+    m.My = s * my;
+    m.dSxx = s * sxx;
+    m.dSxy = s * sxy;
+    m.dSyy = s * syy;
+    m.Qxxx = s * qxxx;
+    m.Qxxy = s * qxxy;
+    m.Qxyy = s * qxyy;
+    m.Qyyy = s * qyyy;
+    return m;
+}
+
+// Landau-Lifshitz frame (the eigenvalue problem closing Sec. 3.2):
+// T^{mu nu} u_nu = -eps u^mu.  With v = u/u^0 and delta = E - eps this is
+//   (S + eps I) v = M,  delta = M . v.
+// In deviation variables S + eps I = a I + dS with a = 4 eps0/3 + dE - delta
+// (the z row decouples: M_z = S_xz = S_yz = 0, so v_z = 0).  Newton on
+//   g(delta) = delta - M . (aI + dS)^{-1} M,   g'(delta) = 1 - |v|^2,
+// from delta = 0.  g is increasing and concave (g'' = -2 v.(aI + dS)^{-1} v),
+// and g(0) <= 0, so Newton from delta = 0 rises monotonically onto the
+// physical root (eps > 0, |v| < 1).
+template <typename TL>
+struct Frame {
+    TL ddelta_eps;  // eps - eps0 = dE - delta
+    TL eps;         // eps0 + dE - delta
+    TL vx, vy;      // 3-velocity
+    TL v2, g2;      // |v|^2, gamma^2 = 1/(1 - |v|^2)
+};
+
+template <typename TL>
+__device__ __forceinline__ Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL dSxy, TL dSyy) {
+    const TL a0 = (TL)(4.0 / 3.0) * eps0 + dE;
+    TL delta = 0, vx = 0, vy = 0;
+    const TL tol = std::is_same<TL, double>::value ? (TL)4e-16 : (TL)2e-7;
+    const int maxit = std::is_same<TL, double>::value ? 24 : 12;
+    for (int it = 0; it < maxit; ++it) {
+        const TL a = a0 - delta;
+        const TL axx = a + dSxx, ayy = a + dSyy;
+        const TL inv_det = (TL)1 / (axx * ayy - dSxy * dSxy);
+        vx = (ayy * Mx - dSxy * My) * inv_det;
+        vy = (axx * My - dSxy * Mx) * inv_det;
+        const TL g = delta - (Mx * vx + My * vy);
+        const TL gp = (TL)1 - (vx * vx + vy * vy);
+        const TL step = g / gp;
+        delta -= step;
+        if (!(fabs(step) > tol * fabs(delta))) break;  // also exits on NaN
+    }
+    // velocity at the converged root
+    {
+        const TL a = a0 - delta;
+        const TL axx = a + dSxx, ayy = a + dSyy;
+        const TL inv_det = (TL)1 / (axx * ayy - dSxy * dSxy);
+        vx = (ayy * Mx - dSxy * My) * inv_det;
+        vy = (axx * My - dSxy * Mx) * inv_det;
+    }
+    Frame<TL> fr;
+    fr.ddelta_eps = dE - delta;
+    fr.eps = eps0 + fr.ddelta_eps;
+    fr.vx = vx;
+    fr.vy = vy;
+    fr.v2 = vx * vx + vy * vy;
+    fr.g2 = (TL)1 / ((TL)1 - fr.v2);
+    return fr;
+}
+
+// Fused collision of one node (steps (c)-(e) of Sec. 3.3) on the gathered
+// deviations q[c] (in place), returning the frame for diagnostics.
+//
+// Equilibrium (Eqs. rel_pdf_exp, rel_pdf_exp_coef with T_eq of Eq.
+// stressEnergyT, P = eps/3, App. A norms): f_eq,i = w_i [-(3/2) T00 + 3 v_i.M_eq
+// + (15/2) v_i S_eq v_i]; for |v_i| = 1 and xi = v_i . v this is
+//   f_eq,c = W_c eps [3 - 2 gamma^2 + gamma^2 (4 xi + 10 xi^2)],
+// so q_eq,c = [eps - eps0 + eps gamma^2 (4 xi + 10 xi^2 - 2 |v|^2)] / s.
+// Relaxation (Eq. boltzmanneq_rel, Anderson-Witting): rate
+// (u^0 - v_c . u)/tau = gamma (1 - xi)/tau.
+// Driving term (Eq. forceTerm, App. B), F^mu = (0, F_x, F_y, 0), prefactor
+// -6 so that sum G = F.M and sum G v = F E:
+//   G_c = -6 W_c [ F.M/4 - (F.c) E/2 + (5/4) F_a c_b c_c Q^abc - (5/2)(F.c)(c.M) ]
+// with the moments of the post-stream populations.
+template <typename TC, typename TL, bool FORCED>
+__device__ __forceinline__ Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
+    const TC s = (TC)p.scale;
+    const NodeMoments<TC> m = node_moments<TC>(q, s);
+    const Frame<TL> fr = landau_solve<TL>((TL)p.eps0, (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
+                                          (TL)m.dSyy);
+    const TC inv_s = (TC)(1.0 / p.scale);
+    const TL eg2 = fr.eps * fr.g2;
+    const TC P0 = (TC)((fr.ddelta_eps - (TL)2 * eg2 * fr.v2)) * inv_s;
+    const TC P1 = (TC)((TL)4 * eg2) * inv_s;
+    const TC P2 = (TC)((TL)10 * eg2) * inv_s;
+    const TC vx = (TC)fr.vx, vy = (TC)fr.vy;
+    const TC om = (TC)(sqrt(fr.g2) * (TL)p.inv_tau);  // gamma / tau
+
+    TC G0 = 0, G1 = 0, G3 = 0, Pxx = 0, Pxy = 0, Pyy = 0, Pzz = 0;
+    if constexpr (FORCED) {
+        const TC E = (TC)p.eps0 + m.dE;
+        const TC FM = Fx * m.Mx + Fy * m.My;
+        const TC c6 = (TC)(-6.0) * inv_s;
+        G0 = c6 * (TC)0.25 * FM;
+        G1 = c6 * (TC)(-0.5) * E;
+        G3 = c6 * (TC)(-2.5);
+        const TC c54 = c6 * (TC)1.25;
+        const TC Qxzz = m.Mx - m.Qxxx - m.Qxyy;
+        const TC Qyzz = m.My - m.Qxxy - m.Qyyy;
+        Pxx = c54 * (Fx * m.Qxxx + Fy * m.Qxxy);
+        Pxy = c54 * (Fx * m.Qxxy + Fy * m.Qxyy);
+        Pyy = c54 * (Fx * m.Qxyy + Fy * m.Qyyy);
+        Pzz = c54 * (Fx * Qxzz + Fy * Qyzz);
+    }
+
+    static_for<0, NC>([&](auto C) {
+        constexpr int c = decltype(C)::value;
+        constexpr double cx = cls_cx(c), cy = cls_cy(c), vz2 = cls_vz2(c);
+        TC xi = 0;
+        if constexpr (cx != 0.0) xi += (TC)cx * vx;
+        if constexpr (cy != 0.0) xi += (TC)cy * vy;
+        const TC qeq = P0 + xi * (P1 + P2 * xi);
+        const TC omc = om - om * xi;
+        TC qn = q[c] - omc * (q[c] - qeq);
+        if constexpr (FORCED) {
+            TC Fc = 0, cM = 0;
+            if constexpr (cx != 0.0) {
+                Fc += (TC)cx * Fx;
+                cM += (TC)cx * m.Mx;
+            }
+            if constexpr (cy != 0.0) {
+                Fc += (TC)cy * Fy;
+                cM += (TC)cy * m.My;
+            }
+            TC g = G0 + Fc * (G1 + G3 * cM);
+            if constexpr (cx != 0.0) g += (TC)(cx * cx) * Pxx;
+            if constexpr (cx != 0.0 && cy != 0.0) g += (TC)(2.0 * cx * cy) * Pxy;
+            if constexpr (cy != 0.0) g += (TC)(cy * cy) * Pyy;
+            if constexpr (vz2 != 0.0) g += (TC)vz2 * Pzz;
+            qn += g;
+        }
+        q[c] = qn;
+    });
+    return fr;
+}
+
+}  // namespace rlbk

@@ -1,0 +1,93 @@
+// rlbm_internal.h -- handle layout and kernel launchers shared by the
+// translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <utility>
+
+#include "../../include/rlbm.h"
+#include "rlbm_device.cuh"
+
+namespace rlbk {
+
+// One forcing mode: integer wavevector and the four synthesis coefficients
+// F_x += ax cos(psi) - bx sin(psi), F_y += ay cos(psi) - by sin(psi),
+// psi = 2 pi (kx x/nx + ky y/ny): ax = 2 r amp cos(th) cos(ph),
+// bx = 2 r amp cos(th) sin(ph), ay, by likewise with sin(th).
+struct Mode {
+    int kx, ky;
+    double ax, bx, ay, by;
+};
+
+struct Launch {
+    cudaStream_t stream;
+    int kernel;  // rlbm_kernel actually used
+};
+
+// Step launchers (defined in the per-form translation units).
+cudaError_t launch_step(int dtype, int landau, int kernel, bool forced, const void *qin, void *qout, const void *F,
+                        const StepParams &p, cudaStream_t s);
+cudaError_t launch_moments(int dtype, int landau, const void *qin, const StepParams &p, double *eps, double *vx,
+                           double *vy, double *partials, int *bad, cudaStream_t s);
+int moments_blocks(const StepParams &p);
+
+// Auxiliary kernels (k_aux.cu).
+cudaError_t launch_init(int dtype, void *q, const StepParams &p, const double *eps, const double *vx,
+                        const double *vy, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double *partials, int nblocks, double base_E, double *totals,
+                                   cudaStream_t s);
+cudaError_t launch_twiddles(int dtype, void *tw, int n, cudaStream_t s);
+cudaError_t launch_draw_modes(Mode *modes, int nmodes, double amp, unsigned long long seed,
+                              unsigned long long epoch, cudaStream_t s);
+cudaError_t launch_synth_force(int dtype, void *F, const Mode *modes, int nmodes, const void *twx, const void *twy,
+                               const StepParams &p, cudaStream_t s);
+cudaError_t launch_decode_class(int dtype, const void *q, int c, const StepParams &p, double *out, cudaStream_t s);
+cudaError_t launch_encode_class(int dtype, void *q, int c, const StepParams &p, const double *in, cudaStream_t s);
+cudaError_t launch_force_to_f64(int dtype, const void *F, int comp, const StepParams &p, double *out,
+                                cudaStream_t s);
+cudaError_t launch_spectrum(const double *vx, const double *vy, int nx, int ny, int nshells, double *work,
+                            double *Ek, cudaStream_t s);
+size_t spectrum_work_doubles(int nx, int ny);
+
+size_t storage_bytes(int dtype);
+size_t compute_bytes(int dtype);
+
+}  // namespace rlbk
+
+struct rlbm {
+    int nx = 0, ny = 0, pitch = 0;
+    double tau = 0;
+    rlbm_opts opts{};
+    rlbm_forcing forcing{};
+    bool forced = false;
+    int nmodes = 0;
+    int kernel = 0;
+    bool own_stream = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    void *q[2] = {nullptr, nullptr};  // ping-pong population buffers [17][ny][pitch]
+    int cur = 0;                      // index of the current (post-collision) state
+    void *F = nullptr;                // force field [2][ny][pitch] (compute type)
+    void *twx = nullptr, *twy = nullptr;
+    rlbk::Mode *modes = nullptr;
+    double *fields = nullptr;         // 3 * nx * ny doubles: staging for init / moments outputs
+    double *partials = nullptr;       // per-block partial sums of the moments kernel
+    double *totals = nullptr;         // 3 doubles
+    int *bad = nullptr;               // device counter of failed nodes
+    double *spec_work = nullptr;      // spectrum work area
+    size_t spec_work_bytes = 0;
+    double *host_pinned = nullptr;    // pinned staging, 3 * nx * ny doubles
+    size_t device_bytes = 0;
+
+    long long step = 0;
+    long long force_epoch = -1;  // epoch whose force is in F
+
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (steps, parity) -> graph
+
+    rlbm_status status = RLBM_OK;
+    std::string msg;
+};

@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every entry point include/rlbm.h declares, and rejects
+invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rlbm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2101_06187_gb300 as rl
+    return rl.library()
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"RLBM_API[^;(]*?\b(rlbm_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("rlbm_create", "rlbm_step", "rlbm_moments", "rlbm_energy_spectrum", "rlbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (rlbm_\w+)", out))
+    assert set(_declared()) <= exported
+
+
+def test_binding_names_match_header():
+    import paper_2101_06187_gb300 as rl
+    assert sorted(rl.EXPORTS) == _declared()
+    for name in rl.EXPORTS:
+        assert callable(getattr(rl, name)), name
+
+
+def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
+    import paper_2101_06187_gb300 as rl
+    out = ctypes.c_void_p()
+    F = rl.Forcing
+
+    def create(nx, ny, tau, forcing=None, opts=None, st=0):
+        return lib.rlbm_create(nx, ny, st, tau, ctypes.byref(forcing) if forcing else None,
+                               ctypes.byref(opts) if opts else None, ctypes.byref(out))
+
+    assert create(3, 16, 0.8) == rl.RLBM_ERR_ARG          # nx < 4
+    assert create(16, 2, 0.8) == rl.RLBM_ERR_ARG          # ny < 4
+    assert create(16, 16, 0.5) == rl.RLBM_ERR_ARG         # tau must exceed 1/2
+    assert create(16, 16, float("nan")) == rl.RLBM_ERR_ARG
+    assert create(16, 16, 0.8, st=1) == rl.RLBM_ERR_ARG   # unknown stencil
+    assert create(16, 16, 0.8, F(2, 8, 1e-3, 1, 100)) == rl.RLBM_ERR_ARG   # kmax >= n/2
+    assert create(16, 16, 0.8, F(0, 3, 1e-3, 1, 100)) == rl.RLBM_ERR_ARG   # kmin < 1
+    assert create(16, 16, 0.8, F(3, 2, 1e-3, 1, 100)) == rl.RLBM_ERR_ARG   # kmin > kmax
+    assert create(16, 16, 0.8, F(1, 3, -1.0, 1, 100)) == rl.RLBM_ERR_ARG   # amp < 0
+    assert create(16, 16, 0.8, F(1, 3, 1e-3, 1, 0)) == rl.RLBM_ERR_ARG     # redraw period
+    o = rl.rlbm_opts_default()
+    o.dtype = 9
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
+    o = rl.rlbm_opts_default()
+    o.scale = -1.0
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
+    assert out.value is None
+    assert lib.rlbm_create(16, 16, 0, 0.8, None, None, None) == rl.RLBM_ERR_ARG
+
+
+def test_null_handle_calls_are_rejected(lib):
+    import paper_2101_06187_gb300 as rl
+    assert lib.rlbm_step(None, 1) == rl.RLBM_ERR_ARG
+    assert lib.rlbm_moments(None, None, None, None, None) == rl.RLBM_ERR_ARG
+    assert lib.rlbm_energy_spectrum(None, 4, None) == rl.RLBM_ERR_ARG
+    lib.rlbm_destroy(None)
+    assert lib.rlbm_status_string(rl.RLBM_ERR_NAN) == b"non-finite or non-physical state"
+
+
+def test_opts_defaults(lib):
+    import paper_2101_06187_gb300 as rl
+    o = rl.rlbm_opts_default()
+    assert o.dtype == rl.DTYPES["f32"] and o.landau == 0 and o.use_graphs == 1 and o.eps0 == 1.0 and o.device == -1
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    code = ("import paper_2101_06187_gb300 as rl; rl.LIB_PATH = %r\n"
+            "try:\n    rl.library()\nexcept RuntimeError as e:\n    print('raised', e)\n") % str(tmp_path / "none.so")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert "raised" in r.stdout

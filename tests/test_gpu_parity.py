@@ -1,0 +1,185 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Both sides start from the same seeded macroscopic fields (workloads module)
+and run the same number of steps; nothing computed by the GPU is fed to the
+oracle.  Error measure (the reading of "pointwise max relative error on eps
+and u"): max over nodes of |eps_gpu - eps_ref| / max|eps_ref|, and max over
+nodes and components of |v_gpu - v_ref| / max|v_ref| (normwise, because v
+crosses zero).  Bars: 1e-12 for the FP64 form, 1e-5 for the FP32 form.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2101_06187_gb300 as rl  # noqa: E402
+
+oracle.set_threads(os.cpu_count() or 4)
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel_errors(ref, got):
+    e_r, vx_r, vy_r = ref
+    e_g, vx_g, vy_g = got[:3]
+    err_e = np.max(np.abs(e_g - e_r)) / np.max(np.abs(e_r))
+    vnorm = max(np.max(np.abs(vx_r)), np.max(np.abs(vy_r)), 1e-300)
+    err_v = max(np.max(np.abs(vx_g - vx_r)), np.max(np.abs(vy_g - vy_r))) / vnorm
+    return err_e, err_v
+
+
+def run_pair(nx, ny, tau, nsteps, dtype, fields, forcing=None, landau="fp64", **kw):
+    eps, vx, vy = fields
+    lat = rl.Lattice(nx, ny, tau, dtype=dtype, landau=landau, forcing=forcing, **kw)
+    lat.init_fields(eps, vx, vy)
+    lat.step(nsteps)
+    got = lat.moments()
+    f = oracle.init(nx, ny, eps, vx, vy)
+    if forcing:
+        oracle.run(f, tau, nsteps, kmin=forcing["kmin"], kmax=forcing["kmax"], amp=forcing["amp"],
+                   seed=forcing["seed"], redraw=forcing["redraw_period"])
+    else:
+        oracle.run(f, tau, nsteps)
+    ref = oracle.fields(f)
+    return lat, f, ref, got
+
+
+FORCING_SMALL = dict(kmin=2, kmax=4, amp=2e-4, seed=123456789, redraw_period=7)
+
+
+@pytest.mark.parametrize("dtype,landau", [("f64", "fp64"), ("f32", "fp64"), ("f32", "fp32")])
+@pytest.mark.parametrize("shape", [(37, 29), (64, 48), (4, 4)])
+def test_forced_run_matches_oracle(dtype, landau, shape):
+    """Ragged lattices spanning several 32x8 tiles, and the 4x4 minimum."""
+    nx, ny = shape
+    forcing = FORCING_SMALL if min(nx, ny) > 8 else dict(kmin=1, kmax=1, amp=2e-4, seed=5, redraw_period=3)
+    fields = workloads.random_smooth(nx, ny, seed=nx * 1000 + ny, deps=0.05, vmax=0.05)
+    lat, f, ref, got = run_pair(nx, ny, 0.7, 100, dtype, fields, forcing, landau)
+    err_e, err_v = rel_errors(ref, got)
+    assert err_e < TOL[dtype] and err_v < TOL[dtype], (err_e, err_v)
+    if dtype == "f64":
+        # raw populations: the 17 stored classes are the z-mirror sums of the oracle's 26
+        pops = lat.populations()
+        merged = oracle.merge_classes(f)
+        assert np.max(np.abs(pops - merged)) < 1e-13 * np.max(np.abs(merged))
+    lat.close()
+
+
+def test_force_field_matches_oracle():
+    nx, ny = 96, 80
+    forcing = dict(kmin=3, kmax=6, amp=1e-3, seed=2101061870, redraw_period=10)
+    for dtype, tol in (("f64", 1e-14), ("f32", 2e-6)):
+        lat = rl.Lattice(nx, ny, 0.8, dtype=dtype, forcing=forcing)
+        for epoch in (0, 3):
+            lat.init_fields()
+            if epoch:
+                lat.step(epoch * forcing["redraw_period"])
+            Fx, Fy = lat.force()
+            Ox, Oy = oracle.force_field(nx, ny, 3, 6, 1e-3, 2101061870, epoch)
+            scale = max(np.max(np.abs(Ox)), np.max(np.abs(Oy)))
+            assert np.max(np.abs(Fx - Ox)) < tol * scale
+            assert np.max(np.abs(Fy - Oy)) < tol * scale
+        lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_unforced_totals_conserved_and_match_oracle(dtype):
+    nx, ny = 48, 40
+    fields = workloads.random_smooth(nx, ny, seed=3, deps=0.1, vmax=0.1)
+    lat = rl.Lattice(nx, ny, 0.6, dtype=dtype)
+    lat.init_fields(*fields)
+    t0 = lat.moments()[3]
+    lat.step(200)
+    t1 = lat.moments()[3]
+    f = oracle.init(nx, ny, *fields)
+    tref = oracle.totals(f)[:3]
+    tol = 1e-13 if dtype == "f64" else 1e-6
+    assert abs(t0[0] - tref[0]) < tol * tref[0]
+    np.testing.assert_allclose(t0[1:], tref[1:], rtol=0, atol=tol * tref[0])
+    assert abs(t1[0] - t0[0]) < tol * t0[0]
+    np.testing.assert_allclose(t1[1:], t0[1:], rtol=0, atol=tol * t0[0])
+    lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+def test_rest_state_is_fixed_point(dtype):
+    lat = rl.Lattice(32, 32, 0.52, dtype=dtype)
+    lat.init_fields()
+    lat.step(500)
+    e, vx, vy, tot = lat.moments()
+    tol = 1e-14 if dtype == "f64" else 1e-7
+    assert np.max(np.abs(e - 1.0)) < tol and np.max(np.abs(vx)) < tol and np.max(np.abs(vy)) < tol
+    lat.close()
+
+
+def test_graph_and_direct_launches_agree_bitwise():
+    nx, ny = 64, 64
+    fields = workloads.random_smooth(nx, ny, seed=11)
+    out = []
+    for graphs in (True, False):
+        lat = rl.Lattice(nx, ny, 0.7, dtype="f32", forcing=FORCING_SMALL, use_graphs=graphs)
+        lat.init_fields(*fields)
+        for n in (1, 6, 13, 2, 41):  # odd/even chunks across epoch boundaries
+            lat.step(n)
+        out.append(lat.populations())
+        lat.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_step_zero_and_info():
+    lat = rl.Lattice(16, 12, 0.8, dtype="f32", forcing=dict(kmin=1, kmax=2, amp=1e-4, seed=1, redraw_period=4))
+    lat.init_fields()
+    p0 = lat.populations()
+    lat.step(0)
+    np.testing.assert_array_equal(lat.populations(), p0)
+    info = lat.info()
+    assert info["nx"] == 16 and info["ny"] == 12 and info["nclasses"] == 17 and info["step"] == 0
+    assert info["bytes_per_node"] == 2 * 17 * 4 + 2 * 4
+    lat.step(5)
+    assert lat.info()["step"] == 5
+    lat.close()
+
+
+def test_invalid_initial_fields_rejected():
+    lat = rl.Lattice(8, 8, 0.8, dtype="f64")
+    with pytest.raises(rl.RLBMError):
+        lat.init_fields(np.full(64, -1.0))
+    with pytest.raises(rl.RLBMError):
+        lat.init_fields(None, np.full(64, 1.2), None)
+    lat.close()
+
+
+def test_energy_spectrum_matches_oracle():
+    nx = ny = 64
+    fields = workloads.random_smooth(nx, ny, seed=21, vmax=0.05)
+    forcing = dict(kmin=3, kmax=5, amp=1e-4, seed=77, redraw_period=10)
+    lat, f, ref, got = run_pair(nx, ny, 0.6, 30, "f64", fields, forcing)
+    E_g = lat.energy_spectrum(40)
+    E_o = oracle.energy_spectrum(ref[1], ref[2], 40)
+    np.testing.assert_allclose(E_g, E_o, rtol=1e-10, atol=1e-24)
+    lat.close()
+
+
+def test_energy_spectrum_non_power_of_two_side():
+    nx, ny = 48, 40  # direct-DFT path on both axes
+    fields = workloads.random_smooth(nx, ny, seed=22, vmax=0.05)
+    lat, f, ref, got = run_pair(nx, ny, 0.6, 10, "f64", fields)
+    E_g = lat.energy_spectrum(30)
+    E_o = oracle.energy_spectrum(ref[1], ref[2], 30)
+    np.testing.assert_allclose(E_g, E_o, rtol=1e-10, atol=1e-24)
+    lat.close()
