@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16", "f16"])
-    ap.add_argument("--landau", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--landau", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "staged"])
     ap.add_argument("--n", type=int, default=0, help="override lattice side (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-form table, e2e and CPU baseline")
@@ -151,12 +152,14 @@ def time_steps(torch, lat, steps, flush):
     return np.array([a.elapsed_time(b) for a, b in evs])  # ms
 
 
-def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, init=None):
+def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, init=None, tune=True):
     lat = rl.Lattice(n, n, w.tau, dtype=form, landau=landau, kernel=kernel, forcing=forcing_of(w))
     if init is not None:
         lat.init_fields(*init)
     else:
         lat.init_fields()
+    if tune:
+        lat.autotune(10)
     lat.step(warmup)
     lat.synchronize()
     ms = time_steps(torch, lat, steps, flush)
@@ -310,7 +313,8 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(smi_index) as clocks:
-        ms, kernel_ms, info, n_epoch = measure_form(torch, rl, w, n, args.form, args.landau, args.kernel, K, W, flush)
+        ms, kernel_ms, info, n_epoch = measure_form(torch, rl, w, n, args.form, args.landau, args.kernel, K, W, flush,
+                                                    tune=not args.no_tune)
     torch.cuda.synchronize()
     step_ms = float(ms.mean())
     total_s = float(ms.sum()) / 1e3
@@ -350,7 +354,8 @@ def main():
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.form != "f64" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": n, "ny": n, "form": args.form, "landau": args.landau,
-                   "kernel": ["auto", "gather", "staged"][info["kernel"]], "tau": w.tau,
+                   "kernel": ["auto", "gather", "staged"][info["kernel"]],
+                   "block": [info["block_x"], info["block_y"]], "tau": w.tau,
                    "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm" if args.form != "f64" else "alu", "achieved": achieved, "peak": hbm_peak,
@@ -366,7 +371,7 @@ def main():
         oracle.build()
         oracle.set_threads(os.cpu_count() or 1)
         forms = {}
-        for form, landau in (("f32", "fp64"), ("f32", "fp32"), ("f64", "fp64"), ("bf16", "fp64"), ("f16", "fp64")):
+        for form, landau in (("f32", "fp32"), ("f32", "fp64"), ("f64", "fp64"), ("bf16", "fp32"), ("f16", "fp32")):
             if form == args.form and landau == args.landau:
                 g = glups_total / world
                 km = kernel_ms

@@ -72,8 +72,10 @@ typedef enum { RLBM_STENCIL_SPH26_SLAB = 0 } rlbm_stencil;
  * BF16 / F16: 16-bit storage, FP32 arithmetic. */
 typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16 = 2, RLBM_F16 = 3 } rlbm_dtype;
 
-/* Precision of the per-node Landau-frame solve for the F32/16-bit forms
- * (the F64 form always solves in FP64). */
+/* Precision of the per-node Landau-frame solve in the fused step of the
+ * F32/16-bit forms (the F64 form always solves in FP64; rlbm_moments always
+ * solves in FP64).  The solve is a Newton iteration on the small deviation
+ * delta = E - eps, so FP32 keeps full FP32 accuracy of eps and v. */
 typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
 
 /* Kernel variant of the fused step (RLBM_KERNEL_AUTO picks the fastest
@@ -105,7 +107,7 @@ typedef void (*rlbm_free_fn)(void *ptr, size_t bytes, void *ctx);
 
 typedef struct {
     int dtype;            /* rlbm_dtype (default RLBM_F32) */
-    int landau;           /* rlbm_landau (default RLBM_LANDAU_FP64) */
+    int landau;           /* rlbm_landau (default RLBM_LANDAU_FP32) */
     int kernel;           /* rlbm_kernel (default RLBM_KERNEL_AUTO) */
     int use_graphs;       /* 1: replay the step loop as CUDA graphs (default 1) */
     double eps0;          /* reference energy density of the deviation (default 1) */
@@ -122,6 +124,7 @@ typedef struct {
     int nclasses;             /* 17 stored in-plane classes */
     int dtype;                /* rlbm_dtype */
     int kernel;               /* rlbm_kernel actually used */
+    int block_x, block_y;     /* thread-block shape of the fused step */
     int nmodes;               /* forcing modes (0 = unforced) */
     int64_t step;             /* steps taken since init */
     double tau, eps0, scale;
@@ -190,6 +193,15 @@ RLBM_API rlbm_status rlbm_set_populations(rlbm_t *h, const double *f);
 RLBM_API rlbm_status rlbm_get_force(rlbm_t *h, double *Fx, double *Fy);
 
 RLBM_API rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info);
+
+/* Time every launch configuration of the fused step (kernel variant and
+ * thread-block shape) for `reps` launches each (reps < 1: 20) on the
+ * handle's lattice and keep the fastest.  The trial launches read the
+ * current state and write only the spare buffer, so the simulation state is
+ * unchanged.  The choice is cached per (nx, ny, dtype, landau, forced) for
+ * handles created later in the process with RLBM_KERNEL_AUTO.  Outputs may
+ * be NULL.  Synchronises. */
+RLBM_API rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *kernel, int *block_x, int *block_y);
 
 /* Wait for all work queued on the handle's stream. */
 RLBM_API rlbm_status rlbm_synchronize(rlbm_t *h);

@@ -35,7 +35,7 @@ NCLASSES = 17
 EXPORTS = (
     "rlbm_opts_default", "rlbm_create", "rlbm_init_fields", "rlbm_init_fields_device", "rlbm_step", "rlbm_moments",
     "rlbm_moments_device", "rlbm_energy_spectrum", "rlbm_get_populations", "rlbm_set_populations", "rlbm_get_force",
-    "rlbm_get_info", "rlbm_synchronize", "rlbm_last_error", "rlbm_destroy", "rlbm_status_string",
+    "rlbm_get_info", "rlbm_autotune", "rlbm_synchronize", "rlbm_last_error", "rlbm_destroy", "rlbm_status_string",
 )
 
 
@@ -63,7 +63,8 @@ class Opts(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_int), ("nclasses", ctypes.c_int),
-                ("dtype", ctypes.c_int), ("kernel", ctypes.c_int), ("nmodes", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("kernel", ctypes.c_int), ("block_x", ctypes.c_int),
+                ("block_y", ctypes.c_int), ("nmodes", ctypes.c_int),
                 ("step", ctypes.c_int64), ("tau", ctypes.c_double), ("eps0", ctypes.c_double),
                 ("scale", ctypes.c_double), ("bytes_per_node", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
                 ("populations", ctypes.c_void_p)]
@@ -98,6 +99,8 @@ def _load():
         lib.rlbm_get_force.argtypes = [h, _dp, _dp]
         lib.rlbm_get_info.argtypes = [h, ctypes.POINTER(Info)]
         lib.rlbm_synchronize.argtypes = [h]
+        lib.rlbm_autotune.argtypes = [h, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]
         lib.rlbm_last_error.argtypes = [h, ctypes.c_char_p, ctypes.c_size_t]
         lib.rlbm_destroy.argtypes = [h]
         lib.rlbm_destroy.restype = None
@@ -105,7 +108,7 @@ def _load():
         lib.rlbm_status_string.restype = ctypes.c_char_p
         for name in ("rlbm_create", "rlbm_init_fields", "rlbm_init_fields_device", "rlbm_step", "rlbm_moments",
                      "rlbm_moments_device", "rlbm_energy_spectrum", "rlbm_get_populations", "rlbm_set_populations",
-                     "rlbm_get_force", "rlbm_get_info", "rlbm_synchronize", "rlbm_last_error"):
+                     "rlbm_get_force", "rlbm_get_info", "rlbm_autotune", "rlbm_synchronize", "rlbm_last_error"):
             getattr(lib, name).restype = ctypes.c_int
         _lib_handle = lib
         return lib
@@ -232,6 +235,13 @@ def rlbm_get_info(h) -> Info:
     return info
 
 
+def rlbm_autotune(h, reps: int = 20):
+    k, bx, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(h, _load().rlbm_autotune(h, int(reps), ctypes.byref(k), ctypes.byref(bx), ctypes.byref(by)),
+           "rlbm_autotune")
+    return k.value, bx.value, by.value
+
+
 def rlbm_synchronize(h):
     _check(h, _load().rlbm_synchronize(h), "rlbm_synchronize")
 
@@ -263,7 +273,7 @@ class Lattice:
     stream for this lattice).
     """
 
-    def __init__(self, nx: int, ny: int, tau: float, *, dtype: str = "f32", landau: str = "fp64",
+    def __init__(self, nx: int, ny: int, tau: float, *, dtype: str = "f32", landau: str = "fp32",
                  forcing: Optional[dict] = None, eps0: float = 1.0, scale: float = 0.0, kernel: str = "auto",
                  use_graphs: bool = True, allocator: str = "torch", stream=None, device: Optional[int] = None):
         import torch
@@ -375,6 +385,10 @@ class Lattice:
     def info(self) -> dict:
         i = rlbm_get_info(self.handle)
         return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def autotune(self, reps: int = 20):
+        """Pick the fastest launch configuration of the fused step (state unchanged)."""
+        return rlbm_autotune(self.handle, reps)
 
     def synchronize(self):
         rlbm_synchronize(self.handle)

@@ -11,15 +11,18 @@ inline dim3 gather_block() { return dim3(32, 8, 1); }
 inline dim3 gather_grid(const StepParams &p) { return dim3((p.nx + 31) / 32, (p.ny + 7) / 8, 1); }
 
 template <typename TS, typename TC, typename TL>
-cudaError_t launch_step_t(int /*kernel*/, bool forced, const void *qin, void *qout, const void *F,
+cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, void *qout, const void *F,
                           const StepParams &p, cudaStream_t s) {
     const TS *in = static_cast<const TS *>(qin);
     TS *out = static_cast<TS *>(qout);
     const TC *f = static_cast<const TC *>(F);
+    if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
+    const dim3 block(cfg.bx, cfg.by, 1);
+    const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
     if (forced)
-        k_step_gather<TS, TC, TL, true><<<gather_grid(p), gather_block(), 0, s>>>(in, out, f, p);
+        k_step_gather<TS, TC, TL, true><<<grid, block, 0, s>>>(in, out, f, p);
     else
-        k_step_gather<TS, TC, TL, false><<<gather_grid(p), gather_block(), 0, s>>>(in, out, f, p);
+        k_step_gather<TS, TC, TL, false><<<grid, block, 0, s>>>(in, out, f, p);
     return cudaGetLastError();
 }
 

@@ -2,14 +2,14 @@
 #include "k_launch.cuh"
 
 namespace rlbk {
-cudaError_t launch_step_f32(int kernel, int landau, bool forced, const void *qin, void *qout, const void *F,
+cudaError_t launch_step_f32(const LaunchCfg &cfg, int landau, bool forced, const void *qin, void *qout, const void *F,
                             const StepParams &p, cudaStream_t s) {
-    if (landau == RLBM_LANDAU_FP32) return launch_step_t<float, float, float>(kernel, forced, qin, qout, F, p, s);
-    return launch_step_t<float, float, double>(kernel, forced, qin, qout, F, p, s);
+    if (landau == RLBM_LANDAU_FP32) return launch_step_t<float, float, float>(cfg, forced, qin, qout, F, p, s);
+    return launch_step_t<float, float, double>(cfg, forced, qin, qout, F, p, s);
 }
 cudaError_t launch_moments_f32(int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                                double *vy, double *partials, int *bad, cudaStream_t s) {
-    if (landau == RLBM_LANDAU_FP32) return launch_moments_t<float, float, float>(qin, p, eps, vx, vy, partials, bad, s);
+    (void)landau;  // diagnostics always solve the frame in FP64
     return launch_moments_t<float, float, double>(qin, p, eps, vx, vy, partials, bad, s);
 }
 }  // namespace rlbk

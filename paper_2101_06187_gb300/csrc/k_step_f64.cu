@@ -2,9 +2,9 @@
 #include "k_launch.cuh"
 
 namespace rlbk {
-cudaError_t launch_step_f64(int kernel, int, bool forced, const void *qin, void *qout, const void *F,
+cudaError_t launch_step_f64(const LaunchCfg &cfg, int, bool forced, const void *qin, void *qout, const void *F,
                             const StepParams &p, cudaStream_t s) {
-    return launch_step_t<double, double, double>(kernel, forced, qin, qout, F, p, s);
+    return launch_step_t<double, double, double>(cfg, forced, qin, qout, F, p, s);
 }
 cudaError_t launch_moments_f64(int, const void *qin, const StepParams &p, double *eps, double *vx, double *vy,
                                double *partials, int *bad, cudaStream_t s) {

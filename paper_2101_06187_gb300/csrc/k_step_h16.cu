@@ -3,24 +3,21 @@
 #include "k_launch.cuh"
 
 namespace rlbk {
-cudaError_t launch_step_h16(int dtype, int kernel, int landau, bool forced, const void *qin, void *qout,
+cudaError_t launch_step_h16(int dtype, const LaunchCfg &cfg, int landau, bool forced, const void *qin, void *qout,
                             const void *F, const StepParams &p, cudaStream_t s) {
     if (dtype == RLBM_BF16) {
         if (landau == RLBM_LANDAU_FP32)
-            return launch_step_t<__nv_bfloat16, float, float>(kernel, forced, qin, qout, F, p, s);
-        return launch_step_t<__nv_bfloat16, float, double>(kernel, forced, qin, qout, F, p, s);
+            return launch_step_t<__nv_bfloat16, float, float>(cfg, forced, qin, qout, F, p, s);
+        return launch_step_t<__nv_bfloat16, float, double>(cfg, forced, qin, qout, F, p, s);
     }
-    if (landau == RLBM_LANDAU_FP32) return launch_step_t<__half, float, float>(kernel, forced, qin, qout, F, p, s);
-    return launch_step_t<__half, float, double>(kernel, forced, qin, qout, F, p, s);
+    if (landau == RLBM_LANDAU_FP32) return launch_step_t<__half, float, float>(cfg, forced, qin, qout, F, p, s);
+    return launch_step_t<__half, float, double>(cfg, forced, qin, qout, F, p, s);
 }
 cudaError_t launch_moments_h16(int dtype, int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                                double *vy, double *partials, int *bad, cudaStream_t s) {
-    if (dtype == RLBM_BF16) {
-        if (landau == RLBM_LANDAU_FP32)
-            return launch_moments_t<__nv_bfloat16, float, float>(qin, p, eps, vx, vy, partials, bad, s);
+    (void)landau;  // diagnostics always solve the frame in FP64
+    if (dtype == RLBM_BF16)
         return launch_moments_t<__nv_bfloat16, float, double>(qin, p, eps, vx, vy, partials, bad, s);
-    }
-    if (landau == RLBM_LANDAU_FP32) return launch_moments_t<__half, float, float>(qin, p, eps, vx, vy, partials, bad, s);
     return launch_moments_t<__half, float, double>(qin, p, eps, vx, vy, partials, bad, s);
 }
 }  // namespace rlbk

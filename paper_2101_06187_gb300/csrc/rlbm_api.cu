@@ -7,17 +7,20 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "rlbm_internal.h"
 
 namespace rlbk {
 
-cudaError_t launch_step_f64(int kernel, int landau, bool forced, const void *qin, void *qout, const void *F,
-                            const StepParams &p, cudaStream_t s);
-cudaError_t launch_step_f32(int kernel, int landau, bool forced, const void *qin, void *qout, const void *F,
-                            const StepParams &p, cudaStream_t s);
-cudaError_t launch_step_h16(int dtype, int kernel, int landau, bool forced, const void *qin, void *qout,
+cudaError_t launch_step_f64(const LaunchCfg &cfg, int landau, bool forced, const void *qin, void *qout,
+                            const void *F, const StepParams &p, cudaStream_t s);
+cudaError_t launch_step_f32(const LaunchCfg &cfg, int landau, bool forced, const void *qin, void *qout,
+                            const void *F, const StepParams &p, cudaStream_t s);
+cudaError_t launch_step_h16(int dtype, const LaunchCfg &cfg, int landau, bool forced, const void *qin, void *qout,
                             const void *F, const StepParams &p, cudaStream_t s);
 cudaError_t launch_moments_f64(int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                                double *vy, double *partials, int *bad, cudaStream_t s);
@@ -26,12 +29,12 @@ cudaError_t launch_moments_f32(int landau, const void *qin, const StepParams &p,
 cudaError_t launch_moments_h16(int dtype, int landau, const void *qin, const StepParams &p, double *eps,
                                double *vx, double *vy, double *partials, int *bad, cudaStream_t s);
 
-cudaError_t launch_step(int dtype, int landau, int kernel, bool forced, const void *qin, void *qout, const void *F,
-                        const StepParams &p, cudaStream_t s) {
+cudaError_t launch_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
+                        const void *F, const StepParams &p, cudaStream_t s) {
     switch (dtype) {
-    case RLBM_F64: return launch_step_f64(kernel, landau, forced, qin, qout, F, p, s);
-    case RLBM_F32: return launch_step_f32(kernel, landau, forced, qin, qout, F, p, s);
-    default: return launch_step_h16(dtype, kernel, landau, forced, qin, qout, F, p, s);
+    case RLBM_F64: return launch_step_f64(cfg, landau, forced, qin, qout, F, p, s);
+    case RLBM_F32: return launch_step_f32(cfg, landau, forced, qin, qout, F, p, s);
+    default: return launch_step_h16(dtype, cfg, landau, forced, qin, qout, F, p, s);
     }
 }
 
@@ -148,7 +151,7 @@ static rlbm_status ensure_force(rlbm_t *h) {
 static rlbm_status launch_steps(rlbm_t *h, int n) {
     const StepParams p = params_of(h);
     for (int i = 0; i < n; ++i) {
-        CUDA_TRY(h, launch_step(h->opts.dtype, h->opts.landau, h->kernel, h->forced, h->q[h->cur], h->q[h->cur ^ 1],
+        CUDA_TRY(h, launch_step(h->opts.dtype, h->opts.landau, h->cfg, h->forced, h->q[h->cur], h->q[h->cur ^ 1],
                                 h->F, p, h->stream));
         h->cur ^= 1;
     }
@@ -186,6 +189,25 @@ static rlbm_status run_chunk(rlbm_t *h, int n) {
     return RLBM_OK;
 }
 
+// Launch configurations tried by rlbm_autotune, and the winners per
+// (nx, ny, dtype, landau, forced), shared by all handles of the process.
+static const LaunchCfg kCandidates[] = {
+    {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
+    {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 64, 2},
+    {RLBM_KERNEL_GATHER, 128, 1}, {RLBM_KERNEL_GATHER, 32, 2},
+};
+static std::map<std::tuple<int, int, int, int, int>, LaunchCfg> g_tuned;
+static std::mutex g_tuned_mu;
+
+static std::tuple<int, int, int, int, int> tune_key(const rlbm_t *h) {
+    return std::make_tuple(h->nx, h->ny, h->opts.dtype, h->opts.landau, h->forced ? 1 : 0);
+}
+
+static void drop_graphs(rlbm_t *h) {
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
 extern "C" {
 
 const char *rlbm_status_string(rlbm_status s) {
@@ -205,7 +227,7 @@ void rlbm_opts_default(rlbm_opts *o) {
     if (!o) return;
     memset(o, 0, sizeof *o);
     o->dtype = RLBM_F32;
-    o->landau = RLBM_LANDAU_FP64;
+    o->landau = RLBM_LANDAU_FP32;
     o->kernel = RLBM_KERNEL_AUTO;
     o->use_graphs = 1;
     o->eps0 = 1.0;
@@ -219,8 +241,7 @@ void rlbm_destroy(rlbm_t *h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
-    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
-    h->graphs.clear();
+    drop_graphs(h);
     dev_free(h, h->q[0], q_bytes(h));
     dev_free(h, h->q[1], q_bytes(h));
     if (h->F) dev_free(h, h->F, F_bytes(h));
@@ -276,7 +297,6 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     h->opts = o;
     h->forcing = fz;
     h->forced = forced;
-    h->kernel = RLBM_KERNEL_GATHER;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {
             delete h;
@@ -288,6 +308,16 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         return RLBM_ERR_CUDA;
     }
     h->stream = static_cast<cudaStream_t>(o.stream);
+    if (o.kernel == RLBM_KERNEL_AUTO) {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        auto it = g_tuned.find(tune_key(h));
+        if (it != g_tuned.end()) {
+            h->cfg = it->second;
+            h->tuned = true;
+        }
+    } else {
+        h->cfg.kernel = o.kernel;
+    }
 
     std::vector<Mode> modes;
     if (forced) h->nmodes = enumerate_modes(fz.kmin, fz.kmax, &modes);
@@ -513,7 +543,9 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
     info->pitch = h->pitch;
     info->nclasses = NC;
     info->dtype = h->opts.dtype;
-    info->kernel = h->kernel;
+    info->kernel = h->cfg.kernel;
+    info->block_x = h->cfg.bx;
+    info->block_y = h->cfg.by;
     info->nmodes = h->forced ? h->nmodes : 0;
     info->step = h->step;
     info->tau = h->tau;
@@ -522,6 +554,54 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
     info->bytes_per_node = (size_t)2 * NC * storage_bytes(h->opts.dtype) + (h->forced ? 2 * compute_bytes(h->opts.dtype) : 0);
     info->device_bytes = h->device_bytes;
     info->populations = h->q[h->cur];
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x, int *block_y) {
+    CHECK_HANDLE(h);
+    if (reps < 1) reps = 20;
+    rlbm_status st = ensure_force(h);
+    if (st != RLBM_OK) return st;
+    const StepParams p = params_of(h);
+    cudaEvent_t a = nullptr, b = nullptr;
+    CUDA_TRY(h, cudaEventCreate(&a));
+    CUDA_TRY(h, cudaEventCreate(&b));
+    float best_ms = 1e30f;
+    LaunchCfg best = h->cfg;
+    for (const LaunchCfg &c : kCandidates) {
+        if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
+        // the trial steps read the current state and overwrite only the spare buffer
+        bool ok = true;
+        for (int i = 0; i < 2 + reps && ok; ++i) {
+            if (i == 2) ok = cudaEventRecord(a, h->stream) == cudaSuccess;
+            ok = ok && launch_step(h->opts.dtype, h->opts.landau, c, h->forced, h->q[h->cur], h->q[h->cur ^ 1], h->F,
+                                   p, h->stream) == cudaSuccess;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            continue;
+        }
+        CUDA_TRY(h, cudaEventRecord(b, h->stream));
+        CUDA_TRY(h, cudaEventSynchronize(b));
+        float ms = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->cfg = best;
+    h->tuned = true;
+    drop_graphs(h);
+    {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        g_tuned[tune_key(h)] = best;
+    }
+    if (chosen_kernel) *chosen_kernel = best.kernel;
+    if (block_x) *block_x = best.bx;
+    if (block_y) *block_y = best.by;
     return RLBM_OK;
 }
 

@@ -28,8 +28,14 @@ struct Launch {
 };
 
 // Step launchers (defined in the per-form translation units).
-cudaError_t launch_step(int dtype, int landau, int kernel, bool forced, const void *qin, void *qout, const void *F,
-                        const StepParams &p, cudaStream_t s);
+// Launch shape of the fused step (kernel variant and thread-block shape).
+struct LaunchCfg {
+    int kernel = RLBM_KERNEL_GATHER;
+    int bx = 32, by = 8;
+};
+
+cudaError_t launch_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
+                        const void *F, const StepParams &p, cudaStream_t s);
 cudaError_t launch_moments(int dtype, int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                            double *vy, double *partials, int *bad, cudaStream_t s);
 int moments_blocks(const StepParams &p);
@@ -64,8 +70,8 @@ struct rlbm {
     rlbm_forcing forcing{};
     bool forced = false;
     int nmodes = 0;
-    int kernel = 0;
-    bool own_stream = false;
+    rlbk::LaunchCfg cfg;
+    bool tuned = false;
     cudaStream_t stream = nullptr;
     int device = 0;
 

@@ -88,7 +88,7 @@ def test_null_handle_calls_are_rejected(lib):
 def test_opts_defaults(lib):
     import paper_2101_06187_gb300 as rl
     o = rl.rlbm_opts_default()
-    assert o.dtype == rl.DTYPES["f32"] and o.landau == 0 and o.use_graphs == 1 and o.eps0 == 1.0 and o.device == -1
+    assert o.dtype == rl.DTYPES["f32"] and o.landau == rl.LANDAU["fp32"] and o.use_graphs == 1 and o.eps0 == 1.0 and o.device == -1
 
 
 def test_binding_fails_loudly_without_the_library(tmp_path):

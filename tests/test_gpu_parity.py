@@ -67,7 +67,9 @@ FORCING_SMALL = dict(kmin=2, kmax=4, amp=2e-4, seed=123456789, redraw_period=7)
 def test_forced_run_matches_oracle(dtype, landau, shape):
     """Ragged lattices spanning several 32x8 tiles, and the 4x4 minimum."""
     nx, ny = shape
-    forcing = FORCING_SMALL if min(nx, ny) > 8 else dict(kmin=1, kmax=1, amp=2e-4, seed=5, redraw_period=3)
+    # the 4x4 lattice damps its only modes fast; a stronger force keeps |v| ~ 1e-2 there, so the
+    # normwise velocity error measures the arithmetic rather than the FP64 floor eps_mach * E / |v|
+    forcing = FORCING_SMALL if min(nx, ny) > 8 else dict(kmin=1, kmax=1, amp=2e-3, seed=5, redraw_period=3)
     fields = workloads.random_smooth(nx, ny, seed=nx * 1000 + ny, deps=0.05, vmax=0.05)
     lat, f, ref, got = run_pair(nx, ny, 0.7, 100, dtype, fields, forcing, landau)
     err_e, err_v = rel_errors(ref, got)
@@ -136,6 +138,26 @@ def test_graph_and_direct_launches_agree_bitwise():
         lat.init_fields(*fields)
         for n in (1, 6, 13, 2, 41):  # odd/even chunks across epoch boundaries
             lat.step(n)
+        out.append(lat.populations())
+        lat.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_autotune_keeps_state_and_results():
+    nx, ny = 96, 64
+    fields = workloads.random_smooth(nx, ny, seed=12)
+    out = []
+    for tune in (False, True):
+        lat = rl.Lattice(nx, ny, 0.7, dtype="f32", forcing=FORCING_SMALL, kernel="gather")
+        lat.init_fields(*fields)
+        lat.step(3)
+        if tune:
+            p0 = lat.populations()
+            k, bx, by = lat.autotune(3)
+            assert bx * by <= 256 and k == rl.KERNELS["gather"]
+            np.testing.assert_array_equal(lat.populations(), p0)
+            assert (lat.info()["block_x"], lat.info()["block_y"]) == (bx, by)
+        lat.step(20)
         out.append(lat.populations())
         lat.close()
     np.testing.assert_array_equal(out[0], out[1])
