@@ -78,9 +78,12 @@ typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16 = 2, RLBM_F16 = 3 } rlbm_dt
  * delta = E - eps, so FP32 keeps full FP32 accuracy of eps and v. */
 typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
 
-/* Kernel variant of the fused step (RLBM_KERNEL_AUTO picks the fastest
- * available for the form and lattice). */
-typedef enum { RLBM_KERNEL_AUTO = 0, RLBM_KERNEL_GATHER = 1, RLBM_KERNEL_STAGED = 2 } rlbm_kernel;
+/* Kernel variant of the fused step.  GATHER: one node per thread.
+ * GATHER_VEC: a run of 4 nodes (2 for F64) along x per thread with 128-bit
+ * (64-bit for 16-bit storage) loads and stores; needs nx divisible by that
+ * run.  AUTO: the autotuned choice if one is cached for this lattice, else
+ * GATHER_VEC when nx allows it, else GATHER. */
+typedef enum { RLBM_KERNEL_AUTO = 0, RLBM_KERNEL_GATHER = 1, RLBM_KERNEL_GATHER_VEC = 2 } rlbm_kernel;
 
 /* Stirring force (Sec. 5).  Modes are the integer wavevectors k with
  * kmin <= |k| <= kmax (k = 0 excluded), one per Hermitian pair (ky > 0, or

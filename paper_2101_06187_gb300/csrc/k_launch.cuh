@@ -3,6 +3,7 @@
 #pragma once
 
 #include "k_step_gather.cuh"
+#include "k_step_vec.cuh"
 #include "rlbm_internal.h"
 
 namespace rlbk {
@@ -18,6 +19,17 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
     const TC *f = static_cast<const TC *>(F);
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
     const dim3 block(cfg.bx, cfg.by, 1);
+    if (cfg.kernel == RLBM_KERNEL_GATHER_VEC) {
+        constexpr int V = VecOf<TS>::V;
+        if (p.nx % V != 0 || p.pitch % V != 0) return cudaErrorInvalidValue;
+        const int runs = p.nx / V;
+        const dim3 grid((runs + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
+        if (forced)
+            k_step_vec<TS, TC, TL, true><<<grid, block, 0, s>>>(in, out, f, p);
+        else
+            k_step_vec<TS, TC, TL, false><<<grid, block, 0, s>>>(in, out, f, p);
+        return cudaGetLastError();
+    }
     const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
     if (forced)
         k_step_gather<TS, TC, TL, true><<<grid, block, 0, s>>>(in, out, f, p);

@@ -192,9 +192,11 @@ static rlbm_status run_chunk(rlbm_t *h, int n) {
 // Launch configurations tried by rlbm_autotune, and the winners per
 // (nx, ny, dtype, landau, forced), shared by all handles of the process.
 static const LaunchCfg kCandidates[] = {
+    {RLBM_KERNEL_GATHER_VEC, 32, 4}, {RLBM_KERNEL_GATHER_VEC, 64, 2}, {RLBM_KERNEL_GATHER_VEC, 128, 1},
+    {RLBM_KERNEL_GATHER_VEC, 32, 8}, {RLBM_KERNEL_GATHER_VEC, 64, 4}, {RLBM_KERNEL_GATHER_VEC, 128, 2},
+    {RLBM_KERNEL_GATHER_VEC, 256, 1}, {RLBM_KERNEL_GATHER_VEC, 32, 2}, {RLBM_KERNEL_GATHER_VEC, 64, 1},
     {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
-    {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 64, 2},
-    {RLBM_KERNEL_GATHER, 128, 1}, {RLBM_KERNEL_GATHER, 32, 2},
+    {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
 };
 static std::map<std::tuple<int, int, int, int, int>, LaunchCfg> g_tuned;
 static std::mutex g_tuned_mu;
@@ -269,7 +271,7 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (opts) o = *opts;
     if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
     if (o.landau != RLBM_LANDAU_FP64 && o.landau != RLBM_LANDAU_FP32) return RLBM_ERR_ARG;
-    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_STAGED) return RLBM_ERR_ARG;
+    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_GATHER_VEC) return RLBM_ERR_ARG;
     if (o.eps0 == 0.0) o.eps0 = 1.0;
     if (!(o.eps0 > 0.0) || !isfinite(o.eps0)) return RLBM_ERR_ARG;
     if (o.scale == 0.0) o.scale = (o.dtype == RLBM_BF16 || o.dtype == RLBM_F16) ? 1.0 / 64.0 : 1.0;
@@ -317,6 +319,12 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         }
     } else {
         h->cfg.kernel = o.kernel;
+    }
+    if (!h->tuned && o.kernel == RLBM_KERNEL_AUTO) {
+        const int run = (o.dtype == RLBM_F64) ? 2 : 4;
+        h->cfg.kernel = (nx % run == 0) ? RLBM_KERNEL_GATHER_VEC : RLBM_KERNEL_GATHER;
+        h->cfg.bx = (h->cfg.kernel == RLBM_KERNEL_GATHER_VEC) ? 64 : 128;
+        h->cfg.by = (h->cfg.kernel == RLBM_KERNEL_GATHER_VEC) ? 2 : 1;
     }
 
     std::vector<Mode> modes;

@@ -16,9 +16,12 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <type_traits>
 
 namespace rlbk {
+
+#define RLBM_HD __host__ __device__
 
 constexpr int NC = 17;
 
@@ -58,7 +61,7 @@ __host__ __device__ constexpr double cls_tx(int c) { return -cls_cx(c) - (double
 __host__ __device__ constexpr double cls_ty(int c) { return -cls_cy(c) - (double)cls_oy(c); }
 
 template <int I, int N, class F>
-__device__ __forceinline__ void static_for(F &&f) {
+RLBM_HD inline void static_for(F &&f) {
     if constexpr (I < N) {
         f(std::integral_constant<int, I>{});
         static_for<I + 1, N>(f);
@@ -108,25 +111,41 @@ struct NodeMoments {
     TC dE, Mx, My, dSxx, dSxy, dSyy, Qxxx, Qxxy, Qxyy, Qyyy;
 };
 
+// The 16 moving classes form 8 opposite pairs (c, -c) of equal weight.
+RLBM_HD constexpr int pair_pos(int k) { return k == 0 ? 1 : k == 1 ? 3 : k == 2 ? 5 : k == 3 ? 7 : k == 4 ? 9 : k == 5 ? 10 : k == 6 ? 13 : 14; }
+RLBM_HD constexpr int pair_neg(int k) { return k == 0 ? 2 : k == 1 ? 4 : k == 2 ? 6 : k == 3 ? 8 : k == 4 ? 12 : k == 5 ? 11 : k == 6 ? 16 : 15; }
+constexpr int NPAIR = 8;
+
+// Moments from pair sums s = q_c + q_-c (even moments E, S) and differences
+// d = q_c - q_-c (odd moments M, Q).
 template <typename TC>
-__device__ __forceinline__ NodeMoments<TC> node_moments(const TC (&q)[NC], TC s) {
-    NodeMoments<TC> m;
-    TC e = 0, mx = 0, my = 0, sxx = 0, sxy = 0, syy = 0, qxxx = 0, qxxy = 0, qxyy = 0, qyyy = 0;
-    static_for<0, NC>([&](auto C) {
-        constexpr int c = decltype(C)::value;
+RLBM_HD inline NodeMoments<TC> node_moments(const TC (&q)[NC], TC s) {
+    TC e = (TC)cls_w(0) * q[0];
+    TC mx = 0, my = 0, sxx = 0, sxy = 0, syy = 0, qxxx = 0, qxxy = 0, qxyy = 0, qyyy = 0;
+    static_for<0, NPAIR>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        constexpr int c = pair_pos(k), cn = pair_neg(k);
         constexpr double w = cls_w(c), cx = cls_cx(c), cy = cls_cy(c);
-        const TC wq = (TC)w * q[c];
-        e += wq;
-        if constexpr (cx != 0.0) mx += (TC)cx * wq;
-        if constexpr (cy != 0.0) my += (TC)cy * wq;
-        if constexpr (cx != 0.0) sxx += (TC)(cx * cx) * wq;
-        if constexpr (cx != 0.0 && cy != 0.0) sxy += (TC)(cx * cy) * wq;
-        if constexpr (cy != 0.0) syy += (TC)(cy * cy) * wq;
-        if constexpr (cx != 0.0) qxxx += (TC)(cx * cx * cx) * wq;
-        if constexpr (cx != 0.0 && cy != 0.0) qxxy += (TC)(cx * cx * cy) * wq;
-        if constexpr (cx != 0.0 && cy != 0.0) qxyy += (TC)(cx * cy * cy) * wq;
-        if constexpr (cy != 0.0) qyyy += (TC)(cy * cy * cy) * wq;
+        const TC sp = q[c] + q[cn];
+        const TC dp = q[c] - q[cn];
+        e += (TC)w * sp;
+        if constexpr (cx != 0.0) {
+            mx += (TC)(w * cx) * dp;
+            sxx += (TC)(w * cx * cx) * sp;
+            qxxx += (TC)(w * cx * cx * cx) * dp;
+        }
+        if constexpr (cy != 0.0) {
+            my += (TC)(w * cy) * dp;
+            syy += (TC)(w * cy * cy) * sp;
+            qyyy += (TC)(w * cy * cy * cy) * dp;
+        }
+        if constexpr (cx != 0.0 && cy != 0.0) {
+            sxy += (TC)(w * cx * cy) * sp;
+            qxxy += (TC)(w * cx * cx * cy) * dp;
+            qxyy += (TC)(w * cx * cy * cy) * dp;
+        }
     });
+    NodeMoments<TC> m;
     m.dE = s * e;
     m.Mx = s * mx;
     m.My = s * my;
@@ -140,6 +159,27 @@ __device__ __forceinline__ NodeMoments<TC> node_moments(const TC (&q)[NC], TC s)
     return m;
 }
 
+template <typename T>
+RLBM_HD inline T absval(T x) { return x < (T)0 ? -x : x; }
+
+template <typename T>
+RLBM_HD inline T recip(T x) {
+#ifdef __CUDA_ARCH__
+    if constexpr (std::is_same<T, float>::value) return __frcp_rn(x);
+#endif
+    return (T)1 / x;
+}
+
+template <typename T>
+RLBM_HD inline T rsqrt_(T x) {
+#ifdef __CUDA_ARCH__
+    if constexpr (std::is_same<T, float>::value) return rsqrtf(x);
+    else return rsqrt(x);
+#else
+    return (T)1 / std::sqrt(x);
+#endif
+}
+
 // Landau-Lifshitz frame (the eigenvalue problem closing Sec. 3.2):
 // T^{mu nu} u_nu = -eps u^mu.  With v = u/u^0 and delta = E - eps this is
 //   (S + eps I) v = M,  delta = M . v.
@@ -148,48 +188,54 @@ __device__ __forceinline__ NodeMoments<TC> node_moments(const TC (&q)[NC], TC s)
 //   g(delta) = delta - M . (aI + dS)^{-1} M,   g'(delta) = 1 - |v|^2,
 // from delta = 0.  g is increasing and concave (g'' = -2 v.(aI + dS)^{-1} v),
 // and g(0) <= 0, so Newton from delta = 0 rises monotonically onto the
-// physical root (eps > 0, |v| < 1).
+// physical root (eps > 0, |v| < 1).  Three unrolled steps reach FP32
+// round-off for |v| <~ 0.1; further steps run only where needed.
 template <typename TL>
 struct Frame {
     TL ddelta_eps;  // eps - eps0 = dE - delta
     TL eps;         // eps0 + dE - delta
     TL vx, vy;      // 3-velocity
     TL v2, g2;      // |v|^2, gamma^2 = 1/(1 - |v|^2)
+    TL gamma;
 };
 
 template <typename TL>
-__device__ __forceinline__ Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL dSxy, TL dSyy) {
+RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL dSxy, TL dSyy) {
     const TL a0 = (TL)(4.0 / 3.0) * eps0 + dE;
     TL delta = 0, vx = 0, vy = 0;
-    const TL tol = std::is_same<TL, double>::value ? (TL)4e-16 : (TL)2e-7;
-    const int maxit = std::is_same<TL, double>::value ? 24 : 12;
-    for (int it = 0; it < maxit; ++it) {
-        const TL a = a0 - delta;
+    constexpr bool dbl = std::is_same<TL, double>::value;
+    const TL tol = dbl ? (TL)4e-16 : (TL)1e-7;
+    auto velocity = [&](TL d) {
+        const TL a = a0 - d;
         const TL axx = a + dSxx, ayy = a + dSyy;
-        const TL inv_det = (TL)1 / (axx * ayy - dSxy * dSxy);
+        const TL inv_det = recip<TL>(axx * ayy - dSxy * dSxy);
         vx = (ayy * Mx - dSxy * My) * inv_det;
         vy = (axx * My - dSxy * Mx) * inv_det;
+    };
+    auto newton = [&]() -> TL {
+        velocity(delta);
         const TL g = delta - (Mx * vx + My * vy);
         const TL gp = (TL)1 - (vx * vx + vy * vy);
-        const TL step = g / gp;
+        const TL step = g * recip<TL>(gp);
         delta -= step;
-        if (!(fabs(step) > tol * fabs(delta))) break;  // also exits on NaN
+        return step;
+    };
+    newton();
+    newton();
+    TL step = newton();
+    for (int it = 3; it < (dbl ? 24 : 12); ++it) {
+        if (!(absval(step) > tol * absval(delta))) break;  // also exits on NaN
+        step = newton();
     }
-    // velocity at the converged root
-    {
-        const TL a = a0 - delta;
-        const TL axx = a + dSxx, ayy = a + dSyy;
-        const TL inv_det = (TL)1 / (axx * ayy - dSxy * dSxy);
-        vx = (ayy * Mx - dSxy * My) * inv_det;
-        vy = (axx * My - dSxy * Mx) * inv_det;
-    }
+    velocity(delta);
     Frame<TL> fr;
     fr.ddelta_eps = dE - delta;
     fr.eps = eps0 + fr.ddelta_eps;
     fr.vx = vx;
     fr.vy = vy;
     fr.v2 = vx * vx + vy * vy;
-    fr.g2 = (TL)1 / ((TL)1 - fr.v2);
+    fr.gamma = rsqrt_<TL>((TL)1 - fr.v2);
+    fr.g2 = fr.gamma * fr.gamma;
     return fr;
 }
 
@@ -200,71 +246,84 @@ __device__ __forceinline__ Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, 
 // stressEnergyT, P = eps/3, App. A norms): f_eq,i = w_i [-(3/2) T00 + 3 v_i.M_eq
 // + (15/2) v_i S_eq v_i]; for |v_i| = 1 and xi = v_i . v this is
 //   f_eq,c = W_c eps [3 - 2 gamma^2 + gamma^2 (4 xi + 10 xi^2)],
-// so q_eq,c = [eps - eps0 + eps gamma^2 (4 xi + 10 xi^2 - 2 |v|^2)] / s.
+// so q_eq,c = P0 + P1 xi + P2 xi^2 with P0 = [eps - eps0 - 2 eps gamma^2 |v|^2]/s,
+// P1 = 4 eps gamma^2 / s, P2 = 10 eps gamma^2 / s.
 // Relaxation (Eq. boltzmanneq_rel, Anderson-Witting): rate
-// (u^0 - v_c . u)/tau = gamma (1 - xi)/tau.
+// (u^0 - v_c . u)/tau = om (1 - xi), om = gamma/tau.
 // Driving term (Eq. forceTerm, App. B), F^mu = (0, F_x, F_y, 0), prefactor
 // -6 so that sum G = F.M and sum G v = F E:
 //   G_c = -6 W_c [ F.M/4 - (F.c) E/2 + (5/4) F_a c_b c_c Q^abc - (5/2)(F.c)(c.M) ]
-// with the moments of the post-stream populations.
+// with the moments of the post-stream populations, and Q^azz = M^a - Q^axx - Q^ayy,
+// v_z^2 = 1 - c_x^2 - c_y^2.
+//
+// Per class the update q' = q (1 - om + om xi) + om (1 - xi) q_eq + G/(W s)
+// is a cubic polynomial in (c_x, c_y); splitting it into the part even in c
+//   K0 + Kxx c_x^2 + Kxy c_x c_y + Kyy c_y^2
+// and the odd part  xi [om (P1 - P0) - om P2 xi^2] + G1 (F.c)
+// lets each opposite pair (c, -c) share one evaluation.
 template <typename TC, typename TL, bool FORCED>
-__device__ __forceinline__ Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
+RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
     const TC s = (TC)p.scale;
     const NodeMoments<TC> m = node_moments<TC>(q, s);
     const Frame<TL> fr = landau_solve<TL>((TL)p.eps0, (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
                                           (TL)m.dSyy);
     const TC inv_s = (TC)(1.0 / p.scale);
     const TL eg2 = fr.eps * fr.g2;
-    const TC P0 = (TC)((fr.ddelta_eps - (TL)2 * eg2 * fr.v2)) * inv_s;
+    const TC P0 = (TC)(fr.ddelta_eps - (TL)2 * eg2 * fr.v2) * inv_s;
     const TC P1 = (TC)((TL)4 * eg2) * inv_s;
     const TC P2 = (TC)((TL)10 * eg2) * inv_s;
     const TC vx = (TC)fr.vx, vy = (TC)fr.vy;
-    const TC om = (TC)(sqrt(fr.g2) * (TL)p.inv_tau);  // gamma / tau
+    const TC om = (TC)(fr.gamma * (TL)p.inv_tau);
 
-    TC G0 = 0, G1 = 0, G3 = 0, Pxx = 0, Pxy = 0, Pyy = 0, Pzz = 0;
+    // even part K0 + Kxx cx^2 + Kxy cx cy + Kyy cy^2, odd part coefficients
+    const TC e2 = om * (P2 - P1);
+    TC K0 = om * P0, Kxx = e2 * vx * vx, Kxy = (TC)2 * e2 * vx * vy, Kyy = e2 * vy * vy;
+    const TC o1 = om * (P1 - P0), o3 = om * P2;
+    TC G1 = 0;
     if constexpr (FORCED) {
         const TC E = (TC)p.eps0 + m.dE;
-        const TC FM = Fx * m.Mx + Fy * m.My;
         const TC c6 = (TC)(-6.0) * inv_s;
-        G0 = c6 * (TC)0.25 * FM;
+        const TC G0 = c6 * (TC)0.25 * (Fx * m.Mx + Fy * m.My);
         G1 = c6 * (TC)(-0.5) * E;
-        G3 = c6 * (TC)(-2.5);
+        const TC G3 = c6 * (TC)(-2.5);
         const TC c54 = c6 * (TC)1.25;
         const TC Qxzz = m.Mx - m.Qxxx - m.Qxyy;
         const TC Qyzz = m.My - m.Qxxy - m.Qyyy;
-        Pxx = c54 * (Fx * m.Qxxx + Fy * m.Qxxy);
-        Pxy = c54 * (Fx * m.Qxxy + Fy * m.Qxyy);
-        Pyy = c54 * (Fx * m.Qxyy + Fy * m.Qyyy);
-        Pzz = c54 * (Fx * Qxzz + Fy * Qyzz);
+        const TC Pxx = c54 * (Fx * m.Qxxx + Fy * m.Qxxy);
+        const TC Pxy = c54 * (Fx * m.Qxxy + Fy * m.Qxyy);
+        const TC Pyy = c54 * (Fx * m.Qxyy + Fy * m.Qyyy);
+        const TC Pzz = c54 * (Fx * Qxzz + Fy * Qyzz);
+        K0 += G0 + Pzz;
+        Kxx += G3 * Fx * m.Mx + Pxx - Pzz;
+        Kxy += G3 * (Fx * m.My + Fy * m.Mx) + (TC)2 * Pxy;
+        Kyy += G3 * Fy * m.My + Pyy - Pzz;
     }
-
-    static_for<0, NC>([&](auto C) {
-        constexpr int c = decltype(C)::value;
-        constexpr double cx = cls_cx(c), cy = cls_cy(c), vz2 = cls_vz2(c);
+    const TC a0 = (TC)1 - om;
+    q[0] = q[0] * a0 + K0;
+    static_for<0, NPAIR>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        constexpr int c = pair_pos(k), cn = pair_neg(k);
+        constexpr double cx = cls_cx(c), cy = cls_cy(c);
         TC xi = 0;
-        if constexpr (cx != 0.0) xi += (TC)cx * vx;
-        if constexpr (cy != 0.0) xi += (TC)cy * vy;
-        const TC qeq = P0 + xi * (P1 + P2 * xi);
-        const TC omc = om - om * xi;
-        TC qn = q[c] - omc * (q[c] - qeq);
-        if constexpr (FORCED) {
-            TC Fc = 0, cM = 0;
-            if constexpr (cx != 0.0) {
-                Fc += (TC)cx * Fx;
-                cM += (TC)cx * m.Mx;
-            }
-            if constexpr (cy != 0.0) {
-                Fc += (TC)cy * Fy;
-                cM += (TC)cy * m.My;
-            }
-            TC g = G0 + Fc * (G1 + G3 * cM);
-            if constexpr (cx != 0.0) g += (TC)(cx * cx) * Pxx;
-            if constexpr (cx != 0.0 && cy != 0.0) g += (TC)(2.0 * cx * cy) * Pxy;
-            if constexpr (cy != 0.0) g += (TC)(cy * cy) * Pyy;
-            if constexpr (vz2 != 0.0) g += (TC)vz2 * Pzz;
-            qn += g;
+        [[maybe_unused]] TC Fc = 0;
+        TC even = K0;
+        if constexpr (cx != 0.0) {
+            xi += (TC)cx * vx;
+            even += (TC)(cx * cx) * Kxx;
+            if constexpr (FORCED) Fc += (TC)cx * Fx;
         }
-        q[c] = qn;
+        if constexpr (cy != 0.0) {
+            xi += (TC)cy * vy;
+            even += (TC)(cy * cy) * Kyy;
+            if constexpr (FORCED) Fc += (TC)cy * Fy;
+        }
+        if constexpr (cx != 0.0 && cy != 0.0) even += (TC)(cx * cy) * Kxy;
+        TC odd = xi * (o1 - o3 * xi * xi);
+        if constexpr (FORCED) odd += G1 * Fc;
+        const TC oxi = om * xi;
+        const TC qp = q[c], qn = q[cn];
+        q[c] = qp * (a0 + oxi) + (even + odd);
+        q[cn] = qn * (a0 - oxi) + (even - odd);
     });
     return fr;
 }

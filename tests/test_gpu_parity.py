@@ -63,15 +63,18 @@ FORCING_SMALL = dict(kmin=2, kmax=4, amp=2e-4, seed=123456789, redraw_period=7)
 
 
 @pytest.mark.parametrize("dtype,landau", [("f64", "fp64"), ("f32", "fp64"), ("f32", "fp32")])
-@pytest.mark.parametrize("shape", [(37, 29), (64, 48), (4, 4)])
-def test_forced_run_matches_oracle(dtype, landau, shape):
-    """Ragged lattices spanning several 32x8 tiles, and the 4x4 minimum."""
+@pytest.mark.parametrize("shape,kernel", [((37, 29), "gather"), ((64, 48), "gather"), ((4, 4), "gather"),
+                                          ((64, 48), "vec"), ((4, 4), "vec"), ((136, 40), "vec")])
+def test_forced_run_matches_oracle(dtype, landau, shape, kernel):
+    """Ragged lattices spanning several thread blocks, and the 4x4 minimum,
+    for both kernel variants (the vector kernel needs nx divisible by its run)."""
     nx, ny = shape
     # the 4x4 lattice damps its only modes fast; a stronger force keeps |v| ~ 1e-2 there, so the
     # normwise velocity error measures the arithmetic rather than the FP64 floor eps_mach * E / |v|
     forcing = FORCING_SMALL if min(nx, ny) > 8 else dict(kmin=1, kmax=1, amp=2e-3, seed=5, redraw_period=3)
     fields = workloads.random_smooth(nx, ny, seed=nx * 1000 + ny, deps=0.05, vmax=0.05)
-    lat, f, ref, got = run_pair(nx, ny, 0.7, 100, dtype, fields, forcing, landau)
+    lat, f, ref, got = run_pair(nx, ny, 0.7, 100, dtype, fields, forcing, landau, kernel=kernel)
+    assert lat.info()["kernel"] == rl.KERNELS[kernel]
     err_e, err_v = rel_errors(ref, got)
     assert err_e < TOL[dtype] and err_v < TOL[dtype], (err_e, err_v)
     if dtype == "f64":
@@ -143,6 +146,29 @@ def test_graph_and_direct_launches_agree_bitwise():
     np.testing.assert_array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+def test_vector_and_scalar_kernels_agree(dtype):
+    nx, ny = 128, 72
+    fields = workloads.random_smooth(nx, ny, seed=13, vmax=0.05)
+    out = []
+    for kernel in ("gather", "vec"):
+        lat = rl.Lattice(nx, ny, 0.6, dtype=dtype, forcing=FORCING_SMALL, kernel=kernel)
+        lat.init_fields(*fields)
+        lat.step(30)
+        out.append(lat.populations())
+        lat.close()
+    tol = {"f64": 1e-14, "f32": 1e-6, "bf16": 2e-2, "f16": 2e-3}[dtype]
+    _, w = oracle.stencil()
+    assert np.max(np.abs(out[0] - out[1])) <= tol * np.max(np.abs(out[0]))
+
+
+def test_vector_kernel_rejects_unaligned_width():
+    lat = rl.Lattice(37, 16, 0.7, dtype="f32", kernel="vec")
+    with pytest.raises(rl.RLBMError):
+        lat.step(1)
+    lat.close()
+
+
 def test_autotune_keeps_state_and_results():
     nx, ny = 96, 64
     fields = workloads.random_smooth(nx, ny, seed=12)
@@ -154,7 +180,7 @@ def test_autotune_keeps_state_and_results():
         if tune:
             p0 = lat.populations()
             k, bx, by = lat.autotune(3)
-            assert bx * by <= 256 and k == rl.KERNELS["gather"]
+            assert bx * by <= 256 and k == rl.KERNELS["gather"]  # kernel fixed by the caller
             np.testing.assert_array_equal(lat.populations(), p0)
             assert (lat.info()["block_x"], lat.info()["block_y"]) == (bx, by)
         lat.step(20)
