@@ -72,6 +72,9 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     o = rl.rlbm_opts_default()
     o.scale = -1.0
     assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
+    o = rl.rlbm_opts_default()
+    o.kernel = rl.KERNELS["vec"]
+    assert create(37, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # vector kernel needs nx % 4 == 0
     assert out.value is None
     assert lib.rlbm_create(16, 16, 0, 0.8, None, None, None) == rl.RLBM_ERR_ARG
 

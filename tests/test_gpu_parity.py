@@ -162,13 +162,6 @@ def test_vector_and_scalar_kernels_agree(dtype):
     assert np.max(np.abs(out[0] - out[1])) <= tol * np.max(np.abs(out[0]))
 
 
-def test_vector_kernel_rejects_unaligned_width():
-    lat = rl.Lattice(37, 16, 0.7, dtype="f32", kernel="vec")
-    with pytest.raises(rl.RLBMError):
-        lat.step(1)
-    lat.close()
-
-
 def test_autotune_keeps_state_and_results():
     nx, ny = 96, 64
     fields = workloads.random_smooth(nx, ny, seed=12)
