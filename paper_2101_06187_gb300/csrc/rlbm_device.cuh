@@ -170,16 +170,6 @@ RLBM_HD inline T recip(T x) {
     return (T)1 / x;
 }
 
-template <typename T>
-RLBM_HD inline T rsqrt_(T x) {
-#ifdef __CUDA_ARCH__
-    if constexpr (std::is_same<T, float>::value) return rsqrtf(x);
-    else return rsqrt(x);
-#else
-    return (T)1 / std::sqrt(x);
-#endif
-}
-
 // Landau-Lifshitz frame (the eigenvalue problem closing Sec. 3.2):
 // T^{mu nu} u_nu = -eps u^mu.  With v = u/u^0 and delta = E - eps this is
 //   (S + eps I) v = M,  delta = M . v.
@@ -234,8 +224,10 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
     fr.vx = vx;
     fr.vy = vy;
     fr.v2 = vx * vx + vy * vy;
-    fr.gamma = rsqrt_<TL>((TL)1 - fr.v2);
-    fr.g2 = fr.gamma * fr.gamma;
+    // correctly rounded 1/(1 - v^2) and sqrt: the equilibrium must carry the
+    // frame's energy-momentum to round-off, or the collision stops conserving
+    fr.g2 = recip<TL>((TL)1 - fr.v2);
+    fr.gamma = std::sqrt(fr.g2);
     return fr;
 }
 
