@@ -206,6 +206,32 @@ RLBM_API rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info);
  * be NULL.  Synchronises. */
 RLBM_API rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *kernel, int *block_x, int *block_y);
 
+/* Allocation-free moments (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory, e.g. applications that run
+ * on a memory budget fixed up front, loops that must not take the implicit
+ * synchronisation of cudaMalloc, or hosts whose device memory belongs to
+ * another framework's pool).  Computes what rlbm_moments_device computes
+ * from a caller-owned population array: d_q is the device state
+ * [17][ny][pitch] of storage type `dtype` (for example rlbm_info_t.populations
+ * and .pitch of a handle), eps0 and scale its deviation parameters; d_eps,
+ * d_vx, d_vy (nx*ny FP64 each, any may be NULL) and d_totals (3 FP64, may be
+ * NULL) are caller-owned device outputs.  Async on `stream` (NULL = legacy
+ * default stream).  No device or host memory is allocated: the scratch (FP64
+ * per-block partial sums and a failed-node counter) lives in one static
+ * device array of 1.5 MiB that every GPU loading the library holds until the
+ * process exits.  The lattice must satisfy ceil(nx/32) * ceil(ny/8) <=
+ * RLBM_STATIC_MAX_BLOCKS (e.g. 4096 x 4096); larger lattices get
+ * RLBM_ERR_ARG.  The first call on a device looks the scratch address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the scratch and
+ * clear the counter they need, so calls that overlap on the GPU (different
+ * streams, no ordering) race: order them on one stream.  Errors:
+ * RLBM_ERR_ARG, RLBM_ERR_CUDA (no handle, so no message). */
+#define RLBM_STATIC_MAX_BLOCKS 65536
+RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, int nx, int ny, int pitch, double eps0,
+                                         double scale, double *d_eps, double *d_vx, double *d_vy, double *d_totals,
+                                         void *stream);
+
 /* Wait for all work queued on the handle's stream. */
 RLBM_API rlbm_status rlbm_synchronize(rlbm_t *h);
 

@@ -35,7 +35,8 @@ NCLASSES = 17
 EXPORTS = (
     "rlbm_opts_default", "rlbm_create", "rlbm_init_fields", "rlbm_init_fields_device", "rlbm_step", "rlbm_moments",
     "rlbm_moments_device", "rlbm_energy_spectrum", "rlbm_get_populations", "rlbm_set_populations", "rlbm_get_force",
-    "rlbm_get_info", "rlbm_autotune", "rlbm_synchronize", "rlbm_last_error", "rlbm_destroy", "rlbm_status_string",
+    "rlbm_get_info", "rlbm_autotune", "rlbm_moments_static", "rlbm_synchronize", "rlbm_last_error", "rlbm_destroy",
+    "rlbm_status_string",
 )
 
 
@@ -99,6 +100,10 @@ def _load():
         lib.rlbm_get_force.argtypes = [h, _dp, _dp]
         lib.rlbm_get_info.argtypes = [h, ctypes.POINTER(Info)]
         lib.rlbm_synchronize.argtypes = [h]
+        lib.rlbm_moments_static.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.rlbm_moments_static.restype = ctypes.c_int
         lib.rlbm_autotune.argtypes = [h, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]
         lib.rlbm_last_error.argtypes = [h, ctypes.c_char_p, ctypes.c_size_t]
@@ -240,6 +245,15 @@ def rlbm_autotune(h, reps: int = 20):
     _check(h, _load().rlbm_autotune(h, int(reps), ctypes.byref(k), ctypes.byref(bx), ctypes.byref(by)),
            "rlbm_autotune")
     return k.value, bx.value, by.value
+
+
+def rlbm_moments_static(dtype: int, d_q: int, nx: int, ny: int, pitch: int, eps0: float, scale: float,
+                        d_eps: int = 0, d_vx: int = 0, d_vy: int = 0, d_totals: int = 0, stream: int = 0):
+    """Allocation-free moments from a caller-owned device population array
+    (see include/rlbm.h); all pointers are device addresses as ints."""
+    st = _load().rlbm_moments_static(int(dtype), d_q or None, int(nx), int(ny), int(pitch), float(eps0), float(scale),
+                                     d_eps or None, d_vx or None, d_vy or None, d_totals or None, stream or None)
+    _check(None, st, "rlbm_moments_static")
 
 
 def rlbm_synchronize(h):
