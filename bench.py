@@ -173,6 +173,52 @@ def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, in
     return ms, kernel_ms, info, int(is_epoch.sum())
 
 
+def measure_ensemble(torch, rl, flush, steps=20, warmup=5):
+    """The 64-member ensemble (sides 256..1024): per-step timing with an L2
+    flush between steps, and the throughput of a replayed 100-step graph."""
+    runs = [dict(nx=w.nx, ny=w.ny, tau=w.tau,
+                 forcing=dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw))
+            for w in workloads.ensemble()]
+    ens = rl.Ensemble(runs, dtype="f32", landau="fp32")
+    bx, by, grid = ens.autotune(5)
+    ens.step(warmup)
+    ens.synchronize()
+    stream = ens._torch_stream
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            flush.fill_(1.0)
+            a.record(stream)
+            ens.step(1)
+            b.record(stream)
+            evs.append((a, b))
+    stream.synchronize()
+    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    info = ens.info()
+    # a full forcing epoch replayed as one graph (starts at an epoch boundary)
+    ens.step((-info["step"]) % 100)
+    ens.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        ens.step(100)
+        b.record(stream)
+    stream.synchronize()
+    graph_ms = a.elapsed_time(b)
+    info = ens.info()
+    ens.close()
+    peak, _ = load_peaks()
+    step_ms = float(np.median(ms))
+    return {"workload": "64 stirred runs, sides {256,384,512,768,1024}, tau U[0.51,0.7], bands around U[4,12]",
+            "nodes": int(info["nodes"]), "glups": info["nodes"] / (step_ms / 1e3) / 1e9,
+            "hbm_frac": info["bytes_per_step"] / (step_ms / 1e3) / 1e9 / peak,
+            "glups_graph_100_steps": info["nodes"] * 100 / (graph_ms / 1e3) / 1e9,
+            "block": [bx, by], "grid": grid, "tiles": int(info["ntiles"]), "launches_per_step": 1}
+
+
 def parity_error(rl, oracle, form, landau):
     """Max relative error vs the FP64 oracle after 100 forced steps on a
     128 x 128 lattice started from seeded smooth fields (the parity bar)."""
@@ -386,6 +432,7 @@ def main():
                 "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak, "bytes_per_node": bp,
                 "max_rel_err_vs_oracle": err}
         line["forms"] = forms
+        line["ensemble"] = measure_ensemble(torch, rl, flush)
         line["e2e"] = e2e_glups(rl, w, n, args.form, args.landau)
         g, desc, th = cpu_oracle_glups(oracle, w, n, args.cpu_seconds)
         line["cpu_baseline"] = {"value": g, "unit": "GLUPS", "cores": th, "kind": "oracle", "sample": desc}

@@ -235,6 +235,57 @@ RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, int nx, int
 /* Wait for all work queued on the handle's stream. */
 RLBM_API rlbm_status rlbm_synchronize(rlbm_t *h);
 
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent lattices (the paper's stirred runs, Sec. 5,
+ * at several sizes, relaxation times and driven bands) advanced together.
+ * Each member behaves exactly like an rlbm_t with the ensemble's options;
+ * one step of the ensemble is a single launch over a flat list of tiles of
+ * all members (a grid-stride loop, so the grid is sized to the GPU), and
+ * chunks of steps inside a forcing epoch replay as CUDA graphs.  All members
+ * share one step counter, stream, storage form and the vector kernel (each
+ * nx divisible by 4, or by 2 for F64). */
+typedef struct rlbm_batch rlbm_batch_t;
+
+typedef struct {
+    int nx, ny;
+    double tau;
+    rlbm_forcing forcing; /* amp = 0: unforced member */
+} rlbm_run_desc;
+
+typedef struct {
+    int nruns, dtype;
+    int block_x, block_y, grid, ntiles; /* launch shape of the ensemble step */
+    int64_t step;
+    int64_t nodes;                      /* lattice nodes over all members */
+    size_t bytes_per_step;              /* algorithmic HBM bytes of one ensemble step */
+    size_t device_bytes;
+} rlbm_batch_info_t;
+
+/* Create nruns members (validation as rlbm_create, per member); all start at
+ * rest at step 0.  Errors: RLBM_ERR_ARG, RLBM_ERR_ALLOC, RLBM_ERR_CUDA. */
+RLBM_API rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_opts *opts,
+                                       rlbm_batch_t **out);
+/* Initialise member `run` as rlbm_init_fields does, at the ensemble's
+ * current step (the step counter is shared and not reset). */
+RLBM_API rlbm_status rlbm_batch_init_fields(rlbm_batch_t *b, int run, const double *eps, const double *vx,
+                                            const double *vy);
+/* Advance every member n steps (async). */
+RLBM_API rlbm_status rlbm_batch_step(rlbm_batch_t *b, int n);
+/* Per-member diagnostics, as the single-lattice calls (synchronise). */
+RLBM_API rlbm_status rlbm_batch_moments(rlbm_batch_t *b, int run, double *eps, double *vx, double *vy,
+                                        double totals[3]);
+RLBM_API rlbm_status rlbm_batch_energy_spectrum(rlbm_batch_t *b, int run, int nshells, double *Ek);
+RLBM_API rlbm_status rlbm_batch_get_populations(rlbm_batch_t *b, int run, double *f);
+/* Time tile shapes and persistent grid sizes (multiples of the SM count,
+ * or one block per tile) for the ensemble step and keep the fastest; the
+ * state is unchanged.  Outputs may be NULL.  Synchronises. */
+RLBM_API rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *block_y, int *grid);
+RLBM_API rlbm_status rlbm_batch_get_info(rlbm_batch_t *b, rlbm_batch_info_t *info);
+RLBM_API rlbm_status rlbm_batch_synchronize(rlbm_batch_t *b);
+RLBM_API rlbm_status rlbm_batch_last_error(rlbm_batch_t *b, char *buf, size_t len);
+/* Release the ensemble and all members (NULL-safe; synchronises). */
+RLBM_API void rlbm_batch_destroy(rlbm_batch_t *b);
+
 /* Copy the handle's last error message (NUL-terminated, truncated to len). */
 RLBM_API rlbm_status rlbm_last_error(rlbm_t *h, char *buf, size_t len);
 

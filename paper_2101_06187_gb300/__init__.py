@@ -36,7 +36,9 @@ EXPORTS = (
     "rlbm_opts_default", "rlbm_create", "rlbm_init_fields", "rlbm_init_fields_device", "rlbm_step", "rlbm_moments",
     "rlbm_moments_device", "rlbm_energy_spectrum", "rlbm_get_populations", "rlbm_set_populations", "rlbm_get_force",
     "rlbm_get_info", "rlbm_autotune", "rlbm_moments_static", "rlbm_synchronize", "rlbm_last_error", "rlbm_destroy",
-    "rlbm_status_string",
+    "rlbm_status_string", "rlbm_batch_create", "rlbm_batch_init_fields", "rlbm_batch_step", "rlbm_batch_moments",
+    "rlbm_batch_energy_spectrum", "rlbm_batch_get_populations", "rlbm_batch_autotune", "rlbm_batch_get_info",
+    "rlbm_batch_synchronize", "rlbm_batch_last_error", "rlbm_batch_destroy",
 )
 
 
@@ -69,6 +71,16 @@ class Info(ctypes.Structure):
                 ("step", ctypes.c_int64), ("tau", ctypes.c_double), ("eps0", ctypes.c_double),
                 ("scale", ctypes.c_double), ("bytes_per_node", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
                 ("populations", ctypes.c_void_p)]
+
+
+class RunDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau", ctypes.c_double), ("forcing", Forcing)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("nruns", ctypes.c_int), ("dtype", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+                ("grid", ctypes.c_int), ("ntiles", ctypes.c_int), ("step", ctypes.c_int64), ("nodes", ctypes.c_int64),
+                ("bytes_per_step", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t)]
 
 
 _lib_lock = threading.Lock()
@@ -104,6 +116,25 @@ def _load():
                                             ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.rlbm_moments_static.restype = ctypes.c_int
+        b = ctypes.c_void_p
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.rlbm_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(RunDesc), ctypes.POINTER(Opts),
+                                          ctypes.POINTER(ctypes.c_void_p)]
+        lib.rlbm_batch_init_fields.argtypes = [b, ctypes.c_int, _dp, _dp, _dp]
+        lib.rlbm_batch_step.argtypes = [b, ctypes.c_int]
+        lib.rlbm_batch_moments.argtypes = [b, ctypes.c_int, _dp, _dp, _dp, _dp]
+        lib.rlbm_batch_energy_spectrum.argtypes = [b, ctypes.c_int, ctypes.c_int, _dp]
+        lib.rlbm_batch_get_populations.argtypes = [b, ctypes.c_int, _dp]
+        lib.rlbm_batch_autotune.argtypes = [b, ctypes.c_int, ip, ip, ip]
+        lib.rlbm_batch_get_info.argtypes = [b, ctypes.POINTER(BatchInfo)]
+        lib.rlbm_batch_synchronize.argtypes = [b]
+        lib.rlbm_batch_last_error.argtypes = [b, ctypes.c_char_p, ctypes.c_size_t]
+        lib.rlbm_batch_destroy.argtypes = [b]
+        lib.rlbm_batch_destroy.restype = None
+        for name in ("rlbm_batch_create", "rlbm_batch_init_fields", "rlbm_batch_step", "rlbm_batch_moments",
+                     "rlbm_batch_energy_spectrum", "rlbm_batch_get_populations", "rlbm_batch_autotune",
+                     "rlbm_batch_get_info", "rlbm_batch_synchronize", "rlbm_batch_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
         lib.rlbm_autotune.argtypes = [h, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]
         lib.rlbm_last_error.argtypes = [h, ctypes.c_char_p, ctypes.c_size_t]
@@ -124,14 +155,14 @@ def library():
     return _load()
 
 
-def _check(h, st: int, what: str):
+def _check(h, st: int, what: str, batch: bool = False):
     if st == RLBM_OK:
         return
     lib = _load()
     msg = lib.rlbm_status_string(st).decode()
     if h:
         buf = ctypes.create_string_buffer(512)
-        lib.rlbm_last_error(h, buf, 512)
+        (lib.rlbm_batch_last_error if batch else lib.rlbm_last_error)(h, buf, 512)
         if buf.value:
             msg += ": " + buf.value.decode()
     raise RLBMError(st, "%s failed: %s" % (what, msg))
@@ -270,6 +301,64 @@ def rlbm_status_string(status: int) -> str:
     return _load().rlbm_status_string(int(status)).decode()
 
 
+def rlbm_batch_create(runs, opts: Optional[Opts]):
+    arr = (RunDesc * len(runs))(*runs)
+    out = ctypes.c_void_p()
+    st = _load().rlbm_batch_create(len(runs), arr, ctypes.byref(opts) if opts else None, ctypes.byref(out))
+    _check(None, st, "rlbm_batch_create")
+    return out
+
+
+def rlbm_batch_init_fields(b, run: int, eps=None, vx=None, vy=None):
+    _check(b, _load().rlbm_batch_init_fields(b, int(run), _p(eps), _p(vx), _p(vy)), "rlbm_batch_init_fields", True)
+
+
+def rlbm_batch_step(b, n: int):
+    _check(b, _load().rlbm_batch_step(b, int(n)), "rlbm_batch_step", True)
+
+
+def rlbm_batch_moments(b, run: int, eps, vx, vy, totals):
+    _check(b, _load().rlbm_batch_moments(b, int(run), _p(eps), _p(vx), _p(vy), _p(totals)), "rlbm_batch_moments",
+           True)
+
+
+def rlbm_batch_energy_spectrum(b, run: int, nshells: int, Ek):
+    _check(b, _load().rlbm_batch_energy_spectrum(b, int(run), int(nshells), _p(Ek)), "rlbm_batch_energy_spectrum",
+           True)
+
+
+def rlbm_batch_get_populations(b, run: int, f):
+    _check(b, _load().rlbm_batch_get_populations(b, int(run), _p(f)), "rlbm_batch_get_populations", True)
+
+
+def rlbm_batch_autotune(b, reps: int = 10):
+    bx, by, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(b, _load().rlbm_batch_autotune(b, int(reps), ctypes.byref(bx), ctypes.byref(by), ctypes.byref(g)),
+           "rlbm_batch_autotune", True)
+    return bx.value, by.value, g.value
+
+
+def rlbm_batch_get_info(b) -> BatchInfo:
+    info = BatchInfo()
+    _check(b, _load().rlbm_batch_get_info(b, ctypes.byref(info)), "rlbm_batch_get_info", True)
+    return info
+
+
+def rlbm_batch_synchronize(b):
+    _check(b, _load().rlbm_batch_synchronize(b), "rlbm_batch_synchronize", True)
+
+
+def rlbm_batch_last_error(b) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _load().rlbm_batch_last_error(b, buf, 512)
+    return buf.value.decode()
+
+
+def rlbm_batch_destroy(b):
+    if b:
+        _load().rlbm_batch_destroy(b)
+
+
 def rlbm_destroy(h):
     if h:
         _load().rlbm_destroy(h)
@@ -406,3 +495,101 @@ class Lattice:
 
     def synchronize(self):
         rlbm_synchronize(self.handle)
+
+
+class Ensemble:
+    """Independent lattices advanced together by one launch per step.
+
+    runs: list of dicts with nx, ny, tau and optional forcing (as for
+    Lattice).  dtype / landau / allocator / stream as for Lattice.
+    """
+
+    def __init__(self, runs, *, dtype: str = "f32", landau: str = "fp32", use_graphs: bool = True,
+                 allocator: str = "torch", stream=None, device: Optional[int] = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the RLBM library runs on the GPU only")
+        self._b = None
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = dev
+        if stream is None:
+            self._torch_stream = torch.cuda.Stream(device=dev)
+            s = self._torch_stream.cuda_stream
+        elif isinstance(stream, int):
+            self._torch_stream = None
+            s = stream
+        else:
+            self._torch_stream = stream
+            s = stream.cuda_stream
+        o = rlbm_opts_default()
+        o.dtype = DTYPES[dtype]
+        o.landau = LANDAU[landau]
+        o.use_graphs = 1 if use_graphs else 0
+        o.stream = s
+        o.device = dev
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(dev, s)
+            o.alloc = self._alloc.alloc
+            o.free = self._alloc.free
+        descs = []
+        self.shapes = []
+        for r in runs:
+            fz = r.get("forcing") or {}
+            f = Forcing(int(fz.get("kmin", 0)), int(fz.get("kmax", 0)), float(fz.get("amp", 0.0)),
+                        int(fz.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF, int(fz.get("redraw_period", 100)))
+            descs.append(RunDesc(int(r["nx"]), int(r["ny"]), float(r["tau"]), f))
+            self.shapes.append((int(r["ny"]), int(r["nx"])))
+        self._b = rlbm_batch_create(descs, o)
+
+    def close(self):
+        if self._b:
+            rlbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    @property
+    def handle(self):
+        if not self._b:
+            raise RuntimeError("ensemble is closed")
+        return self._b
+
+    def init_fields(self, run: int, eps=None, vx=None, vy=None):
+        ny, nx = self.shapes[run]
+        n = nx * ny
+        rlbm_batch_init_fields(self.handle, run, _f64(eps, n), _f64(vx, n), _f64(vy, n))
+
+    def step(self, n: int = 1):
+        rlbm_batch_step(self.handle, n)
+
+    def moments(self, run: int):
+        ny, nx = self.shapes[run]
+        eps, vx, vy, tot = np.empty((ny, nx)), np.empty((ny, nx)), np.empty((ny, nx)), np.empty(3)
+        rlbm_batch_moments(self.handle, run, eps, vx, vy, tot)
+        return eps, vx, vy, tot
+
+    def energy_spectrum(self, run: int, nshells: int) -> np.ndarray:
+        E = np.empty(int(nshells))
+        rlbm_batch_energy_spectrum(self.handle, run, nshells, E)
+        return E
+
+    def populations(self, run: int) -> np.ndarray:
+        ny, nx = self.shapes[run]
+        f = np.empty((NCLASSES, ny, nx))
+        rlbm_batch_get_populations(self.handle, run, f)
+        return f
+
+    def autotune(self, reps: int = 10):
+        return rlbm_batch_autotune(self.handle, reps)
+
+    def info(self) -> dict:
+        i = rlbm_batch_get_info(self.handle)
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def synchronize(self):
+        rlbm_batch_synchronize(self.handle)

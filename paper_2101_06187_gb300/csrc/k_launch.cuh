@@ -39,6 +39,14 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
 }
 
 template <typename TS, typename TC, typename TL>
+cudaError_t launch_batch_t(const LaunchCfg &cfg, int grid, const void *runs, int nruns, int ntiles, cudaStream_t s) {
+    if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256 || grid < 1) return cudaErrorInvalidConfiguration;
+    k_step_batch<TS, TC, TL><<<grid, dim3(cfg.bx, cfg.by, 1), 0, s>>>(static_cast<const BatchRun *>(runs), nruns,
+                                                                      ntiles);
+    return cudaGetLastError();
+}
+
+template <typename TS, typename TC, typename TL>
 cudaError_t launch_moments_t(const void *qin, const StepParams &p, double *eps, double *vx, double *vy,
                              double *partials, int *bad, cudaStream_t s) {
     k_moments<TS, TC, TL><<<gather_grid(p), gather_block(), 0, s>>>(static_cast<const TS *>(qin), p, eps, vx, vy,

@@ -12,4 +12,9 @@ cudaError_t launch_moments_f32(int landau, const void *qin, const StepParams &p,
     (void)landau;  // diagnostics always solve the frame in FP64
     return launch_moments_t<float, float, double>(qin, p, eps, vx, vy, partials, bad, s);
 }
+cudaError_t launch_batch_f32(const LaunchCfg &cfg, int landau, int grid, const void *runs, int nruns, int ntiles,
+                             cudaStream_t s) {
+    if (landau == RLBM_LANDAU_FP32) return launch_batch_t<float, float, float>(cfg, grid, runs, nruns, ntiles, s);
+    return launch_batch_t<float, float, double>(cfg, grid, runs, nruns, ntiles, s);
+}
 }  // namespace rlbk

@@ -10,4 +10,8 @@ cudaError_t launch_moments_f64(int, const void *qin, const StepParams &p, double
                                double *partials, int *bad, cudaStream_t s) {
     return launch_moments_t<double, double, double>(qin, p, eps, vx, vy, partials, bad, s);
 }
+cudaError_t launch_batch_f64(const LaunchCfg &cfg, int, int grid, const void *runs, int nruns, int ntiles,
+                             cudaStream_t s) {
+    return launch_batch_t<double, double, double>(cfg, grid, runs, nruns, ntiles, s);
+}
 }  // namespace rlbk

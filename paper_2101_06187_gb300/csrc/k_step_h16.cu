@@ -20,4 +20,14 @@ cudaError_t launch_moments_h16(int dtype, int landau, const void *qin, const Ste
         return launch_moments_t<__nv_bfloat16, float, double>(qin, p, eps, vx, vy, partials, bad, s);
     return launch_moments_t<__half, float, double>(qin, p, eps, vx, vy, partials, bad, s);
 }
+cudaError_t launch_batch_h16(int dtype, const LaunchCfg &cfg, int landau, int grid, const void *runs, int nruns,
+                             int ntiles, cudaStream_t s) {
+    if (dtype == RLBM_BF16) {
+        if (landau == RLBM_LANDAU_FP32)
+            return launch_batch_t<__nv_bfloat16, float, float>(cfg, grid, runs, nruns, ntiles, s);
+        return launch_batch_t<__nv_bfloat16, float, double>(cfg, grid, runs, nruns, ntiles, s);
+    }
+    if (landau == RLBM_LANDAU_FP32) return launch_batch_t<__half, float, float>(cfg, grid, runs, nruns, ntiles, s);
+    return launch_batch_t<__half, float, double>(cfg, grid, runs, nruns, ntiles, s);
+}
 }  // namespace rlbk

@@ -98,13 +98,11 @@ __device__ __forceinline__ void load_class_row(const TS *__restrict__ row, int x
     if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) r[V + 1] = load_q<TS, TC>(row + xr);
 }
 
+// The fused step for the run of V nodes starting at (x0, y).
 template <typename TS, typename TC, typename TL, bool FORCED>
-__global__ void __launch_bounds__(256) k_step_vec(const TS *__restrict__ qin, TS *__restrict__ qout,
-                                                  const TC *__restrict__ F, StepParams p) {
+__device__ __forceinline__ void step_run(const TS *__restrict__ qin, TS *__restrict__ qout, const TC *__restrict__ F,
+                                         const StepParams &p, int x0, int y) {
     constexpr int V = VecOf<TS>::V;
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= p.nx || y >= p.ny) return;
     const int ym = (y == 0) ? p.ny - 1 : y - 1;
     const int yp = (y == p.ny - 1) ? 0 : y + 1;
     const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
@@ -153,6 +151,48 @@ __global__ void __launch_bounds__(256) k_step_vec(const TS *__restrict__ qin, TS
         for (int i = 0; i < V; ++i) out[i] = q[i][c];
         store_run<TS, TC, V>(qout + (long long)c * p.plane + n0, out);
     });
+}
+
+template <typename TS, typename TC, typename TL, bool FORCED>
+__global__ void __launch_bounds__(256) k_step_vec(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                                  const TC *__restrict__ F, StepParams p) {
+    constexpr int V = VecOf<TS>::V;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= p.nx || y >= p.ny) return;
+    step_run<TS, TC, TL, FORCED>(qin, qout, F, p, x0, y);
+}
+
+// Ensemble of independent lattices advanced by one launch: a flat list of
+// tiles (one thread block's worth of runs, blockDim.x * V columns by
+// blockDim.y rows) over all lattices; each block walks the list with a grid
+// stride, so the grid can be sized to the GPU (a multiple of the SM count)
+// rather than to the work.
+template <typename TS, typename TC, typename TL>
+__global__ void __launch_bounds__(256) k_step_batch(const BatchRun *__restrict__ runs, int nruns, int ntiles) {
+    constexpr int V = VecOf<TS>::V;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        // binary search of the lattice owning tile t
+        int lo = 0, hi = nruns - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (runs[mid].tile0 <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchRun &r = runs[lo];
+        const int local = t - r.tile0;
+        const int tx = local % r.tiles_x, ty = local / r.tiles_x;
+        const int x0 = (tx * blockDim.x + threadIdx.x) * V;
+        const int y = ty * blockDim.y + threadIdx.y;
+        if (x0 < r.p.nx && y < r.p.ny) {
+            if (r.F)
+                step_run<TS, TC, TL, true>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout),
+                                           static_cast<const TC *>(r.F), r.p, x0, y);
+            else
+                step_run<TS, TC, TL, false>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout), nullptr,
+                                            r.p, x0, y);
+        }
+    }
 }
 
 }  // namespace rlbk

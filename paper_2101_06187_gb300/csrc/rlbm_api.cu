@@ -22,6 +22,12 @@ cudaError_t launch_step_f32(const LaunchCfg &cfg, int landau, bool forced, const
                             const void *F, const StepParams &p, cudaStream_t s);
 cudaError_t launch_step_h16(int dtype, const LaunchCfg &cfg, int landau, bool forced, const void *qin, void *qout,
                             const void *F, const StepParams &p, cudaStream_t s);
+cudaError_t launch_batch_f64(const LaunchCfg &cfg, int landau, int grid, const void *runs, int nruns, int ntiles,
+                             cudaStream_t s);
+cudaError_t launch_batch_f32(const LaunchCfg &cfg, int landau, int grid, const void *runs, int nruns, int ntiles,
+                             cudaStream_t s);
+cudaError_t launch_batch_h16(int dtype, const LaunchCfg &cfg, int landau, int grid, const void *runs, int nruns,
+                             int ntiles, cudaStream_t s);
 cudaError_t launch_moments_f64(int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                                double *vy, double *partials, int *bad, cudaStream_t s);
 cudaError_t launch_moments_f32(int landau, const void *qin, const StepParams &p, double *eps, double *vx,
@@ -46,6 +52,17 @@ cudaError_t launch_moments(int dtype, int landau, const void *qin, const StepPar
     default: return launch_moments_h16(dtype, landau, qin, p, eps, vx, vy, partials, bad, s);
     }
 }
+
+cudaError_t launch_batch(int dtype, int landau, const LaunchCfg &cfg, int grid, const void *runs, int nruns,
+                         int ntiles, cudaStream_t s) {
+    switch (dtype) {
+    case RLBM_F64: return launch_batch_f64(cfg, landau, grid, runs, nruns, ntiles, s);
+    case RLBM_F32: return launch_batch_f32(cfg, landau, grid, runs, nruns, ntiles, s);
+    default: return launch_batch_h16(dtype, cfg, landau, grid, runs, nruns, ntiles, s);
+    }
+}
+
+int run_length(int dtype) { return dtype == RLBM_F64 ? 2 : 4; }
 
 int moments_blocks(const StepParams &p) { return ((p.nx + 31) / 32) * ((p.ny + 7) / 8); }
 
@@ -370,17 +387,23 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     return RLBM_OK;
 }
 
-rlbm_status rlbm_init_fields_device(rlbm_t *h, const double *d_eps, const double *d_vx, const double *d_vy) {
-    CHECK_HANDLE(h);
-    CUDA_TRY(h, launch_init(h->opts.dtype, h->q[0], params_of(h), d_eps, d_vx, d_vy, h->stream));
-    h->cur = 0;
-    h->step = 0;
-    h->force_epoch = -1;
+}  // extern "C"
+
+// Write f_eq of the given device fields into the current buffer.  A plain
+// handle restarts its clock (step 0, current buffer 0); an ensemble member
+// keeps the ensemble's clock and buffer parity.
+static rlbm_status init_device_impl(rlbm_t *h, const double *d_eps, const double *d_vx, const double *d_vy,
+                                    bool keep_clock) {
+    if (!keep_clock) {
+        h->cur = 0;
+        h->step = 0;
+        h->force_epoch = -1;
+    }
+    CUDA_TRY(h, launch_init(h->opts.dtype, h->q[h->cur], params_of(h), d_eps, d_vx, d_vy, h->stream));
     return RLBM_OK;
 }
 
-rlbm_status rlbm_init_fields(rlbm_t *h, const double *eps, const double *vx, const double *vy) {
-    CHECK_HANDLE(h);
+static rlbm_status init_host_impl(rlbm_t *h, const double *eps, const double *vx, const double *vy, bool keep_clock) {
     const size_t n = (size_t)h->nx * h->ny;
     const double *src[3] = {eps, vx, vy};
     for (int k = 0; k < 3; ++k) {
@@ -404,10 +427,22 @@ rlbm_status rlbm_init_fields(rlbm_t *h, const double *eps, const double *vx, con
         CUDA_TRY(h, cudaMemcpyAsync(dptr[k], h->host_pinned + k * n, n * sizeof(double), cudaMemcpyHostToDevice,
                                     h->stream));
     }
-    rlbm_status st = rlbm_init_fields_device(h, dptr[0], dptr[1], dptr[2]);
+    rlbm_status st = init_device_impl(h, dptr[0], dptr[1], dptr[2], keep_clock);
     if (st != RLBM_OK) return st;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return RLBM_OK;
+}
+
+extern "C" {
+
+rlbm_status rlbm_init_fields_device(rlbm_t *h, const double *d_eps, const double *d_vx, const double *d_vy) {
+    CHECK_HANDLE(h);
+    return init_device_impl(h, d_eps, d_vx, d_vy, false);
+}
+
+rlbm_status rlbm_init_fields(rlbm_t *h, const double *eps, const double *vx, const double *vy) {
+    CHECK_HANDLE(h);
+    return init_host_impl(h, eps, vx, vy, false);
 }
 
 rlbm_status rlbm_step(rlbm_t *h, int n) {
@@ -626,4 +661,371 @@ rlbm_status rlbm_last_error(rlbm_t *h, char *buf, size_t len) {
     return RLBM_OK;
 }
 
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- ensemble
+// An ensemble keeps one ordinary handle per lattice (buffers, force field,
+// diagnostics) on a shared stream and advances all of them with one
+// k_step_batch launch per step over a flat tile list.
+struct rlbm_batch {
+    std::vector<rlbm_t *> runs;
+    rlbm_opts opts{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    LaunchCfg cfg;         // tile = cfg.bx * run_length columns x cfg.by rows
+    int grid = 0;          // blocks of the persistent launch
+    int ntiles = 0;
+    BatchRun *desc[2] = {nullptr, nullptr};  // device descriptors for parity 0 / 1
+    int cur = 0;
+    long long step = 0;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    rlbm_status status = RLBM_OK;
+    std::string msg;
+};
+
+static rlbm_status bfail(rlbm_batch_t *b, rlbm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    b->msg = buf;
+    if (st == RLBM_ERR_CUDA || st == RLBM_ERR_TIMEOUT) b->status = st;
+    return st;
+}
+
+#define BCUDA_TRY(b, call)                                                                                  \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess) return bfail(b, RLBM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                            __FILE__, __LINE__);                                            \
+    } while (0)
+
+#define CHECK_BATCH(b)                                   \
+    do {                                                 \
+        if (!(b)) return RLBM_ERR_ARG;                   \
+        if ((b)->status != RLBM_OK) return (b)->status;  \
+        if (cudaSetDevice((b)->device) != cudaSuccess) return bfail(b, RLBM_ERR_CUDA, "cudaSetDevice failed"); \
+    } while (0)
+
+static void batch_drop_graphs(rlbm_batch_t *b) {
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// Host copy of the descriptors for a launch shape; returns the tile count.
+static int batch_descriptors(const rlbm_batch_t *b, const LaunchCfg &cfg, int parity, std::vector<BatchRun> *out) {
+    const int V = run_length(b->opts.dtype);
+    int t0 = 0;
+    out->clear();
+    for (rlbm_t *h : b->runs) {
+        BatchRun r;
+        r.qin = h->q[parity];
+        r.qout = h->q[parity ^ 1];
+        r.F = h->forced ? h->F : nullptr;
+        r.p = params_of(h);
+        const int cols = h->nx / V;
+        r.tiles_x = (cols + cfg.bx - 1) / cfg.bx;
+        const int tiles_y = (h->ny + cfg.by - 1) / cfg.by;
+        r.tile0 = t0;
+        t0 += r.tiles_x * tiles_y;
+        out->push_back(r);
+    }
+    return t0;
+}
+
+static rlbm_status batch_upload(rlbm_batch_t *b, const LaunchCfg &cfg) {
+    std::vector<BatchRun> d[2];
+    int nt = 0;
+    for (int par = 0; par < 2; ++par) nt = batch_descriptors(b, cfg, par, &d[par]);
+    BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    for (int par = 0; par < 2; ++par)
+        BCUDA_TRY(b, cudaMemcpy(b->desc[par], d[par].data(), sizeof(BatchRun) * d[par].size(), cudaMemcpyHostToDevice));
+    b->ntiles = nt;
+    return RLBM_OK;
+}
+
+static int sm_count(int device) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
+}
+
+static rlbm_status batch_launch_steps(rlbm_batch_t *b, int n) {
+    for (int i = 0; i < n; ++i) {
+        BCUDA_TRY(b, launch_batch(b->opts.dtype, b->opts.landau, b->cfg, b->grid, b->desc[b->cur], (int)b->runs.size(),
+                                  b->ntiles, b->stream));
+        b->cur ^= 1;
+    }
+    return RLBM_OK;
+}
+
+static rlbm_status batch_run_chunk(rlbm_batch_t *b, int n) {
+    const bool graphs = b->opts.use_graphs && b->stream != nullptr && n >= 2;
+    if (!graphs) return batch_launch_steps(b, n);
+    const int even = n & ~1;
+    auto key = std::make_pair(even, b->cur);
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        const int cur0 = b->cur;
+        BCUDA_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        rlbm_status st = batch_launch_steps(b, even);
+        cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+        b->cur = cur0;
+        if (st != RLBM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ec != cudaSuccess) return bfail(b, RLBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+        ec = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ec != cudaSuccess) return bfail(b, RLBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+        it = b->graphs.emplace(key, ge).first;
+    }
+    BCUDA_TRY(b, cudaGraphLaunch(it->second, b->stream));
+    if (even != n) return batch_launch_steps(b, 1);
+    return RLBM_OK;
+}
+
+// Bring an ensemble member's own bookkeeping in line with the ensemble.
+static void batch_sync_member(const rlbm_batch_t *b, rlbm_t *h) {
+    h->cur = b->cur;
+    h->step = b->step;
+}
+
+static rlbm_status batch_member(rlbm_batch_t *b, int run, rlbm_t **h) {
+    if (run < 0 || run >= (int)b->runs.size()) return bfail(b, RLBM_ERR_ARG, "run index %d out of range", run);
+    *h = b->runs[run];
+    batch_sync_member(b, *h);
+    return RLBM_OK;
+}
+
+static rlbm_status from_member(rlbm_batch_t *b, rlbm_t *h, rlbm_status st) {
+    if (st != RLBM_OK) {
+        b->msg = h->msg;
+        if (st == RLBM_ERR_CUDA || st == RLBM_ERR_TIMEOUT) b->status = st;
+    }
+    return st;
+}
+
+extern "C" {
+
+void rlbm_batch_destroy(rlbm_batch_t *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    batch_drop_graphs(b);
+    if (!b->runs.empty()) {
+        for (int par = 0; par < 2; ++par)
+            dev_free(b->runs[0], b->desc[par], sizeof(BatchRun) * b->runs.size());
+    }
+    for (rlbm_t *h : b->runs) rlbm_destroy(h);
+    delete b;
+}
+
+rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_opts *opts, rlbm_batch_t **out) {
+    if (!out) return RLBM_ERR_ARG;
+    *out = nullptr;
+    if (nruns < 1 || !runs) return RLBM_ERR_ARG;
+    rlbm_opts o;
+    rlbm_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
+    const int V = run_length(o.dtype);
+    for (int r = 0; r < nruns; ++r)
+        if (runs[r].nx % V != 0) return RLBM_ERR_ARG;  // the ensemble kernel works on runs of V nodes
+    rlbm_batch_t *b = new rlbm_batch_t();
+    b->opts = o;
+    b->stream = static_cast<cudaStream_t>(o.stream);
+    rlbm_opts member = o;
+    member.kernel = RLBM_KERNEL_GATHER_VEC;
+    for (int r = 0; r < nruns; ++r) {
+        rlbm_t *h = nullptr;
+        rlbm_status st = rlbm_create(runs[r].nx, runs[r].ny, RLBM_STENCIL_SPH26_SLAB, runs[r].tau, &runs[r].forcing,
+                                     &member, &h);
+        if (st != RLBM_OK) {
+            rlbm_batch_destroy(b);
+            return st;
+        }
+        b->runs.push_back(h);
+    }
+    b->device = b->runs[0]->device;
+    b->opts.landau = b->runs[0]->opts.landau;
+    for (int par = 0; par < 2; ++par) {
+        b->desc[par] = static_cast<BatchRun *>(dev_alloc(b->runs[0], sizeof(BatchRun) * nruns));
+        if (!b->desc[par]) {
+            rlbm_batch_destroy(b);
+            return RLBM_ERR_ALLOC;
+        }
+    }
+    b->cfg.kernel = RLBM_KERNEL_GATHER_VEC;
+    b->cfg.bx = 64;
+    b->cfg.by = 2;
+    rlbm_status st = batch_upload(b, b->cfg);
+    if (st != RLBM_OK) {
+        rlbm_batch_destroy(b);
+        return st;
+    }
+    b->grid = std::min(b->ntiles, 8 * sm_count(b->device));
+    *out = b;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_init_fields(rlbm_batch_t *b, int run, const double *eps, const double *vx, const double *vy) {
+    CHECK_BATCH(b);
+    rlbm_t *h = nullptr;
+    rlbm_status st = batch_member(b, run, &h);
+    if (st != RLBM_OK) return st;
+    return from_member(b, h, init_host_impl(h, eps, vx, vy, true));
+}
+
+rlbm_status rlbm_batch_step(rlbm_batch_t *b, int n) {
+    CHECK_BATCH(b);
+    if (n < 0) return bfail(b, RLBM_ERR_ARG, "negative step count");
+    while (n > 0) {
+        int chunk = n;
+        for (rlbm_t *h : b->runs) {
+            if (!h->forced) continue;
+            batch_sync_member(b, h);
+            rlbm_status st = from_member(b, h, ensure_force(h));
+            if (st != RLBM_OK) return st;
+            const int left = h->forcing.redraw_period - (int)(b->step % h->forcing.redraw_period);
+            chunk = std::min(chunk, left);
+        }
+        rlbm_status st = batch_run_chunk(b, chunk);
+        if (st != RLBM_OK) return st;
+        b->step += chunk;
+        n -= chunk;
+    }
+    for (rlbm_t *h : b->runs) batch_sync_member(b, h);
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_moments(rlbm_batch_t *b, int run, double *eps, double *vx, double *vy, double totals[3]) {
+    CHECK_BATCH(b);
+    rlbm_t *h = nullptr;
+    rlbm_status st = batch_member(b, run, &h);
+    if (st != RLBM_OK) return st;
+    return from_member(b, h, rlbm_moments(h, eps, vx, vy, totals));
+}
+
+rlbm_status rlbm_batch_energy_spectrum(rlbm_batch_t *b, int run, int nshells, double *Ek) {
+    CHECK_BATCH(b);
+    rlbm_t *h = nullptr;
+    rlbm_status st = batch_member(b, run, &h);
+    if (st != RLBM_OK) return st;
+    return from_member(b, h, rlbm_energy_spectrum(h, nshells, Ek));
+}
+
+rlbm_status rlbm_batch_get_populations(rlbm_batch_t *b, int run, double *f) {
+    CHECK_BATCH(b);
+    rlbm_t *h = nullptr;
+    rlbm_status st = batch_member(b, run, &h);
+    if (st != RLBM_OK) return st;
+    return from_member(b, h, rlbm_get_populations(h, f));
+}
+
+rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *block_y, int *grid) {
+    CHECK_BATCH(b);
+    if (reps < 1) reps = 10;
+    for (rlbm_t *h : b->runs) {
+        if (!h->forced) continue;
+        batch_sync_member(b, h);
+        rlbm_status st = from_member(b, h, ensure_force(h));
+        if (st != RLBM_OK) return st;
+    }
+    static const int shapes[][2] = {{32, 4}, {64, 2}, {128, 1}, {32, 8}, {64, 4}, {128, 2}, {32, 2}, {64, 1}};
+    const int sms = sm_count(b->device);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCUDA_TRY(b, cudaEventCreate(&e0));
+    BCUDA_TRY(b, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    LaunchCfg best = b->cfg;
+    int best_grid = b->grid;
+    for (const auto &sh : shapes) {
+        LaunchCfg c;
+        c.kernel = RLBM_KERNEL_GATHER_VEC;
+        c.bx = sh[0];
+        c.by = sh[1];
+        rlbm_status st = batch_upload(b, c);
+        if (st != RLBM_OK) return st;
+        const int grids[] = {sms, 2 * sms, 4 * sms, 8 * sms, 16 * sms, b->ntiles};
+        for (int g : grids) {
+            g = std::min(g, b->ntiles);
+            // trial launches read the current state and overwrite only the spare buffers
+            bool ok = true;
+            for (int i = 0; i < 1 + reps && ok; ++i) {
+                if (i == 1) ok = cudaEventRecord(e0, b->stream) == cudaSuccess;
+                ok = ok && launch_batch(b->opts.dtype, b->opts.landau, c, g, b->desc[b->cur], (int)b->runs.size(),
+                                        b->ntiles, b->stream) == cudaSuccess;
+            }
+            if (!ok) {
+                cudaGetLastError();
+                continue;
+            }
+            BCUDA_TRY(b, cudaEventRecord(e1, b->stream));
+            BCUDA_TRY(b, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCUDA_TRY(b, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+                best_grid = g;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cfg = best;
+    rlbm_status st = batch_upload(b, best);
+    if (st != RLBM_OK) return st;
+    b->grid = std::min(best_grid, b->ntiles);
+    batch_drop_graphs(b);
+    if (block_x) *block_x = best.bx;
+    if (block_y) *block_y = best.by;
+    if (grid) *grid = b->grid;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_get_info(rlbm_batch_t *b, rlbm_batch_info_t *info) {
+    if (!b || !info) return RLBM_ERR_ARG;
+    info->nruns = (int)b->runs.size();
+    info->dtype = b->opts.dtype;
+    info->block_x = b->cfg.bx;
+    info->block_y = b->cfg.by;
+    info->grid = b->grid;
+    info->ntiles = b->ntiles;
+    info->step = b->step;
+    long long nodes = 0;
+    size_t bytes = 0, dev = 0;
+    for (rlbm_t *h : b->runs) {
+        nodes += (long long)h->nx * h->ny;
+        bytes += ((size_t)2 * NC * storage_bytes(h->opts.dtype) + (h->forced ? 2 * compute_bytes(h->opts.dtype) : 0)) *
+                 (size_t)h->nx * h->ny;
+        dev += h->device_bytes;
+    }
+    info->nodes = nodes;
+    info->bytes_per_step = bytes;
+    info->device_bytes = dev;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_synchronize(rlbm_batch_t *b) {
+    CHECK_BATCH(b);
+    BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_last_error(rlbm_batch_t *b, char *buf, size_t len) {
+    if (!b || !buf || len == 0) return RLBM_ERR_ARG;
+    snprintf(buf, len, "%s", b->msg.c_str());
+    return RLBM_OK;
+}
 }  // extern "C"

@@ -101,6 +101,17 @@ struct StepParams {
     int *err;         // device error word (bounded-wait / failure reporting)
 };
 
+// One lattice of an ensemble step (k_step_batch): its buffers, parameters
+// and its range in the flat tile list.
+struct BatchRun {
+    const void *qin;
+    void *qout;
+    const void *F;  // NULL: unforced
+    StepParams p;
+    int tiles_x;    // tiles along x
+    int tile0;      // first global tile index of this lattice
+};
+
 // Moments of the post-stream node (deviation form), Eq. energyMomentumIntegral
 // discretised: with f_c = W_c (eps0 + s q_c),
 //   E = eps0 + dE, dE = s sum W q;  M^a = s sum W q c^a;

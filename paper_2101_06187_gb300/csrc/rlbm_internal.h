@@ -36,6 +36,12 @@ struct LaunchCfg {
 
 cudaError_t launch_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                         const void *F, const StepParams &p, cudaStream_t s);
+// One launch of the ensemble step over `runs` (a device array of BatchRun
+// descriptors, k_step_vec.cuh) with `grid` blocks walking `ntiles` tiles.
+cudaError_t launch_batch(int dtype, int landau, const LaunchCfg &cfg, int grid, const void *runs, int nruns,
+                         int ntiles, cudaStream_t s);
+int run_length(int dtype);
+
 cudaError_t launch_moments(int dtype, int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                            double *vy, double *partials, int *bad, cudaStream_t s);
 int moments_blocks(const StepParams &p);

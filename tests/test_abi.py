@@ -79,6 +79,19 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     assert lib.rlbm_create(16, 16, 0, 0.8, None, None, None) == rl.RLBM_ERR_ARG
 
 
+def test_batch_create_rejects_invalid_members(lib):
+    import paper_2101_06187_gb300 as rl
+    out = ctypes.c_void_p()
+    good = rl.RunDesc(64, 64, 0.7, rl.Forcing(0, 0, 0.0, 0, 100))
+    odd = rl.RunDesc(66, 64, 0.7, rl.Forcing(0, 0, 0.0, 0, 100))  # nx % 4 != 0
+    arr = (rl.RunDesc * 2)(good, odd)
+    assert lib.rlbm_batch_create(2, arr, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG
+    assert lib.rlbm_batch_create(0, arr, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG
+    assert lib.rlbm_batch_create(1, None, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG
+    assert out.value is None
+    lib.rlbm_batch_destroy(None)
+
+
 def test_null_handle_calls_are_rejected(lib):
     import paper_2101_06187_gb300 as rl
     assert lib.rlbm_step(None, 1) == rl.RLBM_ERR_ARG

@@ -1,0 +1,120 @@
+"""GPU tests of the ensemble (batched) step: each member must evolve exactly
+like a lone lattice with the same parameters, match the oracle, and keep its
+state across autotuning and graph replay."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2101_06187_gb300 as rl  # noqa: E402
+
+oracle.set_threads(os.cpu_count() or 4)
+
+RUNS = [
+    dict(nx=64, ny=64, tau=0.6, forcing=dict(kmin=2, kmax=4, amp=2e-4, seed=11, redraw_period=7)),
+    dict(nx=96, ny=40, tau=0.52, forcing=dict(kmin=1, kmax=3, amp=1e-4, seed=12, redraw_period=7)),
+    dict(nx=32, ny=72, tau=0.7, forcing=dict(kmin=2, kmax=3, amp=3e-4, seed=13, redraw_period=5)),
+    dict(nx=128, ny=128, tau=0.51, forcing=None),
+    dict(nx=8, ny=8, tau=0.9, forcing=dict(kmin=1, kmax=2, amp=1e-3, seed=14, redraw_period=3)),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _fields(r, k):
+    return workloads.random_smooth(r["nx"], r["ny"], seed=500 + k, deps=0.03, vmax=0.03)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16"])
+def test_members_evolve_like_lone_lattices(dtype):
+    ens = rl.Ensemble(RUNS, dtype=dtype)
+    for k, r in enumerate(RUNS):
+        ens.init_fields(k, *_fields(r, k))
+    for n in (1, 5, 12, 3):  # chunks crossing the members' redraw epochs
+        ens.step(n)
+    for k, r in enumerate(RUNS):
+        lat = rl.Lattice(r["nx"], r["ny"], r["tau"], dtype=dtype, forcing=r["forcing"], kernel="vec")
+        lat.init_fields(*_fields(r, k))
+        lat.step(21)
+        a, b = ens.populations(k), lat.populations()
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b)), k
+        lat.close()
+    assert ens.info()["step"] == 21
+    ens.close()
+
+
+def test_members_match_oracle():
+    ens = rl.Ensemble(RUNS, dtype="f32")
+    for k, r in enumerate(RUNS):
+        ens.init_fields(k, *_fields(r, k))
+    ens.step(60)
+    for k in (0, 1, 4):
+        r = RUNS[k]
+        f = oracle.init(r["nx"], r["ny"], *_fields(r, k))
+        fz = r["forcing"]
+        oracle.run(f, r["tau"], 60, kmin=fz["kmin"], kmax=fz["kmax"], amp=fz["amp"], seed=fz["seed"],
+                   redraw=fz["redraw_period"])
+        e_o, vx_o, vy_o = oracle.fields(f)
+        e_g, vx_g, vy_g, _ = ens.moments(k)
+        err_e = np.max(np.abs(e_g - e_o)) / np.max(np.abs(e_o))
+        vn = max(np.max(np.abs(vx_o)), np.max(np.abs(vy_o)))
+        err_v = max(np.max(np.abs(vx_g - vx_o)), np.max(np.abs(vy_g - vy_o))) / vn
+        assert err_e < 1e-5 and err_v < 1e-5, (k, err_e, err_v)
+    ens.close()
+
+
+def test_autotune_and_graphs_keep_results():
+    out = []
+    for tune, graphs in ((False, False), (True, True)):
+        ens = rl.Ensemble(RUNS, dtype="f32", use_graphs=graphs)
+        for k, r in enumerate(RUNS):
+            ens.init_fields(k, *_fields(r, k))
+        ens.step(4)
+        if tune:
+            before = [ens.populations(k) for k in range(len(RUNS))]
+            bx, by, grid = ens.autotune(3)
+            assert bx * by <= 256 and grid >= 1
+            for k in range(len(RUNS)):
+                np.testing.assert_array_equal(ens.populations(k), before[k])
+        ens.step(30)
+        out.append([ens.populations(k) for k in range(len(RUNS))])
+        ens.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_ensemble_workload_shape_runs():
+    """The 64-member workload (sides 256..1024, tau in [0.51, 0.7], bands
+    around centres in [4, 12]) steps and stays physical."""
+    runs = [dict(nx=w.nx, ny=w.ny, tau=w.tau,
+                 forcing=dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw))
+            for w in workloads.ensemble()]
+    ens = rl.Ensemble(runs, dtype="f32")
+    ens.autotune(2)
+    ens.step(100)
+    info = ens.info()
+    assert info["nruns"] == 64 and info["step"] == 100
+    for k in (0, 31, 63):
+        e, vx, vy, tot = ens.moments(k)
+        assert np.all(np.isfinite(e)) and np.max(np.hypot(vx, vy)) < 0.1
+    ens.close()
+
+
+def test_bad_member_index_rejected():
+    ens = rl.Ensemble(RUNS[:2], dtype="f32")
+    with pytest.raises(rl.RLBMError):
+        ens.moments(5)
+    ens.close()
