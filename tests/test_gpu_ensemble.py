@@ -45,12 +45,15 @@ def test_members_evolve_like_lone_lattices(dtype):
         ens.init_fields(k, *_fields(r, k))
     for n in (1, 5, 12, 3):  # chunks crossing the members' redraw epochs
         ens.step(n)
+    # same per-node code in both kernels; the compiler may contract a few
+    # products differently, so FP32 agrees to rounding, not bitwise
+    tol = {"f64": 1e-13, "f32": 1e-6, "bf16": 1e-2}[dtype]
     for k, r in enumerate(RUNS):
         lat = rl.Lattice(r["nx"], r["ny"], r["tau"], dtype=dtype, forcing=r["forcing"], kernel="vec")
         lat.init_fields(*_fields(r, k))
         lat.step(21)
         a, b = ens.populations(k), lat.populations()
-        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b)), k
+        assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(b)), k
         lat.close()
     assert ens.info()["step"] == 21
     ens.close()
@@ -115,6 +118,9 @@ def test_ensemble_workload_shape_runs():
 
 def test_bad_member_index_rejected():
     ens = rl.Ensemble(RUNS[:2], dtype="f32")
+    buf = np.empty(64 * 64)
     with pytest.raises(rl.RLBMError):
-        ens.moments(5)
+        rl.rlbm_batch_moments(ens.handle, 5, buf, buf, buf, np.empty(3))
+    with pytest.raises(rl.RLBMError):
+        rl.rlbm_batch_moments(ens.handle, -1, buf, buf, buf, np.empty(3))
     ens.close()
