@@ -77,6 +77,8 @@ def _load():
                                             ctypes.c_uint64, _dp, _dp, _dp]
         lib.oracle_force_field.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_uint64, ctypes.c_uint64, _dp, _dp]
+        lib.oracle_force_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _ip, _ip, _dp, _dp]
         lib.oracle_init.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
         lib.oracle_init.restype = ctypes.c_int
         lib.oracle_step.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp]
@@ -215,6 +217,18 @@ def force_field(nx, ny, kmin, kmax, amp, seed, epoch):
     Fx = np.zeros((ny, nx))
     Fy = np.zeros((ny, nx))
     lib.oracle_force_field(nx, ny, kmin, kmax, float(amp), int(seed), int(epoch), _p(Fx), _p(Fy))
+    return Fx, Fy
+
+
+def force_points(nx, ny, kmin, kmax, amp, seed, epoch, xs, ys):
+    """The stirring force at the nodes (xs[k], ys[k]) only."""
+    lib = _load()
+    xs = np.ascontiguousarray(np.asarray(xs, dtype=np.int32))
+    ys = np.ascontiguousarray(np.asarray(ys, dtype=np.int32))
+    Fx = np.zeros(len(xs))
+    Fy = np.zeros(len(xs))
+    lib.oracle_force_points(nx, ny, kmin, kmax, float(amp), int(seed), int(epoch), len(xs), xs.ctypes.data_as(_ip),
+                            ys.ctypes.data_as(_ip), _p(Fx), _p(Fy))
     return Fx, Fy
 
 

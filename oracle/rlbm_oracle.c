@@ -460,6 +460,39 @@ void oracle_force_field(int nx, int ny, int kmin, int kmax, double amp, uint64_t
     free(th);
 }
 
+/* The same force evaluated only at the npts nodes (xs[k], ys[k]) of an nx x
+ * ny lattice (for checking large lattices point by point). */
+void oracle_force_points(int nx, int ny, int kmin, int kmax, double amp, uint64_t seed, uint64_t epoch, int npts,
+                         const int *xs, const int *ys, double *Fx, double *Fy)
+{
+    int nm = oracle_forcing_modes(kmin, kmax, NULL, NULL, 0);
+    int *kx = (int *)malloc(sizeof(int) * (nm > 0 ? nm : 1));
+    int *ky = (int *)malloc(sizeof(int) * (nm > 0 ? nm : 1));
+    double *mag = (double *)malloc(sizeof(double) * (nm > 0 ? nm : 1));
+    double *ph = (double *)malloc(sizeof(double) * (nm > 0 ? nm : 1));
+    double *th = (double *)malloc(sizeof(double) * (nm > 0 ? nm : 1));
+    oracle_forcing_modes(kmin, kmax, kx, ky, nm);
+    oracle_forcing_draw(kmin, kmax, amp, seed, epoch, mag, ph, th);
+    for (int k = 0; k < npts; ++k) {
+        double fx = 0.0, fy = 0.0;
+        for (int m = 0; m < nm; ++m) {
+            double arg = 2.0 * ORACLE_PI *
+                             ((double)wrap((long)kx[m] * xs[k], nx) / nx + (double)wrap((long)ky[m] * ys[k], ny) / ny) +
+                         ph[m];
+            double c = cos(arg);
+            fx += 2.0 * mag[m] * cos(th[m]) * c;
+            fy += 2.0 * mag[m] * sin(th[m]) * c;
+        }
+        Fx[k] = fx;
+        Fy[k] = fy;
+    }
+    free(kx);
+    free(ky);
+    free(mag);
+    free(ph);
+    free(th);
+}
+
 /* ---------------------------------------------------------------------------
  * Initialisation (step (a)): f* = f_eq(eps, u) of the initial fields.  eps,
  * vx, vy are nx*ny arrays (vx, vy the 3-velocity); NULL means eps = 1, v = 0.

@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(256) k_moments(const TS *__restrict__ qin, Ste
     if (x < p.nx && y < p.ny) {
         TC q[NC];
         gather_node<TS, TC>(qin, p, x, y, q);
-        const NodeMoments<TC> m = node_moments<TC>(q, (TC)p.scale);
-        const Frame<TL> fr = landau_solve<TL>((TL)p.eps0, (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
+        const NodeMoments<TC> m = node_moments<TC>(q, par_scale<TC>(p));
+        const Frame<TL> fr = landau_solve<TL>(par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
                                               (TL)m.dSyy);
         const long long n = (long long)y * p.nx + x;
         const bool ok = (fr.v2 < (TL)1) && (fr.eps > (TL)0) && isfinite((double)fr.eps);

@@ -130,6 +130,7 @@ static StepParams params_of(const rlbm_t *h) {
     p.eps0 = h->opts.eps0;
     p.scale = h->opts.scale;
     p.err = nullptr;
+    finish_params(p);
     return p;
 }
 

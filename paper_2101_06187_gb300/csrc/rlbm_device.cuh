@@ -98,8 +98,41 @@ struct StepParams {
     double inv_tau;   // 1/tau (Delta t = 1)
     double eps0;      // reference energy density of the deviation
     double scale;     // s
+    double inv_scale; // 1/s
+    // FP32 copies, so the FP32 kernels never touch the (slow) FP64 pipe
+    float inv_tau_f, eps0_f, scale_f, inv_scale_f;
     int *err;         // device error word (bounded-wait / failure reporting)
 };
+
+// Fill the derived fields of a StepParams from inv_tau, eps0 and scale.
+RLBM_HD inline void finish_params(StepParams &p) {
+    p.inv_scale = 1.0 / p.scale;
+    p.inv_tau_f = (float)p.inv_tau;
+    p.eps0_f = (float)p.eps0;
+    p.scale_f = (float)p.scale;
+    p.inv_scale_f = (float)p.inv_scale;
+}
+
+template <typename T>
+RLBM_HD inline T par_eps0(const StepParams &p) {
+    if constexpr (std::is_same<T, float>::value) return p.eps0_f;
+    else return p.eps0;
+}
+template <typename T>
+RLBM_HD inline T par_scale(const StepParams &p) {
+    if constexpr (std::is_same<T, float>::value) return p.scale_f;
+    else return p.scale;
+}
+template <typename T>
+RLBM_HD inline T par_inv_scale(const StepParams &p) {
+    if constexpr (std::is_same<T, float>::value) return p.inv_scale_f;
+    else return p.inv_scale;
+}
+template <typename T>
+RLBM_HD inline T par_inv_tau(const StepParams &p) {
+    if constexpr (std::is_same<T, float>::value) return p.inv_tau_f;
+    else return p.inv_tau;
+}
 
 // One lattice of an ensemble step (k_step_batch): its buffers, parameters
 // and its range in the flat tile list.
@@ -266,17 +299,17 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
 // lets each opposite pair (c, -c) share one evaluation.
 template <typename TC, typename TL, bool FORCED>
 RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
-    const TC s = (TC)p.scale;
+    const TC s = par_scale<TC>(p);
     const NodeMoments<TC> m = node_moments<TC>(q, s);
-    const Frame<TL> fr = landau_solve<TL>((TL)p.eps0, (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
+    const Frame<TL> fr = landau_solve<TL>(par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
                                           (TL)m.dSyy);
-    const TC inv_s = (TC)(1.0 / p.scale);
+    const TC inv_s = par_inv_scale<TC>(p);
     const TL eg2 = fr.eps * fr.g2;
     const TC P0 = (TC)(fr.ddelta_eps - (TL)2 * eg2 * fr.v2) * inv_s;
     const TC P1 = (TC)((TL)4 * eg2) * inv_s;
     const TC P2 = (TC)((TL)10 * eg2) * inv_s;
     const TC vx = (TC)fr.vx, vy = (TC)fr.vy;
-    const TC om = (TC)(fr.gamma * (TL)p.inv_tau);
+    const TC om = (TC)(fr.gamma * par_inv_tau<TL>(p));
 
     // even part K0 + Kxx cx^2 + Kxy cx cy + Kyy cy^2, odd part coefficients
     const TC e2 = om * (P2 - P1);
@@ -284,7 +317,7 @@ RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParam
     const TC o1 = om * (P1 - P0), o3 = om * P2;
     TC G1 = 0;
     if constexpr (FORCED) {
-        const TC E = (TC)p.eps0 + m.dE;
+        const TC E = par_eps0<TC>(p) + m.dE;
         const TC c6 = (TC)(-6.0) * inv_s;
         const TC G0 = c6 * (TC)0.25 * (Fx * m.Mx + Fy * m.My);
         G1 = c6 * (TC)(-0.5) * E;

@@ -63,6 +63,7 @@ extern "C" RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, 
     p.eps0 = eps0;
     p.scale = scale;
     p.err = nullptr;
+    rlbk::finish_params(p);
     const int nblocks = rlbk::moments_blocks(p);
     if (nblocks > kMaxBlocks) return RLBM_ERR_ARG;  // lattice exceeds the static scratch
     void *scratch = nullptr;

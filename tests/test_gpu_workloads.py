@@ -1,0 +1,148 @@
+"""The benchmark workloads at their full sizes, through the C ABI, in the
+launch configuration the benchmark uses (autotuned).
+
+* 128^2 shear wave, FP64 form, tau = 0.8: parity with the oracle over 100
+  steps; decay over 2000 steps against the linear-mode analysis; totals
+  conserved; rest state fixed.
+* 1024^2 stirred run (tau = 0.52, shell 4..6, amplitude 1e-5): 100 steps
+  against the oracle at full size, FP32 and FP64 forms.
+* 4096^2 (16-bit forms) and 8192^2 (FP32): too large for the oracle, so
+  (a) a lattice started from a field periodic with period 64 must stay an
+  exact tiling of the oracle's 64^2 run (a property that holds at any size),
+  and (b) the force field at sampled nodes must equal the oracle's force at
+  those nodes.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from linear_modes import _predict_velocity_mode
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2101_06187_gb300 as rl  # noqa: E402
+
+oracle.set_threads(os.cpu_count() or 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _errs(ref, got):
+    e_r, vx_r, vy_r = ref
+    e_g, vx_g, vy_g = got[:3]
+    err_e = np.max(np.abs(e_g - e_r)) / np.max(np.abs(e_r))
+    vn = max(np.max(np.abs(vx_r)), np.max(np.abs(vy_r)))
+    err_v = max(np.max(np.abs(vx_g - vx_r)), np.max(np.abs(vy_g - vy_r))) / vn
+    return err_e, err_v
+
+
+def _forcing(w):
+    return dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw)
+
+
+# --------------------------------------------------------------------------- 128^2 shear wave
+def test_shear_wave_128_parity_decay_conservation():
+    w = workloads.SHEAR_128
+    n = w.nx
+    eps, vx, vy = workloads.shear_wave(n, n, w.extra["u0"])
+    lat = rl.Lattice(n, n, w.tau, dtype="f64")
+    lat.autotune(5)
+    lat.init_fields(eps, vx, vy)
+    t0 = lat.moments()[3]
+    lat.step(100)
+    got = lat.moments()
+    f = oracle.init(n, n, eps, vx, vy)
+    oracle.run(f, w.tau, 100)
+    err_e, err_v = _errs(oracle.fields(f), got)
+    assert err_e < 1e-12 and err_v < 1e-12, (err_e, err_v)
+    lat.step(w.steps - 100)
+    e, vxg, vyg, t1 = lat.moments()
+    # decay of the shear mode against the linearised step (independent of both codes)
+    v, wt = oracle.stencil()
+    c0 = np.fft.fft(vx[:, 0])[1] / n
+    _, pred, _ = _predict_velocity_mode(v, wt, (0.0, 2 * np.pi / n), w.tau, w.steps, c0, 0.0)
+    sim = np.fft.fft(vxg[:, 0])[1] / n
+    assert abs(sim - pred) < 1e-4 * abs(pred), (sim, pred)
+    assert np.max(np.abs(vyg)) < 1e-12
+    assert abs(t1[0] - t0[0]) < 1e-13 * t0[0]
+    np.testing.assert_allclose(t1[1:], t0[1:], rtol=0, atol=1e-13 * t0[0])
+    lat.close()
+
+
+# --------------------------------------------------------------------------- 1024^2 stirred
+@pytest.fixture(scope="module")
+def stirred_1024_oracle():
+    w = workloads.STIRRED_1024
+    f = oracle.init(w.nx, w.ny)
+    oracle.run(f, w.tau, 100, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+    return oracle.fields(f)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-5), ("f64", 1e-12)])
+def test_stirred_1024_full_size_matches_oracle(stirred_1024_oracle, dtype, tol):
+    w = workloads.STIRRED_1024
+    lat = rl.Lattice(w.nx, w.ny, w.tau, dtype=dtype, forcing=_forcing(w))
+    lat.autotune(5)
+    lat.init_fields()
+    lat.step(100)
+    err_e, err_v = _errs(stirred_1024_oracle, lat.moments())
+    assert err_e < tol and err_v < tol, (err_e, err_v)
+    lat.close()
+
+
+# --------------------------------------------------------------------------- 4096^2 / 8192^2
+TILED_TOL = {"f32": 1e-5, "bf16": 5e-3, "f16": 5e-4}
+
+
+@pytest.fixture(scope="module")
+def tiled_reference():
+    period, tau, nsteps = 64, 0.51, 20
+    e, a, b = workloads.random_smooth(period, period, seed=77, deps=0.02, vmax=0.02)
+    f = oracle.init(period, period, e, a, b)
+    oracle.run(f, tau, nsteps)
+    return period, tau, nsteps, oracle.fields(f)
+
+
+@pytest.mark.parametrize("n,dtype", [(4096, "bf16"), (4096, "f16"), (4096, "f32"), (8192, "f32")])
+def test_full_size_lattice_stays_an_exact_tiling(tiled_reference, n, dtype):
+    period, tau, nsteps, ref = tiled_reference
+    e, a, b = workloads.random_tiled(n, n, period, seed=77, deps=0.02, vmax=0.02)
+    lat = rl.Lattice(n, n, tau, dtype=dtype)
+    lat.autotune(3)
+    lat.init_fields(e, a, b)
+    lat.step(nsteps)
+    e_g, vx_g, vy_g, _ = lat.moments()
+    lat.close()
+    rep = n // period
+    tiled = tuple(np.tile(r, (rep, rep)) for r in ref)
+    err_e, err_v = _errs(tiled, (e_g, vx_g, vy_g))
+    assert err_e < TILED_TOL[dtype] and err_v < TILED_TOL[dtype], (err_e, err_v)
+
+
+@pytest.mark.parametrize("w,dtype", [(workloads.PRECISION_4096, "bf16"), (workloads.LARGE_8192, "f32")])
+def test_full_size_force_at_sampled_nodes(w, dtype):
+    lat = rl.Lattice(w.nx, w.ny, w.tau, dtype=dtype, forcing=_forcing(w))
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([rng.integers(0, w.nx, 200), [0, w.nx - 1]])
+    ys = np.concatenate([rng.integers(0, w.ny, 200), [w.ny - 1, 0]])
+    for epoch in (0, 2):
+        lat.init_fields()
+        if epoch:
+            lat.step(epoch * w.redraw)
+        Fx, Fy = lat.force()
+        ox, oy = oracle.force_points(w.nx, w.ny, w.kmin, w.kmax, w.amp, w.seed, epoch, xs, ys)
+        scale = max(np.max(np.abs(ox)), np.max(np.abs(oy)))
+        assert np.max(np.abs(Fx[ys, xs] - ox)) < 2e-6 * scale
+        assert np.max(np.abs(Fy[ys, xs] - oy)) < 2e-6 * scale
+    lat.close()

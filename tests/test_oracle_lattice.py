@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import workloads
+from linear_modes import _linear_step, _predict_velocity_mode
 
 scipy_ndimage = pytest.importorskip("scipy.ndimage")
 
@@ -86,37 +87,6 @@ def test_forced_step_injects_FM_and_FE():
 
 
 # --------------------------------------------------------------------------- linear-mode analysis
-def _symbols(v, k):
-    """Fourier symbol of pull-streaming with bilinear interpolation, per direction."""
-    S = np.zeros(len(v), dtype=complex)
-    for i in range(len(v)):
-        sx, sy = -v[i, 0], -v[i, 1]
-        ox, oy = np.floor(sx), np.floor(sy)
-        tx, ty = sx - ox, sy - oy
-        e = lambda dx, dy: np.exp(1j * (k[0] * dx + k[1] * dy))
-        S[i] = ((1 - tx) * (1 - ty) * e(ox, oy) + tx * (1 - ty) * e(ox + 1, oy) + (1 - tx) * ty * e(ox, oy + 1)
-                + tx * ty * e(ox + 1, oy + 1))
-    return S
-
-
-def _linear_step(v, w, k, tau):
-    """Linearised step about eps = 1, u = 0: stream, then BGK towards the
-    linearised equilibrium delta f_eq,i = w_i (delta E + 3 v_i . delta M)."""
-    A = w[:, None] * (1.0 + 3.0 * v @ v.T)
-    C = np.eye(len(w)) - (np.eye(len(w)) - A) / tau
-    return C @ np.diag(_symbols(v, k))
-
-
-def _predict_velocity_mode(v, w, k, tau, nsteps, dv_x, dv_y, deps=0.0):
-    """Linear prediction of the Fourier amplitude of (eps, v) seen by the
-    next collision after nsteps, for an initial f_eq mode of amplitude
-    (deps, dv) (M = 4/3 v and v = 3/4 M at linear order, eps = 1)."""
-    df = w * (deps + 3.0 * (4.0 / 3.0) * (v[:, 0] * dv_x + v[:, 1] * dv_y))
-    fn = np.linalg.matrix_power(_linear_step(v, w, k, tau), nsteps) @ df
-    post = _symbols(v, k) * fn
-    return post.sum(), 0.75 * (v[:, 0] @ post), 0.75 * (v[:, 1] @ post)
-
-
 @pytest.mark.parametrize("tau", [0.8, 0.6])
 def test_shear_wave_matches_linear_mode_analysis(tau):
     N, nst = 32, 200
@@ -204,6 +174,16 @@ def test_force_field_spectrum_is_the_drawn_modes():
     np.testing.assert_allclose(hy, expect_y, rtol=0, atol=1e-16)
     assert np.all((mag >= 0) & (mag < amp))
     assert np.all((ph >= 0) & (ph < 2 * np.pi)) and np.all((th >= 0) & (th < 2 * np.pi))
+
+
+def test_force_points_equal_the_field():
+    nx, ny = 40, 36
+    Fx, Fy = oracle.force_field(nx, ny, 2, 5, 1e-3, 321, 4)
+    rng = np.random.default_rng(0)
+    xs, ys = rng.integers(0, nx, 50), rng.integers(0, ny, 50)
+    px, py = oracle.force_points(nx, ny, 2, 5, 1e-3, 321, 4, xs, ys)
+    np.testing.assert_array_equal(px, Fx[ys, xs])
+    np.testing.assert_array_equal(py, Fy[ys, xs])
 
 
 def test_force_redraw_changes_with_epoch_and_seed():
