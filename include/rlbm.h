@@ -81,9 +81,15 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
 /* Kernel variant of the fused step.  GATHER: one node per thread.
  * GATHER_VEC: a run of 4 nodes (2 for F64) along x per thread with 128-bit
  * (64-bit for 16-bit storage) loads and stores; needs nx divisible by that
- * run.  AUTO: the autotuned choice if one is cached for this lattice, else
- * GATHER_VEC when nx allows it, else GATHER. */
-typedef enum { RLBM_KERNEL_AUTO = 0, RLBM_KERNEL_GATHER = 1, RLBM_KERNEL_GATHER_VEC = 2 } rlbm_kernel;
+ * run.  GATHER_VEC2: a run of 2 nodes (fewer registers); needs nx even.
+ * AUTO: the autotuned choice if one is cached for this lattice, else
+ * GATHER. */
+typedef enum {
+    RLBM_KERNEL_AUTO = 0,
+    RLBM_KERNEL_GATHER = 1,
+    RLBM_KERNEL_GATHER_VEC = 2,
+    RLBM_KERNEL_GATHER_VEC2 = 3
+} rlbm_kernel;
 
 /* Stirring force (Sec. 5).  Modes are the integer wavevectors k with
  * kmin <= |k| <= kmax (k = 0 excluded), one per Hermitian pair (ky > 0, or

@@ -4,6 +4,8 @@
 // (Sec. 4).
 #include <math.h>
 
+#include <algorithm>
+
 #include "rlbm_internal.h"
 
 namespace rlbk {
@@ -187,22 +189,54 @@ cudaError_t launch_twiddles(int dtype, void *tw, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// F(x) = sum_m [a cos psi - b sin psi], psi = 2 pi (kx x/nx + ky y/ny) with
-// e^{i psi} = tw_x[(kx x) mod nx] * tw_y[(ky y) mod ny] (integer phase
-// reduction keeps the argument exact at any lattice size).
+// Per-mode phase tables: X[m][x] = e^{2 pi i kx_m x / nx} and
+// Y[m][y] = e^{2 pi i ky_m y / ny}, read from the twiddle tables with the
+// phase index reduced in integers ((k x) mod n), so the argument is exact at
+// any lattice size.  Built once per lattice.
 template <typename TC>
-__global__ void k_synth_force(TC *F, const Mode *__restrict__ modes, int nmodes, const C2<TC> *__restrict__ twx,
-                              const C2<TC> *__restrict__ twy, StepParams p) {
+__global__ void k_mode_tables(C2<TC> *X, C2<TC> *Y, const Mode *__restrict__ modes, int nmodes,
+                              const C2<TC> *__restrict__ twx, const C2<TC> *__restrict__ twy, int nx, int ny) {
+    const int m = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nmodes) return;
+    if (i < nx) {
+        const long long k = ((long long)modes[m].kx % nx + nx) % nx;
+        X[(long long)m * nx + i] = twx[(k * i) % nx];
+    }
+    if (i < ny) {
+        const long long k = ((long long)modes[m].ky % ny + ny) % ny;
+        Y[(long long)m * ny + i] = twy[(k * i) % ny];
+    }
+}
+
+cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, int nmodes, const void *twx,
+                               const void *twy, int nx, int ny, cudaStream_t s) {
+    if (nmodes <= 0) return cudaSuccess;
+    const dim3 g((std::max(nx, ny) + 255) / 256, nmodes, 1);
+    if (dtype == RLBM_F64)
+        k_mode_tables<double><<<g, 256, 0, s>>>(static_cast<C2<double> *>(X), static_cast<C2<double> *>(Y), modes,
+                                                nmodes, static_cast<const C2<double> *>(twx),
+                                                static_cast<const C2<double> *>(twy), nx, ny);
+    else
+        k_mode_tables<float><<<g, 256, 0, s>>>(static_cast<C2<float> *>(X), static_cast<C2<float> *>(Y), modes,
+                                               nmodes, static_cast<const C2<float> *>(twx),
+                                               static_cast<const C2<float> *>(twy), nx, ny);
+    return cudaGetLastError();
+}
+
+// F(x) = sum_m [a cos psi - b sin psi], psi = 2 pi (kx x/nx + ky y/ny), with
+// e^{i psi} = X[m][x] * Y[m][y].
+template <typename TC>
+__global__ void k_synth_force(TC *F, const Mode *__restrict__ modes, int nmodes, const C2<TC> *__restrict__ X,
+                              const C2<TC> *__restrict__ Y, StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     TC fx = 0, fy = 0;
     for (int m = 0; m < nmodes; ++m) {
         const Mode md = modes[m];
-        const long long kxm = ((long long)md.kx % p.nx + p.nx) % p.nx;
-        const long long kym = ((long long)md.ky % p.ny + p.ny) % p.ny;
-        const C2<TC> a = twx[(kxm * x) % p.nx];
-        const C2<TC> b = twy[(kym * y) % p.ny];
+        const C2<TC> a = X[(long long)m * p.nx + x];
+        const C2<TC> b = Y[(long long)m * p.ny + y];
         const TC cpsi = a.c * b.c - a.s * b.s;
         const TC spsi = a.s * b.c + a.c * b.s;
         fx += (TC)md.ax * cpsi - (TC)md.bx * spsi;
@@ -213,17 +247,16 @@ __global__ void k_synth_force(TC *F, const Mode *__restrict__ modes, int nmodes,
     F[p.plane + n] = fy;
 }
 
-cudaError_t launch_synth_force(int dtype, void *F, const Mode *modes, int nmodes, const void *twx, const void *twy,
+cudaError_t launch_synth_force(int dtype, void *F, const Mode *modes, int nmodes, const void *X, const void *Y,
                                const StepParams &p, cudaStream_t s) {
     dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
     if (dtype == RLBM_F64)
         k_synth_force<double><<<g, b, 0, s>>>(static_cast<double *>(F), modes, nmodes,
-                                              static_cast<const C2<double> *>(twx),
-                                              static_cast<const C2<double> *>(twy), p);
+                                              static_cast<const C2<double> *>(X), static_cast<const C2<double> *>(Y),
+                                              p);
     else
         k_synth_force<float><<<g, b, 0, s>>>(static_cast<float *>(F), modes, nmodes,
-                                             static_cast<const C2<float> *>(twx),
-                                             static_cast<const C2<float> *>(twy), p);
+                                             static_cast<const C2<float> *>(X), static_cast<const C2<float> *>(Y), p);
     return cudaGetLastError();
 }
 

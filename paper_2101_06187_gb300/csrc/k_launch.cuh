@@ -19,22 +19,38 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
     const TC *f = static_cast<const TC *>(F);
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
     const dim3 block(cfg.bx, cfg.by, 1);
-    if (cfg.kernel == RLBM_KERNEL_GATHER_VEC) {
-        constexpr int V = VecOf<TS>::V;
+    if (cfg.kernel == RLBM_KERNEL_GATHER_VEC || cfg.kernel == RLBM_KERNEL_GATHER_VEC2) {
+        constexpr int V4 = VecOf<TS>::V;
+        const int V = (cfg.kernel == RLBM_KERNEL_GATHER_VEC2) ? 2 : V4;
         if (p.nx % V != 0 || p.pitch % V != 0) return cudaErrorInvalidValue;
         const int runs = p.nx / V;
         const dim3 grid((runs + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
-        if (forced)
-            k_step_vec<TS, TC, TL, true><<<grid, block, 0, s>>>(in, out, f, p);
-        else
-            k_step_vec<TS, TC, TL, false><<<grid, block, 0, s>>>(in, out, f, p);
+        if (V == V4) {
+            if (forced)
+                k_step_vec<TS, TC, TL, true, V4><<<grid, block, 0, s>>>(in, out, f, p);
+            else
+                k_step_vec<TS, TC, TL, false, V4><<<grid, block, 0, s>>>(in, out, f, p);
+        } else if constexpr (V4 != 2) {
+            if (forced)
+                k_step_vec<TS, TC, TL, true, 2><<<grid, block, 0, s>>>(in, out, f, p);
+            else
+                k_step_vec<TS, TC, TL, false, 2><<<grid, block, 0, s>>>(in, out, f, p);
+        }
         return cudaGetLastError();
     }
     const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
-    if (forced)
-        k_step_gather<TS, TC, TL, true><<<grid, block, 0, s>>>(in, out, f, p);
-    else
-        k_step_gather<TS, TC, TL, false><<<grid, block, 0, s>>>(in, out, f, p);
+    const bool idx32 = (long long)NC * p.plane < (1ll << 31) - 1;
+    if (idx32) {
+        if (forced)
+            k_step_gather<TS, TC, TL, true, int><<<grid, block, 0, s>>>(in, out, f, p);
+        else
+            k_step_gather<TS, TC, TL, false, int><<<grid, block, 0, s>>>(in, out, f, p);
+    } else {
+        if (forced)
+            k_step_gather<TS, TC, TL, true, long long><<<grid, block, 0, s>>>(in, out, f, p);
+        else
+            k_step_gather<TS, TC, TL, false, long long><<<grid, block, 0, s>>>(in, out, f, p);
+    }
     return cudaGetLastError();
 }
 

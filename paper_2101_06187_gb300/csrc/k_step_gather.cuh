@@ -10,57 +10,60 @@
 namespace rlbk {
 
 // Gather class c at node (x, y) by bilinear pull interpolation (Sec. 3.2).
-// rows[k] / cols[k], k = 0, 1, 2, are the periodic neighbours y-1, y, y+1
-// (x-1, x, x+1); class offsets lie in {-1, 0, +1} (CFL 1).
-template <int c, typename TS, typename TC>
-__device__ __forceinline__ TC gather_class(const TS *__restrict__ plane, const long long (&rowoff)[3],
-                                           const int (&cols)[3]) {
+// rowoff[k] / cols[k], k = 0, 1, 2, are the periodic neighbours y-1, y, y+1
+// (x-1, x, x+1); class offsets lie in {-1, 0, +1} (CFL 1).  I is the index
+// type: 32-bit when 17 planes fit, so each load costs one add.
+template <int c, typename TS, typename TC, typename I>
+__device__ __forceinline__ TC gather_class(const TS *__restrict__ qin, I cbase, const I (&rowoff)[3],
+                                           const I (&cols)[3]) {
     constexpr int ox = cls_ox(c), oy = cls_oy(c);
     constexpr double tx = cls_tx(c), ty = cls_ty(c);
-    const TS *r0 = plane + rowoff[oy + 1];
-    TC v = (TC)((1.0 - tx) * (1.0 - ty)) * load_q<TS, TC>(r0 + cols[ox + 1]);
-    if constexpr (tx != 0.0) v += (TC)(tx * (1.0 - ty)) * load_q<TS, TC>(r0 + cols[ox + 2]);
+    const I r0 = cbase + rowoff[oy + 1];
+    TC v = (TC)((1.0 - tx) * (1.0 - ty)) * load_q<TS, TC>(qin + (r0 + cols[ox + 1]));
+    if constexpr (tx != 0.0) v += (TC)(tx * (1.0 - ty)) * load_q<TS, TC>(qin + (r0 + cols[ox + 2]));
     if constexpr (ty != 0.0) {
-        const TS *r1 = plane + rowoff[oy + 2];
-        v += (TC)((1.0 - tx) * ty) * load_q<TS, TC>(r1 + cols[ox + 1]);
-        if constexpr (tx != 0.0) v += (TC)(tx * ty) * load_q<TS, TC>(r1 + cols[ox + 2]);
+        const I r1 = cbase + rowoff[oy + 2];
+        v += (TC)((1.0 - tx) * ty) * load_q<TS, TC>(qin + (r1 + cols[ox + 1]));
+        if constexpr (tx != 0.0) v += (TC)(tx * ty) * load_q<TS, TC>(qin + (r1 + cols[ox + 2]));
     }
     return v;
 }
 
-template <typename TS, typename TC>
+template <typename TS, typename TC, typename I = long long>
 __device__ __forceinline__ void gather_node(const TS *__restrict__ qin, const StepParams &p, int x, int y,
                                             TC (&q)[NC]) {
     const int ym = (y == 0) ? p.ny - 1 : y - 1;
     const int yp = (y == p.ny - 1) ? 0 : y + 1;
     const int xm = (x == 0) ? p.nx - 1 : x - 1;
     const int xp = (x == p.nx - 1) ? 0 : x + 1;
-    const long long rowoff[3] = {(long long)ym * p.pitch, (long long)y * p.pitch, (long long)yp * p.pitch};
-    const int cols[3] = {xm, x, xp};
+    const I rowoff[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
+    const I cols[3] = {(I)xm, (I)x, (I)xp};
+    const I plane = (I)p.plane;
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
-        q[c] = gather_class<c, TS, TC>(qin + (long long)c * p.plane, rowoff, cols);
+        q[c] = gather_class<c, TS, TC, I>(qin, (I)c * plane, rowoff, cols);
     });
 }
 
-template <typename TS, typename TC, typename TL, bool FORCED>
+template <typename TS, typename TC, typename TL, bool FORCED, typename I>
 __global__ void __launch_bounds__(256) k_step_gather(const TS *__restrict__ qin, TS *__restrict__ qout,
                                                      const TC *__restrict__ F, StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     TC q[NC];
-    gather_node<TS, TC>(qin, p, x, y, q);
-    const long long n = (long long)y * p.pitch + x;
+    gather_node<TS, TC, I>(qin, p, x, y, q);
+    const I n = (I)y * (I)p.pitch + (I)x;
+    const I plane = (I)p.plane;
     TC Fx = 0, Fy = 0;
     if constexpr (FORCED) {
         Fx = __ldg(F + n);
-        Fy = __ldg(F + p.plane + n);
+        Fy = __ldg(F + (plane + n));
     }
     collide_node<TC, TL, FORCED>(q, Fx, Fy, p);
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
-        qout[(long long)c * p.plane + n] = to_storage<TS, TC>(q[c]);
+        qout[(I)c * plane + n] = to_storage<TS, TC>(q[c]);
     });
 }
 

@@ -11,79 +11,78 @@
 
 namespace rlbk {
 
+// Default run length per storage type (16-byte runs for FP32/FP64, 8-byte
+// runs for 16-bit storage).
 template <typename TS>
-struct VecOf;
-template <>
-struct VecOf<float> {
-    static constexpr int V = 4;
-};
-template <>
-struct VecOf<double> {
-    static constexpr int V = 2;
-};
-template <>
-struct VecOf<__nv_bfloat16> {
-    static constexpr int V = 4;
-};
-template <>
-struct VecOf<__half> {
-    static constexpr int V = 4;
+struct VecOf {
+    static constexpr int V = std::is_same<TS, double>::value ? 2 : 4;
 };
 
 // Aligned vector load of V consecutive stored values, converted to TC.
 template <typename TS, typename TC, int V>
 __device__ __forceinline__ void load_run(const TS *__restrict__ p, TC *out) {
-    if constexpr (std::is_same<TS, float>::value) {
+    if constexpr (std::is_same<TS, float>::value && V == 4) {
         const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
         out[0] = v.x;
         out[1] = v.y;
         out[2] = v.z;
         out[3] = v.w;
-    } else if constexpr (std::is_same<TS, double>::value) {
+    } else if constexpr (std::is_same<TS, float>::value && V == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        out[0] = v.x;
+        out[1] = v.y;
+    } else if constexpr (std::is_same<TS, double>::value && V == 2) {
         const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
         out[0] = v.x;
         out[1] = v.y;
-    } else if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
-        const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(p));
-        const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&raw.x);
-        const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&raw.y);
-        const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
-        out[0] = a.x;
-        out[1] = a.y;
-        out[2] = b.x;
-        out[3] = b.y;
+    } else if constexpr (std::is_same<TS, __nv_bfloat16>::value || std::is_same<TS, __half>::value) {
+        using T2 = typename std::conditional<std::is_same<TS, __half>::value, __half2, __nv_bfloat162>::type;
+        auto cvt = [](const T2 &h) -> float2 {
+            if constexpr (std::is_same<TS, __half>::value) return __half22float2(h);
+            else return __bfloat1622float2(h);
+        };
+        if constexpr (V == 4) {
+            const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(p));
+            const float2 a = cvt(*reinterpret_cast<const T2 *>(&raw.x));
+            const float2 b = cvt(*reinterpret_cast<const T2 *>(&raw.y));
+            out[0] = a.x;
+            out[1] = a.y;
+            out[2] = b.x;
+            out[3] = b.y;
+        } else {
+            const unsigned int raw = __ldg(reinterpret_cast<const unsigned int *>(p));
+            const float2 a = cvt(*reinterpret_cast<const T2 *>(&raw));
+            out[0] = a.x;
+            out[1] = a.y;
+        }
     } else {
-        const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(p));
-        const __half2 lo = *reinterpret_cast<const __half2 *>(&raw.x);
-        const __half2 hi = *reinterpret_cast<const __half2 *>(&raw.y);
-        const float2 a = __half22float2(lo), b = __half22float2(hi);
-        out[0] = a.x;
-        out[1] = a.y;
-        out[2] = b.x;
-        out[3] = b.y;
+        static_assert(V == 4 || V == 2, "unsupported run length");
     }
 }
 
 template <typename TS, typename TC, int V>
 __device__ __forceinline__ void store_run(TS *__restrict__ p, const TC *in) {
-    if constexpr (std::is_same<TS, float>::value) {
+    if constexpr (std::is_same<TS, float>::value && V == 4) {
         *reinterpret_cast<float4 *>(p) = make_float4(in[0], in[1], in[2], in[3]);
-    } else if constexpr (std::is_same<TS, double>::value) {
+    } else if constexpr (std::is_same<TS, float>::value && V == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(in[0], in[1]);
+    } else if constexpr (std::is_same<TS, double>::value && V == 2) {
         *reinterpret_cast<double2 *>(p) = make_double2(in[0], in[1]);
-    } else if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
-        const __nv_bfloat162 lo = __floats2bfloat162_rn((float)in[0], (float)in[1]);
-        const __nv_bfloat162 hi = __floats2bfloat162_rn((float)in[2], (float)in[3]);
-        uint2 raw;
-        raw.x = *reinterpret_cast<const unsigned int *>(&lo);
-        raw.y = *reinterpret_cast<const unsigned int *>(&hi);
-        *reinterpret_cast<uint2 *>(p) = raw;
-    } else {
-        const __half2 lo = __floats2half2_rn((float)in[0], (float)in[1]);
-        const __half2 hi = __floats2half2_rn((float)in[2], (float)in[3]);
-        uint2 raw;
-        raw.x = *reinterpret_cast<const unsigned int *>(&lo);
-        raw.y = *reinterpret_cast<const unsigned int *>(&hi);
-        *reinterpret_cast<uint2 *>(p) = raw;
+    } else if constexpr (std::is_same<TS, __nv_bfloat16>::value || std::is_same<TS, __half>::value) {
+        auto pack = [](float a, float b) -> unsigned int {
+            if constexpr (std::is_same<TS, __half>::value) {
+                const __half2 h = __floats2half2_rn(a, b);
+                return *reinterpret_cast<const unsigned int *>(&h);
+            } else {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                return *reinterpret_cast<const unsigned int *>(&h);
+            }
+        };
+        if constexpr (V == 4) {
+            *reinterpret_cast<uint2 *>(p) = make_uint2(pack((float)in[0], (float)in[1]), pack((float)in[2], (float)in[3]));
+        } else {
+            *reinterpret_cast<unsigned int *>(p) = pack((float)in[0], (float)in[1]);
+        }
     }
 }
 
@@ -99,10 +98,9 @@ __device__ __forceinline__ void load_class_row(const TS *__restrict__ row, int x
 }
 
 // The fused step for the run of V nodes starting at (x0, y).
-template <typename TS, typename TC, typename TL, bool FORCED>
+template <typename TS, typename TC, typename TL, bool FORCED, int V>
 __device__ __forceinline__ void step_run(const TS *__restrict__ qin, TS *__restrict__ qout, const TC *__restrict__ F,
                                          const StepParams &p, int x0, int y) {
-    constexpr int V = VecOf<TS>::V;
     const int ym = (y == 0) ? p.ny - 1 : y - 1;
     const int yp = (y == p.ny - 1) ? 0 : y + 1;
     const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
@@ -153,14 +151,13 @@ __device__ __forceinline__ void step_run(const TS *__restrict__ qin, TS *__restr
     });
 }
 
-template <typename TS, typename TC, typename TL, bool FORCED>
+template <typename TS, typename TC, typename TL, bool FORCED, int V>
 __global__ void __launch_bounds__(256) k_step_vec(const TS *__restrict__ qin, TS *__restrict__ qout,
                                                   const TC *__restrict__ F, StepParams p) {
-    constexpr int V = VecOf<TS>::V;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= p.nx || y >= p.ny) return;
-    step_run<TS, TC, TL, FORCED>(qin, qout, F, p, x0, y);
+    step_run<TS, TC, TL, FORCED, V>(qin, qout, F, p, x0, y);
 }
 
 // Ensemble of independent lattices advanced by one launch: a flat list of
@@ -186,11 +183,11 @@ __global__ void __launch_bounds__(256) k_step_batch(const BatchRun *__restrict__
         const int y = ty * blockDim.y + threadIdx.y;
         if (x0 < r.p.nx && y < r.p.ny) {
             if (r.F)
-                step_run<TS, TC, TL, true>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout),
-                                           static_cast<const TC *>(r.F), r.p, x0, y);
+                step_run<TS, TC, TL, true, V>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout),
+                                              static_cast<const TC *>(r.F), r.p, x0, y);
             else
-                step_run<TS, TC, TL, false>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout), nullptr,
-                                            r.p, x0, y);
+                step_run<TS, TC, TL, false, V>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout), nullptr,
+                                               r.p, x0, y);
         }
     }
 }

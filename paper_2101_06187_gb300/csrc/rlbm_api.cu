@@ -161,7 +161,7 @@ static rlbm_status ensure_force(rlbm_t *h) {
     const StepParams p = params_of(h);
     CUDA_TRY(h, launch_draw_modes(h->modes, h->nmodes, h->forcing.amp, (unsigned long long)h->forcing.seed,
                                   (unsigned long long)e, h->stream));
-    CUDA_TRY(h, launch_synth_force(h->opts.dtype, h->F, h->modes, h->nmodes, h->twx, h->twy, p, h->stream));
+    CUDA_TRY(h, launch_synth_force(h->opts.dtype, h->F, h->modes, h->nmodes, h->tabx, h->taby, p, h->stream));
     h->force_epoch = e;
     return RLBM_OK;
 }
@@ -213,6 +213,8 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_GATHER_VEC, 32, 4}, {RLBM_KERNEL_GATHER_VEC, 64, 2}, {RLBM_KERNEL_GATHER_VEC, 128, 1},
     {RLBM_KERNEL_GATHER_VEC, 32, 8}, {RLBM_KERNEL_GATHER_VEC, 64, 4}, {RLBM_KERNEL_GATHER_VEC, 128, 2},
     {RLBM_KERNEL_GATHER_VEC, 256, 1}, {RLBM_KERNEL_GATHER_VEC, 32, 2}, {RLBM_KERNEL_GATHER_VEC, 64, 1},
+    {RLBM_KERNEL_GATHER_VEC2, 32, 4}, {RLBM_KERNEL_GATHER_VEC2, 64, 2}, {RLBM_KERNEL_GATHER_VEC2, 128, 1},
+    {RLBM_KERNEL_GATHER_VEC2, 32, 8}, {RLBM_KERNEL_GATHER_VEC2, 64, 4}, {RLBM_KERNEL_GATHER_VEC2, 128, 2},
     {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
     {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
 };
@@ -267,6 +269,8 @@ void rlbm_destroy(rlbm_t *h) {
     if (h->F) dev_free(h, h->F, F_bytes(h));
     if (h->twx) dev_free(h, h->twx, tw_bytes(h, h->nx));
     if (h->twy) dev_free(h, h->twy, tw_bytes(h, h->ny));
+    if (h->tabx) dev_free(h, h->tabx, tw_bytes(h, h->nx) * h->nmodes);
+    if (h->taby) dev_free(h, h->taby, tw_bytes(h, h->ny) * h->nmodes);
     if (h->modes) dev_free(h, h->modes, sizeof(Mode) * h->nmodes);
     dev_free(h, h->fields, fields_bytes(h));
     dev_free(h, h->partials, partials_bytes(h));
@@ -289,8 +293,9 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (opts) o = *opts;
     if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
     if (o.landau != RLBM_LANDAU_FP64 && o.landau != RLBM_LANDAU_FP32) return RLBM_ERR_ARG;
-    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_GATHER_VEC) return RLBM_ERR_ARG;
+    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_GATHER_VEC2) return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_GATHER_VEC && nx % (o.dtype == RLBM_F64 ? 2 : 4) != 0) return RLBM_ERR_ARG;
+    if (o.kernel == RLBM_KERNEL_GATHER_VEC2 && nx % 2 != 0) return RLBM_ERR_ARG;
     if (o.eps0 == 0.0) o.eps0 = 1.0;
     if (!(o.eps0 > 0.0) || !isfinite(o.eps0)) return RLBM_ERR_ARG;
     if (o.scale == 0.0) o.scale = (o.dtype == RLBM_BF16 || o.dtype == RLBM_F16) ? 1.0 / 64.0 : 1.0;
@@ -340,10 +345,9 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         h->cfg.kernel = o.kernel;
     }
     if (!h->tuned && o.kernel == RLBM_KERNEL_AUTO) {
-        const int run = (o.dtype == RLBM_F64) ? 2 : 4;
-        h->cfg.kernel = (nx % run == 0) ? RLBM_KERNEL_GATHER_VEC : RLBM_KERNEL_GATHER;
-        h->cfg.bx = (h->cfg.kernel == RLBM_KERNEL_GATHER_VEC) ? 64 : 128;
-        h->cfg.by = (h->cfg.kernel == RLBM_KERNEL_GATHER_VEC) ? 2 : 1;
+        h->cfg.kernel = RLBM_KERNEL_GATHER;
+        h->cfg.bx = 128;
+        h->cfg.by = 2;
     }
 
     std::vector<Mode> modes;
@@ -361,7 +365,9 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         h->twx = dev_alloc(h, tw_bytes(h, nx));
         h->twy = dev_alloc(h, tw_bytes(h, ny));
         h->modes = static_cast<Mode *>(dev_alloc(h, sizeof(Mode) * h->nmodes));
-        ok = ok && h->F && h->twx && h->twy && h->modes;
+        h->tabx = dev_alloc(h, tw_bytes(h, nx) * h->nmodes);
+        h->taby = dev_alloc(h, tw_bytes(h, ny) * h->nmodes);
+        ok = ok && h->F && h->twx && h->twy && h->modes && h->tabx && h->taby;
     }
     if (!ok || cudaMallocHost(&h->host_pinned, fields_bytes(h)) != cudaSuccess) {
         cudaGetLastError();
@@ -375,6 +381,8 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
                                         h->stream);
         if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twx, nx, h->stream);
         if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twy, ny, h->stream);
+        if (e == cudaSuccess)
+            e = launch_mode_tables(o.dtype, h->tabx, h->taby, h->modes, h->nmodes, h->twx, h->twy, nx, ny, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) st = RLBM_ERR_CUDA;
     }

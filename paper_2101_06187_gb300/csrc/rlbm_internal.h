@@ -54,7 +54,9 @@ cudaError_t launch_reduce_partials(const double *partials, int nblocks, double b
 cudaError_t launch_twiddles(int dtype, void *tw, int n, cudaStream_t s);
 cudaError_t launch_draw_modes(Mode *modes, int nmodes, double amp, unsigned long long seed,
                               unsigned long long epoch, cudaStream_t s);
-cudaError_t launch_synth_force(int dtype, void *F, const Mode *modes, int nmodes, const void *twx, const void *twy,
+cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, int nmodes, const void *twx,
+                               const void *twy, int nx, int ny, cudaStream_t s);
+cudaError_t launch_synth_force(int dtype, void *F, const Mode *modes, int nmodes, const void *X, const void *Y,
                                const StepParams &p, cudaStream_t s);
 cudaError_t launch_decode_class(int dtype, const void *q, int c, const StepParams &p, double *out, cudaStream_t s);
 cudaError_t launch_encode_class(int dtype, void *q, int c, const StepParams &p, const double *in, cudaStream_t s);
@@ -85,6 +87,7 @@ struct rlbm {
     int cur = 0;                      // index of the current (post-collision) state
     void *F = nullptr;                // force field [2][ny][pitch] (compute type)
     void *twx = nullptr, *twy = nullptr;
+    void *tabx = nullptr, *taby = nullptr;  // per-mode phase tables [nmodes][nx], [nmodes][ny]
     rlbk::Mode *modes = nullptr;
     double *fields = nullptr;         // 3 * nx * ny doubles: staging for init / moments outputs
     double *partials = nullptr;       // per-block partial sums of the moments kernel

@@ -1,0 +1,91 @@
+"""Long stirred runs: time-averaged energy spectra E(k) (Sec. 4).
+
+Chaotic trajectories of different precisions decorrelate, so long runs are
+compared through time-averaged spectra over the inertial range (k below the
+driven shell), 2% per shell:
+
+* 128 x 128 against the FP64 oracle itself (4000 steps, spectra averaged
+  every 100 steps over the second half);
+* 1024 x 1024 with the stirred workload's parameters (tau = 0.52, shell
+  4..6, amplitude 1e-5): FP32 form against the FP64 form, whose every 100
+  steps are pinned to the oracle at 1e-12 by the parity tests (the oracle
+  itself cannot run 20k steps of a 1024^2 lattice in test time);
+* 1024 x 1024 with the precision workload's band (shell 8..10, tau = 0.51):
+  BF16 and FP16 deviation storage against the FP64 form.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2101_06187_gb300 as rl  # noqa: E402
+
+oracle.set_threads(os.cpu_count() or 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def gpu_mean_spectrum(n, tau, forcing, dtype, steps, start, every, nshells):
+    lat = rl.Lattice(n, n, tau, dtype=dtype, forcing=forcing)
+    lat.init_fields()
+    lat.step(start)
+    acc = np.zeros(nshells)
+    count = 0
+    for _ in range((steps - start) // every):
+        lat.step(every)
+        acc += lat.energy_spectrum(nshells)
+        count += 1
+    lat.close()
+    return acc / count
+
+
+def test_time_averaged_spectrum_matches_oracle_128():
+    n, tau, steps, start, every, nsh = 128, 0.52, 4000, 2000, 100, 12
+    fz = dict(kmin=4, kmax=6, amp=1e-4, seed=4242, redraw_period=100)
+    E_g = gpu_mean_spectrum(n, tau, fz, "f32", steps, start, every, nsh)
+    f = oracle.init(n, n)
+    oracle.run(f, tau, start, kmin=4, kmax=6, amp=1e-4, seed=4242, redraw=100)
+    acc = np.zeros(nsh)
+    cnt = 0
+    for k in range((steps - start) // every):
+        oracle.run(f, tau, every, step0=start + k * every, kmin=4, kmax=6, amp=1e-4, seed=4242, redraw=100)
+        _, vx, vy = oracle.fields(f)
+        acc += oracle.energy_spectrum(vx, vy, nsh)
+        cnt += 1
+    E_o = acc / cnt
+    rel = np.abs(E_g[1:4] - E_o[1:4]) / E_o[1:4]
+    assert np.all(rel < 0.02), rel
+
+
+def test_time_averaged_spectrum_fp32_vs_fp64_1024():
+    w = workloads.STIRRED_1024
+    fz = dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw)
+    args = (w.nx, w.tau, fz)
+    E64 = gpu_mean_spectrum(*args, "f64", 20000, 10000, 500, 8)
+    E32 = gpu_mean_spectrum(*args, "f32", 20000, 10000, 500, 8)
+    rel = np.abs(E32[1:4] - E64[1:4]) / E64[1:4]
+    assert np.all(rel < 0.02), rel
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_time_averaged_spectrum_16bit_vs_fp64_1024(dtype):
+    w = workloads.PRECISION_4096
+    fz = dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw)
+    n = 1024
+    E64 = gpu_mean_spectrum(n, w.tau, fz, "f64", 10000, 5000, 500, 10)
+    E16 = gpu_mean_spectrum(n, w.tau, fz, dtype, 10000, 5000, 500, 10)
+    rel = np.abs(E16[1:8] - E64[1:8]) / E64[1:8]
+    assert np.all(rel < 0.02), rel
