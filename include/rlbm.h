@@ -159,7 +159,9 @@ RLBM_API rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double ta
 /* Initialise with f = f_eq(eps, v) (step (a) of Sec. 3.3) from host FP64
  * fields eps (> 0) and 3-velocity vx, vy (|v| < 1), nx*ny each, row-major;
  * any NULL means eps = eps0 resp. v = 0.  Resets the step counter to 0.
- * Copies the fields through pinned staging (synchronous). */
+ * The fields are copied from the caller's memory and checked on the device;
+ * any entry with eps <= 0, |v| >= 1 or a non-finite value gives RLBM_ERR_ARG
+ * and leaves the state unchanged.  Synchronous. */
 RLBM_API rlbm_status rlbm_init_fields(rlbm_t *h, const double *eps, const double *vx, const double *vy);
 
 /* Same, from device FP64 arrays (async on the handle's stream). */

@@ -64,6 +64,23 @@ cudaError_t launch_init(int dtype, void *q, const StepParams &p, const double *e
     return cudaGetLastError();
 }
 
+// Count initial-field entries with no physical frame: eps <= 0 or not
+// finite, |v| >= 1 or not finite (any pointer may be NULL: default value).
+__global__ void k_check_fields(const double *eps, const double *vx, const double *vy, long long n, int *bad) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double e = eps ? eps[i] : 1.0;
+    const double a = vx ? vx[i] : 0.0, b = vy ? vy[i] : 0.0;
+    const bool ok = isfinite(e) && e > 0.0 && isfinite(a) && isfinite(b) && (a * a + b * b < 1.0);
+    if (!ok) atomicAdd(bad, 1);
+}
+
+cudaError_t launch_check_fields(const double *eps, const double *vx, const double *vy, long long n, int *bad,
+                                cudaStream_t s) {
+    k_check_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(eps, vx, vy, n, bad);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- conservation totals
 // Fixed-order FP64 reduction of the per-block partials: thread t sums
 // partials t, t+256, ..., then a tree over the 256 threads.

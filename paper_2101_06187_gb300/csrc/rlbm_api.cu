@@ -277,7 +277,7 @@ void rlbm_destroy(rlbm_t *h) {
     dev_free(h, h->totals, 4 * sizeof(double));
     dev_free(h, h->bad, sizeof(int) * 4);
     if (h->spec_work) dev_free(h, h->spec_work, h->spec_work_bytes);
-    if (h->host_pinned) cudaFreeHost(h->host_pinned);
+    if (h->host_small) cudaFreeHost(h->host_small);
     delete h;
 }
 
@@ -369,9 +369,9 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         h->taby = dev_alloc(h, tw_bytes(h, ny) * h->nmodes);
         ok = ok && h->F && h->twx && h->twy && h->modes && h->tabx && h->taby;
     }
-    if (!ok || cudaMallocHost(&h->host_pinned, fields_bytes(h)) != cudaSuccess) {
+    if (!ok || cudaMallocHost(&h->host_small, 4096) != cudaSuccess) {
         cudaGetLastError();
-        h->host_pinned = nullptr;
+        h->host_small = nullptr;
         rlbm_destroy(h);
         return RLBM_ERR_ALLOC;
     }
@@ -412,30 +412,25 @@ static rlbm_status init_device_impl(rlbm_t *h, const double *d_eps, const double
     return RLBM_OK;
 }
 
+// The host fields are copied straight from the caller's memory, checked on
+// the device (no host pass over the arrays), and only then turned into
+// populations, so invalid fields leave the state untouched.
 static rlbm_status init_host_impl(rlbm_t *h, const double *eps, const double *vx, const double *vy, bool keep_clock) {
     const size_t n = (size_t)h->nx * h->ny;
     const double *src[3] = {eps, vx, vy};
-    for (int k = 0; k < 3; ++k) {
-        if (!src[k]) continue;
-        for (size_t i = 0; i < n; ++i) {
-            const double a = src[k][i];
-            if (!isfinite(a) || (k == 0 && !(a > 0.0))) return fail(h, RLBM_ERR_ARG, "invalid initial field");
-        }
-    }
-    if (vx || vy)
-        for (size_t i = 0; i < n; ++i) {
-            const double a = vx ? vx[i] : 0.0, b = vy ? vy[i] : 0.0;
-            if (!(a * a + b * b < 1.0)) return fail(h, RLBM_ERR_ARG, "|v| >= 1 in initial field");
-        }
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     double *dptr[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3; ++k) {
         if (!src[k]) continue;
-        memcpy(h->host_pinned + k * n, src[k], n * sizeof(double));
         dptr[k] = h->fields + k * n;
-        CUDA_TRY(h, cudaMemcpyAsync(dptr[k], h->host_pinned + k * n, n * sizeof(double), cudaMemcpyHostToDevice,
-                                    h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(dptr[k], src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     }
+    int *bad_host = reinterpret_cast<int *>(h->host_small);
+    CUDA_TRY(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+    CUDA_TRY(h, launch_check_fields(dptr[0], dptr[1], dptr[2], (long long)n, h->bad, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(bad_host, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (*bad_host) return fail(h, RLBM_ERR_ARG, "%d initial-field entries have eps <= 0, |v| >= 1 or non-finite values",
+                               *bad_host);
     rlbm_status st = init_device_impl(h, dptr[0], dptr[1], dptr[2], keep_clock);
     if (st != RLBM_OK) return st;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -494,18 +489,17 @@ rlbm_status rlbm_moments(rlbm_t *h, double *eps, double *vx, double *vy, double 
     double *dst[3] = {eps, vx, vy};
     for (int k = 0; k < 3; ++k)
         if (dst[k])
-            CUDA_TRY(h, cudaMemcpyAsync(h->host_pinned + k * n, h->fields + k * n, n * sizeof(double),
-                                        cudaMemcpyDeviceToHost, h->stream));
-    double tot[3];
-    int bad = 0;
-    CUDA_TRY(h, cudaMemcpyAsync(&bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    if (totals) CUDA_TRY(h, cudaMemcpyAsync(tot, h->totals, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    for (int k = 0; k < 3; ++k)
-        if (dst[k]) memcpy(dst[k], h->host_pinned + k * n, n * sizeof(double));
+            CUDA_TRY(h, cudaMemcpyAsync(dst[k], h->fields + k * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                        h->stream));
+    int *bad_host = reinterpret_cast<int *>(h->host_small);
+    double *tot_host = h->host_small + 8;
+    CUDA_TRY(h, cudaMemcpyAsync(bad_host, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     if (totals)
-        for (int k = 0; k < 3; ++k) totals[k] = tot[k];
-    if (bad) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", bad);
+        CUDA_TRY(h, cudaMemcpyAsync(tot_host, h->totals, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (totals)
+        for (int k = 0; k < 3; ++k) totals[k] = tot_host[k];
+    if (*bad_host) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", *bad_host);
     return RLBM_OK;
 }
 
@@ -526,12 +520,11 @@ rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
     double *dEk = h->spec_work + spectrum_work_doubles(h->nx, h->ny);
     CUDA_TRY(h, launch_spectrum(h->fields + n, h->fields + 2 * n, h->nx, h->ny, nshells, h->spec_work, dEk,
                                 h->stream));
-    int bad = 0;
-    CUDA_TRY(h, cudaMemcpyAsync(&bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(h->host_pinned, dEk, nshells * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int *bad_host = reinterpret_cast<int *>(h->host_small);
+    CUDA_TRY(h, cudaMemcpyAsync(bad_host, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(Ek, dEk, nshells * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    memcpy(Ek, h->host_pinned, nshells * sizeof(double));
-    if (bad) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", bad);
+    if (*bad_host) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", *bad_host);
     return RLBM_OK;
 }
 
@@ -542,10 +535,8 @@ rlbm_status rlbm_get_populations(rlbm_t *h, double *f) {
     const StepParams p = params_of(h);
     for (int c = 0; c < NC; ++c) {
         CUDA_TRY(h, launch_decode_class(h->opts.dtype, h->q[h->cur], c, p, h->fields, h->stream));
-        CUDA_TRY(h, cudaMemcpyAsync(h->host_pinned, h->fields, n * sizeof(double), cudaMemcpyDeviceToHost,
-                                    h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(f + c * n, h->fields, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-        memcpy(f + c * n, h->host_pinned, n * sizeof(double));
     }
     return RLBM_OK;
 }
@@ -557,9 +548,7 @@ rlbm_status rlbm_set_populations(rlbm_t *h, const double *f) {
     const StepParams p = params_of(h);
     for (int c = 0; c < NC; ++c) {
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-        memcpy(h->host_pinned, f + c * n, n * sizeof(double));
-        CUDA_TRY(h, cudaMemcpyAsync(h->fields, h->host_pinned, n * sizeof(double), cudaMemcpyHostToDevice,
-                                    h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(h->fields, f + c * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         CUDA_TRY(h, launch_encode_class(h->opts.dtype, h->q[h->cur], c, p, h->fields, h->stream));
     }
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -581,10 +570,8 @@ rlbm_status rlbm_get_force(rlbm_t *h, double *Fx, double *Fy) {
     for (int k = 0; k < 2; ++k) {
         if (!dst[k]) continue;
         CUDA_TRY(h, launch_force_to_f64(h->opts.dtype, h->F, k, p, h->fields, h->stream));
-        CUDA_TRY(h, cudaMemcpyAsync(h->host_pinned, h->fields, n * sizeof(double), cudaMemcpyDeviceToHost,
-                                    h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(dst[k], h->fields, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-        memcpy(dst[k], h->host_pinned, n * sizeof(double));
     }
     return RLBM_OK;
 }

@@ -49,6 +49,8 @@ int moments_blocks(const StepParams &p);
 // Auxiliary kernels (k_aux.cu).
 cudaError_t launch_init(int dtype, void *q, const StepParams &p, const double *eps, const double *vx,
                         const double *vy, cudaStream_t s);
+cudaError_t launch_check_fields(const double *eps, const double *vx, const double *vy, long long n, int *bad,
+                                cudaStream_t s);
 cudaError_t launch_reduce_partials(const double *partials, int nblocks, double base_E, double *totals,
                                    cudaStream_t s);
 cudaError_t launch_twiddles(int dtype, void *tw, int n, cudaStream_t s);
@@ -95,7 +97,7 @@ struct rlbm {
     int *bad = nullptr;               // device counter of failed nodes
     double *spec_work = nullptr;      // spectrum work area
     size_t spec_work_bytes = 0;
-    double *host_pinned = nullptr;    // pinned staging, 3 * nx * ny doubles
+    double *host_small = nullptr;     // small pinned buffer for counters and totals
     size_t device_bytes = 0;
 
     long long step = 0;

@@ -68,6 +68,10 @@ def test_shear_wave_128_parity_decay_conservation():
     assert err_e < 1e-12 and err_v < 1e-12, (err_e, err_v)
     lat.step(w.steps - 100)
     e, vxg, vyg, t1 = lat.moments()
+    # the whole 2000-step run against the oracle (round-off accumulates over 20x the steps)
+    oracle.run(f, w.tau, w.steps - 100, step0=100)
+    err_e, err_v = _errs(oracle.fields(f), (e, vxg, vyg))
+    assert err_e < 1e-11 and err_v < 1e-11, (err_e, err_v)
     # decay of the shear mode against the linearised step (independent of both codes)
     v, wt = oracle.stencil()
     c0 = np.fft.fft(vx[:, 0])[1] / n
@@ -75,7 +79,7 @@ def test_shear_wave_128_parity_decay_conservation():
     sim = np.fft.fft(vxg[:, 0])[1] / n
     assert abs(sim - pred) < 1e-4 * abs(pred), (sim, pred)
     # v_y stays at the second-order level (the shear wave drives y-motion only through O(u0^2) terms)
-    assert np.max(np.abs(vyg)) < 1e-5 * np.max(np.abs(vxg))
+    assert np.max(np.abs(vyg)) < w.extra["u0"] ** 2
     assert abs(t1[0] - t0[0]) < 1e-13 * t0[0]
     np.testing.assert_allclose(t1[1:], t0[1:], rtol=0, atol=1e-13 * t0[0])
     lat.close()
