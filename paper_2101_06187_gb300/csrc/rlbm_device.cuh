@@ -217,13 +217,18 @@ RLBM_HD inline T recip(T x) {
 // Landau-Lifshitz frame (the eigenvalue problem closing Sec. 3.2):
 // T^{mu nu} u_nu = -eps u^mu.  With v = u/u^0 and delta = E - eps this is
 //   (S + eps I) v = M,  delta = M . v.
-// In deviation variables S + eps I = a I + dS with a = 4 eps0/3 + dE - delta
-// (the z row decouples: M_z = S_xz = S_yz = 0, so v_z = 0).  Newton on
-//   g(delta) = delta - M . (aI + dS)^{-1} M,   g'(delta) = 1 - |v|^2,
-// from delta = 0.  g is increasing and concave (g'' = -2 v.(aI + dS)^{-1} v),
-// and g(0) <= 0, so Newton from delta = 0 rises monotonically onto the
-// physical root (eps > 0, |v| < 1).  Three unrolled steps reach FP32
-// round-off for |v| <~ 0.1; further steps run only where needed.
+// In deviation variables S + eps I = A0 - delta I with A0 = (4 eps0/3 + dE) I
+// + dS (the z row decouples: M_z = S_xz = S_yz = 0, so v_z = 0).  Newton on
+//   g(delta) = delta - M . (A0 - delta I)^{-1} M,   g'(delta) = 1 - |v|^2.
+// g is increasing and concave (g'' = -2 v.(A0 - delta I)^{-1} v), so Newton
+// from below rises monotonically onto the physical root (eps > 0, |v| < 1).
+// Start: expanding (A0 - delta I)^{-1} in delta gives delta = m1 + m2 delta +
+// O(delta^2) with m1 = M.A0^{-1}M, m2 = |A0^{-1}M|^2, so delta0 = m1/(1 - m2)
+// is already second-order accurate; one Newton step then reaches FP32
+// round-off for typical |v| and further steps run only where needed.  The
+// iterations use fast reciprocals (Newton corrects them); the final frame
+// uses correctly rounded ones, because the equilibrium must carry the
+// frame's energy-momentum to round-off or the collision stops conserving.
 template <typename TL>
 struct Frame {
     TL ddelta_eps;  // eps - eps0 = dE - delta
@@ -233,43 +238,54 @@ struct Frame {
     TL gamma;
 };
 
+template <typename T>
+RLBM_HD inline T fast_recip(T x) {
+#ifdef __CUDA_ARCH__
+    if constexpr (std::is_same<T, float>::value) return __fdividef(1.0f, x);
+#endif
+    return (T)1 / x;
+}
+
 template <typename TL>
 RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL dSxy, TL dSyy) {
     const TL a0 = (TL)(4.0 / 3.0) * eps0 + dE;
-    TL delta = 0, vx = 0, vy = 0;
     constexpr bool dbl = std::is_same<TL, double>::value;
     const TL tol = dbl ? (TL)4e-16 : (TL)1e-7;
-    auto velocity = [&](TL d) {
+    TL vx, vy;
+    auto velocity = [&](TL d, bool exact) {
         const TL a = a0 - d;
         const TL axx = a + dSxx, ayy = a + dSyy;
-        const TL inv_det = recip<TL>(axx * ayy - dSxy * dSxy);
+        const TL det = axx * ayy - dSxy * dSxy;
+        const TL inv_det = exact ? recip<TL>(det) : fast_recip<TL>(det);
         vx = (ayy * Mx - dSxy * My) * inv_det;
         vy = (axx * My - dSxy * Mx) * inv_det;
     };
-    auto newton = [&]() -> TL {
-        velocity(delta);
+    velocity((TL)0, false);
+    const TL m1 = Mx * vx + My * vy;
+    const TL m2 = vx * vx + vy * vy;
+    TL delta = m1 * fast_recip<TL>((TL)1 - m2);
+    TL step;
+    auto newton = [&]() {
+        velocity(delta, false);
         const TL g = delta - (Mx * vx + My * vy);
         const TL gp = (TL)1 - (vx * vx + vy * vy);
-        const TL step = g * recip<TL>(gp);
+        step = g * fast_recip<TL>(gp);
         delta -= step;
-        return step;
     };
     newton();
-    newton();
-    TL step = newton();
-    for (int it = 3; it < (dbl ? 24 : 12); ++it) {
-        if (!(absval(step) > tol * absval(delta))) break;  // also exits on NaN
-        step = newton();
+    // near the root the error after a step is ~ step^2 |v|^2 / a0, so the
+    // iteration has converged once step^2 <= tol |delta| (exits on NaN too)
+    for (int it = 1; it < (dbl ? 24 : 12); ++it) {
+        if (!(step * step > tol * absval(delta))) break;
+        newton();
     }
-    velocity(delta);
+    velocity(delta, true);
     Frame<TL> fr;
     fr.ddelta_eps = dE - delta;
     fr.eps = eps0 + fr.ddelta_eps;
     fr.vx = vx;
     fr.vy = vy;
     fr.v2 = vx * vx + vy * vy;
-    // correctly rounded 1/(1 - v^2) and sqrt: the equilibrium must carry the
-    // frame's energy-momentum to round-off, or the collision stops conserving
     fr.g2 = recip<TL>((TL)1 - fr.v2);
     fr.gamma = std::sqrt(fr.g2);
     return fr;
