@@ -288,6 +288,22 @@ def e2e_glups(rl, w, n, form, landau, reps=3, steps_per_call=100):
             "steps_per_call": steps_per_call}
 
 
+def aggregate_replicas(torch, local_seconds, local_updates, world):
+    """Whole-job figures of independent replicas: the timed region ends when
+    the slowest rank ends (max over ranks), and every rank's lattice updates
+    count.  Returns (max seconds, total GLUPS)."""
+    if world > 1:
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+        u = torch.tensor([float(local_updates)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.barrier()
+        return float(t.item()), float(u.item()) / float(t.item()) / 1e9
+    return local_seconds, local_updates / local_seconds / 1e9
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
@@ -364,14 +380,8 @@ def main():
                                                     tune=not args.no_tune)
     torch.cuda.synchronize()
     step_ms = float(ms.mean())
-    total_s = float(ms.sum()) / 1e3
     nodes = n * n
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-        torch.distributed.barrier()
-    glups_total = world * nodes * K / total_s / 1e9
+    total_s, glups_total = aggregate_replicas(torch, float(ms.sum()) / 1e3, nodes * K, world)
 
     hbm_peak, peak_kind = load_peaks()
     bpn = int(info["bytes_per_node"])

@@ -189,6 +189,27 @@ RLBM_API rlbm_status rlbm_moments_device(rlbm_t *h, double *d_eps, double *d_vx,
  * Ek is a host array of nshells doubles.  Synchronises. */
 RLBM_API rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek);
 
+/* Filtered RMS velocity (Sec. 5: the recorded velocities are filtered to
+ * remove the driven band): sqrt of the lattice mean of |v_f|^2, where v_f
+ * keeps only the Fourier modes of the 3-velocity with |k| < kf (signed
+ * integer wavenumbers; kf = the lower edge of the driven band).  Computed on
+ * the device from the same transform as rlbm_energy_spectrum (Parseval).
+ * Synchronises. */
+RLBM_API rlbm_status rlbm_filtered_velocity(rlbm_t *h, double kf, double *rms);
+
+/* Time statistics of E(k) (App. C): rlbm_spectrum_sample adds the current
+ * spectrum (nshells shells, as rlbm_energy_spectrum) to per-shell running
+ * sums of E and E^2 kept on the device -- async, no host round trip, so a
+ * long run can sample every N steps, N beyond the decorrelation time.
+ * rlbm_spectrum_stats returns the time mean, the standard error of the mean
+ * (sample standard deviation / sqrt(count); the reading of App. C's error
+ * estimate for decorrelated samples) and the sample count (any output may
+ * be NULL; synchronises).  rlbm_spectrum_reset clears the record.  All
+ * samples of a record use the same nshells (else RLBM_ERR_STATE). */
+RLBM_API rlbm_status rlbm_spectrum_sample(rlbm_t *h, int nshells);
+RLBM_API rlbm_status rlbm_spectrum_stats(rlbm_t *h, int nshells, double *mean, double *sem, int *count);
+RLBM_API rlbm_status rlbm_spectrum_reset(rlbm_t *h);
+
 /* Decoded populations f_c = W_c (eps0 + s q_c) of the 17 stored classes,
  * host FP64 [17][ny][nx] (class order: rest; (1,0),(-1,0),(0,1),(0,-1);
  * (a,0),(-a,0),(0,a),(0,-a); (a,a),(-a,a),(a,-a),(-a,-a);

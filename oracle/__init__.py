@@ -316,6 +316,21 @@ def energy_spectrum(vx, vy, nshells: int) -> np.ndarray:
     return E
 
 
+def filtered_velocity_rms(vx, vy, kf: float) -> float:
+    """RMS of the 3-velocity after removing the driven band (Sec. 5): keep
+    the Fourier modes with |k| < kf (signed integer wavenumbers), transform
+    back, and take sqrt(mean |v|^2) over the lattice."""
+    vx = np.asarray(vx, dtype=np.float64)
+    vy = np.asarray(vy, dtype=np.float64)
+    ny, nx = vx.shape
+    kx = np.fft.fftfreq(nx, d=1.0 / nx)
+    ky = np.fft.fftfreq(ny, d=1.0 / ny)
+    keep = (kx[None, :] ** 2 + ky[:, None] ** 2) < kf * kf
+    fx = np.real(np.fft.ifft2(np.fft.fft2(vx) * keep))
+    fy = np.real(np.fft.ifft2(np.fft.fft2(vy) * keep))
+    return float(np.sqrt(np.mean(fx * fx + fy * fy)))
+
+
 def merge_classes(f) -> np.ndarray:
     """Sum the z-mirror pairs of the 26 directions into the 17 in-plane classes.
 

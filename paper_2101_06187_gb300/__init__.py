@@ -38,7 +38,8 @@ EXPORTS = (
     "rlbm_get_info", "rlbm_autotune", "rlbm_moments_static", "rlbm_synchronize", "rlbm_last_error", "rlbm_destroy",
     "rlbm_status_string", "rlbm_batch_create", "rlbm_batch_init_fields", "rlbm_batch_step", "rlbm_batch_moments",
     "rlbm_batch_energy_spectrum", "rlbm_batch_get_populations", "rlbm_batch_autotune", "rlbm_batch_get_info",
-    "rlbm_batch_synchronize", "rlbm_batch_last_error", "rlbm_batch_destroy",
+    "rlbm_batch_synchronize", "rlbm_batch_last_error", "rlbm_batch_destroy", "rlbm_filtered_velocity",
+    "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset",
 )
 
 
@@ -116,6 +117,12 @@ def _load():
                                             ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.rlbm_moments_static.restype = ctypes.c_int
+        lib.rlbm_filtered_velocity.argtypes = [h, ctypes.c_double, _dp]
+        lib.rlbm_spectrum_sample.argtypes = [h, ctypes.c_int]
+        lib.rlbm_spectrum_stats.argtypes = [h, ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_int)]
+        lib.rlbm_spectrum_reset.argtypes = [h]
+        for name in ("rlbm_filtered_velocity", "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset"):
+            getattr(lib, name).restype = ctypes.c_int
         b = ctypes.c_void_p
         ip = ctypes.POINTER(ctypes.c_int)
         lib.rlbm_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(RunDesc), ctypes.POINTER(Opts),
@@ -251,6 +258,27 @@ def rlbm_moments_device(h, d_eps: int = 0, d_vx: int = 0, d_vy: int = 0, d_total
 
 def rlbm_energy_spectrum(h, nshells: int, Ek):
     _check(h, _load().rlbm_energy_spectrum(h, int(nshells), _p(Ek)), "rlbm_energy_spectrum")
+
+
+def rlbm_filtered_velocity(h, kf: float) -> float:
+    rms = np.zeros(1)
+    _check(h, _load().rlbm_filtered_velocity(h, float(kf), _p(rms)), "rlbm_filtered_velocity")
+    return float(rms[0])
+
+
+def rlbm_spectrum_sample(h, nshells: int):
+    _check(h, _load().rlbm_spectrum_sample(h, int(nshells)), "rlbm_spectrum_sample")
+
+
+def rlbm_spectrum_stats(h, nshells: int):
+    mean, sem, cnt = np.empty(int(nshells)), np.empty(int(nshells)), ctypes.c_int()
+    _check(h, _load().rlbm_spectrum_stats(h, int(nshells), _p(mean), _p(sem), ctypes.byref(cnt)),
+           "rlbm_spectrum_stats")
+    return mean, sem, cnt.value
+
+
+def rlbm_spectrum_reset(h):
+    _check(h, _load().rlbm_spectrum_reset(h), "rlbm_spectrum_reset")
 
 
 def rlbm_get_populations(h, f):
@@ -470,6 +498,20 @@ class Lattice:
         E = np.empty(int(nshells))
         rlbm_energy_spectrum(self.handle, nshells, E)
         return E
+
+    def filtered_velocity(self, kf: float) -> float:
+        """RMS velocity with the modes |k| >= kf removed (Sec. 5)."""
+        return rlbm_filtered_velocity(self.handle, kf)
+
+    def spectrum_sample(self, nshells: int):
+        rlbm_spectrum_sample(self.handle, nshells)
+
+    def spectrum_stats(self, nshells: int):
+        """(mean E(k), standard error of the mean, sample count)."""
+        return rlbm_spectrum_stats(self.handle, nshells)
+
+    def spectrum_reset(self):
+        rlbm_spectrum_reset(self.handle)
 
     def populations(self) -> np.ndarray:
         f = np.empty((NCLASSES, self.ny, self.nx))

@@ -419,6 +419,41 @@ __global__ void k_shell_bin(const Z2 *z, int nx, int ny, int nshells, double *Ek
         if (hist[i] != 0.0) atomicAdd(&Ek[i], hist[i]);
 }
 
+// Sum of |Z(k)|^2 over the modes with |k| < kf (signed integer wavenumbers).
+__global__ void k_band_sum(const Z2 *z, int nx, int ny, double kf, double *out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    const long long count = (long long)nx * ny;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int jy = (int)(i / nx), jx = (int)(i % nx);
+        const double kx = (jx < (nx + 1) / 2) ? jx : jx - nx;
+        const double ky = (jy < (ny + 1) / 2) ? jy : jy - ny;
+        if (kx * kx + ky * ky < kf * kf) acc += z[i].re * z[i].re + z[i].im * z[i].im;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+// Per-shell running sums of E and E^2 for time statistics of the spectrum.
+__global__ void k_accumulate(const double *E, int n, double *sum, double *sq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        sum[i] += E[i];
+        sq[i] += E[i] * E[i];
+    }
+}
+
+cudaError_t launch_accumulate(const double *E, int n, double *sum, double *sq, cudaStream_t s) {
+    k_accumulate<<<(n + 255) / 256, 256, 0, s>>>(E, n, sum, sq);
+    return cudaGetLastError();
+}
+
 __global__ void k_scale(double *a, int n, double f) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] *= f;
@@ -449,8 +484,7 @@ static cudaError_t transform_lines(Z2 *z, int n, int lines, long long es, long l
     return cudaGetLastError();
 }
 
-cudaError_t launch_spectrum(const double *vx, const double *vy, int nx, int ny, int nshells, double *work,
-                            double *Ek, cudaStream_t s) {
+static cudaError_t transform_2d(const double *vx, const double *vy, int nx, int ny, double *work, cudaStream_t s) {
     Z2 *z = reinterpret_cast<Z2 *>(work);
     Z2 *wx = z + (size_t)nx * ny;
     Z2 *wy = wx + nx;
@@ -458,7 +492,29 @@ cudaError_t launch_spectrum(const double *vx, const double *vy, int nx, int ny, 
     k_pack_z<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(vx, vy, z, count);
     cudaError_t e = transform_lines(z, nx, ny, 1, nx, wx, s);  // rows
     if (e != cudaSuccess) return e;
-    e = transform_lines(z, ny, nx, nx, 1, wy, s);  // columns
+    return transform_lines(z, ny, nx, nx, 1, wy, s);  // columns
+}
+
+// Mean square of the velocity with every mode |k| >= kf removed:
+// <|v_f|^2> = sum_{|k| < kf} |v_hat(k)|^2 = sum_{|k| < kf} |Z(k)|^2 / (nx ny)^2
+// (the set |k| < kf is symmetric under k -> -k, as for the shells).
+cudaError_t launch_band_power(const double *vx, const double *vy, int nx, int ny, double kf, double *work,
+                              double *out, cudaStream_t s) {
+    cudaError_t e = transform_2d(vx, vy, nx, ny, work, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    k_band_sum<<<304, 256, 0, s>>>(reinterpret_cast<const Z2 *>(work), nx, ny, kf, out);
+    const double count = (double)nx * ny;
+    k_scale<<<1, 32, 0, s>>>(out, 1, 1.0 / (count * count));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum(const double *vx, const double *vy, int nx, int ny, int nshells, double *work,
+                            double *Ek, cudaStream_t s) {
+    Z2 *z = reinterpret_cast<Z2 *>(work);
+    const long long count = (long long)nx * ny;
+    cudaError_t e = transform_2d(vx, vy, nx, ny, work, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(Ek, 0, sizeof(double) * nshells, s);
     if (e != cudaSuccess) return e;

@@ -2,6 +2,8 @@
 // life cycle, device memory, the step loop (direct launches or CUDA-graph
 // replay), diagnostics.
 #include <math.h>
+
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -207,6 +209,19 @@ static rlbm_status run_chunk(rlbm_t *h, int n) {
     return RLBM_OK;
 }
 
+// The spectrum work area (complex lattice + twiddles + shell sums), made on
+// first use.
+static rlbm_status ensure_spectrum_work(rlbm_t *h) {
+    if (std::max(h->nx, h->ny) > 8192) return fail(h, RLBM_ERR_ARG, "spectra support lattice sides up to 8192");
+    if (!h->spec_work) {
+        const size_t need = spectrum_work_doubles(h->nx, h->ny) * sizeof(double) + 4096 * sizeof(double);
+        h->spec_work = static_cast<double *>(dev_alloc(h, need));
+        if (!h->spec_work) return fail(h, RLBM_ERR_ALLOC, "spectrum work area");
+        h->spec_work_bytes = need;
+    }
+    return RLBM_OK;
+}
+
 // Launch configurations tried by rlbm_autotune, and the winners per
 // (nx, ny, dtype, landau, forced), shared by all handles of the process.
 static const LaunchCfg kCandidates[] = {
@@ -277,6 +292,7 @@ void rlbm_destroy(rlbm_t *h) {
     dev_free(h, h->totals, 4 * sizeof(double));
     dev_free(h, h->bad, sizeof(int) * 4);
     if (h->spec_work) dev_free(h, h->spec_work, h->spec_work_bytes);
+    if (h->spec_acc) dev_free(h, h->spec_acc, 2 * 4096 * sizeof(double));
     if (h->host_small) cudaFreeHost(h->host_small);
     delete h;
 }
@@ -506,14 +522,8 @@ rlbm_status rlbm_moments(rlbm_t *h, double *eps, double *vx, double *vy, double 
 rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
     CHECK_HANDLE(h);
     if (nshells < 1 || nshells > 4096 || !Ek) return fail(h, RLBM_ERR_ARG, "nshells must be in [1, 4096]");
-    const int big = std::max(h->nx, h->ny);
-    if (big > 8192) return fail(h, RLBM_ERR_ARG, "spectrum supports lattice sides up to 8192");
-    const size_t need = spectrum_work_doubles(h->nx, h->ny) * sizeof(double) + 4096 * sizeof(double);
-    if (!h->spec_work) {
-        h->spec_work = static_cast<double *>(dev_alloc(h, need));
-        if (!h->spec_work) return fail(h, RLBM_ERR_ALLOC, "spectrum work area");
-        h->spec_work_bytes = need;
-    }
+    rlbm_status st0 = ensure_spectrum_work(h);
+    if (st0 != RLBM_OK) return st0;
     const size_t n = (size_t)h->nx * h->ny;
     rlbm_status st = rlbm_moments_device(h, nullptr, h->fields + n, h->fields + 2 * n, nullptr);
     if (st != RLBM_OK) return st;
@@ -525,6 +535,82 @@ rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
     CUDA_TRY(h, cudaMemcpyAsync(Ek, dEk, nshells * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     if (*bad_host) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", *bad_host);
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_filtered_velocity(rlbm_t *h, double kf, double *rms) {
+    CHECK_HANDLE(h);
+    if (!rms || !(kf >= 0.0)) return fail(h, RLBM_ERR_ARG, "kf must be >= 0 and rms non-NULL");
+    rlbm_status st = ensure_spectrum_work(h);
+    if (st != RLBM_OK) return st;
+    const size_t n = (size_t)h->nx * h->ny;
+    st = rlbm_moments_device(h, nullptr, h->fields + n, h->fields + 2 * n, nullptr);
+    if (st != RLBM_OK) return st;
+    double *dout = h->spec_work + spectrum_work_doubles(h->nx, h->ny);
+    CUDA_TRY(h, launch_band_power(h->fields + n, h->fields + 2 * n, h->nx, h->ny, kf, h->spec_work, dout, h->stream));
+    double *host = h->host_small + 16;
+    int *bad_host = reinterpret_cast<int *>(h->host_small);
+    CUDA_TRY(h, cudaMemcpyAsync(host, dout, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(bad_host, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (*bad_host) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", *bad_host);
+    *rms = std::sqrt(*host);
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_spectrum_reset(rlbm_t *h) {
+    CHECK_HANDLE(h);
+    if (h->spec_acc) CUDA_TRY(h, cudaMemsetAsync(h->spec_acc, 0, 2 * 4096 * sizeof(double), h->stream));
+    h->spec_count = 0;
+    h->spec_nshells = 0;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_spectrum_sample(rlbm_t *h, int nshells) {
+    CHECK_HANDLE(h);
+    if (nshells < 1 || nshells > 4096) return fail(h, RLBM_ERR_ARG, "nshells must be in [1, 4096]");
+    if (h->spec_count > 0 && nshells != h->spec_nshells)
+        return fail(h, RLBM_ERR_STATE, "sampling %d shells into a record of %d (reset first)", nshells,
+                    h->spec_nshells);
+    rlbm_status st = ensure_spectrum_work(h);
+    if (st != RLBM_OK) return st;
+    if (!h->spec_acc) {
+        h->spec_acc = static_cast<double *>(dev_alloc(h, 2 * 4096 * sizeof(double)));
+        if (!h->spec_acc) return fail(h, RLBM_ERR_ALLOC, "spectrum accumulators");
+        CUDA_TRY(h, cudaMemsetAsync(h->spec_acc, 0, 2 * 4096 * sizeof(double), h->stream));
+    }
+    const size_t n = (size_t)h->nx * h->ny;
+    st = rlbm_moments_device(h, nullptr, h->fields + n, h->fields + 2 * n, nullptr);
+    if (st != RLBM_OK) return st;
+    double *dEk = h->spec_work + spectrum_work_doubles(h->nx, h->ny);
+    CUDA_TRY(h, launch_spectrum(h->fields + n, h->fields + 2 * n, h->nx, h->ny, nshells, h->spec_work, dEk,
+                                h->stream));
+    CUDA_TRY(h, launch_accumulate(dEk, nshells, h->spec_acc, h->spec_acc + 4096, h->stream));
+    h->spec_count += 1;
+    h->spec_nshells = nshells;
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_spectrum_stats(rlbm_t *h, int nshells, double *mean, double *sem, int *count) {
+    CHECK_HANDLE(h);
+    if (count) *count = h->spec_count;
+    if (h->spec_count == 0) return fail(h, RLBM_ERR_STATE, "no spectrum samples");
+    if (nshells < 1 || nshells > h->spec_nshells) return fail(h, RLBM_ERR_ARG, "nshells out of range");
+    std::vector<double> sum(nshells), sq(nshells);
+    CUDA_TRY(h, cudaMemcpyAsync(sum.data(), h->spec_acc, nshells * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(sq.data(), h->spec_acc + 4096, nshells * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    const double m = (double)h->spec_count;
+    for (int i = 0; i < nshells; ++i) {
+        const double mu = sum[i] / m;
+        if (mean) mean[i] = mu;
+        if (sem) {
+            const double var = (m > 1) ? std::max(0.0, (sq[i] - m * mu * mu) / (m - 1)) : 0.0;
+            sem[i] = std::sqrt(var / m);
+        }
+    }
     return RLBM_OK;
 }
 

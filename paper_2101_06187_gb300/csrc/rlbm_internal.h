@@ -67,6 +67,9 @@ cudaError_t launch_force_to_f64(int dtype, const void *F, int comp, const StepPa
 cudaError_t launch_spectrum(const double *vx, const double *vy, int nx, int ny, int nshells, double *work,
                             double *Ek, cudaStream_t s);
 size_t spectrum_work_doubles(int nx, int ny);
+cudaError_t launch_band_power(const double *vx, const double *vy, int nx, int ny, double kf, double *work,
+                              double *out, cudaStream_t s);
+cudaError_t launch_accumulate(const double *E, int n, double *sum, double *sq, cudaStream_t s);
 
 size_t storage_bytes(int dtype);
 size_t compute_bytes(int dtype);
@@ -97,6 +100,8 @@ struct rlbm {
     int *bad = nullptr;               // device counter of failed nodes
     double *spec_work = nullptr;      // spectrum work area
     size_t spec_work_bytes = 0;
+    double *spec_acc = nullptr;       // running sums of E and E^2 per shell (2 x 4096)
+    int spec_count = 0, spec_nshells = 0;
     double *host_small = nullptr;     // small pinned buffer for counters and totals
     size_t device_bytes = 0;
 

@@ -240,3 +240,42 @@ def test_energy_spectrum_non_power_of_two_side():
     E_o = oracle.energy_spectrum(ref[1], ref[2], 30)
     np.testing.assert_allclose(E_g, E_o, rtol=1e-10, atol=1e-24)
     lat.close()
+
+
+def test_filtered_velocity_matches_oracle():
+    nx, ny = 64, 48
+    fields = workloads.random_smooth(nx, ny, seed=31, vmax=0.05)
+    forcing = dict(kmin=4, kmax=6, amp=2e-4, seed=5, redraw_period=10)
+    lat, f, ref, got = run_pair(nx, ny, 0.6, 25, "f64", fields, forcing)
+    for kf in (0.5, 2.0, 4.0, 30.0):
+        r_g = lat.filtered_velocity(kf)
+        r_o = oracle.filtered_velocity_rms(ref[1], ref[2], kf)
+        assert abs(r_g - r_o) <= 1e-12 * max(r_o, 1e-300) + 1e-300, (kf, r_g, r_o)
+    lat.close()
+
+
+def test_spectrum_statistics_match_oracle_samples():
+    n, nsh, every, samples = 64, 12, 10, 6
+    fields = workloads.random_smooth(n, n, seed=41, vmax=0.05)
+    forcing = dict(kmin=3, kmax=5, amp=3e-4, seed=9, redraw_period=20)
+    lat = rl.Lattice(n, n, 0.6, dtype="f64", forcing=forcing)
+    lat.init_fields(*fields)
+    f = oracle.init(n, n, *fields)
+    es = []
+    for k in range(samples):
+        lat.step(every)
+        lat.spectrum_sample(nsh)
+        oracle.run(f, 0.6, every, step0=k * every, kmin=3, kmax=5, amp=3e-4, seed=9, redraw=20)
+        _, vx, vy = oracle.fields(f)
+        es.append(oracle.energy_spectrum(vx, vy, nsh))
+    mean, sem, cnt = lat.spectrum_stats(nsh)
+    es = np.array(es)
+    assert cnt == samples
+    np.testing.assert_allclose(mean, es.mean(axis=0), rtol=1e-10, atol=1e-24)
+    np.testing.assert_allclose(sem, es.std(axis=0, ddof=1) / np.sqrt(samples), rtol=1e-6, atol=1e-24)
+    with pytest.raises(rl.RLBMError):
+        lat.spectrum_sample(nsh + 1)  # a record keeps one shell count
+    lat.spectrum_reset()
+    with pytest.raises(rl.RLBMError):
+        lat.spectrum_stats(nsh)  # no samples after a reset
+    lat.close()

@@ -233,3 +233,14 @@ def test_spectrum_parseval():
     e, a, b = workloads.random_smooth(N, N, seed=9, vmax=0.1)
     E = oracle.energy_spectrum(a, b, 30)
     assert abs(E.sum() - 0.5 * np.mean(a * a + b * b)) < 1e-15
+
+
+def test_filtered_velocity_keeps_only_modes_below_kf():
+    N = 64
+    y, x = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    low = 0.01 * np.sin(2 * np.pi * 3 * x / N)
+    high = 0.02 * np.cos(2 * np.pi * (6 * x + 4 * y) / N)  # |k| = 7.2
+    assert abs(oracle.filtered_velocity_rms(low, np.zeros((N, N)), 6) - 0.01 / np.sqrt(2)) < 1e-15
+    assert oracle.filtered_velocity_rms(high, np.zeros((N, N)), 6) < 1e-15
+    both = oracle.filtered_velocity_rms(low + high, high, 6)
+    assert abs(both - 0.01 / np.sqrt(2)) < 1e-15
