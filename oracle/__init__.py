@@ -90,6 +90,17 @@ def _load():
                                    ctypes.c_int]
         lib.oracle_run.restype = ctypes.c_int
         lib.oracle_totals.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp]
+        lib.oracle_tau_of.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.oracle_tau_of.restype = ctypes.c_double
+        lib.oracle_collide_node_ex.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]
+        lib.oracle_collide_node_ex.restype = ctypes.c_int
+        lib.oracle_stream_cfl.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        lib.oracle_fields_ex.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+        lib.oracle_fields_ex.restype = ctypes.c_int
+        lib.oracle_run_ex.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_long,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                      ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.oracle_run_ex.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -164,24 +175,30 @@ def force_term(f_node, F) -> np.ndarray:
     return G
 
 
-def collide(f_node, F, tau: float):
+def tau_of(eps: float, tau: float, eta_s: float = 0.0, dt: float = 1.0) -> float:
+    """Relaxation time in steps: tau, or 5 (eta/s) / (T dt) with eps = 3 T^4 / pi^2."""
+    return float(_load().oracle_tau_of(float(eps), float(tau), float(eta_s), float(dt)))
+
+
+def collide(f_node, F, tau: float, eta_s: float = 0.0, dt: float = 1.0):
     """Collide one node; returns (f_new, eps, u^mu)."""
     lib = _load()
     f = _f64(f_node).copy()
     eps = np.zeros(1)
     u = np.zeros(4)
-    rc = lib.oracle_collide_node(_p(f), _p(_f64(F)) if F is not None else None, float(tau), _p(eps), _p(u))
+    rc = lib.oracle_collide_node_ex(_p(f), _p(_f64(F)) if F is not None else None, float(tau), float(eta_s),
+                                    float(dt), _p(eps), _p(u))
     if rc != 0:
         raise FloatingPointError("Landau solve failed")
     return f, float(eps[0]), u
 
 
-def stream(f) -> np.ndarray:
+def stream(f, cfl: float = 1.0) -> np.ndarray:
     lib = _load()
     f = _f64(f)
     _, ny, nx = f.shape
     out = np.empty_like(f)
-    lib.oracle_stream(_p(f), _p(out), nx, ny)
+    lib.oracle_stream_cfl(_p(f), _p(out), nx, ny, float(cfl))
     return out
 
 
@@ -257,27 +274,30 @@ def step(f, tau, Fx=None, Fy=None) -> np.ndarray:
     return f
 
 
-def fields(f):
+def fields(f, cfl: float = 1.0):
     """(eps, vx, vy) seen by the next collision (post-stream Landau frame)."""
     lib = _load()
     f = _f64(f)
     _, ny, nx = f.shape
     tmp = np.empty_like(f)
     eps, vx, vy = np.empty((ny, nx)), np.empty((ny, nx)), np.empty((ny, nx))
-    lib.oracle_fields(_p(f), _p(tmp), nx, ny, _p(eps), _p(vx), _p(vy))
+    lib.oracle_fields_ex(_p(f), _p(tmp), nx, ny, float(cfl), _p(eps), _p(vx), _p(vy))
     return eps, vx, vy
 
 
-def run(f, tau, nsteps, step0=0, kmin=0, kmax=0, amp=0.0, seed=0, redraw=100) -> np.ndarray:
-    """nsteps steps in place on f with the epoch-redrawn stirring force."""
+def run(f, tau, nsteps, step0=0, kmin=0, kmax=0, amp=0.0, seed=0, redraw=100, cfl=1.0, eta_s=0.0,
+        dt=1.0) -> np.ndarray:
+    """nsteps steps in place on f with the epoch-redrawn stirring force
+    (cfl: streaming displacement per step in cells; eta_s > 0: per-node
+    relaxation time 5 (eta/s) / (T dt))."""
     lib = _load()
     assert f.dtype == np.float64 and f.flags.c_contiguous
     _, ny, nx = f.shape
     tmp = np.empty_like(f)
     Fx = np.zeros((ny, nx))
     Fy = np.zeros((ny, nx))
-    bad = lib.oracle_run(_p(f), _p(tmp), _p(Fx), _p(Fy), nx, ny, float(tau), int(step0), int(nsteps), int(kmin),
-                         int(kmax), float(amp), int(seed), int(redraw))
+    bad = lib.oracle_run_ex(_p(f), _p(tmp), _p(Fx), _p(Fy), nx, ny, float(tau), int(step0), int(nsteps), int(kmin),
+                            int(kmax), float(amp), int(seed), int(redraw), float(cfl), float(eta_s), float(dt))
     if bad:
         raise FloatingPointError("Landau solve failed %d times" % bad)
     return f

@@ -280,12 +280,25 @@ void oracle_force_term(const double *f, const double *F, double *G)
  * 0 for the 2D stirring).  Returns 0, or -1 if the Landau solve failed.
  * On success eps_out / u_out (may be NULL) receive the Landau frame.
  * ------------------------------------------------------------------------- */
-int oracle_collide_node(double *f, const double *F, double tau, double *eps_out, double *u_out)
+/* Relaxation time of a node in units of Delta t.  eta_s <= 0: the constant
+ * tau.  eta_s > 0 (viscosity-to-entropy ratio): tau_R = 5 (eta/s) / T with
+ * the temperature from eps = 3 T^4 / pi^2 (Sec. 3.1, Sec. 3.2), divided by
+ * the time step dt. */
+double oracle_tau_of(double eps, double tau, double eta_s, double dt)
+{
+    if (!(eta_s > 0.0)) return tau;
+    double T = pow(ORACLE_PI * ORACLE_PI * eps / 3.0, 0.25);
+    return 5.0 * eta_s / T / dt;
+}
+
+int oracle_collide_node_ex(double *f, const double *F, double tau, double eta_s, double dt, double *eps_out,
+                           double *u_out)
 {
     build_stencil();
     double T[16], eps, u[4], feq[NDIR], G[NDIR];
     oracle_moments_node(f, T);
     if (oracle_landau(T, &eps, u) < 0) return -1;
+    tau = oracle_tau_of(eps, tau, eta_s, dt);
     oracle_feq(eps, u, feq);
     int have_force = F && (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0);
     if (have_force) oracle_force_term(f, F, G);
@@ -300,10 +313,16 @@ int oracle_collide_node(double *f, const double *F, double tau, double *eps_out,
     return 0;
 }
 
+int oracle_collide_node(double *f, const double *F, double tau, double *eps_out, double *u_out)
+{
+    return oracle_collide_node_ex(f, F, tau, 0.0, 1.0, eps_out, u_out);
+}
+
 /* ---------------------------------------------------------------------------
  * Streaming (step (b)): pull with bilinear interpolation.  Population i at
  * node (x, y) takes the value of the post-collision field of direction i at
- * the off-lattice point (x - v_i^x, y - v_i^y) (CFL 1), interpolated linearly
+ * the off-lattice point (x - l v_i^x, y - l v_i^y), l = Delta t / Delta x the
+ * CFL number (0 < l <= 1: at most one cell), interpolated linearly
  * in x and y between the four surrounding nodes; periodic wrap.  With one
  * node in z, z-streaming is the identity.  The interpolation offset and
  * weights depend only on the displacement:  source = x + floor(-c) + frac,
@@ -315,12 +334,12 @@ static inline long wrap(long a, long n)
     return r < 0 ? r + n : r;
 }
 
-void oracle_stream(const double *fin, double *fout, int nx, int ny)
+void oracle_stream_cfl(const double *fin, double *fout, int nx, int ny, double cfl)
 {
     build_stencil();
     size_t plane = (size_t)nx * (size_t)ny;
     for (int i = 0; i < NDIR; ++i) {
-        double sx = -g_v[i][0], sy = -g_v[i][1];
+        double sx = -cfl * g_v[i][0], sy = -cfl * g_v[i][1];
         double flx = floor(sx), fly = floor(sy);
         double tx = sx - flx, ty = sy - fly; /* fractional parts in [0,1) */
         long ox = (long)flx, oy = (long)fly;
@@ -341,6 +360,8 @@ void oracle_stream(const double *fin, double *fout, int nx, int ny)
         }
     }
 }
+
+void oracle_stream(const double *fin, double *fout, int nx, int ny) { oracle_stream_cfl(fin, fout, nx, ny, 1.0); }
 
 /* ---------------------------------------------------------------------------
  * Philox4x32-10 counter-based generator, written from its published
@@ -525,11 +546,12 @@ int oracle_init(double *f, int nx, int ny, const double *eps, const double *vx, 
  * post-collision state back into f.  Returns 0 or the number of nodes whose
  * Landau solve failed.
  * ------------------------------------------------------------------------- */
-int oracle_step(double *f, double *tmp, int nx, int ny, double tau, const double *Fx, const double *Fy)
+int oracle_step_ex(double *f, double *tmp, int nx, int ny, double tau, const double *Fx, const double *Fy,
+                   double cfl, double eta_s, double dt)
 {
     build_stencil();
     size_t plane = (size_t)nx * (size_t)ny;
-    oracle_stream(f, tmp, nx, ny);
+    oracle_stream_cfl(f, tmp, nx, ny, cfl);
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(+ : bad)
     for (int y = 0; y < ny; ++y)
@@ -538,10 +560,15 @@ int oracle_step(double *f, double *tmp, int nx, int ny, double tau, const double
             double node[NDIR];
             for (int i = 0; i < NDIR; ++i) node[i] = tmp[(size_t)i * plane + n];
             double F[3] = {Fx ? Fx[n] : 0.0, Fy ? Fy[n] : 0.0, 0.0};
-            if (oracle_collide_node(node, F, tau, NULL, NULL) != 0) bad += 1;
+            if (oracle_collide_node_ex(node, F, tau, eta_s, dt, NULL, NULL) != 0) bad += 1;
             for (int i = 0; i < NDIR; ++i) f[(size_t)i * plane + n] = node[i];
         }
     return bad;
+}
+
+int oracle_step(double *f, double *tmp, int nx, int ny, double tau, const double *Fx, const double *Fy)
+{
+    return oracle_step_ex(f, tmp, nx, ny, tau, Fx, Fy, 1.0, 0.0, 1.0);
 }
 
 /* ---------------------------------------------------------------------------
@@ -549,11 +576,11 @@ int oracle_step(double *f, double *tmp, int nx, int ny, double tau, const double
  * tmp, then per node the moments and the Landau frame.  Outputs eps and the
  * 3-velocity v = u^i / u^0 (vx, vy).  Any output pointer may be NULL.
  * ------------------------------------------------------------------------- */
-int oracle_fields(const double *f, double *tmp, int nx, int ny, double *eps, double *vx, double *vy)
+int oracle_fields_ex(const double *f, double *tmp, int nx, int ny, double cfl, double *eps, double *vx, double *vy)
 {
     build_stencil();
     size_t plane = (size_t)nx * (size_t)ny;
-    oracle_stream(f, tmp, nx, ny);
+    oracle_stream_cfl(f, tmp, nx, ny, cfl);
     int bad = 0;
 #pragma omp parallel for schedule(static) reduction(+ : bad)
     for (int y = 0; y < ny; ++y)
@@ -575,14 +602,20 @@ int oracle_fields(const double *f, double *tmp, int nx, int ny, double *eps, dou
     return bad;
 }
 
+int oracle_fields(const double *f, double *tmp, int nx, int ny, double *eps, double *vx, double *vy)
+{
+    return oracle_fields_ex(f, tmp, nx, ny, 1.0, eps, vx, vy);
+}
+
 /* ---------------------------------------------------------------------------
  * A run of nsteps steps starting at global step index step0, with the
  * stirring force redrawn every `redraw` steps (epoch = step / redraw); amp =
  * 0 (or kmax <= 0) means no force.  f holds the post-collision state; tmp,
  * Fx, Fy are caller scratch of 26*nx*ny, nx*ny, nx*ny doubles.
  * ------------------------------------------------------------------------- */
-int oracle_run(double *f, double *tmp, double *Fx, double *Fy, int nx, int ny, double tau, long step0, int nsteps,
-               int kmin, int kmax, double amp, uint64_t seed, int redraw)
+int oracle_run_ex(double *f, double *tmp, double *Fx, double *Fy, int nx, int ny, double tau, long step0,
+                  int nsteps, int kmin, int kmax, double amp, uint64_t seed, int redraw, double cfl, double eta_s,
+                  double dt)
 {
     int forced = (amp > 0.0 && kmax > 0);
     long cur_epoch = -1;
@@ -596,9 +629,15 @@ int oracle_run(double *f, double *tmp, double *Fx, double *Fy, int nx, int ny, d
                 cur_epoch = e;
             }
         }
-        bad += oracle_step(f, tmp, nx, ny, tau, forced ? Fx : NULL, forced ? Fy : NULL);
+        bad += oracle_step_ex(f, tmp, nx, ny, tau, forced ? Fx : NULL, forced ? Fy : NULL, cfl, eta_s, dt);
     }
     return bad;
+}
+
+int oracle_run(double *f, double *tmp, double *Fx, double *Fy, int nx, int ny, double tau, long step0, int nsteps,
+               int kmin, int kmax, double amp, uint64_t seed, int redraw)
+{
+    return oracle_run_ex(f, tmp, Fx, Fy, nx, ny, tau, step0, nsteps, kmin, kmax, amp, seed, redraw, 1.0, 0.0, 1.0);
 }
 
 /* Total energy-momentum of a population field: sum over nodes of T^{0 mu}

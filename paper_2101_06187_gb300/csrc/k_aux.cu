@@ -38,29 +38,38 @@ __device__ __forceinline__ TS store_any(double x) {
 // ---------------------------------------------------------------- initialisation
 // f_c = f_eq,c(eps, v) in deviation form (see collide_node):
 // q_c = [eps - eps0 + eps gamma^2 (4 xi + 10 xi^2 - 2 |v|^2)] / s, xi = c . v.
-template <typename TS>
+template <typename TS, typename TC>
 __global__ void k_init(TS *q, StepParams p, const double *eps, const double *vx, const double *vy) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const long long i = (long long)y * p.nx + x;
-    const double e = eps ? eps[i] : p.eps0;
-    const double a = vx ? vx[i] : 0.0, b = vy ? vy[i] : 0.0;
-    const double v2 = a * a + b * b;
-    const double g2 = 1.0 / (1.0 - v2);
+    const TC de = eps ? (TC)(eps[i] - p.eps0) : (TC)0;  // deviation formed in FP64, then rounded once
+    const TC e = par_eps0<TC>(p) + de;
+    const TC a = vx ? (TC)vx[i] : (TC)0, b = vy ? (TC)vy[i] : (TC)0;
+    const TC v2 = a * a + b * b;
+    const TC eg2 = e / ((TC)1 - v2);
+    const TC inv_s = par_inv_scale<TC>(p);
     const long long n = (long long)y * p.pitch + x;
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
-        const double xi = cls_cx(c) * a + cls_cy(c) * b;
-        const double qc = ((e - p.eps0) + e * g2 * (4.0 * xi + 10.0 * xi * xi - 2.0 * v2)) / p.scale;
-        q[(long long)c * p.plane + n] = store_any<TS>(qc);
+        const TC xi = (TC)cls_cx(c) * a + (TC)cls_cy(c) * b;
+        const TC qc = (de + eg2 * ((TC)4 * xi + (TC)10 * xi * xi - (TC)2 * v2)) * inv_s;
+        q[(long long)c * p.plane + n] = to_storage<TS, TC>(qc);
     });
 }
 
 cudaError_t launch_init(int dtype, void *q, const StepParams &p, const double *eps, const double *vx,
                         const double *vy, cudaStream_t s) {
     dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
-    RLBM_DISPATCH_STORAGE(dtype, TS, k_init<TS><<<g, b, 0, s>>>(static_cast<TS *>(q), p, eps, vx, vy));
+    if (dtype == RLBM_F64)
+        k_init<double, double><<<g, b, 0, s>>>(static_cast<double *>(q), p, eps, vx, vy);
+    else if (dtype == RLBM_F32)
+        k_init<float, float><<<g, b, 0, s>>>(static_cast<float *>(q), p, eps, vx, vy);
+    else if (dtype == RLBM_BF16)
+        k_init<__nv_bfloat16, float><<<g, b, 0, s>>>(static_cast<__nv_bfloat16 *>(q), p, eps, vx, vy);
+    else
+        k_init<__half, float><<<g, b, 0, s>>>(static_cast<__half *>(q), p, eps, vx, vy);
     return cudaGetLastError();
 }
 
@@ -152,7 +161,13 @@ __device__ __forceinline__ double u01_53(unsigned int a, unsigned int b) {
     return (double)m * (1.0 / 9007199254740992.0);
 }
 
-__global__ void k_draw_modes(Mode *modes, int nmodes, double amp, unsigned long long seed,
+template <typename TC>
+struct C4 {
+    TC ax, bx, ay, by;
+};
+
+template <typename TC>
+__global__ void k_draw_modes(Mode *modes, C4<TC> *coef, int nmodes, double amp, unsigned long long seed,
                              unsigned long long epoch) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= nmodes) return;
@@ -173,12 +188,18 @@ __global__ void k_draw_modes(Mode *modes, int nmodes, double amp, unsigned long 
     md.ay = 2.0 * r * sth * cph;
     md.by = 2.0 * r * sth * sph;
     modes[m] = md;
+    coef[m] = C4<TC>{(TC)md.ax, (TC)md.bx, (TC)md.ay, (TC)md.by};
 }
 
-cudaError_t launch_draw_modes(Mode *modes, int nmodes, double amp, unsigned long long seed,
+cudaError_t launch_draw_modes(int dtype, Mode *modes, void *coef, int nmodes, double amp, unsigned long long seed,
                               unsigned long long epoch, cudaStream_t s) {
     if (nmodes <= 0) return cudaSuccess;
-    k_draw_modes<<<(nmodes + 127) / 128, 128, 0, s>>>(modes, nmodes, amp, seed, epoch);
+    if (dtype == RLBM_F64)
+        k_draw_modes<double><<<(nmodes + 127) / 128, 128, 0, s>>>(modes, static_cast<C4<double> *>(coef), nmodes, amp,
+                                                                  seed, epoch);
+    else
+        k_draw_modes<float><<<(nmodes + 127) / 128, 128, 0, s>>>(modes, static_cast<C4<float> *>(coef), nmodes, amp,
+                                                                 seed, epoch);
     return cudaGetLastError();
 }
 
@@ -244,35 +265,35 @@ cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, i
 // F(x) = sum_m [a cos psi - b sin psi], psi = 2 pi (kx x/nx + ky y/ny), with
 // e^{i psi} = X[m][x] * Y[m][y].
 template <typename TC>
-__global__ void k_synth_force(TC *F, const Mode *__restrict__ modes, int nmodes, const C2<TC> *__restrict__ X,
+__global__ void k_synth_force(TC *F, const C4<TC> *__restrict__ coef, int nmodes, const C2<TC> *__restrict__ X,
                               const C2<TC> *__restrict__ Y, StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     TC fx = 0, fy = 0;
     for (int m = 0; m < nmodes; ++m) {
-        const Mode md = modes[m];
+        const C4<TC> c = coef[m];
         const C2<TC> a = X[(long long)m * p.nx + x];
         const C2<TC> b = Y[(long long)m * p.ny + y];
         const TC cpsi = a.c * b.c - a.s * b.s;
         const TC spsi = a.s * b.c + a.c * b.s;
-        fx += (TC)md.ax * cpsi - (TC)md.bx * spsi;
-        fy += (TC)md.ay * cpsi - (TC)md.by * spsi;
+        fx += c.ax * cpsi - c.bx * spsi;
+        fy += c.ay * cpsi - c.by * spsi;
     }
     const long long n = (long long)y * p.pitch + x;
     F[n] = fx;
     F[p.plane + n] = fy;
 }
 
-cudaError_t launch_synth_force(int dtype, void *F, const Mode *modes, int nmodes, const void *X, const void *Y,
+cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const void *X, const void *Y,
                                const StepParams &p, cudaStream_t s) {
     dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
     if (dtype == RLBM_F64)
-        k_synth_force<double><<<g, b, 0, s>>>(static_cast<double *>(F), modes, nmodes,
+        k_synth_force<double><<<g, b, 0, s>>>(static_cast<double *>(F), static_cast<const C4<double> *>(coef), nmodes,
                                               static_cast<const C2<double> *>(X), static_cast<const C2<double> *>(Y),
                                               p);
     else
-        k_synth_force<float><<<g, b, 0, s>>>(static_cast<float *>(F), modes, nmodes,
+        k_synth_force<float><<<g, b, 0, s>>>(static_cast<float *>(F), static_cast<const C4<float> *>(coef), nmodes,
                                              static_cast<const C2<float> *>(X), static_cast<const C2<float> *>(Y), p);
     return cudaGetLastError();
 }

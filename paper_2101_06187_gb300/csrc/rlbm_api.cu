@@ -161,9 +161,9 @@ static rlbm_status ensure_force(rlbm_t *h) {
     const long long e = h->step / h->forcing.redraw_period;
     if (e == h->force_epoch) return RLBM_OK;
     const StepParams p = params_of(h);
-    CUDA_TRY(h, launch_draw_modes(h->modes, h->nmodes, h->forcing.amp, (unsigned long long)h->forcing.seed,
-                                  (unsigned long long)e, h->stream));
-    CUDA_TRY(h, launch_synth_force(h->opts.dtype, h->F, h->modes, h->nmodes, h->tabx, h->taby, p, h->stream));
+    CUDA_TRY(h, launch_draw_modes(h->opts.dtype, h->modes, h->coef, h->nmodes, h->forcing.amp,
+                                  (unsigned long long)h->forcing.seed, (unsigned long long)e, h->stream));
+    CUDA_TRY(h, launch_synth_force(h->opts.dtype, h->F, h->coef, h->nmodes, h->tabx, h->taby, p, h->stream));
     h->force_epoch = e;
     return RLBM_OK;
 }
@@ -284,6 +284,7 @@ void rlbm_destroy(rlbm_t *h) {
     if (h->F) dev_free(h, h->F, F_bytes(h));
     if (h->twx) dev_free(h, h->twx, tw_bytes(h, h->nx));
     if (h->twy) dev_free(h, h->twy, tw_bytes(h, h->ny));
+    if (h->coef) dev_free(h, h->coef, 4 * compute_bytes(h->opts.dtype) * h->nmodes);
     if (h->tabx) dev_free(h, h->tabx, tw_bytes(h, h->nx) * h->nmodes);
     if (h->taby) dev_free(h, h->taby, tw_bytes(h, h->ny) * h->nmodes);
     if (h->modes) dev_free(h, h->modes, sizeof(Mode) * h->nmodes);
@@ -381,9 +382,10 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         h->twx = dev_alloc(h, tw_bytes(h, nx));
         h->twy = dev_alloc(h, tw_bytes(h, ny));
         h->modes = static_cast<Mode *>(dev_alloc(h, sizeof(Mode) * h->nmodes));
+        h->coef = dev_alloc(h, 4 * compute_bytes(o.dtype) * h->nmodes);
         h->tabx = dev_alloc(h, tw_bytes(h, nx) * h->nmodes);
         h->taby = dev_alloc(h, tw_bytes(h, ny) * h->nmodes);
-        ok = ok && h->F && h->twx && h->twy && h->modes && h->tabx && h->taby;
+        ok = ok && h->F && h->twx && h->twy && h->modes && h->coef && h->tabx && h->taby;
     }
     if (!ok || cudaMallocHost(&h->host_small, 4096) != cudaSuccess) {
         cudaGetLastError();

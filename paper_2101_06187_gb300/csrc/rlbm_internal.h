@@ -54,11 +54,11 @@ cudaError_t launch_check_fields(const double *eps, const double *vx, const doubl
 cudaError_t launch_reduce_partials(const double *partials, int nblocks, double base_E, double *totals,
                                    cudaStream_t s);
 cudaError_t launch_twiddles(int dtype, void *tw, int n, cudaStream_t s);
-cudaError_t launch_draw_modes(Mode *modes, int nmodes, double amp, unsigned long long seed,
+cudaError_t launch_draw_modes(int dtype, Mode *modes, void *coef, int nmodes, double amp, unsigned long long seed,
                               unsigned long long epoch, cudaStream_t s);
 cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, int nmodes, const void *twx,
                                const void *twy, int nx, int ny, cudaStream_t s);
-cudaError_t launch_synth_force(int dtype, void *F, const Mode *modes, int nmodes, const void *X, const void *Y,
+cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const void *X, const void *Y,
                                const StepParams &p, cudaStream_t s);
 cudaError_t launch_decode_class(int dtype, const void *q, int c, const StepParams &p, double *out, cudaStream_t s);
 cudaError_t launch_encode_class(int dtype, void *q, int c, const StepParams &p, const double *in, cudaStream_t s);
@@ -94,6 +94,7 @@ struct rlbm {
     void *twx = nullptr, *twy = nullptr;
     void *tabx = nullptr, *taby = nullptr;  // per-mode phase tables [nmodes][nx], [nmodes][ny]
     rlbk::Mode *modes = nullptr;
+    void *coef = nullptr;             // per-mode synthesis coefficients (ax, bx, ay, by) in the compute type
     double *fields = nullptr;         // 3 * nx * ny doubles: staging for init / moments outputs
     double *partials = nullptr;       // per-block partial sums of the moments kernel
     double *totals = nullptr;         // 3 doubles

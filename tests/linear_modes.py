@@ -7,11 +7,12 @@ pin shear decay, sound speed and the viscosity-tau relation."""
 import numpy as np
 
 
-def _symbols(v, k):
-    """Fourier symbol of pull-streaming with bilinear interpolation, per direction."""
+def _symbols(v, k, cfl=1.0):
+    """Fourier symbol of pull-streaming with bilinear interpolation from
+    x - cfl v_i, per direction."""
     S = np.zeros(len(v), dtype=complex)
     for i in range(len(v)):
-        sx, sy = -v[i, 0], -v[i, 1]
+        sx, sy = -cfl * v[i, 0], -cfl * v[i, 1]
         ox, oy = np.floor(sx), np.floor(sy)
         tx, ty = sx - ox, sy - oy
         e = lambda dx, dy: np.exp(1j * (k[0] * dx + k[1] * dy))
@@ -20,21 +21,21 @@ def _symbols(v, k):
     return S
 
 
-def _linear_step(v, w, k, tau):
+def _linear_step(v, w, k, tau, cfl=1.0):
     """Linearised step about eps = 1, u = 0: stream, then BGK towards the
     linearised equilibrium delta f_eq,i = w_i (delta E + 3 v_i . delta M)."""
     A = w[:, None] * (1.0 + 3.0 * v @ v.T)
     C = np.eye(len(w)) - (np.eye(len(w)) - A) / tau
-    return C @ np.diag(_symbols(v, k))
+    return C @ np.diag(_symbols(v, k, cfl))
 
 
-def _predict_velocity_mode(v, w, k, tau, nsteps, dv_x, dv_y, deps=0.0):
+def _predict_velocity_mode(v, w, k, tau, nsteps, dv_x, dv_y, deps=0.0, cfl=1.0):
     """Linear prediction of the Fourier amplitude of (eps, v) seen by the
     next collision after nsteps, for an initial f_eq mode of amplitude
     (deps, dv) (M = 4/3 v and v = 3/4 M at linear order, eps = 1)."""
     df = w * (deps + 3.0 * (4.0 / 3.0) * (v[:, 0] * dv_x + v[:, 1] * dv_y))
-    fn = np.linalg.matrix_power(_linear_step(v, w, k, tau), nsteps) @ df
-    post = _symbols(v, k) * fn
+    fn = np.linalg.matrix_power(_linear_step(v, w, k, tau, cfl), nsteps) @ df
+    post = _symbols(v, k, cfl) * fn
     return post.sum(), 0.75 * (v[:, 0] @ post), 0.75 * (v[:, 1] @ post)
 
 
