@@ -126,6 +126,17 @@ typedef struct {
     rlbm_alloc_fn alloc;  /* optional device allocator */
     rlbm_free_fn free;
     void *alloc_ctx;
+    /* CFL number Delta t / Delta x (0 < cfl <= 1, default 1): populations
+     * stream cfl * v_i cells per step (the paper's runs: Delta t = 0.05 with
+     * lattice spacing 0.32 ... 0.04).  cfl < 1 uses the one-node-per-thread
+     * kernel (RLBM_KERNEL_GATHER). */
+    double cfl;
+    /* eta/s > 0 switches the relaxation time to the paper's
+     * tau_R = 5 (eta/s) / T with eps = 3 T^4 / pi^2 (Sec. 3.1-3.2), node by
+     * node, in steps of dt (the physical time step); tau is then unused.
+     * 0 (default): the constant tau of rlbm_create. */
+    double eta_s;
+    double dt;            /* time step for eta/s mode (default 1) */
 } rlbm_opts;
 
 typedef struct {

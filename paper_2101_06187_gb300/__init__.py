@@ -62,7 +62,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("landau", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("eps0", ctypes.c_double), ("scale", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", ctypes.c_void_p)]
+                ("alloc_ctx", ctypes.c_void_p), ("cfl", ctypes.c_double), ("eta_s", ctypes.c_double),
+                ("dt", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -406,7 +407,8 @@ class Lattice:
 
     def __init__(self, nx: int, ny: int, tau: float, *, dtype: str = "f32", landau: str = "fp32",
                  forcing: Optional[dict] = None, eps0: float = 1.0, scale: float = 0.0, kernel: str = "auto",
-                 use_graphs: bool = True, allocator: str = "torch", stream=None, device: Optional[int] = None):
+                 use_graphs: bool = True, allocator: str = "torch", stream=None, device: Optional[int] = None,
+                 cfl: float = 1.0, eta_s: float = 0.0, dt: float = 1.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the RLBM library runs on the GPU only")
@@ -433,6 +435,9 @@ class Lattice:
         o.scale = float(scale)
         o.stream = s
         o.device = dev
+        o.cfl = float(cfl)
+        o.eta_s = float(eta_s)
+        o.dt = float(dt)
         self._alloc = None
         if allocator == "torch":
             self._alloc = _TorchAllocator(dev, s)

@@ -19,6 +19,8 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
     const TC *f = static_cast<const TC *>(F);
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
     const dim3 block(cfg.bx, cfg.by, 1);
+    if ((cfg.kernel == RLBM_KERNEL_GATHER_VEC || cfg.kernel == RLBM_KERNEL_GATHER_VEC2) && p.cfl != 1.0)
+        return cudaErrorInvalidValue;  // the vector kernels stream at CFL 1 only
     if (cfg.kernel == RLBM_KERNEL_GATHER_VEC || cfg.kernel == RLBM_KERNEL_GATHER_VEC2) {
         constexpr int V4 = VecOf<TS>::V;
         const int V = (cfg.kernel == RLBM_KERNEL_GATHER_VEC2) ? 2 : V4;
@@ -40,17 +42,26 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
     }
     const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
     const bool idx32 = (long long)NC * p.plane < (1ll << 31) - 1;
-    if (idx32) {
-        if (forced)
-            k_step_gather<TS, TC, TL, true, int><<<grid, block, 0, s>>>(in, out, f, p);
-        else
-            k_step_gather<TS, TC, TL, false, int><<<grid, block, 0, s>>>(in, out, f, p);
+    const bool cfl1 = p.cfl == 1.0;
+#define RLBM_GATHER(FOR, IDX, C1) k_step_gather<TS, TC, TL, FOR, IDX, C1><<<grid, block, 0, s>>>(in, out, f, p)
+    if (cfl1) {
+        if (idx32) {
+            if (forced) RLBM_GATHER(true, int, true);
+            else RLBM_GATHER(false, int, true);
+        } else {
+            if (forced) RLBM_GATHER(true, long long, true);
+            else RLBM_GATHER(false, long long, true);
+        }
     } else {
-        if (forced)
-            k_step_gather<TS, TC, TL, true, long long><<<grid, block, 0, s>>>(in, out, f, p);
-        else
-            k_step_gather<TS, TC, TL, false, long long><<<grid, block, 0, s>>>(in, out, f, p);
+        if (idx32) {
+            if (forced) RLBM_GATHER(true, int, false);
+            else RLBM_GATHER(false, int, false);
+        } else {
+            if (forced) RLBM_GATHER(true, long long, false);
+            else RLBM_GATHER(false, long long, false);
+        }
     }
+#undef RLBM_GATHER
     return cudaGetLastError();
 }
 
@@ -65,8 +76,12 @@ cudaError_t launch_batch_t(const LaunchCfg &cfg, int grid, const void *runs, int
 template <typename TS, typename TC, typename TL>
 cudaError_t launch_moments_t(const void *qin, const StepParams &p, double *eps, double *vx, double *vy,
                              double *partials, int *bad, cudaStream_t s) {
-    k_moments<TS, TC, TL><<<gather_grid(p), gather_block(), 0, s>>>(static_cast<const TS *>(qin), p, eps, vx, vy,
-                                                                    partials, bad);
+    if (p.cfl == 1.0)
+        k_moments<TS, TC, TL, true><<<gather_grid(p), gather_block(), 0, s>>>(static_cast<const TS *>(qin), p, eps, vx,
+                                                                              vy, partials, bad);
+    else
+        k_moments<TS, TC, TL, false><<<gather_grid(p), gather_block(), 0, s>>>(static_cast<const TS *>(qin), p, eps,
+                                                                               vx, vy, partials, bad);
     return cudaGetLastError();
 }
 

@@ -131,6 +131,9 @@ static StepParams params_of(const rlbm_t *h) {
     p.inv_tau = 1.0 / h->tau;
     p.eps0 = h->opts.eps0;
     p.scale = h->opts.scale;
+    p.cfl = h->opts.cfl;
+    // eta/s mode: 1/tau = T dt / (5 eta/s), T = (pi^2 eps / 3)^{1/4}
+    p.eta_k = h->opts.eta_s > 0.0 ? std::pow(M_PI * M_PI / 3.0, 0.25) * h->opts.dt / (5.0 * h->opts.eta_s) : 0.0;
     p.err = nullptr;
     finish_params(p);
     return p;
@@ -271,6 +274,9 @@ void rlbm_opts_default(rlbm_opts *o) {
     o->scale = 0.0;
     o->stream = nullptr;
     o->device = -1;
+    o->cfl = 1.0;
+    o->eta_s = 0.0;
+    o->dt = 1.0;
 }
 
 void rlbm_destroy(rlbm_t *h) {
@@ -318,6 +324,12 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (o.scale == 0.0) o.scale = (o.dtype == RLBM_BF16 || o.dtype == RLBM_F16) ? 1.0 / 64.0 : 1.0;
     if (!(o.scale > 0.0) || !isfinite(o.scale)) return RLBM_ERR_ARG;
     if (o.alloc && !o.free) return RLBM_ERR_ARG;
+    if (o.cfl == 0.0) o.cfl = 1.0;
+    if (o.dt == 0.0) o.dt = 1.0;
+    if (!(o.cfl > 0.0 && o.cfl <= 1.0) || !(o.eta_s >= 0.0) || !isfinite(o.eta_s) || !(o.dt > 0.0) || !isfinite(o.dt))
+        return RLBM_ERR_ARG;
+    if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2))
+        return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
 
     rlbm_forcing fz{};
@@ -698,6 +710,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     LaunchCfg best = h->cfg;
     for (const LaunchCfg &c : kCandidates) {
         if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
+        if (h->opts.cfl != 1.0 && c.kernel != RLBM_KERNEL_GATHER) continue;
         // the trial steps read the current state and overwrite only the spare buffer
         bool ok = true;
         for (int i = 0; i < 2 + reps && ok; ++i) {
@@ -925,6 +938,7 @@ rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_o
     const int V = run_length(o.dtype);
     for (int r = 0; r < nruns; ++r)
         if (runs[r].nx % V != 0) return RLBM_ERR_ARG;  // the ensemble kernel works on runs of V nodes
+    if (!(o.cfl == 0.0 || o.cfl == 1.0)) return RLBM_ERR_ARG;  // and streams at CFL 1
     rlbm_batch_t *b = new rlbm_batch_t();
     b->opts = o;
     b->stream = static_cast<cudaStream_t>(o.stream);

@@ -101,16 +101,50 @@ struct StepParams {
     double inv_scale; // 1/s
     // FP32 copies, so the FP32 kernels never touch the (slow) FP64 pipe
     float inv_tau_f, eps0_f, scale_f, inv_scale_f;
+    // eta/s mode (eta_k > 0): 1/tau = eta_k eps^{1/4}, from tau_R = 5 (eta/s)/T,
+    // eps = 3 T^4/pi^2, in steps of dt: eta_k = (pi^2/3)^{1/4} dt / (5 eta/s)
+    double eta_k;
+    float eta_k_f;
+    // CFL number (streaming displacement cfl * v_i per step) and, for cfl < 1,
+    // the bilinear weights (w00, w10, w01, w11) of each class's pull
+    double cfl;
+    double wt[17][4];
+    float wt_f[17][4];
     int *err;         // device error word (bounded-wait / failure reporting)
 };
 
-// Fill the derived fields of a StepParams from inv_tau, eps0 and scale.
+// Fill the derived fields of a StepParams from inv_tau, eps0, scale, eta_k
+// and cfl.  Pull source of class c: x - cfl c; for 0 < cfl < 1 the corner
+// offset is -1 along an axis where c > 0 and 0 otherwise, with fractional
+// part t = 1 - cfl c (c > 0) or cfl |c| (c < 0).
 RLBM_HD inline void finish_params(StepParams &p) {
     p.inv_scale = 1.0 / p.scale;
     p.inv_tau_f = (float)p.inv_tau;
     p.eps0_f = (float)p.eps0;
     p.scale_f = (float)p.scale;
     p.inv_scale_f = (float)p.inv_scale;
+    p.eta_k_f = (float)p.eta_k;
+    for (int c = 0; c < 17; ++c) {
+        const double cx = cls_cx(c), cy = cls_cy(c);
+        const double tx = cx > 0 ? 1.0 - p.cfl * cx : (cx < 0 ? -p.cfl * cx : 0.0);
+        const double ty = cy > 0 ? 1.0 - p.cfl * cy : (cy < 0 ? -p.cfl * cy : 0.0);
+        p.wt[c][0] = (1.0 - tx) * (1.0 - ty);
+        p.wt[c][1] = tx * (1.0 - ty);
+        p.wt[c][2] = (1.0 - tx) * ty;
+        p.wt[c][3] = tx * ty;
+        for (int k = 0; k < 4; ++k) p.wt_f[c][k] = (float)p.wt[c][k];
+    }
+}
+
+template <typename T>
+RLBM_HD inline T par_wt(const StepParams &p, int c, int k) {
+    if constexpr (std::is_same<T, float>::value) return p.wt_f[c][k];
+    else return p.wt[c][k];
+}
+template <typename T>
+RLBM_HD inline T par_eta_k(const StepParams &p) {
+    if constexpr (std::is_same<T, float>::value) return p.eta_k_f;
+    else return p.eta_k;
 }
 
 template <typename T>
@@ -325,7 +359,10 @@ RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParam
     const TC P1 = (TC)((TL)4 * eg2) * inv_s;
     const TC P2 = (TC)((TL)10 * eg2) * inv_s;
     const TC vx = (TC)fr.vx, vy = (TC)fr.vy;
-    const TC om = (TC)(fr.gamma * par_inv_tau<TL>(p));
+    // relaxation rate: 1/tau, or in eta/s mode T(eps) dt / (5 eta/s)
+    TL inv_tau = par_inv_tau<TL>(p);
+    if (p.eta_k_f > 0.0f) inv_tau = par_eta_k<TL>(p) * std::sqrt(std::sqrt(fr.eps));
+    const TC om = (TC)(fr.gamma * inv_tau);
 
     // even part K0 + Kxx cx^2 + Kxy cx cy + Kyy cy^2, odd part coefficients
     const TC e2 = om * (P2 - P1);

@@ -62,6 +62,8 @@ extern "C" RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, 
     p.inv_tau = 1.0;  // unused by the moments kernel
     p.eps0 = eps0;
     p.scale = scale;
+    p.eta_k = 0.0;
+    p.cfl = 1.0;  // the moments of a CFL-1 lattice
     p.err = nullptr;
     rlbk::finish_params(p);
     const int nblocks = rlbk::moments_blocks(p);

@@ -75,6 +75,15 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     o = rl.rlbm_opts_default()
     o.kernel = rl.KERNELS["vec"]
     assert create(37, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # vector kernel needs nx % 4 == 0
+    o = rl.rlbm_opts_default()
+    o.cfl = 1.5
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # displacement above one cell
+    o.cfl = 0.5
+    o.kernel = rl.KERNELS["vec"]
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # vector kernels stream at CFL 1 only
+    o = rl.rlbm_opts_default()
+    o.eta_s = -0.01
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
     assert out.value is None
     assert lib.rlbm_create(16, 16, 0, 0.8, None, None, None) == rl.RLBM_ERR_ARG
 
@@ -105,6 +114,7 @@ def test_opts_defaults(lib):
     import paper_2101_06187_gb300 as rl
     o = rl.rlbm_opts_default()
     assert o.dtype == rl.DTYPES["f32"] and o.landau == rl.LANDAU["fp32"] and o.use_graphs == 1 and o.eps0 == 1.0 and o.device == -1
+    assert o.cfl == 1.0 and o.eta_s == 0.0 and o.dt == 1.0
 
 
 def test_binding_fails_loudly_without_the_library(tmp_path):

@@ -279,3 +279,23 @@ def test_spectrum_statistics_match_oracle_samples():
     with pytest.raises(rl.RLBMError):
         lat.spectrum_stats(nsh)  # no samples after a reset
     lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("cfl,eta_s", [(0.5, 0.0), (0.15625, 0.01), (1.0, 0.01)])
+def test_cfl_and_eta_over_s_match_oracle(dtype, cfl, eta_s):
+    """The paper's own parameters: Delta t = 0.05 on lattice spacing 0.32
+    (cfl = 0.15625) with eta/s = 0.01, i.e. tau from the local temperature."""
+    nx, ny = 48, 40
+    dt = 0.05
+    fields = workloads.random_smooth(nx, ny, seed=61, deps=0.05, vmax=0.05)
+    forcing = dict(kmin=2, kmax=4, amp=2e-4, seed=17, redraw_period=9)
+    lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, forcing=forcing, cfl=cfl, eta_s=eta_s, dt=dt)
+    lat.init_fields(*fields)
+    lat.step(80)
+    got = lat.moments()
+    f = oracle.init(nx, ny, *fields)
+    oracle.run(f, 0.7, 80, kmin=2, kmax=4, amp=2e-4, seed=17, redraw=9, cfl=cfl, eta_s=eta_s, dt=dt)
+    err_e, err_v = rel_errors(oracle.fields(f, cfl), got)
+    assert err_e < TOL[dtype] and err_v < TOL[dtype], (err_e, err_v)
+    lat.close()
