@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--landau", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2", "packed"])
     ap.add_argument("--n", type=int, default=0, help="override lattice side (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-form table, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
@@ -411,7 +411,7 @@ def main():
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.form != "f64" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": n, "ny": n, "form": args.form, "landau": args.landau,
-                   "kernel": ["auto", "gather", "vec", "vec2"][info["kernel"]],
+                   "kernel": ["auto", "gather", "vec", "vec2", "packed"][info["kernel"]],
                    "block": [info["block_x"], info["block_y"]], "tau": w.tau,
                    "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},

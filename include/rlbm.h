@@ -82,13 +82,16 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * GATHER_VEC: a run of 4 nodes (2 for F64) along x per thread with 128-bit
  * (64-bit for 16-bit storage) loads and stores; needs nx divisible by that
  * run.  GATHER_VEC2: a run of 2 nodes (fewer registers); needs nx even.
- * AUTO: the autotuned choice if one is cached for this lattice, else
- * GATHER. */
+ * PACKED: 2 nodes per thread whose arithmetic runs in packed FP32 lanes
+ * (two nodes per instruction); FP32 compute with RLBM_LANDAU_FP32, nx even.
+ * The vector and packed variants stream at CFL 1 only.  AUTO: the
+ * autotuned choice if one is cached for this lattice, else GATHER. */
 typedef enum {
     RLBM_KERNEL_AUTO = 0,
     RLBM_KERNEL_GATHER = 1,
     RLBM_KERNEL_GATHER_VEC = 2,
-    RLBM_KERNEL_GATHER_VEC2 = 3
+    RLBM_KERNEL_GATHER_VEC2 = 3,
+    RLBM_KERNEL_PACKED = 4
 } rlbm_kernel;
 
 /* Stirring force (Sec. 5).  Modes are the integer wavevectors k with

@@ -28,7 +28,7 @@ RLBM_OK, RLBM_ERR_ARG, RLBM_ERR_ALLOC, RLBM_ERR_CUDA, RLBM_ERR_TIMEOUT, RLBM_ERR
 RLBM_STENCIL_SPH26_SLAB = 0
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 LANDAU = {"fp64": 0, "fp32": 1}
-KERNELS = {"auto": 0, "gather": 1, "vec": 2, "vec2": 3}
+KERNELS = {"auto": 0, "gather": 1, "vec": 2, "vec2": 3, "packed": 4}
 NCLASSES = 17
 
 # Symbols declared in include/rlbm.h (checked by the ABI test).

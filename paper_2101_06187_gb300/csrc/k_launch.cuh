@@ -3,6 +3,7 @@
 #pragma once
 
 #include "k_step_gather.cuh"
+#include "k_step_pair.cuh"
 #include "k_step_vec.cuh"
 #include "rlbm_internal.h"
 
@@ -19,8 +20,28 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
     const TC *f = static_cast<const TC *>(F);
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
     const dim3 block(cfg.bx, cfg.by, 1);
-    if ((cfg.kernel == RLBM_KERNEL_GATHER_VEC || cfg.kernel == RLBM_KERNEL_GATHER_VEC2) && p.cfl != 1.0)
+    if ((cfg.kernel == RLBM_KERNEL_GATHER_VEC || cfg.kernel == RLBM_KERNEL_GATHER_VEC2 ||
+         cfg.kernel == RLBM_KERNEL_PACKED) &&
+        p.cfl != 1.0)
         return cudaErrorInvalidValue;  // the vector kernels stream at CFL 1 only
+    if (cfg.kernel == RLBM_KERNEL_PACKED) {
+        if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
+            if (p.nx % 2 != 0) return cudaErrorInvalidValue;
+            const dim3 grid((p.nx / 2 + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
+#define RLBM_PAIR(MB)                                                        \
+    do {                                                                     \
+        if (forced) k_step_pair<TS, true, MB><<<grid, block, 0, s>>>(in, out, f, p);  \
+        else k_step_pair<TS, false, MB><<<grid, block, 0, s>>>(in, out, f, p);        \
+    } while (0)
+            if (cfg.minb == 3) RLBM_PAIR(3);
+            else if (cfg.minb == 2) RLBM_PAIR(2);
+            else RLBM_PAIR(1);
+#undef RLBM_PAIR
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;  // packed lanes are FP32 with the FP32 Landau solve
+        }
+    }
     if (cfg.kernel == RLBM_KERNEL_GATHER_VEC || cfg.kernel == RLBM_KERNEL_GATHER_VEC2) {
         constexpr int V4 = VecOf<TS>::V;
         const int V = (cfg.kernel == RLBM_KERNEL_GATHER_VEC2) ? 2 : V4;

@@ -233,6 +233,11 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_GATHER_VEC, 256, 1}, {RLBM_KERNEL_GATHER_VEC, 32, 2}, {RLBM_KERNEL_GATHER_VEC, 64, 1},
     {RLBM_KERNEL_GATHER_VEC2, 32, 4}, {RLBM_KERNEL_GATHER_VEC2, 64, 2}, {RLBM_KERNEL_GATHER_VEC2, 128, 1},
     {RLBM_KERNEL_GATHER_VEC2, 32, 8}, {RLBM_KERNEL_GATHER_VEC2, 64, 4}, {RLBM_KERNEL_GATHER_VEC2, 128, 2},
+    {RLBM_KERNEL_PACKED, 32, 4}, {RLBM_KERNEL_PACKED, 64, 2}, {RLBM_KERNEL_PACKED, 128, 1},
+    {RLBM_KERNEL_PACKED, 32, 8}, {RLBM_KERNEL_PACKED, 64, 4}, {RLBM_KERNEL_PACKED, 128, 2},
+    {RLBM_KERNEL_PACKED, 64, 2, 2}, {RLBM_KERNEL_PACKED, 128, 1, 2}, {RLBM_KERNEL_PACKED, 128, 2, 2},
+    {RLBM_KERNEL_PACKED, 64, 2, 3}, {RLBM_KERNEL_PACKED, 128, 1, 3}, {RLBM_KERNEL_PACKED, 128, 2, 3},
+    {RLBM_KERNEL_PACKED, 64, 4, 3}, {RLBM_KERNEL_PACKED, 32, 8, 3},
     {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
     {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
 };
@@ -316,7 +321,10 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (opts) o = *opts;
     if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
     if (o.landau != RLBM_LANDAU_FP64 && o.landau != RLBM_LANDAU_FP32) return RLBM_ERR_ARG;
-    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_GATHER_VEC2) return RLBM_ERR_ARG;
+    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_PACKED) return RLBM_ERR_ARG;
+    if (o.kernel == RLBM_KERNEL_PACKED &&
+        (nx % 2 != 0 || o.dtype == RLBM_F64 || o.landau != RLBM_LANDAU_FP32))
+        return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_GATHER_VEC && nx % (o.dtype == RLBM_F64 ? 2 : 4) != 0) return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_GATHER_VEC2 && nx % 2 != 0) return RLBM_ERR_ARG;
     if (o.eps0 == 0.0) o.eps0 = 1.0;
@@ -328,7 +336,8 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (o.dt == 0.0) o.dt = 1.0;
     if (!(o.cfl > 0.0 && o.cfl <= 1.0) || !(o.eta_s >= 0.0) || !isfinite(o.eta_s) || !(o.dt > 0.0) || !isfinite(o.dt))
         return RLBM_ERR_ARG;
-    if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2))
+    if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2 ||
+                         o.kernel == RLBM_KERNEL_PACKED))
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
 

@@ -113,6 +113,11 @@ struct StepParams {
     int *err;         // device error word (bounded-wait / failure reporting)
 };
 
+// Arithmetic type of one node's lane: float and double here; packed.cuh
+// adds a pair of FP32 lanes (two nodes per instruction).
+template <typename T>
+struct is_f32_lane : std::is_same<T, float> {};
+
 // Fill the derived fields of a StepParams from inv_tau, eps0, scale, eta_k
 // and cfl.  Pull source of class c: x - cfl c; for 0 < cfl < 1 the corner
 // offset is -1 along an axis where c > 0 and 0 otherwise, with fractional
@@ -138,35 +143,41 @@ RLBM_HD inline void finish_params(StepParams &p) {
 
 template <typename T>
 RLBM_HD inline T par_wt(const StepParams &p, int c, int k) {
-    if constexpr (std::is_same<T, float>::value) return p.wt_f[c][k];
+    if constexpr (is_f32_lane<T>::value) return T(p.wt_f[c][k]);
     else return p.wt[c][k];
 }
 template <typename T>
 RLBM_HD inline T par_eta_k(const StepParams &p) {
-    if constexpr (std::is_same<T, float>::value) return p.eta_k_f;
+    if constexpr (is_f32_lane<T>::value) return T(p.eta_k_f);
     else return p.eta_k;
 }
 
 template <typename T>
 RLBM_HD inline T par_eps0(const StepParams &p) {
-    if constexpr (std::is_same<T, float>::value) return p.eps0_f;
+    if constexpr (is_f32_lane<T>::value) return T(p.eps0_f);
     else return p.eps0;
 }
 template <typename T>
 RLBM_HD inline T par_scale(const StepParams &p) {
-    if constexpr (std::is_same<T, float>::value) return p.scale_f;
+    if constexpr (is_f32_lane<T>::value) return T(p.scale_f);
     else return p.scale;
 }
 template <typename T>
 RLBM_HD inline T par_inv_scale(const StepParams &p) {
-    if constexpr (std::is_same<T, float>::value) return p.inv_scale_f;
+    if constexpr (is_f32_lane<T>::value) return T(p.inv_scale_f);
     else return p.inv_scale;
 }
 template <typename T>
 RLBM_HD inline T par_inv_tau(const StepParams &p) {
-    if constexpr (std::is_same<T, float>::value) return p.inv_tau_f;
+    if constexpr (is_f32_lane<T>::value) return T(p.inv_tau_f);
     else return p.inv_tau;
 }
+
+// a * b + c (one fused instruction); overloaded for packed lanes.
+template <typename T>
+RLBM_HD inline T fmadd(T a, T b, T c) { return a * b + c; }
+template <typename T>
+RLBM_HD inline T sqrt_(T x) { return std::sqrt(x); }
 
 // One lattice of an ensemble step (k_step_batch): its buffers, parameters
 // and its range in the flat tile list.
@@ -206,21 +217,21 @@ RLBM_HD inline NodeMoments<TC> node_moments(const TC (&q)[NC], TC s) {
         constexpr double w = cls_w(c), cx = cls_cx(c), cy = cls_cy(c);
         const TC sp = q[c] + q[cn];
         const TC dp = q[c] - q[cn];
-        e += (TC)w * sp;
+        e = fmadd((TC)w, sp, e);
         if constexpr (cx != 0.0) {
-            mx += (TC)(w * cx) * dp;
-            sxx += (TC)(w * cx * cx) * sp;
-            qxxx += (TC)(w * cx * cx * cx) * dp;
+            mx = fmadd((TC)(w * cx), dp, mx);
+            sxx = fmadd((TC)(w * cx * cx), sp, sxx);
+            qxxx = fmadd((TC)(w * cx * cx * cx), dp, qxxx);
         }
         if constexpr (cy != 0.0) {
-            my += (TC)(w * cy) * dp;
-            syy += (TC)(w * cy * cy) * sp;
-            qyyy += (TC)(w * cy * cy * cy) * dp;
+            my = fmadd((TC)(w * cy), dp, my);
+            syy = fmadd((TC)(w * cy * cy), sp, syy);
+            qyyy = fmadd((TC)(w * cy * cy * cy), dp, qyyy);
         }
         if constexpr (cx != 0.0 && cy != 0.0) {
-            sxy += (TC)(w * cx * cy) * sp;
-            qxxy += (TC)(w * cx * cx * cy) * dp;
-            qxyy += (TC)(w * cx * cy * cy) * dp;
+            sxy = fmadd((TC)(w * cx * cy), sp, sxy);
+            qxxy = fmadd((TC)(w * cx * cx * cy), dp, qxxy);
+            qxyy = fmadd((TC)(w * cx * cy * cy), dp, qxyy);
         }
     });
     NodeMoments<TC> m;
@@ -286,25 +297,26 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
     constexpr bool dbl = std::is_same<TL, double>::value;
     const TL tol = dbl ? (TL)4e-16 : (TL)1e-7;
     TL vx, vy;
+    const TL nMx = (TL)0 - Mx, nMy = (TL)0 - My, nSxy = (TL)0 - dSxy;
     auto velocity = [&](TL d, bool exact) {
         const TL a = a0 - d;
         const TL axx = a + dSxx, ayy = a + dSyy;
-        const TL det = axx * ayy - dSxy * dSxy;
-        const TL inv_det = exact ? recip<TL>(det) : fast_recip<TL>(det);
-        vx = (ayy * Mx - dSxy * My) * inv_det;
-        vy = (axx * My - dSxy * Mx) * inv_det;
+        const TL det = fmadd(axx, ayy, nSxy * dSxy);
+        const TL inv_det = exact ? recip(det) : fast_recip(det);
+        vx = fmadd(ayy, Mx, nSxy * My) * inv_det;
+        vy = fmadd(axx, My, nSxy * Mx) * inv_det;
     };
     velocity((TL)0, false);
-    const TL m1 = Mx * vx + My * vy;
-    const TL m2 = vx * vx + vy * vy;
-    TL delta = m1 * fast_recip<TL>((TL)1 - m2);
+    const TL m1 = fmadd(Mx, vx, My * vy);
+    const TL m2 = fmadd(vx, vx, vy * vy);
+    TL delta = m1 * fast_recip((TL)1 - m2);
     TL step;
     auto newton = [&]() {
         velocity(delta, false);
-        const TL g = delta - (Mx * vx + My * vy);
-        const TL gp = (TL)1 - (vx * vx + vy * vy);
-        step = g * fast_recip<TL>(gp);
-        delta -= step;
+        const TL g = fmadd(nMx, vx, fmadd(nMy, vy, delta));
+        const TL gp = fmadd((TL)0 - vx, vx, fmadd((TL)0 - vy, vy, (TL)1));
+        step = g * fast_recip(gp);
+        delta = delta - step;
     };
     newton();
     // near the root the error after a step is ~ step^2 |v|^2 / a0, so the
@@ -319,9 +331,9 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
     fr.eps = eps0 + fr.ddelta_eps;
     fr.vx = vx;
     fr.vy = vy;
-    fr.v2 = vx * vx + vy * vy;
-    fr.g2 = recip<TL>((TL)1 - fr.v2);
-    fr.gamma = std::sqrt(fr.g2);
+    fr.v2 = fmadd(vx, vx, vy * vy);
+    fr.g2 = recip((TL)1 - fr.v2);
+    fr.gamma = sqrt_(fr.g2);
     return fr;
 }
 
@@ -355,40 +367,40 @@ RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParam
                                           (TL)m.dSyy);
     const TC inv_s = par_inv_scale<TC>(p);
     const TL eg2 = fr.eps * fr.g2;
-    const TC P0 = (TC)(fr.ddelta_eps - (TL)2 * eg2 * fr.v2) * inv_s;
+    const TC P0 = (TC)(fmadd((TL)(-2) * eg2, fr.v2, fr.ddelta_eps)) * inv_s;
     const TC P1 = (TC)((TL)4 * eg2) * inv_s;
     const TC P2 = (TC)((TL)10 * eg2) * inv_s;
     const TC vx = (TC)fr.vx, vy = (TC)fr.vy;
     // relaxation rate: 1/tau, or in eta/s mode T(eps) dt / (5 eta/s)
     TL inv_tau = par_inv_tau<TL>(p);
-    if (p.eta_k_f > 0.0f) inv_tau = par_eta_k<TL>(p) * std::sqrt(std::sqrt(fr.eps));
+    if (p.eta_k_f > 0.0f) inv_tau = par_eta_k<TL>(p) * sqrt_(sqrt_(fr.eps));
     const TC om = (TC)(fr.gamma * inv_tau);
 
     // even part K0 + Kxx cx^2 + Kxy cx cy + Kyy cy^2, odd part coefficients
     const TC e2 = om * (P2 - P1);
     TC K0 = om * P0, Kxx = e2 * vx * vx, Kxy = (TC)2 * e2 * vx * vy, Kyy = e2 * vy * vy;
-    const TC o1 = om * (P1 - P0), o3 = om * P2;
+    const TC o1 = om * (P1 - P0), no3 = (TC)0 - om * P2;
     TC G1 = 0;
     if constexpr (FORCED) {
         const TC E = par_eps0<TC>(p) + m.dE;
         const TC c6 = (TC)(-6.0) * inv_s;
-        const TC G0 = c6 * (TC)0.25 * (Fx * m.Mx + Fy * m.My);
+        const TC G0 = c6 * (TC)0.25 * fmadd(Fx, m.Mx, Fy * m.My);
         G1 = c6 * (TC)(-0.5) * E;
         const TC G3 = c6 * (TC)(-2.5);
         const TC c54 = c6 * (TC)1.25;
         const TC Qxzz = m.Mx - m.Qxxx - m.Qxyy;
         const TC Qyzz = m.My - m.Qxxy - m.Qyyy;
-        const TC Pxx = c54 * (Fx * m.Qxxx + Fy * m.Qxxy);
-        const TC Pxy = c54 * (Fx * m.Qxxy + Fy * m.Qxyy);
-        const TC Pyy = c54 * (Fx * m.Qxyy + Fy * m.Qyyy);
-        const TC Pzz = c54 * (Fx * Qxzz + Fy * Qyzz);
-        K0 += G0 + Pzz;
-        Kxx += G3 * Fx * m.Mx + Pxx - Pzz;
-        Kxy += G3 * (Fx * m.My + Fy * m.Mx) + (TC)2 * Pxy;
-        Kyy += G3 * Fy * m.My + Pyy - Pzz;
+        const TC Pxx = c54 * fmadd(Fx, m.Qxxx, Fy * m.Qxxy);
+        const TC Pxy = c54 * fmadd(Fx, m.Qxxy, Fy * m.Qxyy);
+        const TC Pyy = c54 * fmadd(Fx, m.Qxyy, Fy * m.Qyyy);
+        const TC Pzz = c54 * fmadd(Fx, Qxzz, Fy * Qyzz);
+        K0 = K0 + (G0 + Pzz);
+        Kxx = fmadd(G3 * Fx, m.Mx, Kxx + (Pxx - Pzz));
+        Kxy = fmadd(G3, fmadd(Fx, m.My, Fy * m.Mx), Kxy + (TC)2 * Pxy);
+        Kyy = fmadd(G3 * Fy, m.My, Kyy + (Pyy - Pzz));
     }
     const TC a0 = (TC)1 - om;
-    q[0] = q[0] * a0 + K0;
+    q[0] = fmadd(q[0], a0, K0);
     static_for<0, NPAIR>([&](auto K) {
         constexpr int k = decltype(K)::value;
         constexpr int c = pair_pos(k), cn = pair_neg(k);
@@ -397,22 +409,22 @@ RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParam
         [[maybe_unused]] TC Fc = 0;
         TC even = K0;
         if constexpr (cx != 0.0) {
-            xi += (TC)cx * vx;
-            even += (TC)(cx * cx) * Kxx;
-            if constexpr (FORCED) Fc += (TC)cx * Fx;
+            xi = (TC)cx * vx;
+            even = fmadd((TC)(cx * cx), Kxx, even);
+            if constexpr (FORCED) Fc = (TC)cx * Fx;
         }
         if constexpr (cy != 0.0) {
-            xi += (TC)cy * vy;
-            even += (TC)(cy * cy) * Kyy;
-            if constexpr (FORCED) Fc += (TC)cy * Fy;
+            xi = fmadd((TC)cy, vy, xi);
+            even = fmadd((TC)(cy * cy), Kyy, even);
+            if constexpr (FORCED) Fc = fmadd((TC)cy, Fy, Fc);
         }
-        if constexpr (cx != 0.0 && cy != 0.0) even += (TC)(cx * cy) * Kxy;
-        TC odd = xi * (o1 - o3 * xi * xi);
-        if constexpr (FORCED) odd += G1 * Fc;
+        if constexpr (cx != 0.0 && cy != 0.0) even = fmadd((TC)(cx * cy), Kxy, even);
+        TC odd = xi * fmadd(no3, xi * xi, o1);
+        if constexpr (FORCED) odd = fmadd(G1, Fc, odd);
         const TC oxi = om * xi;
         const TC qp = q[c], qn = q[cn];
-        q[c] = qp * (a0 + oxi) + (even + odd);
-        q[cn] = qn * (a0 - oxi) + (even - odd);
+        q[c] = fmadd(qp, a0 + oxi, even + odd);
+        q[cn] = fmadd(qn, a0 - oxi, even - odd);
     });
     return fr;
 }

@@ -32,6 +32,7 @@ struct Launch {
 struct LaunchCfg {
     int kernel = RLBM_KERNEL_GATHER;
     int bx = 32, by = 8;
+    int minb = 1;  // packed kernel: register budget (blocks of 256 per SM: 1, 2 or 3)
 };
 
 cudaError_t launch_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
