@@ -89,8 +89,18 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
 template <typename TS, typename TC, typename TL>
 cudaError_t launch_batch_t(const LaunchCfg &cfg, int grid, const void *runs, int nruns, int ntiles, cudaStream_t s) {
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256 || grid < 1) return cudaErrorInvalidConfiguration;
-    k_step_batch<TS, TC, TL><<<grid, dim3(cfg.bx, cfg.by, 1), 0, s>>>(static_cast<const BatchRun *>(runs), nruns,
-                                                                      ntiles);
+    const dim3 block(cfg.bx, cfg.by, 1);
+    const BatchRun *r = static_cast<const BatchRun *>(runs);
+    if (cfg.kernel == RLBM_KERNEL_PACKED) {
+        if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
+            if (cfg.minb == 3) k_step_batch_pair<TS, 3><<<grid, block, 0, s>>>(r, nruns, ntiles);
+            else k_step_batch_pair<TS, 1><<<grid, block, 0, s>>>(r, nruns, ntiles);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    k_step_batch<TS, TC, TL><<<grid, block, 0, s>>>(r, nruns, ntiles);
     return cudaGetLastError();
 }
 

@@ -9,15 +9,10 @@
 
 namespace rlbk {
 
-// MINB: minimum resident blocks of 256 threads per SM asked of the register
-// allocator (1: unconstrained; 2: <= 128 registers; 3: <= 80), so the
-// autotuner can trade registers for occupancy.
-template <typename TS, bool FORCED, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
-                                                   const float *__restrict__ F, StepParams p) {
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= p.nx || y >= p.ny) return;
+// The fused step of the node pair (x0, x0 + 1) of row y in packed lanes.
+template <typename TS, bool FORCED>
+__device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                          const float *__restrict__ F, const StepParams &p, int x0, int y) {
     const int ym = (y == 0) ? p.ny - 1 : y - 1;
     const int yp = (y == p.ny - 1) ? 0 : y + 1;
     const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
@@ -59,6 +54,44 @@ __global__ void __launch_bounds__(256, MINB) k_step_pair(const TS *__restrict__ 
         const float out[2] = {q[c].v.x, q[c].v.y};
         store_run<TS, float, 2>(qout + (long long)c * p.plane + n0, out);
     });
+}
+
+// MINB: minimum resident blocks of 256 threads per SM asked of the register
+// allocator (1: unconstrained; 2: <= 128 registers; 3: <= 80), so the
+// autotuner can trade registers for occupancy.
+template <typename TS, bool FORCED, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                                         const float *__restrict__ F, StepParams p) {
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= p.nx || y >= p.ny) return;
+    step_pair<TS, FORCED>(qin, qout, F, p, x0, y);
+}
+
+// Ensemble step with the packed body (see k_step_batch).
+template <typename TS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_batch_pair(const BatchRun *__restrict__ runs, int nruns,
+                                                               int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int lo = 0, hi = nruns - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (runs[mid].tile0 <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchRun &r = runs[lo];
+        const int local = t - r.tile0;
+        const int tx = local % r.tiles_x, ty = local / r.tiles_x;
+        const int x0 = (tx * blockDim.x + threadIdx.x) * 2;
+        const int y = ty * blockDim.y + threadIdx.y;
+        if (x0 < r.p.nx && y < r.p.ny) {
+            if (r.F)
+                step_pair<TS, true>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout),
+                                    static_cast<const float *>(r.F), r.p, x0, y);
+            else
+                step_pair<TS, false>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout), nullptr, r.p, x0, y);
+        }
+    }
 }
 
 }  // namespace rlbk

@@ -822,7 +822,7 @@ static void batch_drop_graphs(rlbm_batch_t *b) {
 
 // Host copy of the descriptors for a launch shape; returns the tile count.
 static int batch_descriptors(const rlbm_batch_t *b, const LaunchCfg &cfg, int parity, std::vector<BatchRun> *out) {
-    const int V = run_length(b->opts.dtype);
+    const int V = (cfg.kernel == RLBM_KERNEL_PACKED) ? 2 : run_length(b->opts.dtype);
     int t0 = 0;
     out->clear();
     for (rlbm_t *h : b->runs) {
@@ -1049,6 +1049,9 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *bl
         if (st != RLBM_OK) return st;
     }
     static const int shapes[][2] = {{32, 4}, {64, 2}, {128, 1}, {32, 8}, {64, 4}, {128, 2}, {32, 2}, {64, 1}};
+    // body: the vector kernel, or the packed-lane kernel (FP32 compute, FP32 Landau)
+    const bool packed_ok = b->opts.dtype != RLBM_F64 && b->opts.landau == RLBM_LANDAU_FP32;
+    static const int bodies[][2] = {{RLBM_KERNEL_GATHER_VEC, 1}, {RLBM_KERNEL_PACKED, 1}, {RLBM_KERNEL_PACKED, 3}};
     const int sms = sm_count(b->device);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     BCUDA_TRY(b, cudaEventCreate(&e0));
@@ -1056,9 +1059,12 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *bl
     float best_ms = 1e30f;
     LaunchCfg best = b->cfg;
     int best_grid = b->grid;
+    for (const auto &body : bodies)
     for (const auto &sh : shapes) {
+        if (body[0] == RLBM_KERNEL_PACKED && !packed_ok) continue;
         LaunchCfg c;
-        c.kernel = RLBM_KERNEL_GATHER_VEC;
+        c.kernel = body[0];
+        c.minb = body[1];
         c.bx = sh[0];
         c.by = sh[1];
         rlbm_status st = batch_upload(b, c);

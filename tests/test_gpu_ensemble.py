@@ -95,8 +95,9 @@ def test_autotune_and_graphs_keep_results():
         ens.step(30)
         out.append([ens.populations(k) for k in range(len(RUNS))])
         ens.close()
+    # the tuned run may use another kernel body (packed lanes): FP32 rounding, not bitwise
     for a, b in zip(*out):
-        np.testing.assert_array_equal(a, b)
+        assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(a))
 
 
 def test_ensemble_workload_shape_runs():
