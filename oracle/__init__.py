@@ -40,13 +40,17 @@ _ip = ctypes.POINTER(ctypes.c_int)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 
 
+_SRCS = (_SRC, os.path.join(_HERE, "ring2d_oracle.c"))
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (idempotent)."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    if not force and os.path.exists(_LIB_PATH) and all(
+            os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src) for src in _SRCS):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
-           _SRC, "-o", tmp, "-lm"]
+           *_SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -101,6 +105,25 @@ def _load():
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
                                       ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         lib.oracle_run_ex.restype = ctypes.c_int
+        lib.ring_stencil.argtypes = [_dp, _dp]
+        lib.ring_moments_node.argtypes = [_dp, _dp]
+        lib.ring_landau.argtypes = [_dp, _dp, _dp]
+        lib.ring_landau.restype = ctypes.c_int
+        lib.ring_ideal_T.argtypes = [ctypes.c_double, _dp, _dp]
+        lib.ring_feq.argtypes = [ctypes.c_double, _dp, _dp]
+        lib.ring_force_term.argtypes = [_dp, _dp, _dp]
+        lib.ring_collide_node.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp]
+        lib.ring_collide_node.restype = ctypes.c_int
+        lib.ring_stream.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int]
+        lib.ring_init.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        lib.ring_init.restype = ctypes.c_int
+        lib.ring_run.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_long,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                 ctypes.c_int]
+        lib.ring_run.restype = ctypes.c_int
+        lib.ring_fields.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        lib.ring_fields.restype = ctypes.c_int
+        lib.ring_totals.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp]
         _lib = lib
         return lib
 
@@ -370,3 +393,105 @@ def merge_classes(f) -> np.ndarray:
             if abs(v[i, 0] - tx) < 1e-12 and abs(v[i, 1] - ty) < 1e-12:
                 out[c] += f[i]
     return out
+
+
+# --------------------------------------------------------------------------- 2D ring model
+RING = 8
+
+
+class ring:
+    """The genuinely 2D massless variant (8-direction ring, P = eps/2); see
+    ring2d_oracle.c.  Populations are (8, ny, nx) FP64 arrays."""
+
+    @staticmethod
+    def stencil():
+        lib = _load()
+        v = np.zeros((RING, 2))
+        w = np.zeros(RING)
+        lib.ring_stencil(_p(v), _p(w))
+        return v, w
+
+    @staticmethod
+    def moments(f_node):
+        T = np.zeros((3, 3))
+        _load().ring_moments_node(_p(_f64(f_node)), _p(T))
+        return T
+
+    @staticmethod
+    def landau(T):
+        eps, u = np.zeros(1), np.zeros(3)
+        it = _load().ring_landau(_p(_f64(T)), _p(eps), _p(u))
+        return float(eps[0]), u, int(it)
+
+    @staticmethod
+    def ideal_T(eps, u):
+        T = np.zeros((3, 3))
+        _load().ring_ideal_T(float(eps), _p(_f64(u)), _p(T))
+        return T
+
+    @staticmethod
+    def feq(eps, u):
+        out = np.zeros(RING)
+        _load().ring_feq(float(eps), _p(_f64(u)), _p(out))
+        return out
+
+    @staticmethod
+    def force_term(f_node, F):
+        G = np.zeros(RING)
+        _load().ring_force_term(_p(_f64(f_node)), _p(_f64(F)), _p(G))
+        return G
+
+    @staticmethod
+    def collide(f_node, F, tau):
+        f = _f64(f_node).copy()
+        eps, u = np.zeros(1), np.zeros(3)
+        rc = _load().ring_collide_node(_p(f), _p(_f64(F)) if F is not None else None, float(tau), _p(eps), _p(u))
+        if rc != 0:
+            raise FloatingPointError("Landau solve failed")
+        return f, float(eps[0]), u
+
+    @staticmethod
+    def stream(f):
+        f = _f64(f)
+        _, ny, nx = f.shape
+        out = np.empty_like(f)
+        _load().ring_stream(_p(f), _p(out), nx, ny)
+        return out
+
+    @staticmethod
+    def init(nx, ny, eps=None, vx=None, vy=None):
+        f = np.zeros((RING, ny, nx))
+        conv = lambda a: None if a is None else _f64(a).reshape(ny, nx)
+        rc = _load().ring_init(_p(f), nx, ny, _p(conv(eps)), _p(conv(vx)), _p(conv(vy)))
+        if rc != 0:
+            raise ValueError("invalid initial fields")
+        return f
+
+    @staticmethod
+    def run(f, tau, nsteps, step0=0, kmin=0, kmax=0, amp=0.0, seed=0, redraw=100):
+        assert f.dtype == np.float64 and f.flags.c_contiguous
+        _, ny, nx = f.shape
+        tmp = np.empty_like(f)
+        Fx, Fy = np.zeros((ny, nx)), np.zeros((ny, nx))
+        bad = _load().ring_run(_p(f), _p(tmp), _p(Fx), _p(Fy), nx, ny, float(tau), int(step0), int(nsteps), int(kmin),
+                               int(kmax), float(amp), int(seed), int(redraw))
+        if bad:
+            raise FloatingPointError("Landau solve failed %d times" % bad)
+        return f
+
+    @staticmethod
+    def fields(f):
+        f = _f64(f)
+        _, ny, nx = f.shape
+        tmp = np.empty_like(f)
+        eps, vx, vy = np.empty((ny, nx)), np.empty((ny, nx)), np.empty((ny, nx))
+        _load().ring_fields(_p(f), _p(tmp), nx, ny, _p(eps), _p(vx), _p(vy))
+        return eps, vx, vy
+
+    @staticmethod
+    def totals(f):
+        f = _f64(f)
+        _, ny, nx = f.shape
+        out = np.zeros(3)
+        _load().ring_totals(_p(f), nx, ny, _p(out))
+        return out
