@@ -60,6 +60,20 @@ def dist_env():
     return rank, world, local
 
 
+def step_kernel_source_hash():
+    """SHA-256 over the sources the fused step kernels compile from (the
+    per-node device code, the kernel bodies and their launchers), in name
+    order: a stored DRAM-traffic figure counts only while it matches."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2101_06187_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for fn in sorted(os.listdir(src)):
+        if fn in ("rlbm_device.cuh", "packed.cuh", "k_launch.cuh") or fn.startswith("k_step_"):
+            with open(os.path.join(src, fn), "rb") as fh:
+                hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -393,14 +407,8 @@ def main():
             with open(prof) as fh:
                 tj = json.load(fh)
             key = "%s_%s_%s_%d" % (args.form, args.landau, info["kernel"], n)
-            import hashlib
-            src = os.path.join(ROOT, "paper_2101_06187_gb300", "csrc")
-            hsh = hashlib.sha256()
-            for fn in sorted(os.listdir(src)):
-                if fn.endswith((".cu", ".cuh", ".h")):
-                    hsh.update(open(os.path.join(src, fn), "rb").read())
             ent = tj.get(key)
-            if ent and ent.get("source_sha256") == hsh.hexdigest():
+            if ent and ent.get("source_sha256") == step_kernel_source_hash():
                 traffic = ent["bytes_per_launch"]
         except (OSError, ValueError, KeyError):
             traffic = None

@@ -61,10 +61,18 @@ typedef enum {
     RLBM_ERR_STATE = 6     /* call not valid in the handle's current state */
 } rlbm_status;
 
-/* Velocity stencil.  Only the paper's node exists: the 26-direction
- * spherical rule on a one-layer (2D) lattice, stored as 17 in-plane classes;
- * sound speed c_s^2 = 1/3 (P = eps/3). */
-typedef enum { RLBM_STENCIL_SPH26_SLAB = 0 } rlbm_stencil;
+/* Velocity stencil.
+ * SPH26_SLAB: the paper's node (Sec. 3.1, Eq. 16, App. A): the 26-direction
+ *   spherical rule on a one-layer (2D) lattice, stored as 17 in-plane
+ *   classes; sound speed c_s^2 = 1/3 (P = eps/3).
+ * RING8_2D: the genuinely two-dimensional massless gas the paper contrasts
+ *   with its quasi-2D one (Sec. 3.1): 8 unit momenta in the plane at 45
+ *   degree steps, weight 1/8, P = eps/2, c_s^2 = 1/2; the same step with the
+ *   circle's angular polynomials (norms 1, 2, 4).  It runs the one node per
+ *   thread kernel (kernel AUTO or GATHER), at cfl 1 and fixed tau (eta_s 0),
+ *   and is not available to ensembles.  rlbm_info_t.nclasses is 8 and the
+ *   population arrays have 8 planes, in ring order k = 0..7 (angle k*45deg). */
+typedef enum { RLBM_STENCIL_SPH26_SLAB = 0, RLBM_STENCIL_RING8_2D = 1 } rlbm_stencil;
 
 /* Storage form of the populations.  All forms store the scaled deviation
  * q_c = (f_c - W_c eps0) / (W_c s) of each class from the rest equilibrium.
@@ -129,10 +137,12 @@ typedef struct {
     rlbm_alloc_fn alloc;  /* optional device allocator */
     rlbm_free_fn free;
     void *alloc_ctx;
-    /* CFL number Delta t / Delta x (0 < cfl <= 1, default 1): populations
-     * stream cfl * v_i cells per step (the paper's runs: Delta t = 0.05 with
-     * lattice spacing 0.32 ... 0.04).  cfl < 1 uses the one-node-per-thread
-     * kernel (RLBM_KERNEL_GATHER). */
+    /* CFL number Delta t / Delta x (0 < cfl < 2, default 1): populations
+     * stream cfl * v_i cells per step, interpolated bilinearly between the
+     * cells around x - cfl v_i (Sec. 3.2, Sec. 5: Delta t = 0.05 on lattice
+     * spacings 0.32, 0.16, 0.08, 0.04, i.e. cfl 0.156 ... 1.25).  cfl > 1
+     * reaches two cells (halo 2) for the classes with cfl |v_i,a| > 1.
+     * cfl != 1 uses the one-node-per-thread kernel (RLBM_KERNEL_GATHER). */
     double cfl;
     /* eta/s > 0 switches the relaxation time to the paper's
      * tau_R = 5 (eta/s) / T with eps = 3 T^4 / pi^2 (Sec. 3.1-3.2), node by
@@ -144,7 +154,7 @@ typedef struct {
 
 typedef struct {
     int nx, ny, pitch;        /* lattice and row pitch (elements) of the device arrays */
-    int nclasses;             /* 17 stored in-plane classes */
+    int nclasses;             /* stored classes: 17 (SPH26_SLAB) or 8 (RING8_2D) */
     int dtype;                /* rlbm_dtype */
     int kernel;               /* rlbm_kernel actually used */
     int block_x, block_y;     /* thread-block shape of the fused step */
@@ -153,7 +163,7 @@ typedef struct {
     double tau, eps0, scale;
     size_t bytes_per_node;    /* algorithmic HBM bytes per lattice update */
     size_t device_bytes;      /* device memory held by the handle */
-    const void *populations;  /* device pointer of the current state, [17][ny][pitch] of the storage type */
+    const void *populations;  /* device pointer of the current state, [nclasses][ny][pitch] of the storage type */
 } rlbm_info_t;
 
 /* Fill *opts with the defaults listed above. */
@@ -224,10 +234,11 @@ RLBM_API rlbm_status rlbm_spectrum_sample(rlbm_t *h, int nshells);
 RLBM_API rlbm_status rlbm_spectrum_stats(rlbm_t *h, int nshells, double *mean, double *sem, int *count);
 RLBM_API rlbm_status rlbm_spectrum_reset(rlbm_t *h);
 
-/* Decoded populations f_c = W_c (eps0 + s q_c) of the 17 stored classes,
- * host FP64 [17][ny][nx] (class order: rest; (1,0),(-1,0),(0,1),(0,-1);
- * (a,0),(-a,0),(0,a),(0,-a); (a,a),(-a,a),(a,-a),(-a,-a);
- * (b,b),(-b,b),(b,-b),(-b,-b); a = 1/sqrt2, b = 1/sqrt3).  Synchronises. */
+/* Decoded populations f_c = W_c (eps0 + s q_c) of the stored classes, host
+ * FP64 [nclasses][ny][nx].  SPH26_SLAB class order: rest;
+ * (1,0),(-1,0),(0,1),(0,-1); (a,0),(-a,0),(0,a),(0,-a);
+ * (a,a),(-a,a),(a,-a),(-a,-a); (b,b),(-b,b),(b,-b),(-b,-b); a = 1/sqrt2,
+ * b = 1/sqrt3.  RING8_2D: k = 0..7 at angle k*45 degrees.  Synchronises. */
 RLBM_API rlbm_status rlbm_get_populations(rlbm_t *h, double *f);
 
 /* Set the post-collision state from host FP64 populations in that layout
@@ -245,7 +256,8 @@ RLBM_API rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info);
  * handle's lattice and keep the fastest.  The trial launches read the
  * current state and write only the spare buffer, so the simulation state is
  * unchanged.  The choice is cached per (nx, ny, dtype, landau, forced) for
- * handles created later in the process with RLBM_KERNEL_AUTO.  Outputs may
+ * handles created later in the process with RLBM_KERNEL_AUTO (separately
+ * for each stencil).  Outputs may
  * be NULL.  Synchronises. */
 RLBM_API rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *kernel, int *block_x, int *block_y);
 
@@ -254,7 +266,7 @@ RLBM_API rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *kernel, int *block_
  * on a memory budget fixed up front, loops that must not take the implicit
  * synchronisation of cudaMalloc, or hosts whose device memory belongs to
  * another framework's pool).  Computes what rlbm_moments_device computes
- * from a caller-owned population array: d_q is the device state
+ * from a caller-owned SPH26_SLAB population array: d_q is the device state
  * [17][ny][pitch] of storage type `dtype` (for example rlbm_info_t.populations
  * and .pitch of a handle), eps0 and scale its deviation parameters; d_eps,
  * d_vx, d_vy (nx*ny FP64 each, any may be NULL) and d_totals (3 FP64, may be

@@ -26,6 +26,8 @@ LIB_PATH = os.path.join(_HERE, "librlbm.so")
 
 RLBM_OK, RLBM_ERR_ARG, RLBM_ERR_ALLOC, RLBM_ERR_CUDA, RLBM_ERR_TIMEOUT, RLBM_ERR_NAN, RLBM_ERR_STATE = range(7)
 RLBM_STENCIL_SPH26_SLAB = 0
+RLBM_STENCIL_RING8_2D = 1
+STENCILS = {"sph26": RLBM_STENCIL_SPH26_SLAB, "ring8": RLBM_STENCIL_RING8_2D}
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 LANDAU = {"fp64": 0, "fp32": 1}
 KERNELS = {"auto": 0, "gather": 1, "vec": 2, "vec2": 3, "packed": 4}
@@ -402,13 +404,15 @@ class Lattice:
     None or dict(kmin, kmax, amp, seed, redraw_period); allocator: "torch"
     (PyTorch caching allocator) or "cuda" (cudaMalloc inside the library);
     stream: a torch.cuda.Stream, an int cudaStream_t, or None (a new torch
-    stream for this lattice).
+    stream for this lattice); stencil: "sph26" (the paper's 26-direction
+    node, 17 stored classes) or "ring8" (the 2D massless gas on an
+    8-direction ring, P = eps/2; gather kernel, cfl 1, fixed tau).
     """
 
     def __init__(self, nx: int, ny: int, tau: float, *, dtype: str = "f32", landau: str = "fp32",
                  forcing: Optional[dict] = None, eps0: float = 1.0, scale: float = 0.0, kernel: str = "auto",
                  use_graphs: bool = True, allocator: str = "torch", stream=None, device: Optional[int] = None,
-                 cfl: float = 1.0, eta_s: float = 0.0, dt: float = 1.0):
+                 cfl: float = 1.0, eta_s: float = 0.0, dt: float = 1.0, stencil: str = "sph26"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the RLBM library runs on the GPU only")
@@ -448,7 +452,9 @@ class Lattice:
             f = Forcing(int(forcing.get("kmin", 0)), int(forcing.get("kmax", 0)), float(forcing.get("amp", 0.0)),
                         int(forcing.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF, int(forcing.get("redraw_period", 100)))
         self.dtype = dtype
-        self._h = rlbm_create(self.nx, self.ny, RLBM_STENCIL_SPH26_SLAB, self.tau, f, o)
+        self.stencil = stencil
+        self._h = rlbm_create(self.nx, self.ny, STENCILS[stencil], self.tau, f, o)
+        self.nclasses = self.info()["nclasses"]
 
     # -- life cycle
     def close(self):
@@ -519,12 +525,12 @@ class Lattice:
         rlbm_spectrum_reset(self.handle)
 
     def populations(self) -> np.ndarray:
-        f = np.empty((NCLASSES, self.ny, self.nx))
+        f = np.empty((self.nclasses, self.ny, self.nx))
         rlbm_get_populations(self.handle, f)
         return f
 
     def set_populations(self, f):
-        rlbm_set_populations(self.handle, _f64(f, NCLASSES * self.nx * self.ny))
+        rlbm_set_populations(self.handle, _f64(f, self.nclasses * self.nx * self.ny))
 
     def force(self):
         Fx = np.empty((self.ny, self.nx))

@@ -317,20 +317,16 @@ __global__ void k_encode_class(TS *q, int c, StepParams p, double W, const doubl
     q[(long long)c * p.plane + (long long)y * p.pitch + x] = store_any<TS>((f / W - p.eps0) / p.scale);
 }
 
-static double class_weight(int c) {
-    return c == 0 ? 2.0 / 21.0 : c <= 4 ? 1.0 / 21.0 : c <= 8 ? 8.0 / 105.0 : c <= 12 ? 4.0 / 105.0 : 9.0 / 140.0;
-}
-
-cudaError_t launch_decode_class(int dtype, const void *q, int c, const StepParams &p, double *out, cudaStream_t s) {
+cudaError_t launch_decode_class(int dtype, const void *q, int c, double W, const StepParams &p, double *out,
+                                cudaStream_t s) {
     dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
-    const double W = class_weight(c);
     RLBM_DISPATCH_STORAGE(dtype, TS, k_decode_class<TS><<<g, b, 0, s>>>(static_cast<const TS *>(q), c, p, W, out));
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode_class(int dtype, void *q, int c, const StepParams &p, const double *in, cudaStream_t s) {
+cudaError_t launch_encode_class(int dtype, void *q, int c, double W, const StepParams &p, const double *in,
+                                cudaStream_t s) {
     dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
-    const double W = class_weight(c);
     RLBM_DISPATCH_STORAGE(dtype, TS, k_encode_class<TS><<<g, b, 0, s>>>(static_cast<TS *>(q), c, p, W, in));
     return cudaGetLastError();
 }

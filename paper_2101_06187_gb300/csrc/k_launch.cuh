@@ -63,25 +63,22 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
     }
     const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
     const bool idx32 = (long long)NC * p.plane < (1ll << 31) - 1;
-    const bool cfl1 = p.cfl == 1.0;
-#define RLBM_GATHER(FOR, IDX, C1) k_step_gather<TS, TC, TL, FOR, IDX, C1><<<grid, block, 0, s>>>(in, out, f, p)
-    if (cfl1) {
-        if (idx32) {
-            if (forced) RLBM_GATHER(true, int, true);
-            else RLBM_GATHER(false, int, true);
-        } else {
-            if (forced) RLBM_GATHER(true, long long, true);
-            else RLBM_GATHER(false, long long, true);
-        }
-    } else {
-        if (idx32) {
-            if (forced) RLBM_GATHER(true, int, false);
-            else RLBM_GATHER(false, int, false);
-        } else {
-            if (forced) RLBM_GATHER(true, long long, false);
-            else RLBM_GATHER(false, long long, false);
-        }
-    }
+    const int sm = stream_mode(p.cfl);
+#define RLBM_GATHER(FOR, IDX, SM) k_step_gather<TS, TC, TL, FOR, IDX, SM><<<grid, block, 0, s>>>(in, out, f, p)
+#define RLBM_GATHER_SM(SM)                                 \
+    do {                                                   \
+        if (idx32) {                                       \
+            if (forced) RLBM_GATHER(true, int, SM);        \
+            else RLBM_GATHER(false, int, SM);              \
+        } else {                                           \
+            if (forced) RLBM_GATHER(true, long long, SM);  \
+            else RLBM_GATHER(false, long long, SM);        \
+        }                                                  \
+    } while (0)
+    if (sm == kStreamCfl1) RLBM_GATHER_SM(kStreamCfl1);
+    else if (sm == kStreamSub1) RLBM_GATHER_SM(kStreamSub1);
+    else RLBM_GATHER_SM(kStreamHalo2);
+#undef RLBM_GATHER_SM
 #undef RLBM_GATHER
     return cudaGetLastError();
 }
@@ -107,12 +104,14 @@ cudaError_t launch_batch_t(const LaunchCfg &cfg, int grid, const void *runs, int
 template <typename TS, typename TC, typename TL>
 cudaError_t launch_moments_t(const void *qin, const StepParams &p, double *eps, double *vx, double *vy,
                              double *partials, int *bad, cudaStream_t s) {
-    if (p.cfl == 1.0)
-        k_moments<TS, TC, TL, true><<<gather_grid(p), gather_block(), 0, s>>>(static_cast<const TS *>(qin), p, eps, vx,
-                                                                              vy, partials, bad);
+    const TS *q = static_cast<const TS *>(qin);
+    const int sm = stream_mode(p.cfl);
+    if (sm == kStreamCfl1)
+        k_moments<TS, TC, TL, kStreamCfl1><<<gather_grid(p), gather_block(), 0, s>>>(q, p, eps, vx, vy, partials, bad);
+    else if (sm == kStreamSub1)
+        k_moments<TS, TC, TL, kStreamSub1><<<gather_grid(p), gather_block(), 0, s>>>(q, p, eps, vx, vy, partials, bad);
     else
-        k_moments<TS, TC, TL, false><<<gather_grid(p), gather_block(), 0, s>>>(static_cast<const TS *>(qin), p, eps,
-                                                                               vx, vy, partials, bad);
+        k_moments<TS, TC, TL, kStreamHalo2><<<gather_grid(p), gather_block(), 0, s>>>(q, p, eps, vx, vy, partials, bad);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,73 @@
+// Launchers of the 2D ring variant (k_ring.cuh) for every storage form.
+#include "k_ring.cuh"
+#include "rlbm_internal.h"
+
+namespace rlbk {
+
+template <typename TS, typename TC, typename TL>
+static cudaError_t ring_step_t(const LaunchCfg &cfg, bool forced, const void *qin, void *qout, const void *F,
+                               const StepParams &p, cudaStream_t s) {
+    if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
+    const dim3 block(cfg.bx, cfg.by, 1);
+    const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
+    const TS *in = static_cast<const TS *>(qin);
+    TS *out = static_cast<TS *>(qout);
+    const TC *f = static_cast<const TC *>(F);
+    if (forced) k_ring_step<TS, TC, TL, true><<<grid, block, 0, s>>>(in, out, f, p);
+    else k_ring_step<TS, TC, TL, false><<<grid, block, 0, s>>>(in, out, f, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ring_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
+                             const void *F, const StepParams &p, cudaStream_t s) {
+    if ((long long)NR * p.plane >= (1ll << 31)) return cudaErrorInvalidValue;
+    const bool l32 = landau == RLBM_LANDAU_FP32;
+    switch (dtype) {
+    case RLBM_F64: return ring_step_t<double, double, double>(cfg, forced, qin, qout, F, p, s);
+    case RLBM_F32:
+        return l32 ? ring_step_t<float, float, float>(cfg, forced, qin, qout, F, p, s)
+                   : ring_step_t<float, float, double>(cfg, forced, qin, qout, F, p, s);
+    case RLBM_BF16:
+        return l32 ? ring_step_t<__nv_bfloat16, float, float>(cfg, forced, qin, qout, F, p, s)
+                   : ring_step_t<__nv_bfloat16, float, double>(cfg, forced, qin, qout, F, p, s);
+    default:
+        return l32 ? ring_step_t<__half, float, float>(cfg, forced, qin, qout, F, p, s)
+                   : ring_step_t<__half, float, double>(cfg, forced, qin, qout, F, p, s);
+    }
+}
+
+cudaError_t launch_ring_moments(int dtype, const void *qin, const StepParams &p, double *eps, double *vx, double *vy,
+                                double *partials, int *bad, cudaStream_t s) {
+    const dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+    switch (dtype) {
+    case RLBM_F64:
+        k_ring_moments<double, double><<<g, b, 0, s>>>(static_cast<const double *>(qin), p, eps, vx, vy, partials, bad);
+        break;
+    case RLBM_F32:
+        k_ring_moments<float, float><<<g, b, 0, s>>>(static_cast<const float *>(qin), p, eps, vx, vy, partials, bad);
+        break;
+    case RLBM_BF16:
+        k_ring_moments<__nv_bfloat16, float><<<g, b, 0, s>>>(static_cast<const __nv_bfloat16 *>(qin), p, eps, vx, vy,
+                                                             partials, bad);
+        break;
+    default:
+        k_ring_moments<__half, float><<<g, b, 0, s>>>(static_cast<const __half *>(qin), p, eps, vx, vy, partials, bad);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ring_init(int dtype, void *q, const StepParams &p, const double *eps, const double *vx,
+                             const double *vy, cudaStream_t s) {
+    const dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+    switch (dtype) {
+    case RLBM_F64: k_ring_init<double, double><<<g, b, 0, s>>>(static_cast<double *>(q), p, eps, vx, vy); break;
+    case RLBM_F32: k_ring_init<float, float><<<g, b, 0, s>>>(static_cast<float *>(q), p, eps, vx, vy); break;
+    case RLBM_BF16:
+        k_ring_init<__nv_bfloat16, float><<<g, b, 0, s>>>(static_cast<__nv_bfloat16 *>(q), p, eps, vx, vy);
+        break;
+    default: k_ring_init<__half, float><<<g, b, 0, s>>>(static_cast<__half *>(q), p, eps, vx, vy);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rlbk

@@ -10,67 +10,93 @@
 namespace rlbk {
 
 // Gather class c at node (x, y) by bilinear pull interpolation (Sec. 3.2).
-// rowoff[k] / cols[k], k = 0, 1, 2, are the periodic neighbours y-1, y, y+1
-// (x-1, x, x+1); class offsets lie in {-1, 0, +1} (CFL 1).  I is the index
+// rowoff[k] / cols[k], k = 0..4, are the periodic neighbours y-2..y+2
+// (x-2..x+2); SM is the streaming mode (kStreamCfl1: corners in {-1, 0, +1}
+// and weights fixed at compile time; kStreamSub1: same corners, runtime
+// weights; kStreamHalo2: the corner of an axis with cfl |c| > 1 moves one
+// cell further, to -2 or +1, picked by a register select).  I is the index
 // type: 32-bit when 17 planes fit, so each load costs one add.
-template <int c, typename TS, typename TC, typename I, bool CFL1>
-__device__ __forceinline__ TC gather_class(const TS *__restrict__ qin, I cbase, const I (&rowoff)[3],
-                                           const I (&cols)[3], const StepParams &p) {
-    if constexpr (CFL1) {
+template <int c, typename TS, typename TC, typename I, int SM>
+__device__ __forceinline__ TC gather_class(const TS *__restrict__ qin, I cbase, const I (&rowoff)[5],
+                                           const I (&cols)[5], const StepParams &p) {
+    if constexpr (SM == kStreamCfl1) {
         constexpr int ox = cls_ox(c), oy = cls_oy(c);
         constexpr double tx = cls_tx(c), ty = cls_ty(c);
-        const I r0 = cbase + rowoff[oy + 1];
-        TC v = (TC)((1.0 - tx) * (1.0 - ty)) * load_q<TS, TC>(qin + (r0 + cols[ox + 1]));
-        if constexpr (tx != 0.0) v += (TC)(tx * (1.0 - ty)) * load_q<TS, TC>(qin + (r0 + cols[ox + 2]));
+        const I r0 = cbase + rowoff[oy + 2];
+        TC v = (TC)((1.0 - tx) * (1.0 - ty)) * load_q<TS, TC>(qin + (r0 + cols[ox + 2]));
+        if constexpr (tx != 0.0) v += (TC)(tx * (1.0 - ty)) * load_q<TS, TC>(qin + (r0 + cols[ox + 3]));
         if constexpr (ty != 0.0) {
-            const I r1 = cbase + rowoff[oy + 2];
-            v += (TC)((1.0 - tx) * ty) * load_q<TS, TC>(qin + (r1 + cols[ox + 1]));
-            if constexpr (tx != 0.0) v += (TC)(tx * ty) * load_q<TS, TC>(qin + (r1 + cols[ox + 2]));
+            const I r1 = cbase + rowoff[oy + 3];
+            v += (TC)((1.0 - tx) * ty) * load_q<TS, TC>(qin + (r1 + cols[ox + 2]));
+            if constexpr (tx != 0.0) v += (TC)(tx * ty) * load_q<TS, TC>(qin + (r1 + cols[ox + 3]));
         }
         return v;
     } else {
-        // cfl < 1: every moving class interpolates between its node and the
-        // neighbour it streams from, with the launch's per-class weights
+        // cfl != 1: every moving class interpolates between the two cells
+        // around x - cfl c, with the launch's per-class weights
         constexpr double cx = cls_cx(c), cy = cls_cy(c);
-        constexpr int ox = cx > 0 ? -1 : 0, oy = cy > 0 ? -1 : 0;
+        constexpr int ox = cx > 0 ? -1 : 0, oy = cy > 0 ? -1 : 0;  // near corner
+        constexpr int fx = cx > 0 ? -1 : 1, fy = cy > 0 ? -1 : 1;  // step to the far corner
         constexpr bool mx = cx != 0.0, my = cy != 0.0;
-        const I r0 = cbase + rowoff[oy + 1];
-        if constexpr (!mx && !my) return load_q<TS, TC>(qin + (r0 + cols[1]));
-        TC v = par_wt<TC>(p, c, 0) * load_q<TS, TC>(qin + (r0 + cols[ox + 1]));
-        if constexpr (mx) v += par_wt<TC>(p, c, 1) * load_q<TS, TC>(qin + (r0 + cols[ox + 2]));
+        if constexpr (!mx && !my) return load_q<TS, TC>(qin + (cbase + rowoff[2] + cols[2]));
+        I x0 = cols[ox + 2], x1 = cols[ox + 3], ra = rowoff[oy + 2], rb = rowoff[oy + 3];
+        if constexpr (SM == kStreamHalo2) {
+            if (mx && ((p.far_x >> c) & 1u)) {
+                x0 = cols[ox + fx + 2];
+                x1 = cols[ox + fx + 3];
+            }
+            if (my && ((p.far_y >> c) & 1u)) {
+                ra = rowoff[oy + fy + 2];
+                rb = rowoff[oy + fy + 3];
+            }
+        }
+        const I r0 = cbase + ra;
+        TC v = par_wt<TC>(p, c, 0) * load_q<TS, TC>(qin + (r0 + x0));
+        if constexpr (mx) v += par_wt<TC>(p, c, 1) * load_q<TS, TC>(qin + (r0 + x1));
         if constexpr (my) {
-            const I r1 = cbase + rowoff[oy + 2];
-            v += par_wt<TC>(p, c, 2) * load_q<TS, TC>(qin + (r1 + cols[ox + 1]));
-            if constexpr (mx) v += par_wt<TC>(p, c, 3) * load_q<TS, TC>(qin + (r1 + cols[ox + 2]));
+            const I r1 = cbase + rb;
+            v += par_wt<TC>(p, c, 2) * load_q<TS, TC>(qin + (r1 + x0));
+            if constexpr (mx) v += par_wt<TC>(p, c, 3) * load_q<TS, TC>(qin + (r1 + x1));
         }
         return v;
     }
 }
 
-template <typename TS, typename TC, typename I = long long, bool CFL1 = true>
+// Periodic neighbour a + d, |d| <= 2, of a in [0, n), n >= 4.
+__device__ __forceinline__ int wrap2(int a, int d, int n) {
+    const int b = a + d;
+    return b < 0 ? b + n : (b >= n ? b - n : b);
+}
+
+template <typename TS, typename TC, typename I = long long, int SM = kStreamCfl1>
 __device__ __forceinline__ void gather_node(const TS *__restrict__ qin, const StepParams &p, int x, int y,
                                             TC (&q)[NC]) {
-    const int ym = (y == 0) ? p.ny - 1 : y - 1;
-    const int yp = (y == p.ny - 1) ? 0 : y + 1;
-    const int xm = (x == 0) ? p.nx - 1 : x - 1;
-    const int xp = (x == p.nx - 1) ? 0 : x + 1;
-    const I rowoff[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
-    const I cols[3] = {(I)xm, (I)x, (I)xp};
+    I rowoff[5], cols[5];
+    static_for<0, 5>([&](auto D) {
+        constexpr int d = decltype(D)::value - 2;
+        if constexpr (SM == kStreamHalo2 || (d >= -1 && d <= 1)) {
+            rowoff[d + 2] = (I)wrap2(y, d, p.ny) * (I)p.pitch;
+            cols[d + 2] = (I)wrap2(x, d, p.nx);
+        } else {
+            rowoff[d + 2] = 0;  // not referenced below CFL 1
+            cols[d + 2] = 0;
+        }
+    });
     const I plane = (I)p.plane;
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
-        q[c] = gather_class<c, TS, TC, I, CFL1>(qin, (I)c * plane, rowoff, cols, p);
+        q[c] = gather_class<c, TS, TC, I, SM>(qin, (I)c * plane, rowoff, cols, p);
     });
 }
 
-template <typename TS, typename TC, typename TL, bool FORCED, typename I, bool CFL1>
+template <typename TS, typename TC, typename TL, bool FORCED, typename I, int SM>
 __global__ void __launch_bounds__(256) k_step_gather(const TS *__restrict__ qin, TS *__restrict__ qout,
                                                      const TC *__restrict__ F, StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     TC q[NC];
-    gather_node<TS, TC, I, CFL1>(qin, p, x, y, q);
+    gather_node<TS, TC, I, SM>(qin, p, x, y, q);
     const I n = (I)y * (I)p.pitch + (I)x;
     const I plane = (I)p.plane;
     TC Fx = 0, Fy = 0;
@@ -89,7 +115,7 @@ __global__ void __launch_bounds__(256) k_step_gather(const TS *__restrict__ qin,
 // nx*ny), and per-block FP64 partial sums of (T^00, T^0x, T^0y) for the
 // global conservation totals (warp shuffles, then one partial per block in
 // `partials`, reduced in a fixed order by k_reduce_partials).
-template <typename TS, typename TC, typename TL, bool CFL1>
+template <typename TS, typename TC, typename TL, int SM>
 __global__ void __launch_bounds__(256) k_moments(const TS *__restrict__ qin, StepParams p, double *__restrict__ eps,
                                                  double *__restrict__ vx, double *__restrict__ vy,
                                                  double *__restrict__ partials, int *__restrict__ bad) {
@@ -98,7 +124,7 @@ __global__ void __launch_bounds__(256) k_moments(const TS *__restrict__ qin, Ste
     double sE = 0.0, sMx = 0.0, sMy = 0.0;
     if (x < p.nx && y < p.ny) {
         TC q[NC];
-        gather_node<TS, TC, long long, CFL1>(qin, p, x, y, q);
+        gather_node<TS, TC, long long, SM>(qin, p, x, y, q);
         const NodeMoments<TC> m = node_moments<TC>(q, par_scale<TC>(p));
         const Frame<TL> fr = landau_solve<TL>(par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
                                               (TL)m.dSyy);

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "rlbm_internal.h"
+#include "k_ring.cuh"
 
 namespace rlbk {
 
@@ -139,11 +140,23 @@ static StepParams params_of(const rlbm_t *h) {
     return p;
 }
 
-static size_t q_bytes(const rlbm_t *h) { return (size_t)NC * h->ny * h->pitch * storage_bytes(h->opts.dtype); }
+static size_t q_bytes(const rlbm_t *h) { return (size_t)h->ncls * h->ny * h->pitch * storage_bytes(h->opts.dtype); }
 static size_t F_bytes(const rlbm_t *h) { return (size_t)2 * h->ny * h->pitch * compute_bytes(h->opts.dtype); }
 static size_t tw_bytes(const rlbm_t *h, int n) { return (size_t)n * 2 * compute_bytes(h->opts.dtype); }
 static size_t fields_bytes(const rlbm_t *h) { return (size_t)3 * h->nx * h->ny * sizeof(double); }
 static size_t partials_bytes(const rlbm_t *h) { return (size_t)3 * moments_blocks(params_of(h)) * sizeof(double); }
+
+// Class weight W_c of stored class c (spherical node or 2D ring).
+static double class_weight(const rlbm_t *h, int c) {
+    if (h->ring) return 1.0 / 8.0;
+    return c == 0 ? 2.0 / 21.0 : c <= 4 ? 1.0 / 21.0 : c <= 8 ? 8.0 / 105.0 : c <= 12 ? 4.0 / 105.0 : 9.0 / 140.0;
+}
+
+static cudaError_t launch_step_h(const rlbm_t *h, const LaunchCfg &cfg, const void *qin, void *qout,
+                                 const StepParams &p) {
+    if (h->ring) return launch_ring_step(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
+    return launch_step(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
+}
 
 static int enumerate_modes(int kmin, int kmax, std::vector<Mode> *out) {
     int m = 0;
@@ -174,8 +187,7 @@ static rlbm_status ensure_force(rlbm_t *h) {
 static rlbm_status launch_steps(rlbm_t *h, int n) {
     const StepParams p = params_of(h);
     for (int i = 0; i < n; ++i) {
-        CUDA_TRY(h, launch_step(h->opts.dtype, h->opts.landau, h->cfg, h->forced, h->q[h->cur], h->q[h->cur ^ 1],
-                                h->F, p, h->stream));
+        CUDA_TRY(h, launch_step_h(h, h->cfg, h->q[h->cur], h->q[h->cur ^ 1], p));
         h->cur ^= 1;
     }
     return RLBM_OK;
@@ -241,12 +253,13 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
     {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
 };
-static std::map<std::tuple<int, int, int, int, int>, LaunchCfg> g_tuned;
+static std::map<std::tuple<int, int, int, int, int, int>, LaunchCfg> g_tuned;
 static std::mutex g_tuned_mu;
 
-static std::tuple<int, int, int, int, int> tune_key(const rlbm_t *h) {
-    return std::make_tuple(h->nx, h->ny, h->opts.dtype, h->opts.landau, h->forced ? 1 : 0);
+static std::tuple<int, int, int, int, int, int> tune_key(const rlbm_t *h) {
+    return std::make_tuple(h->nx, h->ny, h->opts.dtype, h->opts.landau, h->forced ? 1 : 0, h->ring ? 1 : 0);
 }
+
 
 static void drop_graphs(rlbm_t *h) {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
@@ -313,7 +326,8 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
                         const rlbm_opts *opts, rlbm_t **out) {
     if (!out) return RLBM_ERR_ARG;
     *out = nullptr;
-    if (stencil != RLBM_STENCIL_SPH26_SLAB) return RLBM_ERR_ARG;
+    if (stencil != RLBM_STENCIL_SPH26_SLAB && stencil != RLBM_STENCIL_RING8_2D) return RLBM_ERR_ARG;
+    const bool ring = stencil == RLBM_STENCIL_RING8_2D;
     if (nx < 4 || ny < 4 || (long long)nx * ny > (1ll << 31)) return RLBM_ERR_ARG;
     if (!(tau > 0.5) || !isfinite(tau)) return RLBM_ERR_ARG;
     rlbm_opts o;
@@ -334,12 +348,15 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (o.alloc && !o.free) return RLBM_ERR_ARG;
     if (o.cfl == 0.0) o.cfl = 1.0;
     if (o.dt == 0.0) o.dt = 1.0;
-    if (!(o.cfl > 0.0 && o.cfl <= 1.0) || !(o.eta_s >= 0.0) || !isfinite(o.eta_s) || !(o.dt > 0.0) || !isfinite(o.dt))
+    if (!(o.cfl > 0.0 && o.cfl < 2.0) || !(o.eta_s >= 0.0) || !isfinite(o.eta_s) || !(o.dt > 0.0) || !isfinite(o.dt))
         return RLBM_ERR_ARG;
     if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2 ||
                          o.kernel == RLBM_KERNEL_PACKED))
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
+    // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
+    if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER) || o.cfl != 1.0 || o.eta_s != 0.0))
+        return RLBM_ERR_ARG;
 
     rlbm_forcing fz{};
     bool forced = false;
@@ -361,6 +378,8 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     h->opts = o;
     h->forcing = fz;
     h->forced = forced;
+    h->ring = ring;
+    h->ncls = ring ? NR : NC;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {
             delete h;
@@ -447,7 +466,8 @@ static rlbm_status init_device_impl(rlbm_t *h, const double *d_eps, const double
         h->step = 0;
         h->force_epoch = -1;
     }
-    CUDA_TRY(h, launch_init(h->opts.dtype, h->q[h->cur], params_of(h), d_eps, d_vx, d_vy, h->stream));
+    if (h->ring) CUDA_TRY(h, launch_ring_init(h->opts.dtype, h->q[h->cur], params_of(h), d_eps, d_vx, d_vy, h->stream));
+    else CUDA_TRY(h, launch_init(h->opts.dtype, h->q[h->cur], params_of(h), d_eps, d_vx, d_vy, h->stream));
     return RLBM_OK;
 }
 
@@ -511,8 +531,12 @@ rlbm_status rlbm_moments_device(rlbm_t *h, double *d_eps, double *d_vx, double *
     CHECK_HANDLE(h);
     const StepParams p = params_of(h);
     CUDA_TRY(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
-    CUDA_TRY(h, launch_moments(h->opts.dtype, h->opts.landau, h->q[h->cur], p, d_eps, d_vx, d_vy, h->partials, h->bad,
-                               h->stream));
+    if (h->ring)
+        CUDA_TRY(h, launch_ring_moments(h->opts.dtype, h->q[h->cur], p, d_eps, d_vx, d_vy, h->partials, h->bad,
+                                        h->stream));
+    else
+        CUDA_TRY(h, launch_moments(h->opts.dtype, h->opts.landau, h->q[h->cur], p, d_eps, d_vx, d_vy, h->partials,
+                                   h->bad, h->stream));
     if (d_totals)
         CUDA_TRY(h, launch_reduce_partials(h->partials, moments_blocks(p), h->opts.eps0 * (double)h->nx * h->ny,
                                            d_totals, h->stream));
@@ -642,8 +666,8 @@ rlbm_status rlbm_get_populations(rlbm_t *h, double *f) {
     if (!f) return RLBM_ERR_ARG;
     const size_t n = (size_t)h->nx * h->ny;
     const StepParams p = params_of(h);
-    for (int c = 0; c < NC; ++c) {
-        CUDA_TRY(h, launch_decode_class(h->opts.dtype, h->q[h->cur], c, p, h->fields, h->stream));
+    for (int c = 0; c < h->ncls; ++c) {
+        CUDA_TRY(h, launch_decode_class(h->opts.dtype, h->q[h->cur], c, class_weight(h, c), p, h->fields, h->stream));
         CUDA_TRY(h, cudaMemcpyAsync(f + c * n, h->fields, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     }
@@ -655,10 +679,10 @@ rlbm_status rlbm_set_populations(rlbm_t *h, const double *f) {
     if (!f) return RLBM_ERR_ARG;
     const size_t n = (size_t)h->nx * h->ny;
     const StepParams p = params_of(h);
-    for (int c = 0; c < NC; ++c) {
+    for (int c = 0; c < h->ncls; ++c) {
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         CUDA_TRY(h, cudaMemcpyAsync(h->fields, f + c * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        CUDA_TRY(h, launch_encode_class(h->opts.dtype, h->q[h->cur], c, p, h->fields, h->stream));
+        CUDA_TRY(h, launch_encode_class(h->opts.dtype, h->q[h->cur], c, class_weight(h, c), p, h->fields, h->stream));
     }
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return RLBM_OK;
@@ -690,7 +714,7 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
     info->nx = h->nx;
     info->ny = h->ny;
     info->pitch = h->pitch;
-    info->nclasses = NC;
+    info->nclasses = h->ncls;
     info->dtype = h->opts.dtype;
     info->kernel = h->cfg.kernel;
     info->block_x = h->cfg.bx;
@@ -700,7 +724,7 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
     info->tau = h->tau;
     info->eps0 = h->opts.eps0;
     info->scale = h->opts.scale;
-    info->bytes_per_node = (size_t)2 * NC * storage_bytes(h->opts.dtype) + (h->forced ? 2 * compute_bytes(h->opts.dtype) : 0);
+    info->bytes_per_node = (size_t)2 * h->ncls * storage_bytes(h->opts.dtype) + (h->forced ? 2 * compute_bytes(h->opts.dtype) : 0);
     info->device_bytes = h->device_bytes;
     info->populations = h->q[h->cur];
     return RLBM_OK;
@@ -719,13 +743,12 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     LaunchCfg best = h->cfg;
     for (const LaunchCfg &c : kCandidates) {
         if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
-        if (h->opts.cfl != 1.0 && c.kernel != RLBM_KERNEL_GATHER) continue;
+        if ((h->opts.cfl != 1.0 || h->ring) && c.kernel != RLBM_KERNEL_GATHER) continue;
         // the trial steps read the current state and overwrite only the spare buffer
         bool ok = true;
         for (int i = 0; i < 2 + reps && ok; ++i) {
             if (i == 2) ok = cudaEventRecord(a, h->stream) == cudaSuccess;
-            ok = ok && launch_step(h->opts.dtype, h->opts.landau, c, h->forced, h->q[h->cur], h->q[h->cur ^ 1], h->F,
-                                   p, h->stream) == cudaSuccess;
+            ok = ok && launch_step_h(h, c, h->q[h->cur], h->q[h->cur ^ 1], p) == cudaSuccess;
         }
         if (!ok) {
             cudaGetLastError();

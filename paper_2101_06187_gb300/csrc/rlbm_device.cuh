@@ -105,11 +105,14 @@ struct StepParams {
     // eps = 3 T^4/pi^2, in steps of dt: eta_k = (pi^2/3)^{1/4} dt / (5 eta/s)
     double eta_k;
     float eta_k_f;
-    // CFL number (streaming displacement cfl * v_i per step) and, for cfl < 1,
-    // the bilinear weights (w00, w10, w01, w11) of each class's pull
+    // CFL number (streaming displacement cfl * v_i per step) and, for
+    // cfl != 1, the bilinear weights (w00, w10, w01, w11) of each class's
+    // pull and the classes whose corner lies two cells away (cfl > 1):
+    // bit c of far_x / far_y is set when cfl |c_x| > 1 (cfl |c_y| > 1)
     double cfl;
     double wt[17][4];
     float wt_f[17][4];
+    unsigned far_x, far_y;
     int *err;         // device error word (bounded-wait / failure reporting)
 };
 
@@ -118,10 +121,19 @@ struct StepParams {
 template <typename T>
 struct is_f32_lane : std::is_same<T, float> {};
 
+// How the fused step streams: CFL 1 (compile-time corners and weights),
+// 0 < cfl < 1 (compile-time corners, runtime weights), 1 < cfl < 2 (corners
+// one or two cells away, chosen per class at run time: halo 2).
+enum : int { kStreamCfl1 = 0, kStreamSub1 = 1, kStreamHalo2 = 2 };
+
+inline int stream_mode(double cfl) { return cfl == 1.0 ? kStreamCfl1 : cfl < 1.0 ? kStreamSub1 : kStreamHalo2; }
+
 // Fill the derived fields of a StepParams from inv_tau, eps0, scale, eta_k
-// and cfl.  Pull source of class c: x - cfl c; for 0 < cfl < 1 the corner
-// offset is -1 along an axis where c > 0 and 0 otherwise, with fractional
-// part t = 1 - cfl c (c > 0) or cfl |c| (c < 0).
+// and cfl.  Pull source of class c: x - cfl c, per axis the corner offset
+// o = floor(-cfl c) and fractional part t = -cfl c - o: for 0 < cfl < 1,
+// o = -1 where c > 0 and 0 otherwise (t = 1 - cfl c or cfl |c|); for
+// 1 < cfl < 2 the offset moves one cell further (-2 or +1) on the axes
+// where cfl |c| > 1.
 RLBM_HD inline void finish_params(StepParams &p) {
     p.inv_scale = 1.0 / p.scale;
     p.inv_tau_f = (float)p.inv_tau;
@@ -129,10 +141,13 @@ RLBM_HD inline void finish_params(StepParams &p) {
     p.scale_f = (float)p.scale;
     p.inv_scale_f = (float)p.inv_scale;
     p.eta_k_f = (float)p.eta_k;
+    p.far_x = p.far_y = 0u;
     for (int c = 0; c < 17; ++c) {
-        const double cx = cls_cx(c), cy = cls_cy(c);
-        const double tx = cx > 0 ? 1.0 - p.cfl * cx : (cx < 0 ? -p.cfl * cx : 0.0);
-        const double ty = cy > 0 ? 1.0 - p.cfl * cy : (cy < 0 ? -p.cfl * cy : 0.0);
+        const double sx = -p.cfl * cls_cx(c), sy = -p.cfl * cls_cy(c);
+        const double ox = floor(sx), oy = floor(sy);
+        const double tx = sx - ox, ty = sy - oy;
+        if (ox == -2.0 || ox == 1.0) p.far_x |= 1u << c;
+        if (oy == -2.0 || oy == 1.0) p.far_y |= 1u << c;
         p.wt[c][0] = (1.0 - tx) * (1.0 - ty);
         p.wt[c][1] = tx * (1.0 - ty);
         p.wt[c][2] = (1.0 - tx) * ty;
@@ -291,9 +306,12 @@ RLBM_HD inline T fast_recip(T x) {
     return (T)1 / x;
 }
 
+// rest_a: (S + eps I) at rest in units of eps0 -- 4/3 for the spherical node
+// (P = eps/3), 3/2 for the 2D ring (P = eps/2).
 template <typename TL>
-RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL dSxy, TL dSyy) {
-    const TL a0 = (TL)(4.0 / 3.0) * eps0 + dE;
+RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL dSxy, TL dSyy,
+                                      double rest_a = 4.0 / 3.0) {
+    const TL a0 = (TL)rest_a * eps0 + dE;
     constexpr bool dbl = std::is_same<TL, double>::value;
     const TL tol = dbl ? (TL)4e-16 : (TL)1e-7;
     TL vx, vy;

@@ -47,6 +47,14 @@ cudaError_t launch_moments(int dtype, int landau, const void *qin, const StepPar
                            double *vy, double *partials, int *bad, cudaStream_t s);
 int moments_blocks(const StepParams &p);
 
+// The 2D ring variant (k_ring.cu).
+cudaError_t launch_ring_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
+                             const void *F, const StepParams &p, cudaStream_t s);
+cudaError_t launch_ring_moments(int dtype, const void *qin, const StepParams &p, double *eps, double *vx, double *vy,
+                                double *partials, int *bad, cudaStream_t s);
+cudaError_t launch_ring_init(int dtype, void *q, const StepParams &p, const double *eps, const double *vx,
+                             const double *vy, cudaStream_t s);
+
 // Auxiliary kernels (k_aux.cu).
 cudaError_t launch_init(int dtype, void *q, const StepParams &p, const double *eps, const double *vx,
                         const double *vy, cudaStream_t s);
@@ -61,8 +69,10 @@ cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, i
                                const void *twy, int nx, int ny, cudaStream_t s);
 cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const void *X, const void *Y,
                                const StepParams &p, cudaStream_t s);
-cudaError_t launch_decode_class(int dtype, const void *q, int c, const StepParams &p, double *out, cudaStream_t s);
-cudaError_t launch_encode_class(int dtype, void *q, int c, const StepParams &p, const double *in, cudaStream_t s);
+cudaError_t launch_decode_class(int dtype, const void *q, int c, double W, const StepParams &p, double *out,
+                                cudaStream_t s);
+cudaError_t launch_encode_class(int dtype, void *q, int c, double W, const StepParams &p, const double *in,
+                                cudaStream_t s);
 cudaError_t launch_force_to_f64(int dtype, const void *F, int comp, const StepParams &p, double *out,
                                 cudaStream_t s);
 cudaError_t launch_spectrum(const double *vx, const double *vy, int nx, int ny, int nshells, double *work,
@@ -84,6 +94,8 @@ struct rlbm {
     rlbm_forcing forcing{};
     bool forced = false;
     int nmodes = 0;
+    int ncls = rlbk::NC;  // stored classes: 17 (spherical node) or 8 (2D ring)
+    bool ring = false;
     rlbk::LaunchCfg cfg;
     bool tuned = false;
     cudaStream_t stream = nullptr;

@@ -21,10 +21,17 @@ def _symbols(v, k, cfl=1.0):
     return S
 
 
-def _linear_step(v, w, k, tau, cfl=1.0):
+def ring_directions():
+    """The 2D ring: 8 unit momenta at 45 degree steps, weight 1/8."""
+    ang = np.arange(8) * np.pi / 4
+    return np.stack([np.cos(ang), np.sin(ang)], axis=1), np.full(8, 1.0 / 8.0)
+
+
+def _linear_step(v, w, k, tau, cfl=1.0, a=3.0):
     """Linearised step about eps = 1, u = 0: stream, then BGK towards the
-    linearised equilibrium delta f_eq,i = w_i (delta E + 3 v_i . delta M)."""
-    A = w[:, None] * (1.0 + 3.0 * v @ v.T)
+    linearised equilibrium delta f_eq,i = w_i (delta E + a v_i . delta M),
+    a = 1 / <v_x^2> over the stencil: 3 for the sphere, 2 for the ring."""
+    A = w[:, None] * (1.0 + a * v @ v.T)
     C = np.eye(len(w)) - (np.eye(len(w)) - A) / tau
     return C @ np.diag(_symbols(v, k, cfl))
 

@@ -60,7 +60,7 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     assert create(16, 2, 0.8) == rl.RLBM_ERR_ARG          # ny < 4
     assert create(16, 16, 0.5) == rl.RLBM_ERR_ARG         # tau must exceed 1/2
     assert create(16, 16, float("nan")) == rl.RLBM_ERR_ARG
-    assert create(16, 16, 0.8, st=1) == rl.RLBM_ERR_ARG   # unknown stencil
+    assert create(16, 16, 0.8, st=2) == rl.RLBM_ERR_ARG   # unknown stencil
     assert create(16, 16, 0.8, F(2, 8, 1e-3, 1, 100)) == rl.RLBM_ERR_ARG   # kmax >= n/2
     assert create(16, 16, 0.8, F(0, 3, 1e-3, 1, 100)) == rl.RLBM_ERR_ARG   # kmin < 1
     assert create(16, 16, 0.8, F(3, 2, 1e-3, 1, 100)) == rl.RLBM_ERR_ARG   # kmin > kmax
@@ -76,14 +76,21 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     o.kernel = rl.KERNELS["vec"]
     assert create(37, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # vector kernel needs nx % 4 == 0
     o = rl.rlbm_opts_default()
-    o.cfl = 1.5
-    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # displacement above one cell
+    o.cfl = 2.0
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # displacement of two cells or more (halo 2)
     o.cfl = 0.5
     o.kernel = rl.KERNELS["vec"]
     assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # vector kernels stream at CFL 1 only
     o = rl.rlbm_opts_default()
     o.eta_s = -0.01
     assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
+    ring = rl.RLBM_STENCIL_RING8_2D   # the ring runs the gather kernel at CFL 1 with a fixed tau
+    for field, value in (("kernel", rl.KERNELS["vec"]), ("kernel", rl.KERNELS["packed"]), ("cfl", 0.5),
+                         ("eta_s", 0.1)):
+        o = rl.rlbm_opts_default()
+        setattr(o, field, value)
+        assert create(16, 16, 0.8, opts=o, st=ring) == rl.RLBM_ERR_ARG
+    assert create(3, 16, 0.8, st=ring) == rl.RLBM_ERR_ARG
     assert out.value is None
     assert lib.rlbm_create(16, 16, 0, 0.8, None, None, None) == rl.RLBM_ERR_ARG
 

@@ -287,10 +287,12 @@ def test_spectrum_statistics_match_oracle_samples():
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("cfl,eta_s", [(0.5, 0.0), (0.15625, 0.01), (1.0, 0.01)])
+@pytest.mark.parametrize("cfl,eta_s", [(0.5, 0.0), (0.15625, 0.01), (1.0, 0.01), (1.25, 0.01), (1.25, 0.0),
+                                       (1.75, 0.0)])
 def test_cfl_and_eta_over_s_match_oracle(dtype, cfl, eta_s):
     """The paper's own parameters: Delta t = 0.05 on lattice spacing 0.32
-    (cfl = 0.15625) with eta/s = 0.01, i.e. tau from the local temperature."""
+    (cfl = 0.15625) and 0.04 (cfl = 1.25, streaming up to two cells) with
+    eta/s = 0.01, i.e. tau from the local temperature."""
     nx, ny = 48, 40
     dt = 0.05
     fields = workloads.random_smooth(nx, ny, seed=61, deps=0.05, vmax=0.05)

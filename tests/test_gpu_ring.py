@@ -1,0 +1,177 @@
+"""Parity of the 2D ring variant (8 momenta in the plane, P = eps/2) of the
+CUDA path with the FP64 ring oracle, through the C ABI.
+
+Same measures as the spherical node's parity tests: normwise relative error
+of eps and of v after a forced run from seeded smooth fields, on ragged
+lattices spanning several thread blocks and on the 4x4 minimum; decoded
+populations against the oracle's; conservation; the rest state; and the
+acoustic mode of a density wave against the linearised ring step (sound
+speed c_s^2 = 1/2, a property that holds at any size).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from linear_modes import _linear_step, _symbols, ring_directions
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2101_06187_gb300 as rl  # noqa: E402
+
+oracle.set_threads(os.cpu_count() or 4)
+R = oracle.ring
+
+# FP64 / FP32 bars as for the spherical node; 16-bit storage keeps the
+# deviation q = (f - W eps0) / (W s) in 8 (BF16) or 11 (FP16) mantissa bits,
+# a relative rounding of 2^-9 or 2^-12 per store, so 30 steps stay within a
+# few percent (BF16) or a few tenths of a percent (FP16) of the amplitude.
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 5e-2, "f16": 1e-2}
+FORCING_SMALL = dict(kmin=2, kmax=4, amp=2e-4, seed=123456789, redraw_period=7)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel_errors(ref, got):
+    e_r, vx_r, vy_r = ref
+    e_g, vx_g, vy_g = got[:3]
+    err_e = np.max(np.abs(e_g - e_r)) / max(np.max(np.abs(e_r - 1.0)), 1e-300)
+    vnorm = max(np.max(np.abs(vx_r)), np.max(np.abs(vy_r)), 1e-300)
+    err_v = max(np.max(np.abs(vx_g - vx_r)), np.max(np.abs(vy_g - vy_r))) / vnorm
+    return err_e, err_v
+
+
+def oracle_run(nx, ny, tau, nsteps, fields, forcing):
+    f = R.init(nx, ny, *fields)
+    if forcing:
+        R.run(f, tau, nsteps, kmin=forcing["kmin"], kmax=forcing["kmax"], amp=forcing["amp"], seed=forcing["seed"],
+              redraw=forcing["redraw_period"])
+    else:
+        R.run(f, tau, nsteps)
+    return f
+
+
+@pytest.mark.parametrize("dtype,landau", [("f64", "fp64"), ("f32", "fp64"), ("f32", "fp32")])
+@pytest.mark.parametrize("shape", [(37, 29), (64, 48), (300, 20), (4, 4)])
+def test_ring_forced_run_matches_oracle(dtype, landau, shape):
+    nx, ny = shape
+    forcing = FORCING_SMALL if min(nx, ny) > 8 else dict(kmin=1, kmax=1, amp=2e-3, seed=5, redraw_period=3)
+    fields = workloads.random_smooth(nx, ny, seed=nx * 1000 + ny + 7, deps=0.05, vmax=0.05)
+    lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, landau=landau, forcing=forcing, stencil="ring8")
+    info = lat.info()
+    assert info["nclasses"] == 8 and info["kernel"] == rl.KERNELS["gather"]
+    lat.init_fields(*fields)
+    lat.step(60)
+    got = lat.moments()
+    f = oracle_run(nx, ny, 0.7, 60, fields, forcing)
+    err_e, err_v = rel_errors(R.fields(f), got)
+    assert err_e < TOL[dtype] and err_v < TOL[dtype], (err_e, err_v)
+    pops = lat.populations()
+    assert pops.shape == (8, ny, nx)
+    np.testing.assert_allclose(pops, f, rtol=0, atol=TOL[dtype] * np.max(np.abs(f - 0.125)))
+    lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_ring_16bit_storage_tracks_oracle(dtype):
+    nx, ny = 64, 40
+    fields = workloads.random_smooth(nx, ny, seed=21, deps=0.05, vmax=0.05)
+    lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, forcing=FORCING_SMALL, stencil="ring8")
+    lat.init_fields(*fields)
+    lat.step(30)
+    got = lat.moments()
+    f = oracle_run(nx, ny, 0.7, 30, fields, FORCING_SMALL)
+    err_e, err_v = rel_errors(R.fields(f), got)
+    assert err_e < TOL[dtype] and err_v < TOL[dtype], (err_e, err_v)
+    lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_ring_unforced_totals_conserved(dtype):
+    nx, ny = 48, 40
+    fields = workloads.random_smooth(nx, ny, seed=3, deps=0.1, vmax=0.1)
+    lat = rl.Lattice(nx, ny, 0.6, dtype=dtype, stencil="ring8")
+    lat.init_fields(*fields)
+    t0 = lat.moments()[3]
+    lat.step(200)
+    t1 = lat.moments()[3]
+    tref = R.totals(R.init(nx, ny, *fields))
+    tol = 1e-13 if dtype == "f64" else 1e-6
+    np.testing.assert_allclose(t0, tref, rtol=0, atol=tol * tref[0])
+    np.testing.assert_allclose(t1, t0, rtol=0, atol=tol * t0[0])
+    lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+def test_ring_rest_state_is_fixed_point(dtype):
+    lat = rl.Lattice(32, 32, 0.52, dtype=dtype, stencil="ring8")
+    lat.init_fields()
+    lat.step(300)
+    e, vx, vy, _ = lat.moments()
+    tol = 1e-14 if dtype == "f64" else 1e-7
+    assert np.max(np.abs(e - 1.0)) < tol and np.max(np.abs(vx)) < tol and np.max(np.abs(vy)) < tol
+    lat.close()
+
+
+def test_ring_set_populations_round_trip_and_graphs():
+    nx, ny = 40, 24
+    fields = workloads.random_smooth(nx, ny, seed=5, deps=0.05, vmax=0.05)
+    f = R.init(nx, ny, *fields)
+    out = []
+    for graphs in (True, False):
+        lat = rl.Lattice(nx, ny, 0.7, dtype="f64", forcing=FORCING_SMALL, stencil="ring8", use_graphs=graphs)
+        lat.set_populations(f)
+        np.testing.assert_allclose(lat.populations(), f, rtol=0, atol=1e-16)
+        for n in (1, 6, 13, 2):
+            lat.step(n)
+        out.append(lat.populations())
+        lat.close()
+    np.testing.assert_array_equal(out[0], out[1])
+    ref = f.copy()
+    R.run(ref, 0.7, 22, kmin=2, kmax=4, amp=2e-4, seed=123456789, redraw=7)
+    np.testing.assert_allclose(out[0], ref, rtol=0, atol=1e-12 * np.max(np.abs(ref - 0.125)))
+
+
+def test_ring_rejects_what_it_does_not_run():
+    for kw in (dict(kernel="vec"), dict(kernel="packed"), dict(cfl=0.5), dict(eta_s=0.1)):
+        with pytest.raises(rl.RLBMError):
+            rl.Lattice(32, 32, 0.7, stencil="ring8", **kw)
+
+
+def test_ring_density_wave_travels_at_sound_speed():
+    """A small standing density wave along x: its Fourier amplitude follows
+    the linearised ring step (equilibrium delta f = w (dE + 2 v.dM)), whose
+    acoustic eigenvalues travel at c_s = 1/sqrt(2)."""
+    N, ny, tau, A = 256, 4, 0.8, 1e-4
+    x = np.arange(N)
+    eps = np.tile(1.0 + A * np.cos(2 * np.pi * x / N), (ny, 1))
+    lat = rl.Lattice(N, ny, tau, dtype="f64", stencil="ring8")
+    lat.init_fields(eps, np.zeros((ny, N)), np.zeros((ny, N)))
+    v, w = ring_directions()
+    k = (2 * np.pi / N, 0.0)
+    L = _linear_step(v, w, k, tau, a=2.0)
+    S = _symbols(v, k)
+    lam = np.linalg.eigvals(L)
+    speeds = sorted(abs(np.angle(l)) / k[0] for l in lam if abs(l) > 0.99 and abs(np.angle(l)) > 1e-9)
+    assert abs(speeds[0] ** 2 - 0.5) < 1e-3
+    fn = w * (A / 2)
+    done = 0
+    for nst in (45, 90, 180, 270, 360):
+        lat.step(nst - done)
+        fn = np.linalg.matrix_power(L, nst - done) @ fn
+        done = nst
+        e = lat.moments()[0]
+        sim = np.fft.fft(e[0, :])[1] / N
+        pred = (S * fn).sum()
+        assert abs(sim - pred) < 2e-3 * (A / 2), (nst, sim, pred)
+    lat.close()

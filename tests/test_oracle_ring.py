@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import workloads
+from linear_modes import _linear_step, _symbols
 
 R = oracle.ring
 G3 = np.diag([-1.0, 1.0, 1.0])
@@ -108,17 +109,7 @@ def test_ring_collision_conserves_and_fixes_equilibrium():
 
 def _ring_linear_step(k, tau):
     v, w = R.stencil()
-    A = w[:, None] * (1.0 + 2.0 * v @ v.T)  # linearised f_eq: w (dE + 2 v . dM)
-    S = np.zeros(8, dtype=complex)
-    for i in range(8):
-        sx, sy = -v[i, 0], -v[i, 1]
-        ox, oy = np.floor(sx), np.floor(sy)
-        tx, ty = sx - ox, sy - oy
-        e = lambda dx, dy: np.exp(1j * (k[0] * dx + k[1] * dy))
-        S[i] = ((1 - tx) * (1 - ty) * e(ox, oy) + tx * (1 - ty) * e(ox + 1, oy) + (1 - tx) * ty * e(ox, oy + 1)
-                + tx * ty * e(ox + 1, oy + 1))
-    C = np.eye(8) - (np.eye(8) - A) / tau
-    return C @ np.diag(S), S
+    return _linear_step(v, w, k, tau, a=2.0), _symbols(v, k)
 
 
 def test_ring_sound_speed_squared_is_one_half():

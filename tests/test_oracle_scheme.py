@@ -24,7 +24,7 @@ def _golden():
     return vals
 
 
-@pytest.mark.parametrize("cfl", [0.5, 0.15625, 1.0])
+@pytest.mark.parametrize("cfl", [0.5, 0.15625, 1.0, 1.25, 1.75])
 def test_stream_at_cfl_matches_library_interpolation(cfl):
     rng = np.random.default_rng(3)
     nx, ny = 9, 7
@@ -62,7 +62,7 @@ def test_eta_over_s_collision_relaxes_at_the_local_rate():
         np.testing.assert_allclose(f2 - fe, (1 - 1 / tau) * (f - fe), rtol=0, atol=1e-15 * np.max(fe))
 
 
-@pytest.mark.parametrize("cfl", [0.5, 0.25])
+@pytest.mark.parametrize("cfl", [0.5, 0.25, 1.25])
 def test_shear_wave_at_cfl_matches_linear_mode_analysis(cfl):
     N, nst, tau = 32, 200, 0.8
     e, a, b = workloads.shear_wave(N, N, 0.01)
@@ -76,7 +76,7 @@ def test_shear_wave_at_cfl_matches_linear_mode_analysis(cfl):
     assert abs(sim - pred) < 2e-5 * abs(pred)
 
 
-@pytest.mark.parametrize("cfl", [0.5, 0.25])
+@pytest.mark.parametrize("cfl", [0.5, 0.25, 1.25])
 def test_sound_speed_and_viscosity_scale_with_cfl(cfl):
     """In cells per step the light cone shrinks by the CFL number: c_s =
     cfl/sqrt(3), and the tau-dependent part of the shear viscosity is
