@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--landau", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2", "packed"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2", "packed", "tma"])
     ap.add_argument("--n", type=int, default=0, help="override lattice side (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-form table, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
@@ -149,6 +149,22 @@ def forcing_of(w):
     return dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw)
 
 
+class L2Flush:
+    """Evict the lattice from L2 between timed steps: write a buffer larger
+    than L2, then read a second one, so that the lines left in L2 are clean
+    and the next step neither finds its inputs there nor pays for writing
+    back the flush's own dirty lines."""
+
+    def __init__(self, torch, nbytes):
+        self.w = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+        self.r = torch.zeros(nbytes // 4, dtype=torch.float32, device="cuda")
+        self.sink = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def __call__(self):
+        self.w.fill_(1.0)
+        self.sink.copy_(self.r.sum())
+
+
 def time_steps(torch, lat, steps, flush):
     """Per-step CUDA-event timing on the lattice stream with an L2 flush in between."""
     stream = lat._torch_stream
@@ -157,7 +173,7 @@ def time_steps(torch, lat, steps, flush):
         for _ in range(steps):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            flush.fill_(1.0)
+            flush()
             a.record(stream)
             lat.step(1)
             b.record(stream)
@@ -203,7 +219,7 @@ def measure_ensemble(torch, rl, flush, steps=20, warmup=5):
         for _ in range(steps):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            flush.fill_(1.0)
+            flush()
             a.record(stream)
             ens.step(1)
             b.record(stream)
@@ -381,7 +397,7 @@ def main():
 
     w, n = workload_for(args)
     K, W = args.steps, max(3, args.warmup)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch, L2_FLUSH_BYTES)
     dev_index = torch.cuda.current_device()
     phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
     smi_index = int(phys[dev_index]) if phys and phys[0].isdigit() and dev_index < len(phys) else dev_index
@@ -419,10 +435,10 @@ def main():
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.form != "f64" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": n, "ny": n, "form": args.form, "landau": args.landau,
-                   "kernel": ["auto", "gather", "vec", "vec2", "packed"][info["kernel"]],
+                   "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]],
                    "block": [info["block_x"], info["block_y"]], "tau": w.tau,
                    "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
-                   "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "l2": "flushed between timed steps (256 MB write, then 256 MB read)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm" if args.form != "f64" else "alu", "achieved": achieved, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_node": bpn,

@@ -92,14 +92,21 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * run.  GATHER_VEC2: a run of 2 nodes (fewer registers); needs nx even.
  * PACKED: 2 nodes per thread whose arithmetic runs in packed FP32 lanes
  * (two nodes per instruction); FP32 compute with RLBM_LANDAU_FP32, nx even.
- * The vector and packed variants stream at CFL 1 only.  AUTO: the
+ * TMA: the packed body fed from shared memory: a persistent kernel whose
+ * CTAs stage each 64 x 8 tile of all classes (with its halo) and the tile's
+ * force through the tensor-memory accelerator, double-buffered, so the next
+ * tile's copy overlaps the current tile's arithmetic; RLBM_F32 storage with
+ * RLBM_LANDAU_FP32, nx even, SPH26_SLAB.  A wait on a tile copy that gives
+ * up (bounded) makes the next synchronising call return RLBM_ERR_TIMEOUT.
+ * The vector, packed and TMA variants stream at CFL 1 only.  AUTO: the
  * autotuned choice if one is cached for this lattice, else GATHER. */
 typedef enum {
     RLBM_KERNEL_AUTO = 0,
     RLBM_KERNEL_GATHER = 1,
     RLBM_KERNEL_GATHER_VEC = 2,
     RLBM_KERNEL_GATHER_VEC2 = 3,
-    RLBM_KERNEL_PACKED = 4
+    RLBM_KERNEL_PACKED = 4,
+    RLBM_KERNEL_TMA = 5
 } rlbm_kernel;
 
 /* Stirring force (Sec. 5).  Modes are the integer wavevectors k with

@@ -135,7 +135,7 @@ static StepParams params_of(const rlbm_t *h) {
     p.cfl = h->opts.cfl;
     // eta/s mode: 1/tau = T dt / (5 eta/s), T = (pi^2 eps / 3)^{1/4}
     p.eta_k = h->opts.eta_s > 0.0 ? std::pow(M_PI * M_PI / 3.0, 0.25) * h->opts.dt / (5.0 * h->opts.eta_s) : 0.0;
-    p.err = nullptr;
+    p.err = h->errword;
     finish_params(p);
     return p;
 }
@@ -155,6 +155,11 @@ static double class_weight(const rlbm_t *h, int c) {
 static cudaError_t launch_step_h(const rlbm_t *h, const LaunchCfg &cfg, const void *qin, void *qout,
                                  const StepParams &p) {
     if (h->ring) return launch_ring_step(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
+    if (cfg.kernel == RLBM_KERNEL_TMA) {
+        if (!h->tm_ready) return cudaErrorNotSupported;
+        const CUtensorMap &mq = (qin == h->q[0]) ? h->tm_q[0] : h->tm_q[1];
+        return launch_step_tma(cfg, h->forced, mq, h->tm_F, qin, qout, p, h->stream);
+    }
     return launch_step(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
 }
 
@@ -250,6 +255,7 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_PACKED, 64, 2, 2}, {RLBM_KERNEL_PACKED, 128, 1, 2}, {RLBM_KERNEL_PACKED, 128, 2, 2},
     {RLBM_KERNEL_PACKED, 64, 2, 3}, {RLBM_KERNEL_PACKED, 128, 1, 3}, {RLBM_KERNEL_PACKED, 128, 2, 3},
     {RLBM_KERNEL_PACKED, 64, 4, 3}, {RLBM_KERNEL_PACKED, 32, 8, 3},
+    {RLBM_KERNEL_TMA, 32, 8, 2}, {RLBM_KERNEL_TMA, 32, 8, 1},
     {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
     {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
 };
@@ -260,6 +266,16 @@ static std::tuple<int, int, int, int, int, int> tune_key(const rlbm_t *h) {
     return std::make_tuple(h->nx, h->ny, h->opts.dtype, h->opts.landau, h->forced ? 1 : 0, h->ring ? 1 : 0);
 }
 
+
+// The device error word of the bounded waits (synchronises): a wait that
+// gave up leaves the state of that step undefined, so the error is sticky.
+static rlbm_status check_errword(rlbm_t *h) {
+    int *w = reinterpret_cast<int *>(h->host_small) + 64;
+    CUDA_TRY(h, cudaMemcpyAsync(w, h->errword, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (*w) return fail(h, RLBM_ERR_TIMEOUT, "a bounded wait on a tile copy gave up (error word %d)", *w);
+    return RLBM_OK;
+}
 
 static void drop_graphs(rlbm_t *h) {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
@@ -316,6 +332,7 @@ void rlbm_destroy(rlbm_t *h) {
     dev_free(h, h->partials, partials_bytes(h));
     dev_free(h, h->totals, 4 * sizeof(double));
     dev_free(h, h->bad, sizeof(int) * 4);
+    dev_free(h, h->errword, sizeof(int) * 4);
     if (h->spec_work) dev_free(h, h->spec_work, h->spec_work_bytes);
     if (h->spec_acc) dev_free(h, h->spec_acc, 2 * 4096 * sizeof(double));
     if (h->host_small) cudaFreeHost(h->host_small);
@@ -335,7 +352,9 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (opts) o = *opts;
     if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
     if (o.landau != RLBM_LANDAU_FP64 && o.landau != RLBM_LANDAU_FP32) return RLBM_ERR_ARG;
-    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_PACKED) return RLBM_ERR_ARG;
+    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_TMA) return RLBM_ERR_ARG;
+    if (o.kernel == RLBM_KERNEL_TMA && (nx % 2 != 0 || o.dtype != RLBM_F32 || o.landau != RLBM_LANDAU_FP32))
+        return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_PACKED &&
         (nx % 2 != 0 || o.dtype == RLBM_F64 || o.landau != RLBM_LANDAU_FP32))
         return RLBM_ERR_ARG;
@@ -351,7 +370,7 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (!(o.cfl > 0.0 && o.cfl < 2.0) || !(o.eta_s >= 0.0) || !isfinite(o.eta_s) || !(o.dt > 0.0) || !isfinite(o.dt))
         return RLBM_ERR_ARG;
     if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2 ||
-                         o.kernel == RLBM_KERNEL_PACKED))
+                         o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_TMA))
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
@@ -416,7 +435,8 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     h->partials = static_cast<double *>(dev_alloc(h, partials_bytes(h)));
     h->totals = static_cast<double *>(dev_alloc(h, 4 * sizeof(double)));
     h->bad = static_cast<int *>(dev_alloc(h, sizeof(int) * 4));
-    bool ok = h->q[0] && h->q[1] && h->fields && h->partials && h->totals && h->bad;
+    h->errword = static_cast<int *>(dev_alloc(h, sizeof(int) * 4));
+    bool ok = h->q[0] && h->q[1] && h->fields && h->partials && h->totals && h->bad && h->errword;
     if (forced) {
         h->F = dev_alloc(h, F_bytes(h));
         h->twx = dev_alloc(h, tw_bytes(h, nx));
@@ -443,6 +463,18 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
             e = launch_mode_tables(o.dtype, h->tabx, h->taby, h->modes, h->nmodes, h->twx, h->twy, nx, ny, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) st = RLBM_ERR_CUDA;
+    }
+    if (st == RLBM_OK && cudaMemsetAsync(h->errword, 0, sizeof(int) * 4, h->stream) != cudaSuccess) st = RLBM_ERR_CUDA;
+    // tensor maps for the TMA kernel where it applies (a host-side encoding)
+    if (st == RLBM_OK && !ring && o.dtype == RLBM_F32 && o.landau == RLBM_LANDAU_FP32 && nx % 2 == 0 && o.cfl == 1.0) {
+        const StepParams p = params_of(h);
+        bool enc = tma_encode_state(&h->tm_q[0], h->q[0], p) == cudaSuccess &&
+                   tma_encode_state(&h->tm_q[1], h->q[1], p) == cudaSuccess;
+        if (enc && forced) enc = tma_encode_force(&h->tm_F, h->F, p) == cudaSuccess;
+        else if (enc) h->tm_F = h->tm_q[0];  // never read by the unforced kernel
+        h->tm_ready = enc;
+        cudaGetLastError();
+        if (!enc && o.kernel == RLBM_KERNEL_TMA) st = RLBM_ERR_CUDA;
     }
     if (st == RLBM_OK) st = rlbm_init_fields_device(h, nullptr, nullptr, nullptr);
     if (st == RLBM_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = RLBM_ERR_CUDA;
@@ -562,6 +594,8 @@ rlbm_status rlbm_moments(rlbm_t *h, double *eps, double *vx, double *vy, double 
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     if (totals)
         for (int k = 0; k < 3; ++k) totals[k] = tot_host[k];
+    st = check_errword(h);
+    if (st != RLBM_OK) return st;
     if (*bad_host) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", *bad_host);
     return RLBM_OK;
 }
@@ -744,6 +778,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     for (const LaunchCfg &c : kCandidates) {
         if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
         if ((h->opts.cfl != 1.0 || h->ring) && c.kernel != RLBM_KERNEL_GATHER) continue;
+        if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) continue;
         // the trial steps read the current state and overwrite only the spare buffer
         bool ok = true;
         for (int i = 0; i < 2 + reps && ok; ++i) {
@@ -781,7 +816,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
 rlbm_status rlbm_synchronize(rlbm_t *h) {
     CHECK_HANDLE(h);
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    return RLBM_OK;
+    return check_errword(h);
 }
 
 rlbm_status rlbm_last_error(rlbm_t *h, char *buf, size_t len) {

@@ -2,6 +2,7 @@
 // translation units of the library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <map>
@@ -32,7 +33,7 @@ struct Launch {
 struct LaunchCfg {
     int kernel = RLBM_KERNEL_GATHER;
     int bx = 32, by = 8;
-    int minb = 1;  // packed kernel: register budget (blocks of 256 per SM: 1, 2 or 3)
+    int minb = 1;  // packed kernel: register budget (blocks of 256 per SM: 1, 2 or 3); TMA kernel: CTAs per SM
 };
 
 cudaError_t launch_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
@@ -46,6 +47,13 @@ int run_length(int dtype);
 cudaError_t launch_moments(int dtype, int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                            double *vy, double *partials, int *bad, cudaStream_t s);
 int moments_blocks(const StepParams &p);
+
+// The TMA-pipelined step (k_step_tma.cu): tensor maps of a state buffer
+// and of the force, and the launch (FP32 storage, FP32 Landau, CFL 1).
+cudaError_t tma_encode_state(CUtensorMap *map, const void *q, const StepParams &p);
+cudaError_t tma_encode_force(CUtensorMap *map, const void *F, const StepParams &p);
+cudaError_t launch_step_tma(const LaunchCfg &cfg, bool forced, const CUtensorMap &mq, const CUtensorMap &mf,
+                            const void *qin, void *qout, const StepParams &p, cudaStream_t s);
 
 // The 2D ring variant (k_ring.cu).
 cudaError_t launch_ring_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
@@ -96,6 +104,11 @@ struct rlbm {
     int nmodes = 0;
     int ncls = rlbk::NC;  // stored classes: 17 (spherical node) or 8 (2D ring)
     bool ring = false;
+    // tensor maps of the two state buffers and of the force (TMA kernel)
+    alignas(64) CUtensorMap tm_q[2];
+    alignas(64) CUtensorMap tm_F;
+    bool tm_ready = false;
+    int *errword = nullptr;  // device error word of the bounded waits
     rlbk::LaunchCfg cfg;
     bool tuned = false;
     cudaStream_t stream = nullptr;

@@ -94,11 +94,13 @@ def stirred_1024_oracle():
     return oracle.fields(f)
 
 
-@pytest.mark.parametrize("dtype,tol", [("f32", 1e-5), ("f64", 1e-12)])
-def test_stirred_1024_full_size_matches_oracle(stirred_1024_oracle, dtype, tol):
+@pytest.mark.parametrize("dtype,tol,kernel", [("f32", 1e-5, "auto"), ("f64", 1e-12, "auto"), ("f32", 1e-5, "tma"),
+                                             ("f32", 1e-5, "packed")])
+def test_stirred_1024_full_size_matches_oracle(stirred_1024_oracle, dtype, tol, kernel):
     w = workloads.STIRRED_1024
-    lat = rl.Lattice(w.nx, w.ny, w.tau, dtype=dtype, forcing=_forcing(w))
-    lat.autotune(5)
+    lat = rl.Lattice(w.nx, w.ny, w.tau, dtype=dtype, forcing=_forcing(w), kernel=kernel)
+    if kernel == "auto":
+        lat.autotune(5)
     lat.init_fields()
     lat.step(100)
     err_e, err_v = _errs(stirred_1024_oracle, lat.moments())
@@ -119,12 +121,14 @@ def tiled_reference():
     return period, tau, nsteps, oracle.fields(f)
 
 
-@pytest.mark.parametrize("n,dtype", [(4096, "bf16"), (4096, "f16"), (4096, "f32"), (8192, "f32")])
-def test_full_size_lattice_stays_an_exact_tiling(tiled_reference, n, dtype):
+@pytest.mark.parametrize("n,dtype,kernel", [(4096, "bf16", "auto"), (4096, "f16", "auto"), (4096, "f32", "auto"),
+                                           (8192, "f32", "auto"), (8192, "f32", "tma")])
+def test_full_size_lattice_stays_an_exact_tiling(tiled_reference, n, dtype, kernel):
     period, tau, nsteps, ref = tiled_reference
     e, a, b = workloads.random_tiled(n, n, period, seed=77, deps=0.02, vmax=0.02)
-    lat = rl.Lattice(n, n, tau, dtype=dtype)
-    lat.autotune(3)
+    lat = rl.Lattice(n, n, tau, dtype=dtype, kernel=kernel)
+    if kernel == "auto":
+        lat.autotune(3)
     lat.init_fields(e, a, b)
     lat.step(nsteps)
     e_g, vx_g, vy_g, _ = lat.moments()
