@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--landau", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2", "packed", "tma"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2", "packed", "tma", "twopass"])
     ap.add_argument("--n", type=int, default=0, help="override lattice side (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-form table, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")

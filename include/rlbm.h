@@ -98,15 +98,22 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * tile's copy overlaps the current tile's arithmetic; RLBM_F32 storage with
  * RLBM_LANDAU_FP32, nx even, SPH26_SLAB.  A wait on a tile copy that gives
  * up (bounded) makes the next synchronising call return RLBM_ERR_TIMEOUT.
- * The vector, packed and TMA variants stream at CFL 1 only.  AUTO: the
- * autotuned choice if one is cached for this lattice, else GATHER. */
+ * TWOPASS: the packed body in two passes over the node pair's classes (the
+ * first accumulates the moments pair by pair, the second gathers each pair
+ * again and writes its update), so no thread keeps all 17 populations live
+ * across the Landau solve: about half the registers, twice the resident
+ * warps; same conditions as PACKED.
+ * The vector, packed, TMA and two-pass variants stream at CFL 1 only.
+ * AUTO: the autotuned choice if one is cached for this lattice, else
+ * GATHER. */
 typedef enum {
     RLBM_KERNEL_AUTO = 0,
     RLBM_KERNEL_GATHER = 1,
     RLBM_KERNEL_GATHER_VEC = 2,
     RLBM_KERNEL_GATHER_VEC2 = 3,
     RLBM_KERNEL_PACKED = 4,
-    RLBM_KERNEL_TMA = 5
+    RLBM_KERNEL_TMA = 5,
+    RLBM_KERNEL_TWOPASS = 6
 } rlbm_kernel;
 
 /* Stirring force (Sec. 5).  Modes are the integer wavevectors k with

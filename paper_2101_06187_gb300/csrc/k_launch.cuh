@@ -21,9 +21,27 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
     const dim3 block(cfg.bx, cfg.by, 1);
     if ((cfg.kernel == RLBM_KERNEL_GATHER_VEC || cfg.kernel == RLBM_KERNEL_GATHER_VEC2 ||
-         cfg.kernel == RLBM_KERNEL_PACKED) &&
+         cfg.kernel == RLBM_KERNEL_PACKED || cfg.kernel == RLBM_KERNEL_TWOPASS) &&
         p.cfl != 1.0)
         return cudaErrorInvalidValue;  // the vector kernels stream at CFL 1 only
+    if (cfg.kernel == RLBM_KERNEL_TWOPASS) {
+        if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
+            if (p.nx % 2 != 0) return cudaErrorInvalidValue;
+            const dim3 grid((p.nx / 2 + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
+#define RLBM_PAIR2(MB)                                                                  \
+    do {                                                                                \
+        if (forced) k_step_pair2<TS, true, MB><<<grid, block, 0, s>>>(in, out, f, p);   \
+        else k_step_pair2<TS, false, MB><<<grid, block, 0, s>>>(in, out, f, p);         \
+    } while (0)
+            if (cfg.minb >= 4) RLBM_PAIR2(4);
+            else if (cfg.minb == 3) RLBM_PAIR2(3);
+            else RLBM_PAIR2(2);
+#undef RLBM_PAIR2
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;  // packed lanes are FP32 with the FP32 Landau solve
+        }
+    }
     if (cfg.kernel == RLBM_KERNEL_PACKED) {
         if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
             if (p.nx % 2 != 0) return cudaErrorInvalidValue;

@@ -56,6 +56,85 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
     });
 }
 
+// Two-pass form of step_pair: the first pass gathers one opposite pair at a
+// time and keeps only the moment sums; the collision coefficients follow
+// from them; the second pass gathers each pair again (from L1/L2: the same
+// lines were just read) and writes its updated values.  No node keeps its
+// 17 populations live across the Landau solve, which halves the registers
+// per thread and doubles the warps an SM can hold.  Same arithmetic as
+// step_pair, in the same order.
+template <typename TS, bool FORCED>
+__device__ __forceinline__ void step_pair_twopass(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                                  const float *__restrict__ F, const StepParams &p, int x0, int y) {
+    const int ym = (y == 0) ? p.ny - 1 : y - 1;
+    const int yp = (y == p.ny - 1) ? 0 : y + 1;
+    const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
+    const int xr = (x0 + 2 == p.nx) ? 0 : x0 + 2;
+    const long long rowoff[3] = {(long long)ym * p.pitch, (long long)y * p.pitch, (long long)yp * p.pitch};
+    auto gather = [&](const TS *src, auto C) -> pf2 {
+        constexpr int c = decltype(C)::value;
+        constexpr int ox = cls_ox(c), oy = cls_oy(c);
+        constexpr double tx = cls_tx(c), ty = cls_ty(c);
+        const TS *plane = src + (long long)c * p.plane;
+        float a[4];
+        load_class_row<c, TS, float, 2>(plane + rowoff[oy + 1], x0, xl, xr, a);
+        pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
+        if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
+        if constexpr (ty != 0.0) {
+            float b[4];
+            load_class_row<c, TS, float, 2>(plane + rowoff[oy + 2], x0, xl, xr, b);
+            v = fmadd(pf2((float)((1.0 - tx) * ty)), pf2(b[ox + 1], b[ox + 2]), v);
+            if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
+        }
+        return v;
+    };
+    using I0 = std::integral_constant<int, 0>;
+
+    MomentSums<pf2> acc = moments_begin<pf2>(gather(qin, I0{}));
+    static_for<0, NPAIR>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        moments_add_pair<k, pf2>(acc, gather(qin, std::integral_constant<int, pair_pos(k)>{}),
+                                 gather(qin, std::integral_constant<int, pair_neg(k)>{}));
+    });
+    const NodeMoments<pf2> m = moments_end<pf2>(acc, par_scale<pf2>(p));
+
+    const long long n0 = (long long)y * p.pitch + x0;
+    pf2 Fx = 0.0f, Fy = 0.0f;
+    if constexpr (FORCED) {
+        float fx[2], fy[2];
+        load_run<float, float, 2>(F + n0, fx);
+        load_run<float, float, 2>(F + p.plane + n0, fy);
+        Fx = pf2(fx[0], fx[1]);
+        Fy = pf2(fy[0], fy[1]);
+    }
+    CollideCoef<pf2> cf;
+    collide_coef<pf2, pf2, FORCED>(m, Fx, Fy, p, cf);
+
+    const TS *again = qin + p.reload_offset;
+    auto store = [&](int c, pf2 v) {
+        const float out[2] = {v.v.x, v.v.y};
+        store_run<TS, float, 2>(qout + (long long)c * p.plane + n0, out);
+    };
+    store(0, collide_rest<pf2>(gather(again, I0{}), cf));
+    static_for<0, NPAIR>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        pf2 qp = gather(again, std::integral_constant<int, pair_pos(k)>{});
+        pf2 qn = gather(again, std::integral_constant<int, pair_neg(k)>{});
+        collide_pair<k, pf2, FORCED>(qp, qn, cf);
+        store(pair_pos(k), qp);
+        store(pair_neg(k), qn);
+    });
+}
+
+template <typename TS, bool FORCED, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_pair2(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                                          const float *__restrict__ F, StepParams p) {
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= p.nx || y >= p.ny) return;
+    step_pair_twopass<TS, FORCED>(qin, qout, F, p, x0, y);
+}
+
 // MINB: minimum resident blocks of 256 threads per SM asked of the register
 // allocator (1: unconstrained; 2: <= 128 registers; 3: <= 80), so the
 // autotuner can trade registers for occupancy.

@@ -256,6 +256,10 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_PACKED, 64, 2, 3}, {RLBM_KERNEL_PACKED, 128, 1, 3}, {RLBM_KERNEL_PACKED, 128, 2, 3},
     {RLBM_KERNEL_PACKED, 64, 4, 3}, {RLBM_KERNEL_PACKED, 32, 8, 3},
     {RLBM_KERNEL_TMA, 32, 8, 2}, {RLBM_KERNEL_TMA, 32, 8, 1},
+    {RLBM_KERNEL_TWOPASS, 64, 2, 2}, {RLBM_KERNEL_TWOPASS, 128, 1, 2}, {RLBM_KERNEL_TWOPASS, 32, 8, 2},
+    {RLBM_KERNEL_TWOPASS, 64, 2, 3}, {RLBM_KERNEL_TWOPASS, 128, 1, 3}, {RLBM_KERNEL_TWOPASS, 32, 8, 3},
+    {RLBM_KERNEL_TWOPASS, 64, 4, 3}, {RLBM_KERNEL_TWOPASS, 64, 2, 4}, {RLBM_KERNEL_TWOPASS, 128, 1, 4},
+    {RLBM_KERNEL_TWOPASS, 32, 8, 4},
     {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
     {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
 };
@@ -352,10 +356,10 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (opts) o = *opts;
     if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
     if (o.landau != RLBM_LANDAU_FP64 && o.landau != RLBM_LANDAU_FP32) return RLBM_ERR_ARG;
-    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_TMA) return RLBM_ERR_ARG;
+    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_TWOPASS) return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_TMA && (nx % 2 != 0 || o.dtype != RLBM_F32 || o.landau != RLBM_LANDAU_FP32))
         return RLBM_ERR_ARG;
-    if (o.kernel == RLBM_KERNEL_PACKED &&
+    if ((o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_TWOPASS) &&
         (nx % 2 != 0 || o.dtype == RLBM_F64 || o.landau != RLBM_LANDAU_FP32))
         return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_GATHER_VEC && nx % (o.dtype == RLBM_F64 ? 2 : 4) != 0) return RLBM_ERR_ARG;
@@ -370,7 +374,8 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     if (!(o.cfl > 0.0 && o.cfl < 2.0) || !(o.eta_s >= 0.0) || !isfinite(o.eta_s) || !(o.dt > 0.0) || !isfinite(o.dt))
         return RLBM_ERR_ARG;
     if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2 ||
-                         o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_TMA))
+                         o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_TMA ||
+                         o.kernel == RLBM_KERNEL_TWOPASS))
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
@@ -419,6 +424,12 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         }
     } else {
         h->cfg.kernel = o.kernel;
+        if (o.kernel == RLBM_KERNEL_TMA) h->cfg.minb = 2;  // two CTAs per SM
+        if (o.kernel == RLBM_KERNEL_TWOPASS) {
+            h->cfg.bx = 64;
+            h->cfg.by = 2;
+            h->cfg.minb = 3;
+        }
     }
     if (!h->tuned && o.kernel == RLBM_KERNEL_AUTO) {
         h->cfg.kernel = RLBM_KERNEL_GATHER;

@@ -113,6 +113,10 @@ struct StepParams {
     double wt[17][4];
     float wt_f[17][4];
     unsigned far_x, far_y;
+    // always 0: added to the state pointer of a second gather pass, so the
+    // compiler cannot merge its loads with the first pass's (re-reading is
+    // what frees the registers of the two-pass kernels)
+    int reload_offset;
     int *err;         // device error word (bounded-wait / failure reporting)
 };
 
@@ -135,6 +139,7 @@ inline int stream_mode(double cfl) { return cfl == 1.0 ? kStreamCfl1 : cfl < 1.0
 // 1 < cfl < 2 the offset moves one cell further (-2 or +1) on the axes
 // where cfl |c| > 1.
 RLBM_HD inline void finish_params(StepParams &p) {
+    p.reload_offset = 0;
     p.inv_scale = 1.0 / p.scale;
     p.inv_tau_f = (float)p.inv_tau;
     p.eps0_f = (float)p.eps0;
@@ -221,46 +226,69 @@ RLBM_HD constexpr int pair_neg(int k) { return k == 0 ? 2 : k == 1 ? 4 : k == 2 
 constexpr int NPAIR = 8;
 
 // Moments from pair sums s = q_c + q_-c (even moments E, S) and differences
-// d = q_c - q_-c (odd moments M, Q).
+// d = q_c - q_-c (odd moments M, Q), accumulated pair by pair (so a kernel
+// may gather one pair at a time) and scaled by s at the end.
+template <typename TC>
+struct MomentSums {
+    TC e, mx, my, sxx, sxy, syy, qxxx, qxxy, qxyy, qyyy;
+};
+
+template <typename TC>
+RLBM_HD inline MomentSums<TC> moments_begin(TC q0) {
+    MomentSums<TC> a;
+    a.e = (TC)cls_w(0) * q0;
+    a.mx = a.my = a.sxx = a.sxy = a.syy = a.qxxx = a.qxxy = a.qxyy = a.qyyy = (TC)0;
+    return a;
+}
+
+template <int k, typename TC>
+RLBM_HD inline void moments_add_pair(MomentSums<TC> &a, TC qp, TC qn) {
+    constexpr int c = pair_pos(k);
+    constexpr double w = cls_w(c), cx = cls_cx(c), cy = cls_cy(c);
+    const TC sp = qp + qn;
+    const TC dp = qp - qn;
+    a.e = fmadd((TC)w, sp, a.e);
+    if constexpr (cx != 0.0) {
+        a.mx = fmadd((TC)(w * cx), dp, a.mx);
+        a.sxx = fmadd((TC)(w * cx * cx), sp, a.sxx);
+        a.qxxx = fmadd((TC)(w * cx * cx * cx), dp, a.qxxx);
+    }
+    if constexpr (cy != 0.0) {
+        a.my = fmadd((TC)(w * cy), dp, a.my);
+        a.syy = fmadd((TC)(w * cy * cy), sp, a.syy);
+        a.qyyy = fmadd((TC)(w * cy * cy * cy), dp, a.qyyy);
+    }
+    if constexpr (cx != 0.0 && cy != 0.0) {
+        a.sxy = fmadd((TC)(w * cx * cy), sp, a.sxy);
+        a.qxxy = fmadd((TC)(w * cx * cx * cy), dp, a.qxxy);
+        a.qxyy = fmadd((TC)(w * cx * cy * cy), dp, a.qxyy);
+    }
+}
+
+template <typename TC>
+RLBM_HD inline NodeMoments<TC> moments_end(const MomentSums<TC> &a, TC s) {
+    NodeMoments<TC> m;
+    m.dE = s * a.e;
+    m.Mx = s * a.mx;
+    m.My = s * a.my;
+    m.dSxx = s * a.sxx;
+    m.dSxy = s * a.sxy;
+    m.dSyy = s * a.syy;
+    m.Qxxx = s * a.qxxx;
+    m.Qxxy = s * a.qxxy;
+    m.Qxyy = s * a.qxyy;
+    m.Qyyy = s * a.qyyy;
+    return m;
+}
+
 template <typename TC>
 RLBM_HD inline NodeMoments<TC> node_moments(const TC (&q)[NC], TC s) {
-    TC e = (TC)cls_w(0) * q[0];
-    TC mx = 0, my = 0, sxx = 0, sxy = 0, syy = 0, qxxx = 0, qxxy = 0, qxyy = 0, qyyy = 0;
+    MomentSums<TC> a = moments_begin<TC>(q[0]);
     static_for<0, NPAIR>([&](auto K) {
         constexpr int k = decltype(K)::value;
-        constexpr int c = pair_pos(k), cn = pair_neg(k);
-        constexpr double w = cls_w(c), cx = cls_cx(c), cy = cls_cy(c);
-        const TC sp = q[c] + q[cn];
-        const TC dp = q[c] - q[cn];
-        e = fmadd((TC)w, sp, e);
-        if constexpr (cx != 0.0) {
-            mx = fmadd((TC)(w * cx), dp, mx);
-            sxx = fmadd((TC)(w * cx * cx), sp, sxx);
-            qxxx = fmadd((TC)(w * cx * cx * cx), dp, qxxx);
-        }
-        if constexpr (cy != 0.0) {
-            my = fmadd((TC)(w * cy), dp, my);
-            syy = fmadd((TC)(w * cy * cy), sp, syy);
-            qyyy = fmadd((TC)(w * cy * cy * cy), dp, qyyy);
-        }
-        if constexpr (cx != 0.0 && cy != 0.0) {
-            sxy = fmadd((TC)(w * cx * cy), sp, sxy);
-            qxxy = fmadd((TC)(w * cx * cx * cy), dp, qxxy);
-            qxyy = fmadd((TC)(w * cx * cy * cy), dp, qxyy);
-        }
+        moments_add_pair<k, TC>(a, q[pair_pos(k)], q[pair_neg(k)]);
     });
-    NodeMoments<TC> m;
-    m.dE = s * e;
-    m.Mx = s * mx;
-    m.My = s * my;
-    m.dSxx = s * sxx;
-    m.dSxy = s * sxy;
-    m.dSyy = s * syy;
-    m.Qxxx = s * qxxx;
-    m.Qxxy = s * qxxy;
-    m.Qxyy = s * qxyy;
-    m.Qyyy = s * qyyy;
-    return m;
+    return moments_end<TC>(a, s);
 }
 
 template <typename T>
@@ -377,10 +405,16 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
 //   K0 + Kxx c_x^2 + Kxy c_x c_y + Kyy c_y^2
 // and the odd part  xi [om (P1 - P0) - om P2 xi^2] + G1 (F.c)
 // lets each opposite pair (c, -c) share one evaluation.
+// Coefficients of the per-class update of one node (below).
+template <typename TC>
+struct CollideCoef {
+    TC K0, Kxx, Kxy, Kyy, o1, no3, G1, om, a0, vx, vy, Fx, Fy;
+};
+
+// Frame and update coefficients of a node from its moments.
 template <typename TC, typename TL, bool FORCED>
-RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
-    const TC s = par_scale<TC>(p);
-    const NodeMoments<TC> m = node_moments<TC>(q, s);
+RLBM_HD inline Frame<TL> collide_coef(const NodeMoments<TC> &m, TC Fx, TC Fy, const StepParams &p,
+                                      CollideCoef<TC> &k) {
     const Frame<TL> fr = landau_solve<TL>(par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
                                           (TL)m.dSyy);
     const TC inv_s = par_inv_scale<TC>(p);
@@ -417,32 +451,64 @@ RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParam
         Kxy = fmadd(G3, fmadd(Fx, m.My, Fy * m.Mx), Kxy + (TC)2 * Pxy);
         Kyy = fmadd(G3 * Fy, m.My, Kyy + (Pyy - Pzz));
     }
-    const TC a0 = (TC)1 - om;
-    q[0] = fmadd(q[0], a0, K0);
+    k.K0 = K0;
+    k.Kxx = Kxx;
+    k.Kxy = Kxy;
+    k.Kyy = Kyy;
+    k.o1 = o1;
+    k.no3 = no3;
+    k.G1 = G1;
+    k.om = om;
+    k.a0 = (TC)1 - om;
+    k.vx = vx;
+    k.vy = vy;
+    k.Fx = Fx;
+    k.Fy = Fy;
+    return fr;
+}
+
+// The rest class: q' = q (1 - om) + K0.
+template <typename TC>
+RLBM_HD inline TC collide_rest(TC q0, const CollideCoef<TC> &k) {
+    return fmadd(q0, k.a0, k.K0);
+}
+
+// Opposite pair k: (q_c, q_-c) -> updated values.
+template <int kp, typename TC, bool FORCED>
+RLBM_HD inline void collide_pair(TC &qp, TC &qn, const CollideCoef<TC> &k) {
+    constexpr int c = pair_pos(kp);
+    constexpr double cx = cls_cx(c), cy = cls_cy(c);
+    TC xi = 0;
+    [[maybe_unused]] TC Fc = 0;
+    TC even = k.K0;
+    if constexpr (cx != 0.0) {
+        xi = (TC)cx * k.vx;
+        even = fmadd((TC)(cx * cx), k.Kxx, even);
+        if constexpr (FORCED) Fc = (TC)cx * k.Fx;
+    }
+    if constexpr (cy != 0.0) {
+        xi = fmadd((TC)cy, k.vy, xi);
+        even = fmadd((TC)(cy * cy), k.Kyy, even);
+        if constexpr (FORCED) Fc = fmadd((TC)cy, k.Fy, Fc);
+    }
+    if constexpr (cx != 0.0 && cy != 0.0) even = fmadd((TC)(cx * cy), k.Kxy, even);
+    TC odd = xi * fmadd(k.no3, xi * xi, k.o1);
+    if constexpr (FORCED) odd = fmadd(k.G1, Fc, odd);
+    const TC oxi = k.om * xi;
+    const TC p0 = qp, n0 = qn;
+    qp = fmadd(p0, k.a0 + oxi, even + odd);
+    qn = fmadd(n0, k.a0 - oxi, even - odd);
+}
+
+template <typename TC, typename TL, bool FORCED>
+RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
+    const NodeMoments<TC> m = node_moments<TC>(q, par_scale<TC>(p));
+    CollideCoef<TC> k;
+    const Frame<TL> fr = collide_coef<TC, TL, FORCED>(m, Fx, Fy, p, k);
+    q[0] = collide_rest<TC>(q[0], k);
     static_for<0, NPAIR>([&](auto K) {
-        constexpr int k = decltype(K)::value;
-        constexpr int c = pair_pos(k), cn = pair_neg(k);
-        constexpr double cx = cls_cx(c), cy = cls_cy(c);
-        TC xi = 0;
-        [[maybe_unused]] TC Fc = 0;
-        TC even = K0;
-        if constexpr (cx != 0.0) {
-            xi = (TC)cx * vx;
-            even = fmadd((TC)(cx * cx), Kxx, even);
-            if constexpr (FORCED) Fc = (TC)cx * Fx;
-        }
-        if constexpr (cy != 0.0) {
-            xi = fmadd((TC)cy, vy, xi);
-            even = fmadd((TC)(cy * cy), Kyy, even);
-            if constexpr (FORCED) Fc = fmadd((TC)cy, Fy, Fc);
-        }
-        if constexpr (cx != 0.0 && cy != 0.0) even = fmadd((TC)(cx * cy), Kxy, even);
-        TC odd = xi * fmadd(no3, xi * xi, o1);
-        if constexpr (FORCED) odd = fmadd(G1, Fc, odd);
-        const TC oxi = om * xi;
-        const TC qp = q[c], qn = q[cn];
-        q[c] = fmadd(qp, a0 + oxi, even + odd);
-        q[cn] = fmadd(qn, a0 - oxi, even - odd);
+        constexpr int kp = decltype(K)::value;
+        collide_pair<kp, TC, FORCED>(q[pair_pos(kp)], q[pair_neg(kp)], k);
     });
     return fr;
 }

@@ -67,12 +67,12 @@ FORCING_SMALL = dict(kmin=2, kmax=4, amp=2e-4, seed=123456789, redraw_period=7)
                                           ((64, 48), "vec"), ((4, 4), "vec"), ((136, 40), "vec"),
                                           ((64, 48), "vec2"), ((66, 40), "packed"), ((4, 4), "packed"),
                                           ((136, 40), "tma"), ((130, 27), "tma"), ((4, 4), "tma"),
-                                          ((64, 8), "tma")])
+                                          ((64, 8), "tma"), ((66, 40), "twopass"), ((4, 4), "twopass")])
 def test_forced_run_matches_oracle(dtype, landau, shape, kernel):
     """Ragged lattices spanning several thread blocks, and the 4x4 minimum,
     for both kernel variants (the vector kernel needs nx divisible by its run)."""
     nx, ny = shape
-    if kernel in ("packed", "tma") and (dtype != "f32" or landau != "fp32"):
+    if kernel in ("packed", "tma", "twopass") and (dtype != "f32" or landau != "fp32"):
         pytest.skip("packed lanes are FP32 with the FP32 Landau solve")
     # the 4x4 lattice damps its only modes fast; a stronger force keeps |v| ~ 1e-2 there, so the
     # normwise velocity error measures the arithmetic rather than the FP64 floor eps_mach * E / |v|
@@ -92,7 +92,8 @@ def test_forced_run_matches_oracle(dtype, landau, shape, kernel):
 
 @pytest.mark.parametrize("dtype,landau,kernel", [("f32", "fp32", "gather"), ("f32", "fp32", "vec"),
                                                  ("f32", "fp64", "vec"), ("f64", "fp64", "vec"),
-                                                 ("f32", "fp32", "packed"), ("f32", "fp32", "tma")])
+                                                 ("f32", "fp32", "packed"), ("f32", "fp32", "tma"),
+                                                 ("f32", "fp32", "twopass")])
 def test_low_viscosity_stirred_run_matches_oracle(dtype, landau, kernel):
     """tau = 0.52 (over-relaxation, omega ~ 1.9): non-hydrodynamic errors decay
     slowly, so any bias of the frame arithmetic accumulates; 128 x 128, 100
@@ -173,7 +174,8 @@ def test_vector_and_scalar_kernels_agree(dtype):
     nx, ny = 128, 72
     fields = workloads.random_smooth(nx, ny, seed=13, vmax=0.05)
     out = []
-    kernels = ("gather", "vec", "vec2") + (("packed",) if dtype != "f64" else ()) + (("tma",) if dtype == "f32" else ())
+    kernels = (("gather", "vec", "vec2") + (("packed", "twopass") if dtype != "f64" else ())
+               + (("tma",) if dtype == "f32" else ()))
     for kernel in kernels:
         lat = rl.Lattice(nx, ny, 0.6, dtype=dtype, forcing=FORCING_SMALL, kernel=kernel)
         lat.init_fields(*fields)

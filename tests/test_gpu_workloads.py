@@ -95,7 +95,7 @@ def stirred_1024_oracle():
 
 
 @pytest.mark.parametrize("dtype,tol,kernel", [("f32", 1e-5, "auto"), ("f64", 1e-12, "auto"), ("f32", 1e-5, "tma"),
-                                             ("f32", 1e-5, "packed")])
+                                             ("f32", 1e-5, "packed"), ("f32", 1e-5, "twopass")])
 def test_stirred_1024_full_size_matches_oracle(stirred_1024_oracle, dtype, tol, kernel):
     w = workloads.STIRRED_1024
     lat = rl.Lattice(w.nx, w.ny, w.tau, dtype=dtype, forcing=_forcing(w), kernel=kernel)
