@@ -40,7 +40,7 @@ _ip = ctypes.POINTER(ctypes.c_int)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 
 
-_SRCS = (_SRC, os.path.join(_HERE, "ring2d_oracle.c"))
+_SRCS = (_SRC, os.path.join(_HERE, "ring2d_oracle.c"), os.path.join(_HERE, "lattice3d_oracle.c"))
 
 
 def build(force: bool = False) -> str:
@@ -124,6 +124,24 @@ def _load():
         lib.ring_fields.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
         lib.ring_fields.restype = ctypes.c_int
         lib.ring_totals.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp]
+        i3 = [ctypes.c_int] * 3
+        lib.oracle3d_stream.argtypes = [_dp, _dp, *i3]
+        lib.oracle3d_init.argtypes = [_dp, *i3, _dp, _dp, _dp, _dp]
+        lib.oracle3d_init.restype = ctypes.c_int
+        lib.oracle3d_forcing_modes.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _ip, _ip, ctypes.c_int]
+        lib.oracle3d_forcing_modes.restype = ctypes.c_int
+        lib.oracle3d_forcing_draw.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                              ctypes.c_uint64, _dp, _dp, _dp]
+        lib.oracle3d_force_field.argtypes = [*i3, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                             ctypes.c_uint64, _dp, _dp, _dp]
+        lib.oracle3d_step.argtypes = [_dp, _dp, *i3, ctypes.c_double, _dp, _dp, _dp]
+        lib.oracle3d_step.restype = ctypes.c_int
+        lib.oracle3d_fields.argtypes = [_dp, _dp, *i3, _dp, _dp, _dp, _dp]
+        lib.oracle3d_fields.restype = ctypes.c_int
+        lib.oracle3d_run.argtypes = [_dp, _dp, _dp, _dp, _dp, *i3, ctypes.c_double, ctypes.c_long, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int]
+        lib.oracle3d_run.restype = ctypes.c_int
+        lib.oracle3d_totals.argtypes = [_dp, *i3, _dp]
         _lib = lib
         return lib
 
@@ -495,3 +513,95 @@ class ring:
         out = np.zeros(3)
         _load().ring_totals(_p(f), nx, ny, _p(out))
         return out
+
+
+# --------------------------------------------------------------------------- 3D lattice
+class lattice3d:
+    """The three-dimensional periodic lattice of the paper's node (see
+    lattice3d_oracle.c).  Populations are (26, nz, ny, nx) FP64 arrays;
+    fields are (nz, ny, nx)."""
+
+    @staticmethod
+    def stream(f):
+        f = _f64(f)
+        _, nz, ny, nx = f.shape
+        out = np.empty_like(f)
+        _load().oracle3d_stream(_p(f), _p(out), nx, ny, nz)
+        return out
+
+    @staticmethod
+    def init(nx, ny, nz, eps=None, vx=None, vy=None, vz=None):
+        f = np.zeros((NDIR, nz, ny, nx))
+        conv = lambda a: None if a is None else _f64(a).reshape(nz, ny, nx)
+        rc = _load().oracle3d_init(_p(f), nx, ny, nz, _p(conv(eps)), _p(conv(vx)), _p(conv(vy)), _p(conv(vz)))
+        if rc != 0:
+            raise ValueError("invalid initial fields")
+        return f
+
+    @staticmethod
+    def forcing_modes(kmin, kmax):
+        lib = _load()
+        n = lib.oracle3d_forcing_modes(kmin, kmax, None, None, None, 0)
+        kx, ky, kz = (np.zeros(max(n, 1), dtype=np.int32) for _ in range(3))
+        lib.oracle3d_forcing_modes(kmin, kmax, kx.ctypes.data_as(_ip), ky.ctypes.data_as(_ip), kz.ctypes.data_as(_ip), n)
+        return kx[:n], ky[:n], kz[:n]
+
+    @staticmethod
+    def forcing_draw(kmin, kmax, amp, seed, epoch):
+        n = len(lattice3d.forcing_modes(kmin, kmax)[0])
+        mag, ph, d = np.zeros(n), np.zeros(n), np.zeros((n, 3))
+        _load().oracle3d_forcing_draw(kmin, kmax, float(amp), int(seed) & 0xFFFFFFFFFFFFFFFF, int(epoch), _p(mag),
+                                      _p(ph), _p(d))
+        return mag, ph, d
+
+    @staticmethod
+    def force_field(nx, ny, nz, kmin, kmax, amp, seed, epoch):
+        F = [np.zeros((nz, ny, nx)) for _ in range(3)]
+        _load().oracle3d_force_field(nx, ny, nz, kmin, kmax, float(amp), int(seed) & 0xFFFFFFFFFFFFFFFF, int(epoch),
+                                     *(_p(a) for a in F))
+        return tuple(F)
+
+    @staticmethod
+    def run(f, tau, nsteps, step0=0, kmin=0, kmax=0, amp=0.0, seed=0, redraw=100):
+        assert f.dtype == np.float64 and f.flags.c_contiguous
+        _, nz, ny, nx = f.shape
+        tmp = np.empty_like(f)
+        F = [np.zeros((nz, ny, nx)) for _ in range(3)]
+        bad = _load().oracle3d_run(_p(f), _p(tmp), *(_p(a) for a in F), nx, ny, nz, float(tau), int(step0),
+                                   int(nsteps), int(kmin), int(kmax), float(amp), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                   int(redraw))
+        if bad:
+            raise FloatingPointError("Landau solve failed %d times" % bad)
+        return f
+
+    @staticmethod
+    def fields(f):
+        f = _f64(f)
+        _, nz, ny, nx = f.shape
+        tmp = np.empty_like(f)
+        out = [np.empty((nz, ny, nx)) for _ in range(4)]
+        _load().oracle3d_fields(_p(f), _p(tmp), nx, ny, nz, *(_p(a) for a in out))
+        return tuple(out)
+
+    @staticmethod
+    def totals(f):
+        f = _f64(f)
+        _, nz, ny, nx = f.shape
+        out = np.zeros(4)
+        _load().oracle3d_totals(_p(f), nx, ny, nz, _p(out))
+        return out
+
+    @staticmethod
+    def energy_spectrum(vx, vy, vz, nshells: int) -> np.ndarray:
+        """E(n) of a 3D velocity field: v_hat = (1/N) sum v exp(-2 pi i k.x/N)
+        (numpy FFT as the transform), shell n collects |k| in [n - 1/2,
+        n + 1/2), E(n) = 1/2 sum_shell |v_hat|^2 over the three components."""
+        comps = [np.asarray(a, dtype=np.float64) for a in (vx, vy, vz)]
+        nz, ny, nx = comps[0].shape
+        p = sum(np.abs(np.fft.fftn(a) / (nx * ny * nz)) ** 2 for a in comps) * 0.5
+        kx = np.fft.fftfreq(nx, d=1.0 / nx)
+        ky = np.fft.fftfreq(ny, d=1.0 / ny)
+        kz = np.fft.fftfreq(nz, d=1.0 / nz)
+        K = np.sqrt(kx[None, None, :] ** 2 + ky[None, :, None] ** 2 + kz[:, None, None] ** 2)
+        shell = np.floor(K + 0.5).astype(np.int64)
+        return np.array([p[shell == n].sum() for n in range(nshells)])

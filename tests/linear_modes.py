@@ -21,6 +21,32 @@ def _symbols(v, k, cfl=1.0):
     return S
 
 
+def _symbols3(v, k):
+    """Fourier symbol of pull-streaming with trilinear interpolation from
+    x - v_i on a 3D lattice, per direction (k a 3-vector)."""
+    S = np.zeros(len(v), dtype=complex)
+    for i in range(len(v)):
+        s = -np.asarray(v[i], dtype=float)
+        o = np.floor(s)
+        t = s - o
+        acc = 0.0
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    wgt = (t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]) * (t[2] if dz else 1 - t[2])
+                    acc = acc + wgt * np.exp(1j * (k[0] * (o[0] + dx) + k[1] * (o[1] + dy) + k[2] * (o[2] + dz)))
+        S[i] = acc
+    return S
+
+
+def linear_step3(v, w, k, tau):
+    """The 3D linearised step about rest: trilinear streaming, then BGK
+    towards delta f_eq,i = w_i (delta E + 3 v_i . delta M)."""
+    A = w[:, None] * (1.0 + 3.0 * v @ v.T)
+    C = np.eye(len(w)) - (np.eye(len(w)) - A) / tau
+    return C @ np.diag(_symbols3(v, k))
+
+
 def ring_directions():
     """The 2D ring: 8 unit momenta at 45 degree steps, weight 1/8."""
     ang = np.arange(8) * np.pi / 4
