@@ -272,6 +272,68 @@ def parity_error(rl, oracle, form, landau):
     return {"eps": err_e, "v": err_v, "case": "128x128, 100 forced steps from seeded smooth fields"}
 
 
+def measure_variants(torch, rl, oracle, flush, hbm_peak, steps=50, warmup=5):
+    """The lattice variants beyond the paper's one-layer node, each timed
+    like the headline (per-step CUDA events, L2 flushed between steps) and
+    checked against its oracle on a small case: the 2D ring (1024^2, FP32)
+    and the 3D lattice (256^3, FP32), both stirred."""
+    out = {}
+    w = workloads.STIRRED_1024
+    fz = forcing_of(w)
+    cases = (("ring8_1024x1024_f32", lambda: rl.Lattice(1024, 1024, w.tau, dtype="f32", forcing=fz, stencil="ring8"),
+              1024 * 1024),
+             ("lattice3d_256x256x256_f32", lambda: rl.Lattice3D(256, 256, 256, w.tau, dtype="f32", forcing=fz),
+              256 ** 3))
+    for name, make, nodes in cases:
+        lat = make()
+        lat.init_fields()
+        lat.autotune(5)
+        lat.step(warmup)
+        lat.synchronize()
+        ms = time_steps(torch, lat, steps, flush)
+        info = lat.info()
+        lat.close()
+        km = float(np.median(ms))
+        bp = int(info["bytes_per_node"])
+        out[name] = {"glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_node": bp,
+                     "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak,
+                     "block": [info["block_x"], info["block_y"]]}
+    # parity on small cases (FP32 against the FP64 oracles)
+    n, nsteps = 64, 50
+    fields = workloads.random_smooth(n, n, seed=2024, deps=0.02, vmax=0.02)
+    small = dict(kmin=2, kmax=4, amp=2e-4, seed=7, redraw_period=25)
+    lat = rl.Lattice(n, n, 0.6, dtype="f32", forcing=small, stencil="ring8")
+    lat.init_fields(*fields)
+    lat.step(nsteps)
+    got = lat.moments()
+    lat.close()
+    f = oracle.ring.init(n, n, *fields)
+    oracle.ring.run(f, 0.6, nsteps, kmin=2, kmax=4, amp=2e-4, seed=7, redraw=25)
+    out["ring8_1024x1024_f32"]["max_rel_err_vs_oracle"] = _field_errors(oracle.ring.fields(f), got,
+                                                                       "64x64, 50 forced steps")
+    m = 20
+    fields3 = workloads.random_smooth3d(m, m, m, seed=2024, deps=0.02, vmax=0.02)
+    lat = rl.Lattice3D(m, m, m, 0.6, dtype="f32", forcing=dict(small, kmax=3))
+    lat.init_fields(*fields3)
+    lat.step(nsteps)
+    got = lat.moments()
+    lat.close()
+    f = oracle.lattice3d.init(m, m, m, *fields3)
+    oracle.lattice3d.run(f, 0.6, nsteps, kmin=2, kmax=3, amp=2e-4, seed=7, redraw=25)
+    out["lattice3d_256x256x256_f32"]["max_rel_err_vs_oracle"] = _field_errors(oracle.lattice3d.fields(f), got,
+                                                                             "20^3, 50 forced steps")
+    return out
+
+
+def _field_errors(ref, got, case):
+    e_r, *v_r = ref
+    e_g, *v_g = got[:len(ref)]
+    err_e = float(np.max(np.abs(e_g - e_r)) / np.max(np.abs(e_r)))
+    vn = max(float(np.max(np.abs(v))) for v in v_r)
+    err_v = float(max(np.max(np.abs(g - r)) for g, r in zip(v_g, v_r)) / vn)
+    return {"eps": err_e, "v": err_v, "case": case}
+
+
 def cpu_oracle_glups(oracle, w, n, budget_s):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
     the full n x n lattice if a step fits the budget, else a band of rows
@@ -468,6 +530,7 @@ def main():
                 "max_rel_err_vs_oracle": err}
         line["forms"] = forms
         line["ensemble"] = measure_ensemble(torch, rl, flush)
+        line["variants"] = measure_variants(torch, rl, oracle, flush, hbm_peak)
         line["e2e"] = e2e_glups(rl, w, n, args.form, args.landau)
         g, desc, th = cpu_oracle_glups(oracle, w, n, args.cpu_seconds)
         line["cpu_baseline"] = {"value": g, "unit": "GLUPS", "cores": th, "kind": "oracle", "sample": desc}

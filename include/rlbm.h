@@ -177,7 +177,8 @@ typedef struct {
     double tau, eps0, scale;
     size_t bytes_per_node;    /* algorithmic HBM bytes per lattice update */
     size_t device_bytes;      /* device memory held by the handle */
-    const void *populations;  /* device pointer of the current state, [nclasses][ny][pitch] of the storage type */
+    const void *populations;  /* device pointer of the current state, [nclasses][nz][ny][pitch] of the storage type */
+    int nz;                   /* layers: 1, or nz of a 3D lattice */
 } rlbm_info_t;
 
 /* Fill *opts with the defaults listed above. */
@@ -264,6 +265,48 @@ RLBM_API rlbm_status rlbm_set_populations(rlbm_t *h, const double *f);
 RLBM_API rlbm_status rlbm_get_force(rlbm_t *h, double *Fx, double *Fy);
 
 RLBM_API rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info);
+
+/* ---- Three-dimensional lattice ------------------------------------------
+ * The paper's node (the 26-direction spherical rule, Landau frame,
+ * equilibrium, Anderson-Witting relaxation and driving term of Sec. 3 and
+ * App. A-B) on an nx x ny x nz periodic lattice: the three-dimensional model
+ * the conclusion (Sec. 6) names as the next test.  All 26 directions are
+ * stored (nclasses = 26), streamed by trilinear pull interpolation from
+ * x - v_i (Sec. 3.2's linear interpolation in three dimensions, CFL 1);
+ * the moments, frame and driving term keep every tensor component.  The
+ * stirring force of Sec. 5 is carried to a 3D shell: integer k with
+ * kmin <= |k| <= kmax, one mode per pair +-k (representative kz > 0, or
+ * kz = 0 and ky > 0, or kz = ky = 0 and kx > 0, enumerated kz = 0..kmax,
+ * ky = -kmax..kmax, kx = -kmax..kmax); mode m of epoch e draws
+ * Philox(ctr = {e, m, 0, 0}, key = seed) -> magnitude r*amp, phase 2 pi u
+ * and Philox(ctr = {e, m, 1, 0}, key) -> azimuth 2 pi u, mu = 2u - 1, the
+ * direction (sqrt(1 - mu^2) cos az, sqrt(1 - mu^2) sin az, mu) uniform on
+ * the sphere; F(x) = sum_m 2 r amp d cos(2 pi k.x/N + phi).  Populations
+ * and fields are [.][z][y][x]; the device direction order is
+ *   k = 0..2 faces (1,0,0), (0,1,0), (0,0,1); 3..8 edges (a,a,0), (a,-a,0),
+ *   (a,0,a), (a,0,-a), (0,a,a), (0,a,-a); 9..12 corners (b,b,b), (b,b,-b),
+ *   (b,-b,b), (b,-b,-b); k + 13 the opposite of k; a = 1/sqrt2, b = 1/sqrt3.
+ * A 3D handle runs the one-node-per-thread kernel (kernel AUTO or GATHER)
+ * at cfl 1 (eta_s allowed), in every storage form; rlbm_step,
+ * rlbm_get/set_populations, rlbm_get_info, rlbm_autotune, rlbm_synchronize,
+ * rlbm_last_error and rlbm_destroy apply to it, as does
+ * rlbm_init_fields_device (v_z = 0); the other 2D calls return
+ * RLBM_ERR_STATE.  Errors as rlbm_create; nz >= 4, nx*ny*nz <= 2^31,
+ * 2 kmax < min(nx, ny, nz). */
+RLBM_API rlbm_status rlbm_create3d(int nx, int ny, int nz, double tau, const rlbm_forcing *forcing,
+                                   const rlbm_opts *opts, rlbm_t **out);
+/* f = f_eq of host FP64 fields, nx*ny*nz each ([z][y][x]; NULL: eps = 1,
+ * v = 0), validated on the device first (RLBM_ERR_ARG, state untouched);
+ * restarts the clock.  Synchronises. */
+RLBM_API rlbm_status rlbm_init_fields3d(rlbm_t *h, const double *eps, const double *vx, const double *vy,
+                                        const double *vz);
+/* eps and v of the state the next collision sees (FP64 Landau frame), host
+ * FP64 nx*ny*nz each (any may be NULL), and totals[4] = sum over nodes of
+ * (T^00, T^0x, T^0y, T^0z) (may be NULL).  RLBM_ERR_NAN if a node has no
+ * physical frame.  Synchronises. */
+RLBM_API rlbm_status rlbm_moments3d(rlbm_t *h, double *eps, double *vx, double *vy, double *vz, double totals[4]);
+/* Force of the current epoch, host FP64 nx*ny*nz each (any may be NULL). */
+RLBM_API rlbm_status rlbm_get_force3d(rlbm_t *h, double *Fx, double *Fy, double *Fz);
 
 /* Time every launch configuration of the fused step (kernel variant and
  * thread-block shape) for `reps` launches each (reps < 1: 20) on the

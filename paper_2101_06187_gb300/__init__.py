@@ -41,7 +41,8 @@ EXPORTS = (
     "rlbm_status_string", "rlbm_batch_create", "rlbm_batch_init_fields", "rlbm_batch_step", "rlbm_batch_moments",
     "rlbm_batch_energy_spectrum", "rlbm_batch_get_populations", "rlbm_batch_autotune", "rlbm_batch_get_info",
     "rlbm_batch_synchronize", "rlbm_batch_last_error", "rlbm_batch_destroy", "rlbm_filtered_velocity",
-    "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset",
+    "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset", "rlbm_create3d", "rlbm_init_fields3d",
+    "rlbm_moments3d", "rlbm_get_force3d",
 )
 
 
@@ -74,7 +75,7 @@ class Info(ctypes.Structure):
                 ("block_y", ctypes.c_int), ("nmodes", ctypes.c_int),
                 ("step", ctypes.c_int64), ("tau", ctypes.c_double), ("eps0", ctypes.c_double),
                 ("scale", ctypes.c_double), ("bytes_per_node", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
-                ("populations", ctypes.c_void_p)]
+                ("populations", ctypes.c_void_p), ("nz", ctypes.c_int)]
 
 
 class RunDesc(ctypes.Structure):
@@ -125,6 +126,13 @@ def _load():
         lib.rlbm_spectrum_stats.argtypes = [h, ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_int)]
         lib.rlbm_spectrum_reset.argtypes = [h]
         for name in ("rlbm_filtered_velocity", "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib.rlbm_create3d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(Forcing), ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]
+        lib.rlbm_init_fields3d.argtypes = [h, _dp, _dp, _dp, _dp]
+        lib.rlbm_moments3d.argtypes = [h, _dp, _dp, _dp, _dp, _dp]
+        lib.rlbm_get_force3d.argtypes = [h, _dp, _dp, _dp]
+        for name in ("rlbm_create3d", "rlbm_init_fields3d", "rlbm_moments3d", "rlbm_get_force3d"):
             getattr(lib, name).restype = ctypes.c_int
         b = ctypes.c_void_p
         ip = ctypes.POINTER(ctypes.c_int)
@@ -296,6 +304,27 @@ def rlbm_get_force(h, Fx, Fy):
     _check(h, _load().rlbm_get_force(h, _p(Fx), _p(Fy)), "rlbm_get_force")
 
 
+def rlbm_create3d(nx: int, ny: int, nz: int, tau: float, forcing: Optional[Forcing], opts: Optional[Opts]):
+    lib = _load()
+    out = ctypes.c_void_p()
+    st = lib.rlbm_create3d(int(nx), int(ny), int(nz), float(tau), ctypes.byref(forcing) if forcing else None,
+                           ctypes.byref(opts) if opts else None, ctypes.byref(out))
+    _check(None, st, "rlbm_create3d")
+    return out
+
+
+def rlbm_init_fields3d(h, eps=None, vx=None, vy=None, vz=None):
+    _check(h, _load().rlbm_init_fields3d(h, _p(eps), _p(vx), _p(vy), _p(vz)), "rlbm_init_fields3d")
+
+
+def rlbm_moments3d(h, eps, vx, vy, vz, totals):
+    _check(h, _load().rlbm_moments3d(h, _p(eps), _p(vx), _p(vy), _p(vz), _p(totals)), "rlbm_moments3d")
+
+
+def rlbm_get_force3d(h, Fx, Fy, Fz):
+    _check(h, _load().rlbm_get_force3d(h, _p(Fx), _p(Fy), _p(Fz)), "rlbm_get_force3d")
+
+
 def rlbm_get_info(h) -> Info:
     info = Info()
     _check(h, _load().rlbm_get_info(h, ctypes.byref(info)), "rlbm_get_info")
@@ -453,8 +482,11 @@ class Lattice:
                         int(forcing.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF, int(forcing.get("redraw_period", 100)))
         self.dtype = dtype
         self.stencil = stencil
-        self._h = rlbm_create(self.nx, self.ny, STENCILS[stencil], self.tau, f, o)
+        self._h = self._create(f, o)
         self.nclasses = self.info()["nclasses"]
+
+    def _create(self, forcing, opts):
+        return rlbm_create(self.nx, self.ny, STENCILS[self.stencil], self.tau, forcing, opts)
 
     # -- life cycle
     def close(self):
@@ -548,6 +580,47 @@ class Lattice:
 
     def synchronize(self):
         rlbm_synchronize(self.handle)
+
+
+class Lattice3D(Lattice):
+    """A three-dimensional periodic lattice of the paper's node (26 stored
+    directions, trilinear streaming, 3D stirring on a shell).  Same options
+    as Lattice (kernel "auto" or "gather", cfl 1); fields are (nz, ny, nx)
+    arrays, populations (26, nz, ny, nx)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, tau: float, **kw):
+        self.nz = int(nz)
+        super().__init__(nx, ny, tau, **kw)
+
+    def _create(self, forcing, opts):
+        return rlbm_create3d(self.nx, self.ny, self.nz, self.tau, forcing, opts)
+
+    def _shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def init_fields(self, eps=None, vx=None, vy=None, vz=None):
+        n = self.nx * self.ny * self.nz
+        rlbm_init_fields3d(self.handle, _f64(eps, n), _f64(vx, n), _f64(vy, n), _f64(vz, n))
+
+    def moments(self):
+        """(eps, vx, vy, vz, totals): (nz, ny, nx) FP64 fields and totals[4]."""
+        out = [np.empty(self._shape()) for _ in range(4)]
+        tot = np.empty(4)
+        rlbm_moments3d(self.handle, *out, tot)
+        return (*out, tot)
+
+    def populations(self) -> np.ndarray:
+        f = np.empty((self.nclasses,) + self._shape())
+        rlbm_get_populations(self.handle, f)
+        return f
+
+    def set_populations(self, f):
+        rlbm_set_populations(self.handle, _f64(f, self.nclasses * self.nx * self.ny * self.nz))
+
+    def force(self):
+        F = [np.empty(self._shape()) for _ in range(3)]
+        rlbm_get_force3d(self.handle, *F)
+        return tuple(F)
 
 
 class Ensemble:

@@ -128,7 +128,9 @@ static StepParams params_of(const rlbm_t *h) {
     p.nx = h->nx;
     p.ny = h->ny;
     p.pitch = h->pitch;
-    p.plane = (long long)h->ny * h->pitch;
+    p.slab = (long long)h->ny * h->pitch;
+    p.nz = h->nz;
+    p.plane = p.slab * h->nz;
     p.inv_tau = 1.0 / h->tau;
     p.eps0 = h->opts.eps0;
     p.scale = h->opts.scale;
@@ -140,21 +142,34 @@ static StepParams params_of(const rlbm_t *h) {
     return p;
 }
 
-static size_t q_bytes(const rlbm_t *h) { return (size_t)h->ncls * h->ny * h->pitch * storage_bytes(h->opts.dtype); }
-static size_t F_bytes(const rlbm_t *h) { return (size_t)2 * h->ny * h->pitch * compute_bytes(h->opts.dtype); }
+static size_t nodes_of(const rlbm_t *h) { return (size_t)h->nx * h->ny * h->nz; }
+static size_t q_bytes(const rlbm_t *h) {
+    return (size_t)h->ncls * h->nz * h->ny * h->pitch * storage_bytes(h->opts.dtype);
+}
+static size_t F_bytes(const rlbm_t *h) {
+    return (size_t)(h->d3 ? 3 : 2) * h->nz * h->ny * h->pitch * compute_bytes(h->opts.dtype);
+}
 static size_t tw_bytes(const rlbm_t *h, int n) { return (size_t)n * 2 * compute_bytes(h->opts.dtype); }
-static size_t fields_bytes(const rlbm_t *h) { return (size_t)3 * h->nx * h->ny * sizeof(double); }
-static size_t partials_bytes(const rlbm_t *h) { return (size_t)3 * moments_blocks(params_of(h)) * sizeof(double); }
+static size_t fields_bytes(const rlbm_t *h) { return (size_t)(h->d3 ? 4 : 3) * nodes_of(h) * sizeof(double); }
+static size_t partials_bytes(const rlbm_t *h) {
+    return h->d3 ? (size_t)4 * moments3_blocks(params_of(h)) * sizeof(double)
+                 : (size_t)3 * moments_blocks(params_of(h)) * sizeof(double);
+}
+static size_t coef_bytes(const rlbm_t *h) {
+    return h->d3 ? coef3_bytes(h->opts.dtype) * h->nmodes : 4 * compute_bytes(h->opts.dtype) * h->nmodes;
+}
 
 // Class weight W_c of stored class c (spherical node or 2D ring).
 static double class_weight(const rlbm_t *h, int c) {
     if (h->ring) return 1.0 / 8.0;
+    if (h->d3) return class_weight3(c);
     return c == 0 ? 2.0 / 21.0 : c <= 4 ? 1.0 / 21.0 : c <= 8 ? 8.0 / 105.0 : c <= 12 ? 4.0 / 105.0 : 9.0 / 140.0;
 }
 
 static cudaError_t launch_step_h(const rlbm_t *h, const LaunchCfg &cfg, const void *qin, void *qout,
                                  const StepParams &p) {
     if (h->ring) return launch_ring_step(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
+    if (h->d3) return launch_step3(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
     if (cfg.kernel == RLBM_KERNEL_TMA) {
         if (!h->tm_ready) return cudaErrorNotSupported;
         const CUtensorMap &mq = (qin == h->q[0]) ? h->tm_q[0] : h->tm_q[1];
@@ -182,6 +197,14 @@ static rlbm_status ensure_force(rlbm_t *h) {
     const long long e = h->step / h->forcing.redraw_period;
     if (e == h->force_epoch) return RLBM_OK;
     const StepParams p = params_of(h);
+    if (h->d3) {
+        CUDA_TRY(h, launch_draw_modes3(h->opts.dtype, h->modes3, h->coef, h->nmodes, h->forcing.amp,
+                                       (unsigned long long)h->forcing.seed, (unsigned long long)e, h->stream));
+        CUDA_TRY(h, launch_synth_force3(h->opts.dtype, h->F, h->coef, h->nmodes, h->tabx, h->taby, h->tabz, p,
+                                        h->stream));
+        h->force_epoch = e;
+        return RLBM_OK;
+    }
     CUDA_TRY(h, launch_draw_modes(h->opts.dtype, h->modes, h->coef, h->nmodes, h->forcing.amp,
                                   (unsigned long long)h->forcing.seed, (unsigned long long)e, h->stream));
     CUDA_TRY(h, launch_synth_force(h->opts.dtype, h->F, h->coef, h->nmodes, h->tabx, h->taby, p, h->stream));
@@ -267,7 +290,8 @@ static std::map<std::tuple<int, int, int, int, int, int>, LaunchCfg> g_tuned;
 static std::mutex g_tuned_mu;
 
 static std::tuple<int, int, int, int, int, int> tune_key(const rlbm_t *h) {
-    return std::make_tuple(h->nx, h->ny, h->opts.dtype, h->opts.landau, h->forced ? 1 : 0, h->ring ? 1 : 0);
+    return std::make_tuple(h->nx, h->ny, h->opts.dtype, h->opts.landau, h->forced ? 1 : 0,
+                           h->ring ? 1 : (h->d3 ? 2 + h->nz : 0));
 }
 
 
@@ -328,7 +352,10 @@ void rlbm_destroy(rlbm_t *h) {
     if (h->F) dev_free(h, h->F, F_bytes(h));
     if (h->twx) dev_free(h, h->twx, tw_bytes(h, h->nx));
     if (h->twy) dev_free(h, h->twy, tw_bytes(h, h->ny));
-    if (h->coef) dev_free(h, h->coef, 4 * compute_bytes(h->opts.dtype) * h->nmodes);
+    if (h->coef) dev_free(h, h->coef, coef_bytes(h));
+    if (h->twz) dev_free(h, h->twz, tw_bytes(h, h->nz));
+    if (h->tabz) dev_free(h, h->tabz, tw_bytes(h, h->nz) * h->nmodes);
+    if (h->modes3) dev_free(h, h->modes3, mode3_bytes() * h->nmodes);
     if (h->tabx) dev_free(h, h->tabx, tw_bytes(h, h->nx) * h->nmodes);
     if (h->taby) dev_free(h, h->taby, tw_bytes(h, h->ny) * h->nmodes);
     if (h->modes) dev_free(h, h->modes, sizeof(Mode) * h->nmodes);
@@ -343,13 +370,38 @@ void rlbm_destroy(rlbm_t *h) {
     delete h;
 }
 
-rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const rlbm_forcing *forcing,
-                        const rlbm_opts *opts, rlbm_t **out) {
+}  // extern "C"
+
+// The 3D mode list: integer k on the shell, one per pair +-k, the
+// representative with kz > 0, or kz = 0 and ky > 0, or kz = ky = 0 and
+// kx > 0, in the order kz = 0..kmax, ky = -kmax..kmax, kx = -kmax..kmax.
+static int enumerate_modes3(int kmin, int kmax, std::vector<int> *out) {
+    int m = 0;
+    for (int kz = 0; kz <= kmax; ++kz)
+        for (int ky = -kmax; ky <= kmax; ++ky)
+            for (int kx = -kmax; kx <= kmax; ++kx) {
+                if (kz == 0 && (ky < 0 || (ky == 0 && kx <= 0))) continue;
+                const int k2 = kx * kx + ky * ky + kz * kz;
+                if (k2 < kmin * kmin || k2 > kmax * kmax) continue;
+                if (out) {
+                    out->push_back(kx);
+                    out->push_back(ky);
+                    out->push_back(kz);
+                }
+                ++m;
+            }
+    return m;
+}
+
+static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil stencil, double tau,
+                               const rlbm_forcing *forcing, const rlbm_opts *opts, rlbm_t **out) {
     if (!out) return RLBM_ERR_ARG;
     *out = nullptr;
     if (stencil != RLBM_STENCIL_SPH26_SLAB && stencil != RLBM_STENCIL_RING8_2D) return RLBM_ERR_ARG;
     const bool ring = stencil == RLBM_STENCIL_RING8_2D;
-    if (nx < 4 || ny < 4 || (long long)nx * ny > (1ll << 31)) return RLBM_ERR_ARG;
+    if (d3 && (ring || nz < 4)) return RLBM_ERR_ARG;
+    if (!d3) nz = 1;
+    if (nx < 4 || ny < 4 || (long long)nx * ny * nz > (1ll << 31)) return RLBM_ERR_ARG;
     if (!(tau > 0.5) || !isfinite(tau)) return RLBM_ERR_ARG;
     rlbm_opts o;
     rlbm_opts_default(&o);
@@ -381,6 +433,8 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
     if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER) || o.cfl != 1.0 || o.eta_s != 0.0))
         return RLBM_ERR_ARG;
+    // the 3D lattice runs the one-node-per-thread kernel at CFL 1
+    if (d3 && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER) || o.cfl != 1.0)) return RLBM_ERR_ARG;
 
     rlbm_forcing fz{};
     bool forced = false;
@@ -389,6 +443,7 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         if (!(fz.amp >= 0.0) || !isfinite(fz.amp)) return RLBM_ERR_ARG;
         if (fz.amp > 0.0 && fz.kmax > 0) {
             if (fz.kmin < 1 || fz.kmin > fz.kmax || 2 * fz.kmax >= std::min(nx, ny)) return RLBM_ERR_ARG;
+            if (d3 && 2 * fz.kmax >= nz) return RLBM_ERR_ARG;
             if (fz.redraw_period < 1) return RLBM_ERR_ARG;
             forced = true;
         }
@@ -403,7 +458,9 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     h->forcing = fz;
     h->forced = forced;
     h->ring = ring;
-    h->ncls = ring ? NR : NC;
+    h->d3 = d3;
+    h->nz = nz;
+    h->ncls = ring ? NR : d3 ? 26 : NC;  // 3D: all 26 directions stored
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {
             delete h;
@@ -438,7 +495,12 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     }
 
     std::vector<Mode> modes;
-    if (forced) h->nmodes = enumerate_modes(fz.kmin, fz.kmax, &modes);
+    std::vector<int> modes3;
+    if (forced) h->nmodes = d3 ? enumerate_modes3(fz.kmin, fz.kmax, &modes3) : enumerate_modes(fz.kmin, fz.kmax, &modes);
+    if (forced && h->nmodes == 0) {
+        delete h;
+        return RLBM_ERR_ARG;
+    }
 
     h->q[0] = dev_alloc(h, q_bytes(h));
     h->q[1] = dev_alloc(h, q_bytes(h));
@@ -452,11 +514,19 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         h->F = dev_alloc(h, F_bytes(h));
         h->twx = dev_alloc(h, tw_bytes(h, nx));
         h->twy = dev_alloc(h, tw_bytes(h, ny));
-        h->modes = static_cast<Mode *>(dev_alloc(h, sizeof(Mode) * h->nmodes));
-        h->coef = dev_alloc(h, 4 * compute_bytes(o.dtype) * h->nmodes);
+        h->coef = dev_alloc(h, coef_bytes(h));
         h->tabx = dev_alloc(h, tw_bytes(h, nx) * h->nmodes);
         h->taby = dev_alloc(h, tw_bytes(h, ny) * h->nmodes);
-        ok = ok && h->F && h->twx && h->twy && h->modes && h->coef && h->tabx && h->taby;
+        ok = ok && h->F && h->twx && h->twy && h->coef && h->tabx && h->taby;
+        if (d3) {
+            h->modes3 = dev_alloc(h, mode3_bytes() * h->nmodes);
+            h->twz = dev_alloc(h, tw_bytes(h, nz));
+            h->tabz = dev_alloc(h, tw_bytes(h, nz) * h->nmodes);
+            ok = ok && h->modes3 && h->twz && h->tabz;
+        } else {
+            h->modes = static_cast<Mode *>(dev_alloc(h, sizeof(Mode) * h->nmodes));
+            ok = ok && h->modes;
+        }
     }
     if (!ok || cudaMallocHost(&h->host_small, 4096) != cudaSuccess) {
         cudaGetLastError();
@@ -465,7 +535,19 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
         return RLBM_ERR_ALLOC;
     }
     rlbm_status st = RLBM_OK;
-    if (forced) {
+    if (forced && d3) {
+        std::vector<unsigned char> hm(mode3_bytes() * h->nmodes);
+        for (int m = 0; m < h->nmodes; ++m) host_mode3(hm.data(), m, modes3[3 * m], modes3[3 * m + 1], modes3[3 * m + 2]);
+        cudaError_t e = cudaMemcpyAsync(h->modes3, hm.data(), hm.size(), cudaMemcpyHostToDevice, h->stream);
+        void *tw[3] = {h->twx, h->twy, h->twz}, *tab[3] = {h->tabx, h->taby, h->tabz};
+        const int n3[3] = {nx, ny, nz};
+        for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+            e = launch_twiddles(o.dtype, tw[a], n3[a], h->stream);
+            if (e == cudaSuccess) e = launch_mode_tables3(o.dtype, tab[a], h->modes3, h->nmodes, tw[a], n3[a], a, h->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = RLBM_ERR_CUDA;
+    } else if (forced) {
         cudaError_t e = cudaMemcpyAsync(h->modes, modes.data(), sizeof(Mode) * h->nmodes, cudaMemcpyHostToDevice,
                                         h->stream);
         if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twx, nx, h->stream);
@@ -477,7 +559,8 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     }
     if (st == RLBM_OK && cudaMemsetAsync(h->errword, 0, sizeof(int) * 4, h->stream) != cudaSuccess) st = RLBM_ERR_CUDA;
     // tensor maps for the TMA kernel where it applies (a host-side encoding)
-    if (st == RLBM_OK && !ring && o.dtype == RLBM_F32 && o.landau == RLBM_LANDAU_FP32 && nx % 2 == 0 && o.cfl == 1.0) {
+    if (st == RLBM_OK && !ring && !d3 && o.dtype == RLBM_F32 && o.landau == RLBM_LANDAU_FP32 && nx % 2 == 0 &&
+        o.cfl == 1.0) {
         const StepParams p = params_of(h);
         bool enc = tma_encode_state(&h->tm_q[0], h->q[0], p) == cudaSuccess &&
                    tma_encode_state(&h->tm_q[1], h->q[1], p) == cudaSuccess;
@@ -497,19 +580,34 @@ rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const 
     return RLBM_OK;
 }
 
+extern "C" {
+
+rlbm_status rlbm_create(int nx, int ny, rlbm_stencil stencil, double tau, const rlbm_forcing *forcing,
+                        const rlbm_opts *opts, rlbm_t **out) {
+    return create_impl(nx, ny, 1, false, stencil, tau, forcing, opts, out);
+}
+
+rlbm_status rlbm_create3d(int nx, int ny, int nz, double tau, const rlbm_forcing *forcing, const rlbm_opts *opts,
+                          rlbm_t **out) {
+    return create_impl(nx, ny, nz, true, RLBM_STENCIL_SPH26_SLAB, tau, forcing, opts, out);
+}
+
 }  // extern "C"
 
 // Write f_eq of the given device fields into the current buffer.  A plain
 // handle restarts its clock (step 0, current buffer 0); an ensemble member
 // keeps the ensemble's clock and buffer parity.
 static rlbm_status init_device_impl(rlbm_t *h, const double *d_eps, const double *d_vx, const double *d_vy,
-                                    bool keep_clock) {
+                                    bool keep_clock, const double *d_vz = nullptr) {
     if (!keep_clock) {
         h->cur = 0;
         h->step = 0;
         h->force_epoch = -1;
     }
-    if (h->ring) CUDA_TRY(h, launch_ring_init(h->opts.dtype, h->q[h->cur], params_of(h), d_eps, d_vx, d_vy, h->stream));
+    if (h->d3)
+        CUDA_TRY(h, launch_init3(h->opts.dtype, h->q[h->cur], params_of(h), d_eps, d_vx, d_vy, d_vz, h->stream));
+    else if (h->ring)
+        CUDA_TRY(h, launch_ring_init(h->opts.dtype, h->q[h->cur], params_of(h), d_eps, d_vx, d_vy, h->stream));
     else CUDA_TRY(h, launch_init(h->opts.dtype, h->q[h->cur], params_of(h), d_eps, d_vx, d_vy, h->stream));
     return RLBM_OK;
 }
@@ -517,23 +615,25 @@ static rlbm_status init_device_impl(rlbm_t *h, const double *d_eps, const double
 // The host fields are copied straight from the caller's memory, checked on
 // the device (no host pass over the arrays), and only then turned into
 // populations, so invalid fields leave the state untouched.
-static rlbm_status init_host_impl(rlbm_t *h, const double *eps, const double *vx, const double *vy, bool keep_clock) {
-    const size_t n = (size_t)h->nx * h->ny;
-    const double *src[3] = {eps, vx, vy};
-    double *dptr[3] = {nullptr, nullptr, nullptr};
-    for (int k = 0; k < 3; ++k) {
+static rlbm_status init_host_impl(rlbm_t *h, const double *eps, const double *vx, const double *vy, bool keep_clock,
+                                  const double *vz = nullptr) {
+    const size_t n = nodes_of(h);
+    const double *src[4] = {eps, vx, vy, vz};
+    double *dptr[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < (h->d3 ? 4 : 3); ++k) {
         if (!src[k]) continue;
         dptr[k] = h->fields + k * n;
         CUDA_TRY(h, cudaMemcpyAsync(dptr[k], src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     }
     int *bad_host = reinterpret_cast<int *>(h->host_small);
     CUDA_TRY(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
-    CUDA_TRY(h, launch_check_fields(dptr[0], dptr[1], dptr[2], (long long)n, h->bad, h->stream));
+    if (h->d3) CUDA_TRY(h, launch_check_fields3(dptr[0], dptr[1], dptr[2], dptr[3], (long long)n, h->bad, h->stream));
+    else CUDA_TRY(h, launch_check_fields(dptr[0], dptr[1], dptr[2], (long long)n, h->bad, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(bad_host, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     if (*bad_host) return fail(h, RLBM_ERR_ARG, "%d initial-field entries have eps <= 0, |v| >= 1 or non-finite values",
                                *bad_host);
-    rlbm_status st = init_device_impl(h, dptr[0], dptr[1], dptr[2], keep_clock);
+    rlbm_status st = init_device_impl(h, dptr[0], dptr[1], dptr[2], keep_clock, dptr[3]);
     if (st != RLBM_OK) return st;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return RLBM_OK;
@@ -543,12 +643,19 @@ extern "C" {
 
 rlbm_status rlbm_init_fields_device(rlbm_t *h, const double *d_eps, const double *d_vx, const double *d_vy) {
     CHECK_HANDLE(h);
-    return init_device_impl(h, d_eps, d_vx, d_vy, false);
+    return init_device_impl(h, d_eps, d_vx, d_vy, false);  // a 3D handle: v_z = 0
 }
 
 rlbm_status rlbm_init_fields(rlbm_t *h, const double *eps, const double *vx, const double *vy) {
     CHECK_HANDLE(h);
+    if (h->d3) return fail(h, RLBM_ERR_STATE, "3D lattice: use rlbm_init_fields3d");
     return init_host_impl(h, eps, vx, vy, false);
+}
+
+rlbm_status rlbm_init_fields3d(rlbm_t *h, const double *eps, const double *vx, const double *vy, const double *vz) {
+    CHECK_HANDLE(h);
+    if (!h->d3) return fail(h, RLBM_ERR_STATE, "not a 3D lattice");
+    return init_host_impl(h, eps, vx, vy, false, vz);
 }
 
 rlbm_status rlbm_step(rlbm_t *h, int n) {
@@ -572,6 +679,7 @@ rlbm_status rlbm_step(rlbm_t *h, int n) {
 
 rlbm_status rlbm_moments_device(rlbm_t *h, double *d_eps, double *d_vx, double *d_vy, double *d_totals) {
     CHECK_HANDLE(h);
+    if (h->d3) return fail(h, RLBM_ERR_STATE, "3D lattice: use rlbm_moments3d");
     const StepParams p = params_of(h);
     CUDA_TRY(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
     if (h->ring)
@@ -583,6 +691,35 @@ rlbm_status rlbm_moments_device(rlbm_t *h, double *d_eps, double *d_vx, double *
     if (d_totals)
         CUDA_TRY(h, launch_reduce_partials(h->partials, moments_blocks(p), h->opts.eps0 * (double)h->nx * h->ny,
                                            d_totals, h->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_moments3d(rlbm_t *h, double *eps, double *vx, double *vy, double *vz, double totals[4]) {
+    CHECK_HANDLE(h);
+    if (!h->d3) return fail(h, RLBM_ERR_STATE, "not a 3D lattice");
+    const size_t n = nodes_of(h);
+    const StepParams p = params_of(h);
+    double *dst[4] = {eps, vx, vy, vz};
+    double *dev[4];
+    for (int k = 0; k < 4; ++k) dev[k] = dst[k] ? h->fields + k * n : nullptr;
+    CUDA_TRY(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+    CUDA_TRY(h, launch_moments3(h->opts.dtype, h->q[h->cur], p, dev[0], dev[1], dev[2], dev[3], h->partials, h->bad,
+                                h->stream));
+    if (totals)
+        CUDA_TRY(h, launch_reduce_partials4(h->partials, moments3_blocks(p), h->opts.eps0 * (double)n, h->totals,
+                                            h->stream));
+    for (int k = 0; k < 4; ++k)
+        if (dst[k]) CUDA_TRY(h, cudaMemcpyAsync(dst[k], dev[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int *bad_host = reinterpret_cast<int *>(h->host_small);
+    double *tot_host = h->host_small + 8;
+    CUDA_TRY(h, cudaMemcpyAsync(bad_host, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (totals) CUDA_TRY(h, cudaMemcpyAsync(tot_host, h->totals, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (totals)
+        for (int k = 0; k < 4; ++k) totals[k] = tot_host[k];
+    rlbm_status st = check_errword(h);
+    if (st != RLBM_OK) return st;
+    if (*bad_host) return fail(h, RLBM_ERR_NAN, "%d nodes have no physical Landau frame", *bad_host);
     return RLBM_OK;
 }
 
@@ -613,6 +750,7 @@ rlbm_status rlbm_moments(rlbm_t *h, double *eps, double *vx, double *vy, double 
 
 rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
     CHECK_HANDLE(h);
+    if (h->d3) return fail(h, RLBM_ERR_STATE, "not available for a 3D lattice");
     if (nshells < 1 || nshells > 4096 || !Ek) return fail(h, RLBM_ERR_ARG, "nshells must be in [1, 4096]");
     rlbm_status st0 = ensure_spectrum_work(h);
     if (st0 != RLBM_OK) return st0;
@@ -632,6 +770,7 @@ rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
 
 rlbm_status rlbm_filtered_velocity(rlbm_t *h, double kf, double *rms) {
     CHECK_HANDLE(h);
+    if (h->d3) return fail(h, RLBM_ERR_STATE, "not available for a 3D lattice");
     if (!rms || !(kf >= 0.0)) return fail(h, RLBM_ERR_ARG, "kf must be >= 0 and rms non-NULL");
     rlbm_status st = ensure_spectrum_work(h);
     if (st != RLBM_OK) return st;
@@ -660,6 +799,7 @@ rlbm_status rlbm_spectrum_reset(rlbm_t *h) {
 
 rlbm_status rlbm_spectrum_sample(rlbm_t *h, int nshells) {
     CHECK_HANDLE(h);
+    if (h->d3) return fail(h, RLBM_ERR_STATE, "not available for a 3D lattice");
     if (nshells < 1 || nshells > 4096) return fail(h, RLBM_ERR_ARG, "nshells must be in [1, 4096]");
     if (h->spec_count > 0 && nshells != h->spec_nshells)
         return fail(h, RLBM_ERR_STATE, "sampling %d shells into a record of %d (reset first)", nshells,
@@ -709,10 +849,15 @@ rlbm_status rlbm_spectrum_stats(rlbm_t *h, int nshells, double *mean, double *se
 rlbm_status rlbm_get_populations(rlbm_t *h, double *f) {
     CHECK_HANDLE(h);
     if (!f) return RLBM_ERR_ARG;
-    const size_t n = (size_t)h->nx * h->ny;
+    const size_t layer = (size_t)h->nx * h->ny, n = nodes_of(h);
     const StepParams p = params_of(h);
+    const size_t sb = storage_bytes(h->opts.dtype);
     for (int c = 0; c < h->ncls; ++c) {
-        CUDA_TRY(h, launch_decode_class(h->opts.dtype, h->q[h->cur], c, class_weight(h, c), p, h->fields, h->stream));
+        for (int z = 0; z < h->nz; ++z) {
+            const void *qz = static_cast<const char *>(h->q[h->cur]) + (size_t)z * p.slab * sb;
+            CUDA_TRY(h, launch_decode_class(h->opts.dtype, qz, c, class_weight(h, c), p, h->fields + z * layer,
+                                            h->stream));
+        }
         CUDA_TRY(h, cudaMemcpyAsync(f + c * n, h->fields, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     }
@@ -722,19 +867,52 @@ rlbm_status rlbm_get_populations(rlbm_t *h, double *f) {
 rlbm_status rlbm_set_populations(rlbm_t *h, const double *f) {
     CHECK_HANDLE(h);
     if (!f) return RLBM_ERR_ARG;
-    const size_t n = (size_t)h->nx * h->ny;
+    const size_t layer = (size_t)h->nx * h->ny, n = nodes_of(h);
     const StepParams p = params_of(h);
+    const size_t sb = storage_bytes(h->opts.dtype);
     for (int c = 0; c < h->ncls; ++c) {
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         CUDA_TRY(h, cudaMemcpyAsync(h->fields, f + c * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        CUDA_TRY(h, launch_encode_class(h->opts.dtype, h->q[h->cur], c, class_weight(h, c), p, h->fields, h->stream));
+        for (int z = 0; z < h->nz; ++z) {
+            void *qz = static_cast<char *>(h->q[h->cur]) + (size_t)z * p.slab * sb;
+            CUDA_TRY(h, launch_encode_class(h->opts.dtype, qz, c, class_weight(h, c), p, h->fields + z * layer,
+                                            h->stream));
+        }
     }
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return RLBM_OK;
 }
 
+rlbm_status rlbm_get_force3d(rlbm_t *h, double *Fx, double *Fy, double *Fz) {
+    CHECK_HANDLE(h);
+    if (!h->d3) return fail(h, RLBM_ERR_STATE, "not a 3D lattice");
+    const size_t n = nodes_of(h), layer = (size_t)h->nx * h->ny;
+    double *dst[3] = {Fx, Fy, Fz};
+    if (!h->forced) {
+        for (int k = 0; k < 3; ++k)
+            if (dst[k]) memset(dst[k], 0, n * sizeof(double));
+        return RLBM_OK;
+    }
+    rlbm_status st = ensure_force(h);
+    if (st != RLBM_OK) return st;
+    const StepParams p = params_of(h);
+    const size_t cb = compute_bytes(h->opts.dtype);
+    for (int k = 0; k < 3; ++k) {
+        if (!dst[k]) continue;
+        for (int z = 0; z < h->nz; ++z) {
+            // component k of layer z, read as the first component of a one-layer force array
+            const void *Fk = static_cast<const char *>(h->F) + ((size_t)k * p.plane + (size_t)z * p.slab) * cb;
+            CUDA_TRY(h, launch_force_to_f64(h->opts.dtype, Fk, 0, p, h->fields + z * layer, h->stream));
+        }
+        CUDA_TRY(h, cudaMemcpyAsync(dst[k], h->fields, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    }
+    return RLBM_OK;
+}
+
 rlbm_status rlbm_get_force(rlbm_t *h, double *Fx, double *Fy) {
     CHECK_HANDLE(h);
+    if (h->d3) return fail(h, RLBM_ERR_STATE, "3D lattice: use rlbm_get_force3d");
     const size_t n = (size_t)h->nx * h->ny;
     if (!h->forced) {
         if (Fx) memset(Fx, 0, n * sizeof(double));
@@ -760,6 +938,7 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
     info->ny = h->ny;
     info->pitch = h->pitch;
     info->nclasses = h->ncls;
+    info->nz = h->nz;
     info->dtype = h->opts.dtype;
     info->kernel = h->cfg.kernel;
     info->block_x = h->cfg.bx;
@@ -769,7 +948,8 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
     info->tau = h->tau;
     info->eps0 = h->opts.eps0;
     info->scale = h->opts.scale;
-    info->bytes_per_node = (size_t)2 * h->ncls * storage_bytes(h->opts.dtype) + (h->forced ? 2 * compute_bytes(h->opts.dtype) : 0);
+    info->bytes_per_node = (size_t)2 * h->ncls * storage_bytes(h->opts.dtype) +
+                           (h->forced ? (h->d3 ? 3 : 2) * compute_bytes(h->opts.dtype) : 0);
     info->device_bytes = h->device_bytes;
     info->populations = h->q[h->cur];
     return RLBM_OK;
@@ -788,7 +968,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     LaunchCfg best = h->cfg;
     for (const LaunchCfg &c : kCandidates) {
         if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
-        if ((h->opts.cfl != 1.0 || h->ring) && c.kernel != RLBM_KERNEL_GATHER) continue;
+        if ((h->opts.cfl != 1.0 || h->ring || h->d3) && c.kernel != RLBM_KERNEL_GATHER) continue;
         if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) continue;
         // the trial steps read the current state and overwrite only the spare buffer
         bool ok = true;

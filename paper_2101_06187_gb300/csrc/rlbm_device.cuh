@@ -94,7 +94,9 @@ __device__ __forceinline__ TS to_storage(TC x) {
 // ---------------------------------------------------------------- parameters
 struct StepParams {
     int nx, ny, pitch;
-    long long plane;  // elements per class plane = ny * pitch
+    long long plane;  // elements per class plane = nz * ny * pitch
+    int nz;           // layers (1 for the one-layer lattice)
+    long long slab;   // elements per z layer = ny * pitch
     double inv_tau;   // 1/tau (Delta t = 1)
     double eps0;      // reference energy density of the deviation
     double scale;     // s

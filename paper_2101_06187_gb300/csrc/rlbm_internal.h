@@ -55,6 +55,30 @@ cudaError_t tma_encode_force(CUtensorMap *map, const void *F, const StepParams &
 cudaError_t launch_step_tma(const LaunchCfg &cfg, bool forced, const CUtensorMap &mq, const CUtensorMap &mf,
                             const void *qin, void *qout, const StepParams &p, cudaStream_t s);
 
+// The three-dimensional lattice (k_lattice3d.cu).
+cudaError_t launch_step3(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
+                         const void *F, const StepParams &p, cudaStream_t s);
+long long moments3_blocks(const StepParams &p);
+cudaError_t launch_moments3(int dtype, const void *qin, const StepParams &p, double *eps, double *vx, double *vy,
+                            double *vz, double *partials, int *bad, cudaStream_t s);
+cudaError_t launch_reduce_partials4(const double *partials, long long nblocks, double base_E, double *totals,
+                                    cudaStream_t s);
+cudaError_t launch_init3(int dtype, void *q, const StepParams &p, const double *eps, const double *vx,
+                         const double *vy, const double *vz, cudaStream_t s);
+cudaError_t launch_check_fields3(const double *eps, const double *vx, const double *vy, const double *vz, long long n,
+                                 int *bad, cudaStream_t s);
+size_t mode3_bytes();
+size_t coef3_bytes(int dtype);
+void host_mode3(void *dst, int i, int kx, int ky, int kz);
+cudaError_t launch_draw_modes3(int dtype, const void *modes, void *coef, int nmodes, double amp,
+                               unsigned long long seed, unsigned long long epoch, cudaStream_t s);
+cudaError_t launch_mode_tables3(int dtype, void *T, const void *modes, int nmodes, const void *tw, int n, int axis,
+                                cudaStream_t s);
+cudaError_t launch_synth_force3(int dtype, void *F, const void *coef, int nmodes, const void *X, const void *Y,
+                                const void *Z, const StepParams &p, cudaStream_t s);
+double class_weight3(int k);
+void class_vector3(int k, double *c);
+
 // The 2D ring variant (k_ring.cu).
 cudaError_t launch_ring_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                              const void *F, const StepParams &p, cudaStream_t s);
@@ -105,10 +129,16 @@ struct rlbm {
     int ncls = rlbk::NC;  // stored classes: 17 (spherical node) or 8 (2D ring)
     bool ring = false;
     // tensor maps of the two state buffers and of the force (TMA kernel)
-    alignas(64) CUtensorMap tm_q[2];
-    alignas(64) CUtensorMap tm_F;
+    CUtensorMap tm_q[2];
+    CUtensorMap tm_F;
     bool tm_ready = false;
     int *errword = nullptr;  // device error word of the bounded waits
+    // three-dimensional lattice: nz layers, 26 stored directions, 3 force
+    // components, mode table of integer 3-vectors, z phase tables
+    bool d3 = false;
+    int nz = 1;
+    void *modes3 = nullptr;
+    void *twz = nullptr, *tabz = nullptr;
     rlbk::LaunchCfg cfg;
     bool tuned = false;
     cudaStream_t stream = nullptr;

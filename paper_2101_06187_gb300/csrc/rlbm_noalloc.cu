@@ -59,6 +59,8 @@ extern "C" RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, 
     p.ny = ny;
     p.pitch = pitch;
     p.plane = (long long)ny * pitch;
+    p.slab = p.plane;
+    p.nz = 1;
     p.inv_tau = 1.0;  // unused by the moments kernel
     p.eps0 = eps0;
     p.scale = scale;

@@ -1,0 +1,257 @@
+"""Parity of the three-dimensional lattice of the CUDA path (rlbm_create3d,
+26 stored directions, trilinear streaming, 3D stirring) with the FP64 3D
+oracle, through the C ABI.
+
+Error measures as for the one-layer lattice: normwise relative error of eps
+(against its deviation from 1) and of the velocity after forced runs from
+seeded smooth fields, on ragged lattices that span several thread blocks
+and on the 4^3 minimum; decoded populations against the oracle's (direction
+order mapped through the documented device order); conservation; the rest
+state; the force field; the equivalence of a z-uniform 3D run with the
+library's one-layer run; and, at a size the oracle cannot run, a lattice
+built from a periodic tile that must stay an exact tiling of the oracle's
+run of that tile.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2101_06187_gb300 as rl  # noqa: E402
+
+oracle.set_threads(os.cpu_count() or 4)
+L = oracle.lattice3d
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 5e-2, "f16": 1e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def device_directions():
+    """The documented device order: faces, edges, corners, then opposites."""
+    a, b = 1 / np.sqrt(2), 1 / np.sqrt(3)
+    first = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (a, a, 0), (a, -a, 0), (a, 0, a), (a, 0, -a), (0, a, a), (0, a, -a),
+             (b, b, b), (b, b, -b), (b, -b, b), (b, -b, -b)]
+    v = np.array(first + [tuple(-c for c in d) for d in first], dtype=float)
+    return v
+
+
+def oracle_to_device():
+    """perm[k] = oracle direction index of device direction k."""
+    vo, _ = oracle.stencil()
+    vd = device_directions()
+    perm = [int(np.argmin(np.linalg.norm(vo - d, axis=1))) for d in vd]
+    assert sorted(perm) == list(range(26))
+    assert np.allclose(vo[perm], vd, atol=1e-15)
+    return perm
+
+
+def smooth3(nx, ny, nz, seed, deps=0.05, vmax=0.05):
+    return workloads.random_smooth3d(nx, ny, nz, seed=seed, deps=deps, vmax=vmax)
+
+
+def device_weights():
+    w = np.array([1 / 21] * 3 + [4 / 105] * 6 + [9 / 280] * 4)
+    return np.concatenate([w, w])
+
+
+def rel_errors(ref, got):
+    e_r, *v_r = ref
+    e_g, *v_g = got[:4]
+    err_e = np.max(np.abs(e_g - e_r)) / max(np.max(np.abs(e_r - 1.0)), 1e-300)
+    vnorm = max(np.max(np.abs(v)) for v in v_r)
+    err_v = max(np.max(np.abs(g - r)) for g, r in zip(v_g, v_r)) / vnorm
+    return err_e, err_v
+
+
+def oracle_run(shape, tau, nsteps, fields, forcing):
+    nx, ny, nz = shape
+    f = L.init(nx, ny, nz, *fields)
+    if forcing:
+        L.run(f, tau, nsteps, kmin=forcing["kmin"], kmax=forcing["kmax"], amp=forcing["amp"], seed=forcing["seed"],
+              redraw=forcing["redraw_period"])
+    else:
+        L.run(f, tau, nsteps)
+    return f
+
+
+FORCING_SMALL = dict(kmin=1, kmax=2, amp=5e-4, seed=987654321, redraw_period=7)
+
+
+@pytest.mark.parametrize("dtype,landau", [("f64", "fp64"), ("f32", "fp64"), ("f32", "fp32")])
+@pytest.mark.parametrize("shape", [(20, 12, 10), (37, 9, 6), (4, 4, 4)])
+def test_forced_3d_run_matches_oracle(dtype, landau, shape):
+    nx, ny, nz = shape
+    forcing = FORCING_SMALL if min(shape) > 4 else dict(kmin=1, kmax=1, amp=2e-3, seed=5, redraw_period=3)
+    fields = smooth3(nx, ny, nz, seed=nx * 100 + ny + nz)
+    lat = rl.Lattice3D(nx, ny, nz, 0.7, dtype=dtype, landau=landau, forcing=forcing)
+    info = lat.info()
+    assert info["nclasses"] == 26 and info["nz"] == nz
+    lat.init_fields(*fields)
+    lat.step(30)
+    got = lat.moments()
+    f = oracle_run(shape, 0.7, 30, fields, forcing)
+    err_e, err_v = rel_errors(L.fields(f), got)
+    assert err_e < TOL[dtype] and err_v < TOL[dtype], (err_e, err_v)
+    pops = lat.populations()
+    ref = f[oracle_to_device()]
+    dev = np.max(np.abs(ref - device_weights()[:, None, None, None]))
+    np.testing.assert_allclose(pops, ref, rtol=0, atol=TOL[dtype] * dev)
+    lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_16bit_3d_storage_tracks_oracle(dtype):
+    shape = (16, 12, 8)
+    fields = smooth3(*shape, seed=31)
+    lat = rl.Lattice3D(*shape, 0.7, dtype=dtype, forcing=FORCING_SMALL)
+    lat.init_fields(*fields)
+    lat.step(20)
+    got = lat.moments()
+    f = oracle_run(shape, 0.7, 20, fields, FORCING_SMALL)
+    err_e, err_v = rel_errors(L.fields(f), got)
+    assert err_e < TOL[dtype] and err_v < TOL[dtype], (err_e, err_v)
+    lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_unforced_3d_totals_conserved(dtype):
+    shape = (12, 10, 8)
+    fields = smooth3(*shape, seed=3, deps=0.1, vmax=0.1)
+    lat = rl.Lattice3D(*shape, 0.6, dtype=dtype)
+    lat.init_fields(*fields)
+    t0 = lat.moments()[4]
+    lat.step(100)
+    t1 = lat.moments()[4]
+    tref = L.totals(L.init(*shape, *fields))
+    tol = 1e-13 if dtype == "f64" else 1e-6
+    np.testing.assert_allclose(t0, tref, rtol=0, atol=tol * tref[0])
+    np.testing.assert_allclose(t1, t0, rtol=0, atol=tol * t0[0])
+    lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
+def test_rest_state_is_3d_fixed_point(dtype):
+    lat = rl.Lattice3D(12, 8, 6, 0.52, dtype=dtype)
+    lat.init_fields()
+    lat.step(200)
+    e, vx, vy, vz, _ = lat.moments()
+    tol = 1e-14 if dtype == "f64" else 1e-7
+    assert np.max(np.abs(e - 1.0)) < tol and max(np.max(np.abs(v)) for v in (vx, vy, vz)) < tol
+    lat.close()
+
+
+def test_z_uniform_3d_run_is_the_one_layer_run():
+    nx, ny, nz = 48, 40, 5
+    e, a, b = workloads.random_smooth(nx, ny, seed=8, deps=0.05, vmax=0.05)
+    tile = lambda g: np.repeat(g[None], nz, axis=0)
+    lat3 = rl.Lattice3D(nx, ny, nz, 0.7, dtype="f64")
+    lat3.init_fields(tile(e), tile(a), tile(b), None)
+    lat3.step(40)
+    E3, VX3, VY3, VZ3, _ = lat3.moments()
+    lat2 = rl.Lattice(nx, ny, 0.7, dtype="f64", kernel="gather")
+    lat2.init_fields(e, a, b)
+    lat2.step(40)
+    E2, VX2, VY2, _ = lat2.moments()
+    for z in range(nz):
+        np.testing.assert_allclose(E3[z], E2, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(VX3[z], VX2, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(VY3[z], VY2, rtol=0, atol=1e-14)
+    assert np.max(np.abs(VZ3)) < 1e-15
+    lat3.close()
+    lat2.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_3d_force_field_matches_oracle(dtype):
+    nx, ny, nz = 24, 20, 16
+    fz = dict(kmin=2, kmax=4, amp=1e-3, seed=2024, redraw_period=10)
+    lat = rl.Lattice3D(nx, ny, nz, 0.7, dtype=dtype, forcing=fz)
+    tol = 1e-13 if dtype == "f64" else 2e-6
+    for epoch in (0, 3):
+        lat.init_fields()
+        if epoch:
+            lat.step(epoch * fz["redraw_period"])
+        got = lat.force()
+        ref = L.force_field(nx, ny, nz, 2, 4, 1e-3, 2024, epoch)
+        scale = max(np.max(np.abs(r)) for r in ref)
+        for g, r in zip(got, ref):
+            assert np.max(np.abs(g - r)) < tol * scale
+    lat.close()
+
+
+def test_3d_graph_and_direct_launches_agree_bitwise():
+    shape = (16, 12, 8)
+    fields = smooth3(*shape, seed=11)
+    out = []
+    for graphs in (True, False):
+        lat = rl.Lattice3D(*shape, 0.7, dtype="f32", forcing=FORCING_SMALL, use_graphs=graphs)
+        lat.init_fields(*fields)
+        for n in (1, 6, 13, 2):
+            lat.step(n)
+        out.append(lat.populations())
+        lat.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_3d_set_populations_round_trip():
+    shape = (10, 8, 6)
+    f = L.init(*shape, *smooth3(*shape, seed=5))
+    perm = oracle_to_device()
+    lat = rl.Lattice3D(*shape, 0.7, dtype="f64")
+    lat.set_populations(f[perm])
+    np.testing.assert_allclose(lat.populations(), f[perm], rtol=0, atol=1e-16)
+    lat.step(10)
+    ref = f.copy()
+    L.run(ref, 0.7, 10)
+    dev = np.max(np.abs(ref[perm] - device_weights()[:, None, None, None]))
+    np.testing.assert_allclose(lat.populations(), ref[perm], rtol=0, atol=1e-12 * dev)
+    lat.close()
+
+
+def test_3d_rejects_what_it_does_not_run():
+    for kw in (dict(kernel="vec"), dict(kernel="packed"), dict(kernel="tma"), dict(cfl=0.5)):
+        with pytest.raises(rl.RLBMError):
+            rl.Lattice3D(16, 16, 16, 0.7, **kw)
+    with pytest.raises(rl.RLBMError):
+        rl.Lattice3D(16, 16, 3, 0.7)
+    with pytest.raises(rl.RLBMError):  # 2 kmax must stay below nz
+        rl.Lattice3D(32, 32, 8, 0.7, forcing=dict(kmin=2, kmax=4, amp=1e-3, seed=1, redraw_period=10))
+    lat = rl.Lattice3D(8, 8, 8, 0.7)
+    with pytest.raises(rl.RLBMError):
+        rl.rlbm_init_fields(lat.handle)  # the 2D call on a 3D handle
+    lat.close()
+
+
+@pytest.mark.parametrize("n,dtype", [(128, "f32"), (96, "f64")])
+def test_full_size_3d_lattice_stays_an_exact_tiling(n, dtype):
+    period, tau, nsteps = 16, 0.55, 12
+    fields = smooth3(period, period, period, seed=77, deps=0.02, vmax=0.02)
+    f = L.init(period, period, period, *fields)
+    L.run(f, tau, nsteps)
+    ref = L.fields(f)
+    rep = n // period
+    big = [np.tile(a, (rep, rep, rep)) for a in fields]
+    lat = rl.Lattice3D(n, n, n, tau, dtype=dtype)
+    lat.autotune(3)
+    lat.init_fields(*big)
+    lat.step(nsteps)
+    got = lat.moments()
+    lat.close()
+    tiled = [np.tile(r, (rep, rep, rep)) for r in ref]
+    err_e, err_v = rel_errors(tiled, got)
+    tol = 1e-5 if dtype == "f32" else 1e-12
+    assert err_e < tol and err_v < tol, (err_e, err_v)

@@ -93,6 +93,28 @@ def random_smooth(nx: int, ny: int, seed: int, deps: float = 0.05, vmax: float =
     return eps, vx, vy
 
 
+def random_smooth3d(nx: int, ny: int, nz: int, seed: int, deps: float = 0.05, vmax: float = 0.05,
+                    nmodes: int = 4):
+    """Seeded smooth periodic fields on an nx x ny x nz lattice ([z][y][x]):
+    eps = 1 + deps * (a few low 3D Fourier modes) and three velocity
+    components of comparable smoothness, |v| up to about vmax."""
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+
+    def field_():
+        out = np.zeros((nz, ny, nx))
+        for _ in range(nmodes):
+            kx, ky, kz = (int(rng.integers(-2, 3)) for _ in range(3))
+            ph = rng.uniform(0, 2 * np.pi)
+            a = rng.uniform(-1, 1)
+            out += a * np.cos(2 * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz) + ph)
+        return out / nmodes
+
+    eps = 1.0 + deps * field_()
+    return eps, vmax * field_(), vmax * field_(), vmax * field_()
+
+
 def random_tiled(nx: int, ny: int, period: int, seed: int, deps: float = 0.05, vmax: float = 0.05):
     """Fields periodic with a small period (period | nx, ny): the tile of
     `random_smooth(period, period)` repeated over the lattice.  A large
