@@ -286,12 +286,16 @@ RLBM_API rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info);
  *   k = 0..2 faces (1,0,0), (0,1,0), (0,0,1); 3..8 edges (a,a,0), (a,-a,0),
  *   (a,0,a), (a,0,-a), (0,a,a), (0,a,-a); 9..12 corners (b,b,b), (b,b,-b),
  *   (b,-b,b), (b,-b,-b); k + 13 the opposite of k; a = 1/sqrt2, b = 1/sqrt3.
- * A 3D handle runs the one-node-per-thread kernel (kernel AUTO or GATHER)
- * at cfl 1 (eta_s allowed), in every storage form; rlbm_step,
+ * A 3D handle runs the one-node-per-thread kernel (GATHER, every storage
+ * form) or the packed-lane kernel (PACKED: FP32 compute with
+ * RLBM_LANDAU_FP32, nx even) at cfl 1 (eta_s allowed); rlbm_step,
  * rlbm_get/set_populations, rlbm_get_info, rlbm_autotune, rlbm_synchronize,
- * rlbm_last_error and rlbm_destroy apply to it, as does
- * rlbm_init_fields_device (v_z = 0); the other 2D calls return
- * RLBM_ERR_STATE.  Errors as rlbm_create; nz >= 4, nx*ny*nz <= 2^31,
+ * rlbm_last_error and rlbm_destroy apply to it, as do
+ * rlbm_init_fields_device (v_z = 0) and the spectrum calls
+ * (rlbm_energy_spectrum, rlbm_filtered_velocity, rlbm_spectrum_*), which
+ * then bin |k| = (kx^2 + ky^2 + kz^2)^{1/2} over the three velocity
+ * components; rlbm_init_fields, rlbm_moments[_device] and rlbm_get_force
+ * return RLBM_ERR_STATE.  Errors as rlbm_create; nz >= 4, nx*ny*nz <= 2^31,
  * 2 kmax < min(nx, ny, nz). */
 RLBM_API rlbm_status rlbm_create3d(int nx, int ny, int nz, double tau, const rlbm_forcing *forcing,
                                    const rlbm_opts *opts, rlbm_t **out);

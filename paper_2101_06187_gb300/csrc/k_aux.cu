@@ -505,4 +505,108 @@ cudaError_t launch_spectrum(const double *vx, const double *vy, int nx, int ny, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- 3D spectra
+// The three velocity components as two complex fields Z1 = vx + i vy and
+// Z2 = vz, each transformed along x, y and z; over a shell (symmetric under
+// k -> -k) the sum of |Z1|^2 + |Z2|^2 is the sum of |v_hat_x|^2 + |v_hat_y|^2
+// + |v_hat_z|^2, times vol^2.
+__global__ void k_pack_z3(const double *vx, const double *vy, const double *vz, Z2 *z1, Z2 *z2, long long count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        z1[i] = {vx[i], vy[i]};
+        z2[i] = {vz[i], 0.0};
+    }
+}
+
+__device__ __forceinline__ double signed_k(int j, int n) { return (j < (n + 1) / 2) ? j : j - n; }
+
+__global__ void k_shell_bin3(const Z2 *z1, const Z2 *z2, int nx, int ny, int nz, int nshells, double *Ek) {
+    extern __shared__ double hist[];
+    for (int i = threadIdx.x; i < nshells; i += blockDim.x) hist[i] = 0.0;
+    __syncthreads();
+    const long long count = (long long)nx * ny * nz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int jx = (int)(i % nx), jy = (int)((i / nx) % ny), jz = (int)(i / ((long long)nx * ny));
+        const double kx = signed_k(jx, nx), ky = signed_k(jy, ny), kz = signed_k(jz, nz);
+        const int sh = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);
+        if (sh < nshells)
+            atomicAdd(&hist[sh], z1[i].re * z1[i].re + z1[i].im * z1[i].im + z2[i].re * z2[i].re + z2[i].im * z2[i].im);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nshells; i += blockDim.x)
+        if (hist[i] != 0.0) atomicAdd(&Ek[i], hist[i]);
+}
+
+__global__ void k_band_sum3(const Z2 *z1, const Z2 *z2, int nx, int ny, int nz, double kf, double *out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    const long long count = (long long)nx * ny * nz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int jx = (int)(i % nx), jy = (int)((i / nx) % ny), jz = (int)(i / ((long long)nx * ny));
+        const double kx = signed_k(jx, nx), ky = signed_k(jy, ny), kz = signed_k(jz, nz);
+        if (kx * kx + ky * ky + kz * kz < kf * kf)
+            acc += z1[i].re * z1[i].re + z1[i].im * z1[i].im + z2[i].re * z2[i].re + z2[i].im * z2[i].im;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+size_t spectrum_work_doubles3(int nx, int ny, int nz) {
+    return 2 * (2 * (size_t)nx * ny * nz + (size_t)nx + (size_t)ny + (size_t)nz);
+}
+
+static cudaError_t transform_3d_one(Z2 *z, int nx, int ny, int nz, Z2 *w, cudaStream_t s) {
+    const long long slab = (long long)nx * ny;
+    cudaError_t e = transform_lines(z, nx, ny * nz, 1, nx, w, s);  // x lines
+    for (int k = 0; k < nz && e == cudaSuccess; ++k)                  // y lines, slab by slab
+        e = transform_lines(z + k * slab, ny, nx, nx, 1, w + nx, s);
+    if (e == cudaSuccess) e = transform_lines(z, nz, (int)slab, slab, 1, w + nx + ny, s);  // z lines
+    return e;
+}
+
+static cudaError_t transform_3d(const double *vx, const double *vy, const double *vz, int nx, int ny, int nz,
+                                double *work, cudaStream_t s) {
+    const long long count = (long long)nx * ny * nz;
+    Z2 *z1 = reinterpret_cast<Z2 *>(work);
+    Z2 *z2 = z1 + count;
+    Z2 *w = z2 + count;
+    k_pack_z3<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(vx, vy, vz, z1, z2, count);
+    cudaError_t e = transform_3d_one(z1, nx, ny, nz, w, s);
+    if (e == cudaSuccess) e = transform_3d_one(z2, nx, ny, nz, w, s);
+    return e;
+}
+
+cudaError_t launch_spectrum3(const double *vx, const double *vy, const double *vz, int nx, int ny, int nz, int nshells,
+                             double *work, double *Ek, cudaStream_t s) {
+    const long long count = (long long)nx * ny * nz;
+    cudaError_t e = transform_3d(vx, vy, vz, nx, ny, nz, work, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(Ek, 0, sizeof(double) * nshells, s);
+    if (e != cudaSuccess) return e;
+    const Z2 *z1 = reinterpret_cast<const Z2 *>(work);
+    k_shell_bin3<<<304, 256, sizeof(double) * nshells, s>>>(z1, z1 + count, nx, ny, nz, nshells, Ek);
+    k_scale<<<(nshells + 255) / 256, 256, 0, s>>>(Ek, nshells, 0.5 / ((double)count * (double)count));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_power3(const double *vx, const double *vy, const double *vz, int nx, int ny, int nz, double kf,
+                               double *work, double *out, cudaStream_t s) {
+    const long long count = (long long)nx * ny * nz;
+    cudaError_t e = transform_3d(vx, vy, vz, nx, ny, nz, work, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const Z2 *z1 = reinterpret_cast<const Z2 *>(work);
+    k_band_sum3<<<304, 256, 0, s>>>(z1, z1 + count, nx, ny, nz, kf, out);
+    k_scale<<<1, 32, 0, s>>>(out, 1, 1.0 / ((double)count * (double)count));
+    return cudaGetLastError();
+}
+
 }  // namespace rlbk

@@ -55,28 +55,49 @@ __global__ void k_check_fields3(const double *eps, const double *vx, const doubl
         else CALL(__half, float, double);                                        \
     }
 
+template <typename TS, typename TC, typename TL>
+static cudaError_t launch_step3_t(const LaunchCfg &cfg, bool forced, const void *qin, void *qout, const void *F,
+                                  const StepParams &p, cudaStream_t s) {
+    const dim3 block(cfg.bx, cfg.by, 1);
+    const bool idx32 = (long long)N3 * p.plane < (1ll << 31) - 1;
+    const TS *in = static_cast<const TS *>(qin);
+    TS *out = static_cast<TS *>(qout);
+    const TC *f = static_cast<const TC *>(F);
+    if (cfg.kernel == RLBM_KERNEL_PACKED) {
+        if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
+            if (p.nx % 2 != 0) return cudaErrorInvalidValue;
+            const dim3 g2((p.nx / 2 + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, p.nz);
+            if (idx32) {
+                if (forced) k_step3_pair<TS, true, int><<<g2, block, 0, s>>>(in, out, f, p);
+                else k_step3_pair<TS, false, int><<<g2, block, 0, s>>>(in, out, f, p);
+            } else {
+                if (forced) k_step3_pair<TS, true, long long><<<g2, block, 0, s>>>(in, out, f, p);
+                else k_step3_pair<TS, false, long long><<<g2, block, 0, s>>>(in, out, f, p);
+            }
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;  // packed lanes: FP32 compute with the FP32 Landau solve
+        }
+    }
+    const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, p.nz);
+    if (idx32) {
+        if (forced) k_step3<TS, TC, TL, true, int><<<grid, block, 0, s>>>(in, out, f, p);
+        else k_step3<TS, TC, TL, false, int><<<grid, block, 0, s>>>(in, out, f, p);
+    } else {
+        if (forced) k_step3<TS, TC, TL, true, long long><<<grid, block, 0, s>>>(in, out, f, p);
+        else k_step3<TS, TC, TL, false, long long><<<grid, block, 0, s>>>(in, out, f, p);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step3(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                          const void *F, const StepParams &p, cudaStream_t s) {
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256 || p.nz > 65535) return cudaErrorInvalidConfiguration;
-    const dim3 block(cfg.bx, cfg.by, 1);
-    const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, p.nz);
-    const bool idx32 = (long long)N3 * p.plane < (1ll << 31) - 1;
-#define RLBM3_STEP(TS, TC, TL)                                                                                   \
-    do {                                                                                                         \
-        const TS *in = static_cast<const TS *>(qin);                                                             \
-        TS *out = static_cast<TS *>(qout);                                                                       \
-        const TC *f = static_cast<const TC *>(F);                                                                \
-        if (idx32) {                                                                                             \
-            if (forced) k_step3<TS, TC, TL, true, int><<<grid, block, 0, s>>>(in, out, f, p);                    \
-            else k_step3<TS, TC, TL, false, int><<<grid, block, 0, s>>>(in, out, f, p);                          \
-        } else {                                                                                                 \
-            if (forced) k_step3<TS, TC, TL, true, long long><<<grid, block, 0, s>>>(in, out, f, p);              \
-            else k_step3<TS, TC, TL, false, long long><<<grid, block, 0, s>>>(in, out, f, p);                    \
-        }                                                                                                        \
-    } while (0)
+    cudaError_t e = cudaSuccess;
+#define RLBM3_STEP(TS, TC, TL) e = launch_step3_t<TS, TC, TL>(cfg, forced, qin, qout, F, p, s)
     RLBM3_FORMS(dtype, landau, RLBM3_STEP)
 #undef RLBM3_STEP
-    return cudaGetLastError();
+    return e;
 }
 
 static dim3 block3() { return dim3(32, 8, 1); }

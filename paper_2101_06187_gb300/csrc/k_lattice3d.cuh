@@ -17,6 +17,8 @@
 #pragma once
 
 #include "forcing.cuh"
+#include "k_step_vec.cuh"
+#include "packed.cuh"
 #include "rlbm_device.cuh"
 
 namespace rlbk {
@@ -333,6 +335,72 @@ __global__ void __launch_bounds__(256) k_step3(const TS *__restrict__ qin, TS *_
     static_for<0, N3>([&](auto K) {
         constexpr int k = decltype(K)::value;
         qout[(I)k * (I)p.plane + n] = to_storage<TS, TC>(q[k]);
+    });
+}
+
+// Packed-lane form of k_step3: two x-adjacent nodes per thread whose whole
+// arithmetic runs in pairs of FP32 lanes (packed.cuh), one instruction per
+// operation for both nodes.  Each source row of a direction is read once
+// for the pair: columns x0-1 .. x0+2 as the direction's x corner needs.
+template <int ox, bool TXNZ, typename TS, typename I>
+__device__ __forceinline__ void load_row_pair(const TS *__restrict__ row, int x0, int xl, int xr, float (&a)[4]) {
+    load_run<TS, float, 2>(row + x0, &a[1]);
+    if constexpr (ox == -1) a[0] = load_q<TS, float>(row + xl);
+    if constexpr (ox == 1 || (ox == 0 && TXNZ)) a[3] = load_q<TS, float>(row + xr);
+}
+
+template <int k, typename TS, typename I>
+__device__ __forceinline__ pf2 gather3_pair(const TS *__restrict__ qin, I base, const I (&zoff)[3], const I (&yoff)[3],
+                                            int x0, int xl, int xr) {
+    constexpr int ox = d3o(k, 0), oy = d3o(k, 1), oz = d3o(k, 2);
+    constexpr double tx = d3t(k, 0), ty = d3t(k, 1), tz = d3t(k, 2);
+    pf2 v = 0.0f;
+    static_for<0, 4>([&](auto D) {
+        constexpr int d = decltype(D)::value;
+        constexpr int dy = d & 1, dz = (d >> 1) & 1;
+        constexpr double wyz = (dy ? ty : 1.0 - ty) * (dz ? tz : 1.0 - tz);
+        if constexpr (wyz != 0.0) {
+            float a[4];
+            load_row_pair<ox, tx != 0.0, TS, I>(qin + (base + zoff[oz + 1 + dz] + yoff[oy + 1 + dy]), x0, xl, xr, a);
+            v = fmadd(pf2((float)(wyz * (1.0 - tx))), pf2(a[ox + 1], a[ox + 2]), v);
+            if constexpr (tx != 0.0) v = fmadd(pf2((float)(wyz * tx)), pf2(a[ox + 2], a[ox + 3]), v);
+        }
+    });
+    return v;
+}
+
+template <typename TS, bool FORCED, typename I>
+__global__ void __launch_bounds__(256) k_step3_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                                    const float *__restrict__ F, StepParams p) {
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x0 >= p.nx || y >= p.ny) return;
+    const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+    const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+    const int xl = x0 == 0 ? p.nx - 1 : x0 - 1, xr = x0 + 2 == p.nx ? 0 : x0 + 2;
+    const I zoff[3] = {(I)zm * (I)p.slab, (I)z * (I)p.slab, (I)zp * (I)p.slab};
+    const I yoff[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
+    pf2 q[N3];
+    static_for<0, N3>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        q[k] = gather3_pair<k, TS, I>(qin, (I)k * (I)p.plane, zoff, yoff, x0, xl, xr);
+    });
+    const I n0 = zoff[1] + yoff[1] + (I)x0;
+    pf2 Fv[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (FORCED) {
+        static_for<0, 3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            float f2[2];
+            load_run<float, float, 2>(F + ((I)a * (I)p.plane + n0), f2);
+            Fv[a] = pf2(f2[0], f2[1]);
+        });
+    }
+    collide3<pf2, pf2, FORCED>(q, Fv, p);
+    static_for<0, N3>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        const float out[2] = {q[k].v.x, q[k].v.y};
+        store_run<TS, float, 2>(qout + ((I)k * (I)p.plane + n0), out);
     });
 }
 

@@ -254,10 +254,15 @@ static rlbm_status run_chunk(rlbm_t *h, int n) {
 
 // The spectrum work area (complex lattice + twiddles + shell sums), made on
 // first use.
+static size_t spectrum_doubles(const rlbm_t *h) {
+    return h->d3 ? spectrum_work_doubles3(h->nx, h->ny, h->nz) : spectrum_work_doubles(h->nx, h->ny);
+}
+
 static rlbm_status ensure_spectrum_work(rlbm_t *h) {
-    if (std::max(h->nx, h->ny) > 8192) return fail(h, RLBM_ERR_ARG, "spectra support lattice sides up to 8192");
+    if (std::max(std::max(h->nx, h->ny), h->nz) > 8192)
+        return fail(h, RLBM_ERR_ARG, "spectra support lattice sides up to 8192");
     if (!h->spec_work) {
-        const size_t need = spectrum_work_doubles(h->nx, h->ny) * sizeof(double) + 4096 * sizeof(double);
+        const size_t need = spectrum_doubles(h) * sizeof(double) + 4096 * sizeof(double);
         h->spec_work = static_cast<double *>(dev_alloc(h, need));
         if (!h->spec_work) return fail(h, RLBM_ERR_ALLOC, "spectrum work area");
         h->spec_work_bytes = need;
@@ -433,8 +438,10 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
     if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER) || o.cfl != 1.0 || o.eta_s != 0.0))
         return RLBM_ERR_ARG;
-    // the 3D lattice runs the one-node-per-thread kernel at CFL 1
-    if (d3 && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER) || o.cfl != 1.0)) return RLBM_ERR_ARG;
+    // the 3D lattice runs the one-node-per-thread or the packed-lane kernel at CFL 1
+    if (d3 && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER && o.kernel != RLBM_KERNEL_PACKED) ||
+               o.cfl != 1.0))
+        return RLBM_ERR_ARG;
 
     rlbm_forcing fz{};
     bool forced = false;
@@ -748,18 +755,50 @@ rlbm_status rlbm_moments(rlbm_t *h, double *eps, double *vx, double *vy, double 
     return RLBM_OK;
 }
 
+}  // extern "C"
+
+// Velocity components of the state the next collision sees into the fields
+// buffer (vx at n, vy at 2n, vz at 3n for a 3D lattice), on the stream.
+static rlbm_status velocity_to_fields(rlbm_t *h) {
+    const size_t n = nodes_of(h);
+    CUDA_TRY(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+    const StepParams p = params_of(h);
+    if (h->d3)
+        CUDA_TRY(h, launch_moments3(h->opts.dtype, h->q[h->cur], p, nullptr, h->fields + n, h->fields + 2 * n,
+                                    h->fields + 3 * n, h->partials, h->bad, h->stream));
+    else if (h->ring)
+        CUDA_TRY(h, launch_ring_moments(h->opts.dtype, h->q[h->cur], p, nullptr, h->fields + n, h->fields + 2 * n,
+                                        h->partials, h->bad, h->stream));
+    else
+        CUDA_TRY(h, launch_moments(h->opts.dtype, h->opts.landau, h->q[h->cur], p, nullptr, h->fields + n,
+                                   h->fields + 2 * n, h->partials, h->bad, h->stream));
+    return RLBM_OK;
+}
+
+// E(k) of the current velocity into dEk (device, nshells doubles).
+static rlbm_status spectrum_on_device(rlbm_t *h, int nshells, double *dEk) {
+    rlbm_status st = velocity_to_fields(h);
+    if (st != RLBM_OK) return st;
+    const size_t n = nodes_of(h);
+    if (h->d3)
+        CUDA_TRY(h, launch_spectrum3(h->fields + n, h->fields + 2 * n, h->fields + 3 * n, h->nx, h->ny, h->nz, nshells,
+                                     h->spec_work, dEk, h->stream));
+    else
+        CUDA_TRY(h, launch_spectrum(h->fields + n, h->fields + 2 * n, h->nx, h->ny, nshells, h->spec_work, dEk,
+                                    h->stream));
+    return RLBM_OK;
+}
+
+extern "C" {
+
 rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
     CHECK_HANDLE(h);
-    if (h->d3) return fail(h, RLBM_ERR_STATE, "not available for a 3D lattice");
     if (nshells < 1 || nshells > 4096 || !Ek) return fail(h, RLBM_ERR_ARG, "nshells must be in [1, 4096]");
     rlbm_status st0 = ensure_spectrum_work(h);
     if (st0 != RLBM_OK) return st0;
-    const size_t n = (size_t)h->nx * h->ny;
-    rlbm_status st = rlbm_moments_device(h, nullptr, h->fields + n, h->fields + 2 * n, nullptr);
+    double *dEk = h->spec_work + spectrum_doubles(h);
+    rlbm_status st = spectrum_on_device(h, nshells, dEk);
     if (st != RLBM_OK) return st;
-    double *dEk = h->spec_work + spectrum_work_doubles(h->nx, h->ny);
-    CUDA_TRY(h, launch_spectrum(h->fields + n, h->fields + 2 * n, h->nx, h->ny, nshells, h->spec_work, dEk,
-                                h->stream));
     int *bad_host = reinterpret_cast<int *>(h->host_small);
     CUDA_TRY(h, cudaMemcpyAsync(bad_host, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(Ek, dEk, nshells * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -770,15 +809,19 @@ rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
 
 rlbm_status rlbm_filtered_velocity(rlbm_t *h, double kf, double *rms) {
     CHECK_HANDLE(h);
-    if (h->d3) return fail(h, RLBM_ERR_STATE, "not available for a 3D lattice");
     if (!rms || !(kf >= 0.0)) return fail(h, RLBM_ERR_ARG, "kf must be >= 0 and rms non-NULL");
     rlbm_status st = ensure_spectrum_work(h);
     if (st != RLBM_OK) return st;
-    const size_t n = (size_t)h->nx * h->ny;
-    st = rlbm_moments_device(h, nullptr, h->fields + n, h->fields + 2 * n, nullptr);
+    const size_t n = nodes_of(h);
+    st = velocity_to_fields(h);
     if (st != RLBM_OK) return st;
-    double *dout = h->spec_work + spectrum_work_doubles(h->nx, h->ny);
-    CUDA_TRY(h, launch_band_power(h->fields + n, h->fields + 2 * n, h->nx, h->ny, kf, h->spec_work, dout, h->stream));
+    double *dout = h->spec_work + spectrum_doubles(h);
+    if (h->d3)
+        CUDA_TRY(h, launch_band_power3(h->fields + n, h->fields + 2 * n, h->fields + 3 * n, h->nx, h->ny, h->nz, kf,
+                                       h->spec_work, dout, h->stream));
+    else
+        CUDA_TRY(h, launch_band_power(h->fields + n, h->fields + 2 * n, h->nx, h->ny, kf, h->spec_work, dout,
+                                      h->stream));
     double *host = h->host_small + 16;
     int *bad_host = reinterpret_cast<int *>(h->host_small);
     CUDA_TRY(h, cudaMemcpyAsync(host, dout, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -799,7 +842,6 @@ rlbm_status rlbm_spectrum_reset(rlbm_t *h) {
 
 rlbm_status rlbm_spectrum_sample(rlbm_t *h, int nshells) {
     CHECK_HANDLE(h);
-    if (h->d3) return fail(h, RLBM_ERR_STATE, "not available for a 3D lattice");
     if (nshells < 1 || nshells > 4096) return fail(h, RLBM_ERR_ARG, "nshells must be in [1, 4096]");
     if (h->spec_count > 0 && nshells != h->spec_nshells)
         return fail(h, RLBM_ERR_STATE, "sampling %d shells into a record of %d (reset first)", nshells,
@@ -811,12 +853,9 @@ rlbm_status rlbm_spectrum_sample(rlbm_t *h, int nshells) {
         if (!h->spec_acc) return fail(h, RLBM_ERR_ALLOC, "spectrum accumulators");
         CUDA_TRY(h, cudaMemsetAsync(h->spec_acc, 0, 2 * 4096 * sizeof(double), h->stream));
     }
-    const size_t n = (size_t)h->nx * h->ny;
-    st = rlbm_moments_device(h, nullptr, h->fields + n, h->fields + 2 * n, nullptr);
+    double *dEk = h->spec_work + spectrum_doubles(h);
+    st = spectrum_on_device(h, nshells, dEk);
     if (st != RLBM_OK) return st;
-    double *dEk = h->spec_work + spectrum_work_doubles(h->nx, h->ny);
-    CUDA_TRY(h, launch_spectrum(h->fields + n, h->fields + 2 * n, h->nx, h->ny, nshells, h->spec_work, dEk,
-                                h->stream));
     CUDA_TRY(h, launch_accumulate(dEk, nshells, h->spec_acc, h->spec_acc + 4096, h->stream));
     h->spec_count += 1;
     h->spec_nshells = nshells;
@@ -968,7 +1007,8 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     LaunchCfg best = h->cfg;
     for (const LaunchCfg &c : kCandidates) {
         if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
-        if ((h->opts.cfl != 1.0 || h->ring || h->d3) && c.kernel != RLBM_KERNEL_GATHER) continue;
+        if ((h->opts.cfl != 1.0 || h->ring) && c.kernel != RLBM_KERNEL_GATHER) continue;
+        if (h->d3 && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED) continue;
         if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) continue;
         // the trial steps read the current state and overwrite only the spare buffer
         bool ok = true;

@@ -79,6 +79,14 @@ cudaError_t launch_synth_force3(int dtype, void *F, const void *coef, int nmodes
 double class_weight3(int k);
 void class_vector3(int k, double *c);
 
+// Spectra of a 3D lattice (k_aux.cu): work area of spectrum_work_doubles3
+// doubles; Ek[nshells] and the band power on the device.
+size_t spectrum_work_doubles3(int nx, int ny, int nz);
+cudaError_t launch_spectrum3(const double *vx, const double *vy, const double *vz, int nx, int ny, int nz, int nshells,
+                             double *work, double *Ek, cudaStream_t s);
+cudaError_t launch_band_power3(const double *vx, const double *vy, const double *vz, int nx, int ny, int nz, double kf,
+                               double *work, double *out, cudaStream_t s);
+
 // The 2D ring variant (k_ring.cu).
 cudaError_t launch_ring_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                              const void *F, const StepParams &p, cudaStream_t s);

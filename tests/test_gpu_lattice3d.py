@@ -91,15 +91,16 @@ def oracle_run(shape, tau, nsteps, fields, forcing):
 FORCING_SMALL = dict(kmin=1, kmax=2, amp=5e-4, seed=987654321, redraw_period=7)
 
 
-@pytest.mark.parametrize("dtype,landau", [("f64", "fp64"), ("f32", "fp64"), ("f32", "fp32")])
-@pytest.mark.parametrize("shape", [(20, 12, 10), (37, 9, 6), (4, 4, 4)])
-def test_forced_3d_run_matches_oracle(dtype, landau, shape):
+@pytest.mark.parametrize("dtype,landau,kernel", [("f64", "fp64", "gather"), ("f32", "fp64", "gather"),
+                                                 ("f32", "fp32", "gather"), ("f32", "fp32", "packed")])
+@pytest.mark.parametrize("shape", [(20, 12, 10), (38, 9, 6), (4, 4, 4)])
+def test_forced_3d_run_matches_oracle(dtype, landau, kernel, shape):
     nx, ny, nz = shape
     forcing = FORCING_SMALL if min(shape) > 4 else dict(kmin=1, kmax=1, amp=2e-3, seed=5, redraw_period=3)
     fields = smooth3(nx, ny, nz, seed=nx * 100 + ny + nz)
-    lat = rl.Lattice3D(nx, ny, nz, 0.7, dtype=dtype, landau=landau, forcing=forcing)
+    lat = rl.Lattice3D(nx, ny, nz, 0.7, dtype=dtype, landau=landau, forcing=forcing, kernel=kernel)
     info = lat.info()
-    assert info["nclasses"] == 26 and info["nz"] == nz
+    assert info["nclasses"] == 26 and info["nz"] == nz and info["kernel"] == rl.KERNELS[kernel]
     lat.init_fields(*fields)
     lat.step(30)
     got = lat.moments()
@@ -114,10 +115,11 @@ def test_forced_3d_run_matches_oracle(dtype, landau, shape):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_16bit_3d_storage_tracks_oracle(dtype):
+@pytest.mark.parametrize("kernel", ["gather", "packed"])
+def test_16bit_3d_storage_tracks_oracle(dtype, kernel):
     shape = (16, 12, 8)
     fields = smooth3(*shape, seed=31)
-    lat = rl.Lattice3D(*shape, 0.7, dtype=dtype, forcing=FORCING_SMALL)
+    lat = rl.Lattice3D(*shape, 0.7, dtype=dtype, forcing=FORCING_SMALL, kernel=kernel)
     lat.init_fields(*fields)
     lat.step(20)
     got = lat.moments()
@@ -145,7 +147,7 @@ def test_unforced_3d_totals_conserved(dtype):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
 def test_rest_state_is_3d_fixed_point(dtype):
-    lat = rl.Lattice3D(12, 8, 6, 0.52, dtype=dtype)
+    lat = rl.Lattice3D(12, 8, 6, 0.52, dtype=dtype, kernel="gather" if dtype == "f64" else "packed")
     lat.init_fields()
     lat.step(200)
     e, vx, vy, vz, _ = lat.moments()
@@ -223,7 +225,8 @@ def test_3d_set_populations_round_trip():
 
 
 def test_3d_rejects_what_it_does_not_run():
-    for kw in (dict(kernel="vec"), dict(kernel="packed"), dict(kernel="tma"), dict(cfl=0.5)):
+    for kw in (dict(kernel="vec"), dict(kernel="tma"), dict(kernel="twopass"), dict(cfl=0.5),
+               dict(kernel="packed", dtype="f64")):
         with pytest.raises(rl.RLBMError):
             rl.Lattice3D(16, 16, 16, 0.7, **kw)
     with pytest.raises(rl.RLBMError):
@@ -236,8 +239,8 @@ def test_3d_rejects_what_it_does_not_run():
     lat.close()
 
 
-@pytest.mark.parametrize("n,dtype", [(128, "f32"), (96, "f64")])
-def test_full_size_3d_lattice_stays_an_exact_tiling(n, dtype):
+@pytest.mark.parametrize("n,dtype,kernel", [(128, "f32", "auto"), (128, "f32", "packed"), (96, "f64", "auto")])
+def test_full_size_3d_lattice_stays_an_exact_tiling(n, dtype, kernel):
     period, tau, nsteps = 16, 0.55, 12
     fields = smooth3(period, period, period, seed=77, deps=0.02, vmax=0.02)
     f = L.init(period, period, period, *fields)
@@ -245,7 +248,7 @@ def test_full_size_3d_lattice_stays_an_exact_tiling(n, dtype):
     ref = L.fields(f)
     rep = n // period
     big = [np.tile(a, (rep, rep, rep)) for a in fields]
-    lat = rl.Lattice3D(n, n, n, tau, dtype=dtype)
+    lat = rl.Lattice3D(n, n, n, tau, dtype=dtype, kernel=kernel)
     lat.autotune(3)
     lat.init_fields(*big)
     lat.step(nsteps)
@@ -255,3 +258,25 @@ def test_full_size_3d_lattice_stays_an_exact_tiling(n, dtype):
     err_e, err_v = rel_errors(tiled, got)
     tol = 1e-5 if dtype == "f32" else 1e-12
     assert err_e < tol and err_v < tol, (err_e, err_v)
+
+
+def test_3d_spectrum_and_filtered_velocity_match_oracle_definitions():
+    """E(k) over 3D shells and the band-filtered RMS velocity of the device
+    calls against numpy's transform of the library's own fields."""
+    shape = (16, 12, 10)
+    fz = dict(kmin=2, kmax=4, amp=5e-4, seed=3, redraw_period=10)
+    lat = rl.Lattice3D(*shape, 0.7, dtype="f64", forcing=fz)
+    lat.init_fields(*smooth3(*shape, seed=9))
+    lat.step(15)
+    e, vx, vy, vz, _ = lat.moments()
+    E = lat.energy_spectrum(9)
+    ref = L.energy_spectrum(vx, vy, vz, 9)
+    np.testing.assert_allclose(E, ref, rtol=1e-10, atol=1e-22)
+    kf = 3.0
+    comps = [np.fft.fftn(a) / a.size for a in (vx, vy, vz)]
+    nz, ny, nx = vx.shape
+    K = np.sqrt(np.fft.fftfreq(nx, 1 / nx)[None, None, :] ** 2 + np.fft.fftfreq(ny, 1 / ny)[None, :, None] ** 2
+                + np.fft.fftfreq(nz, 1 / nz)[:, None, None] ** 2)
+    want = np.sqrt(sum((np.abs(c[K < kf]) ** 2).sum() for c in comps))
+    assert abs(lat.filtered_velocity(kf) - want) < 1e-12 * max(want, 1e-30)
+    lat.close()
