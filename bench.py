@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override lattice side (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-form table, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--stencil", default="sph26", choices=["sph26", "ring8"],
+                    help="time the 2D ring variant instead of the paper's node (profiling runs)")
+    ap.add_argument("--nz", type=int, default=0,
+                    help="time a 3D lattice of n x n x nz nodes instead of the one-layer lattice (profiling runs)")
     return ap.parse_args()
 
 
@@ -182,8 +186,12 @@ def time_steps(torch, lat, steps, flush):
     return np.array([a.elapsed_time(b) for a, b in evs])  # ms
 
 
-def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, init=None, tune=True):
-    lat = rl.Lattice(n, n, w.tau, dtype=form, landau=landau, kernel=kernel, forcing=forcing_of(w))
+def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, init=None, tune=True, stencil="sph26",
+                 nz=0):
+    if nz > 0:
+        lat = rl.Lattice3D(n, n, nz, w.tau, dtype=form, landau=landau, kernel=kernel, forcing=forcing_of(w))
+    else:
+        lat = rl.Lattice(n, n, w.tau, dtype=form, landau=landau, kernel=kernel, forcing=forcing_of(w), stencil=stencil)
     if init is not None:
         lat.init_fields(*init)
     else:
@@ -469,10 +477,11 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(smi_index) as clocks:
         ms, kernel_ms, info, n_epoch = measure_form(torch, rl, w, n, args.form, args.landau, args.kernel, K, W, flush,
-                                                    tune=not args.no_tune)
+                                                    tune=not args.no_tune, stencil=args.stencil, nz=args.nz)
     torch.cuda.synchronize()
     step_ms = float(ms.mean())
-    nodes = n * n
+    nodes = n * n * max(1, args.nz)
+    variant = args.stencil != "sph26" or args.nz > 0
     total_s, glups_total = aggregate_replicas(torch, float(ms.sum()) / 1e3, nodes * K, world)
 
     hbm_peak, peak_kind = load_peaks()
@@ -485,6 +494,8 @@ def main():
             with open(prof) as fh:
                 tj = json.load(fh)
             key = "%s_%s_%s_%d" % (args.form, args.landau, info["kernel"], n)
+            if variant:
+                key += "_%s_nz%d" % (args.stencil, args.nz)
             ent = tj.get(key)
             if ent and ent.get("source_sha256") == step_kernel_source_hash():
                 traffic = ent["bytes_per_launch"]
@@ -496,7 +507,9 @@ def main():
         "value": glups_total, "unit": "GLUPS", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.form != "f64" else "f64", "data": "synthetic",
-        "config": {"workload": w.name, "nx": n, "ny": n, "form": args.form, "landau": args.landau,
+        "config": {"workload": w.name + ("" if not variant else
+                                          (" (3D lattice %dx%dx%d)" % (n, n, args.nz) if args.nz else " (2D ring)")),
+                   "nx": n, "ny": n, "form": args.form, "landau": args.landau,
                    "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]],
                    "block": [info["block_x"], info["block_y"]], "tau": w.tau,
                    "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
@@ -509,7 +522,7 @@ def main():
         "gpu_launches": int(K + 2 * n_epoch),
     }
 
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and not args.no_extras and not variant:
         import oracle
         oracle.build()
         oracle.set_threads(os.cpu_count() or 1)

@@ -9,6 +9,20 @@ static cudaError_t ring_step_t(const LaunchCfg &cfg, bool forced, const void *qi
                                const StepParams &p, cudaStream_t s) {
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
     const dim3 block(cfg.bx, cfg.by, 1);
+    if (cfg.kernel == RLBM_KERNEL_PACKED) {
+        if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
+            if (p.nx % 2 != 0) return cudaErrorInvalidValue;
+            const dim3 g2((p.nx / 2 + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
+            const TS *in = static_cast<const TS *>(qin);
+            TS *out = static_cast<TS *>(qout);
+            const float *f = static_cast<const float *>(F);
+            if (forced) k_ring_step_pair<TS, true><<<g2, block, 0, s>>>(in, out, f, p);
+            else k_ring_step_pair<TS, false><<<g2, block, 0, s>>>(in, out, f, p);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;  // packed lanes: FP32 compute with the FP32 Landau solve
+        }
+    }
     const dim3 grid((p.nx + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
     const TS *in = static_cast<const TS *>(qin);
     TS *out = static_cast<TS *>(qout);

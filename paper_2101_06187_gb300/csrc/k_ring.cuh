@@ -11,6 +11,8 @@
 // F.Q.  Stored as q_k = (f_k - W eps0) / (W s).
 #pragma once
 
+#include "k_step_vec.cuh"
+#include "packed.cuh"
 #include "rlbm_device.cuh"
 
 namespace rlbk {
@@ -181,6 +183,65 @@ __global__ void __launch_bounds__(256) k_ring_step(const TS *__restrict__ qin, T
     static_for<0, NR>([&](auto K) {
         constexpr int k = decltype(K)::value;
         qout[k * (int)p.plane + n] = to_storage<TS, TC>(q[k]);
+    });
+}
+
+// Packed-lane ring step: two x-adjacent nodes per thread in pairs of FP32
+// lanes (packed.cuh); each source row of a direction is read once for the
+// pair (columns x0-1 .. x0+2 as the direction needs).  nx even.
+template <int k, typename TS>
+__device__ __forceinline__ pf2 ring_gather_pair(const TS *__restrict__ qin, long long cbase, const long long (&rowoff)[3],
+                                                int x0, int xl, int xr) {
+    constexpr int ox = ring_ox(k), oy = ring_oy(k);
+    constexpr double tx = ring_tx(k), ty = ring_ty(k);
+    auto row = [&](const TS *r, float (&a)[4]) {
+        load_run<TS, float, 2>(r + x0, &a[1]);
+        if constexpr (ox == -1) a[0] = load_q<TS, float>(r + xl);
+        if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[3] = load_q<TS, float>(r + xr);
+    };
+    float a[4];
+    row(qin + (cbase + rowoff[oy + 1]), a);
+    pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
+    if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
+    if constexpr (ty != 0.0) {
+        float b[4];
+        row(qin + (cbase + rowoff[oy + 2]), b);
+        v = fmadd(pf2((float)((1.0 - tx) * ty)), pf2(b[ox + 1], b[ox + 2]), v);
+        if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
+    }
+    return v;
+}
+
+template <typename TS, bool FORCED>
+__global__ void __launch_bounds__(256) k_ring_step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                                        const float *__restrict__ F, StepParams p) {
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= p.nx || y >= p.ny) return;
+    const int ym = (y == 0) ? p.ny - 1 : y - 1;
+    const int yp = (y == p.ny - 1) ? 0 : y + 1;
+    const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
+    const int xr = (x0 + 2 == p.nx) ? 0 : x0 + 2;
+    const long long rowoff[3] = {(long long)ym * p.pitch, (long long)y * p.pitch, (long long)yp * p.pitch};
+    pf2 q[NR];
+    static_for<0, NR>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        q[k] = ring_gather_pair<k, TS>(qin, (long long)k * p.plane, rowoff, x0, xl, xr);
+    });
+    const long long n0 = (long long)y * p.pitch + x0;
+    pf2 Fx = 0.0f, Fy = 0.0f;
+    if constexpr (FORCED) {
+        float fx[2], fy[2];
+        load_run<float, float, 2>(F + n0, fx);
+        load_run<float, float, 2>(F + p.plane + n0, fy);
+        Fx = pf2(fx[0], fx[1]);
+        Fy = pf2(fy[0], fy[1]);
+    }
+    ring_collide<pf2, pf2, FORCED>(q, Fx, Fy, p);
+    static_for<0, NR>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        const float out[2] = {q[k].v.x, q[k].v.y};
+        store_run<TS, float, 2>(qout + (long long)k * p.plane + n0, out);
     });
 }
 

@@ -436,7 +436,8 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
-    if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER) || o.cfl != 1.0 || o.eta_s != 0.0))
+    if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER && o.kernel != RLBM_KERNEL_PACKED) ||
+                 o.cfl != 1.0 || o.eta_s != 0.0))
         return RLBM_ERR_ARG;
     // the 3D lattice runs the one-node-per-thread or the packed-lane kernel at CFL 1
     if (d3 && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER && o.kernel != RLBM_KERNEL_PACKED) ||
@@ -1007,8 +1008,8 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     LaunchCfg best = h->cfg;
     for (const LaunchCfg &c : kCandidates) {
         if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
-        if ((h->opts.cfl != 1.0 || h->ring) && c.kernel != RLBM_KERNEL_GATHER) continue;
-        if (h->d3 && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED) continue;
+        if (h->opts.cfl != 1.0 && c.kernel != RLBM_KERNEL_GATHER) continue;
+        if ((h->d3 || h->ring) && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED) continue;
         if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) continue;
         // the trial steps read the current state and overwrite only the spare buffer
         bool ok = true;

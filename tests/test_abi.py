@@ -85,7 +85,7 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     o.eta_s = -0.01
     assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
     ring = rl.RLBM_STENCIL_RING8_2D   # the ring runs the gather kernel at CFL 1 with a fixed tau
-    for field, value in (("kernel", rl.KERNELS["vec"]), ("kernel", rl.KERNELS["packed"]), ("cfl", 0.5),
+    for field, value in (("kernel", rl.KERNELS["vec"]), ("kernel", rl.KERNELS["tma"]), ("cfl", 0.5),
                          ("eta_s", 0.1)):
         o = rl.rlbm_opts_default()
         setattr(o, field, value)

@@ -61,15 +61,16 @@ def oracle_run(nx, ny, tau, nsteps, fields, forcing):
     return f
 
 
-@pytest.mark.parametrize("dtype,landau", [("f64", "fp64"), ("f32", "fp64"), ("f32", "fp32")])
-@pytest.mark.parametrize("shape", [(37, 29), (64, 48), (300, 20), (4, 4)])
-def test_ring_forced_run_matches_oracle(dtype, landau, shape):
+@pytest.mark.parametrize("dtype,landau,kernel", [("f64", "fp64", "gather"), ("f32", "fp64", "gather"),
+                                                 ("f32", "fp32", "gather"), ("f32", "fp32", "packed")])
+@pytest.mark.parametrize("shape", [(38, 29), (64, 48), (300, 20), (4, 4)])
+def test_ring_forced_run_matches_oracle(dtype, landau, kernel, shape):
     nx, ny = shape
     forcing = FORCING_SMALL if min(nx, ny) > 8 else dict(kmin=1, kmax=1, amp=2e-3, seed=5, redraw_period=3)
     fields = workloads.random_smooth(nx, ny, seed=nx * 1000 + ny + 7, deps=0.05, vmax=0.05)
-    lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, landau=landau, forcing=forcing, stencil="ring8")
+    lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, landau=landau, forcing=forcing, stencil="ring8", kernel=kernel)
     info = lat.info()
-    assert info["nclasses"] == 8 and info["kernel"] == rl.KERNELS["gather"]
+    assert info["nclasses"] == 8 and info["kernel"] == rl.KERNELS[kernel]
     lat.init_fields(*fields)
     lat.step(60)
     got = lat.moments()
@@ -83,10 +84,11 @@ def test_ring_forced_run_matches_oracle(dtype, landau, shape):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_ring_16bit_storage_tracks_oracle(dtype):
+@pytest.mark.parametrize("kernel", ["gather", "packed"])
+def test_ring_16bit_storage_tracks_oracle(dtype, kernel):
     nx, ny = 64, 40
     fields = workloads.random_smooth(nx, ny, seed=21, deps=0.05, vmax=0.05)
-    lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, forcing=FORCING_SMALL, stencil="ring8")
+    lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, forcing=FORCING_SMALL, stencil="ring8", kernel=kernel)
     lat.init_fields(*fields)
     lat.step(30)
     got = lat.moments()
@@ -143,7 +145,8 @@ def test_ring_set_populations_round_trip_and_graphs():
 
 
 def test_ring_rejects_what_it_does_not_run():
-    for kw in (dict(kernel="vec"), dict(kernel="packed"), dict(cfl=0.5), dict(eta_s=0.1)):
+    for kw in (dict(kernel="vec"), dict(kernel="tma"), dict(kernel="twopass"), dict(cfl=0.5), dict(eta_s=0.1),
+               dict(kernel="packed", dtype="f64")):
         with pytest.raises(rl.RLBMError):
             rl.Lattice(32, 32, 0.7, stencil="ring8", **kw)
 
