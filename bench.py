@@ -64,17 +64,23 @@ def dist_env():
     return rank, world, local
 
 
-def step_kernel_source_hash():
-    """SHA-256 over the sources the fused step kernels compile from (the
+# Sources each fused-step variant compiles from (kernel id -> files).
+_STEP_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_gather.cuh", "k_step_vec.cuh", "k_step_pair.cuh",
+                 "k_launch.cuh", "k_step_f32.cu", "k_step_f64.cu", "k_step_h16.cu")
+_TMA_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_tma.cuh", "k_step_tma.cu")
+
+
+def step_kernel_source_hash(kernel_id=4):
+    """SHA-256 over the sources a fused-step variant compiles from (the
     per-node device code, the kernel bodies and their launchers), in name
     order: a stored DRAM-traffic figure counts only while it matches."""
     import hashlib
     src = os.path.join(ROOT, "paper_2101_06187_gb300", "csrc")
+    files = _TMA_SOURCES if kernel_id == 5 else _STEP_SOURCES
     hsh = hashlib.sha256()
-    for fn in sorted(os.listdir(src)):
-        if fn in ("rlbm_device.cuh", "packed.cuh", "k_launch.cuh") or fn.startswith("k_step_"):
-            with open(os.path.join(src, fn), "rb") as fh:
-                hsh.update(fh.read())
+    for fn in sorted(files):
+        with open(os.path.join(src, fn), "rb") as fh:
+            hsh.update(fh.read())
     return hsh.hexdigest()
 
 
@@ -497,7 +503,7 @@ def main():
             if variant:
                 key += "_%s_nz%d" % (args.stencil, args.nz)
             ent = tj.get(key)
-            if ent and ent.get("source_sha256") == step_kernel_source_hash():
+            if ent and ent.get("source_sha256") == step_kernel_source_hash(info["kernel"]):
                 traffic = ent["bytes_per_launch"]
         except (OSError, ValueError, KeyError):
             traffic = None
@@ -511,7 +517,7 @@ def main():
                                           (" (3D lattice %dx%dx%d)" % (n, n, args.nz) if args.nz else " (2D ring)")),
                    "nx": n, "ny": n, "form": args.form, "landau": args.landau,
                    "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]],
-                   "block": [info["block_x"], info["block_y"]], "tau": w.tau,
+                   "block": [info["block_x"], info["block_y"]], "launch_budget": info["launch_budget"], "tau": w.tau,
                    "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
                    "l2": "flushed between timed steps (256 MB write, then 256 MB read)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm" if args.form != "f64" else "alu", "achieved": achieved, "peak": hbm_peak,

@@ -180,6 +180,8 @@ typedef struct {
     size_t device_bytes;      /* device memory held by the handle */
     const void *populations;  /* device pointer of the current state, [nclasses][nz][ny][pitch] of the storage type */
     int nz;                   /* layers: 1, or nz of a 3D lattice */
+    int launch_budget;        /* register budget of the chosen launch: minimum resident 256-thread blocks
+                                 per SM asked of the compiler (packed variants), CTAs per SM (TMA), else 1 */
 } rlbm_info_t;
 
 /* Fill *opts with the defaults listed above. */

@@ -75,7 +75,7 @@ class Info(ctypes.Structure):
                 ("block_y", ctypes.c_int), ("nmodes", ctypes.c_int),
                 ("step", ctypes.c_int64), ("tau", ctypes.c_double), ("eps0", ctypes.c_double),
                 ("scale", ctypes.c_double), ("bytes_per_node", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
-                ("populations", ctypes.c_void_p), ("nz", ctypes.c_int)]
+                ("populations", ctypes.c_void_p), ("nz", ctypes.c_int), ("launch_budget", ctypes.c_int)]
 
 
 class RunDesc(ctypes.Structure):

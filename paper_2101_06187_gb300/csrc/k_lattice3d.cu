@@ -67,13 +67,19 @@ static cudaError_t launch_step3_t(const LaunchCfg &cfg, bool forced, const void 
         if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
             if (p.nx % 2 != 0) return cudaErrorInvalidValue;
             const dim3 g2((p.nx / 2 + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, p.nz);
-            if (idx32) {
-                if (forced) k_step3_pair<TS, true, int><<<g2, block, 0, s>>>(in, out, f, p);
-                else k_step3_pair<TS, false, int><<<g2, block, 0, s>>>(in, out, f, p);
-            } else {
-                if (forced) k_step3_pair<TS, true, long long><<<g2, block, 0, s>>>(in, out, f, p);
-                else k_step3_pair<TS, false, long long><<<g2, block, 0, s>>>(in, out, f, p);
-            }
+#define RLBM3_PAIR(MB)                                                                           \
+    do {                                                                                         \
+        if (idx32) {                                                                             \
+            if (forced) k_step3_pair<TS, true, int, MB><<<g2, block, 0, s>>>(in, out, f, p);     \
+            else k_step3_pair<TS, false, int, MB><<<g2, block, 0, s>>>(in, out, f, p);           \
+        } else {                                                                                 \
+            if (forced) k_step3_pair<TS, true, long long, MB><<<g2, block, 0, s>>>(in, out, f, p); \
+            else k_step3_pair<TS, false, long long, MB><<<g2, block, 0, s>>>(in, out, f, p);     \
+        }                                                                                        \
+    } while (0)
+            if (cfg.minb >= 2) RLBM3_PAIR(2);
+            else RLBM3_PAIR(1);
+#undef RLBM3_PAIR
             return cudaGetLastError();
         } else {
             return cudaErrorInvalidValue;  // packed lanes: FP32 compute with the FP32 Landau solve

@@ -369,9 +369,11 @@ __device__ __forceinline__ pf2 gather3_pair(const TS *__restrict__ qin, I base, 
     return v;
 }
 
-template <typename TS, bool FORCED, typename I>
-__global__ void __launch_bounds__(256) k_step3_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
-                                                    const float *__restrict__ F, StepParams p) {
+// MINB: minimum resident 256-thread blocks per SM asked of the register
+// allocator (1: unconstrained; 2: at most 128 registers per thread).
+template <typename TS, bool FORCED, typename I, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step3_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                                          const float *__restrict__ F, StepParams p) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;

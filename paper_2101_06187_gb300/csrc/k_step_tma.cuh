@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
             }
         }
         const bool landed = mbar_wait(bar, (k >> 1) & 1);
-        if (!__syncthreads_and(landed)) {  // one verdict for the whole CTA
+        if (!__syncthreads_and(landed)) {  // one decision for the whole CTA
             ok = false;
             break;
         }

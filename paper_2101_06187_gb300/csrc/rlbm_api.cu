@@ -979,6 +979,7 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
     info->pitch = h->pitch;
     info->nclasses = h->ncls;
     info->nz = h->nz;
+    info->launch_budget = h->cfg.minb;
     info->dtype = h->opts.dtype;
     info->kernel = h->cfg.kernel;
     info->block_x = h->cfg.bx;
