@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20
+METRIC = "GLUPS of the fused stream-collide step (and fraction of HBM peak)"
 
 
 def parse():
@@ -440,11 +441,12 @@ def reference_arm(args):
             break
     dt = time.perf_counter() - t0
     glups = n * n * steps_done / dt / 1e9
-    line = {"impl": "reference", "metric": "GLUPS of the fused stream-collide step", "value": glups, "unit": "GLUPS",
+    line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS",
             "n_gpus": args.gpus, "steps": total_steps, "warmup": args.warmup,
             "ms_per_step": dt / steps_done * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "nx": n, "ny": n, "form": "f64 CPU oracle", "tau": w.tau},
+            "config": {"workload": w.name, "nx": n, "ny": n, "form": "f64 (CPU oracle)", "tau": w.tau,
+                       "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw)},
             "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": "%dx%d lattice, %d forced steps" % (n, n, steps_done)},
             "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -509,7 +511,7 @@ def main():
             traffic = None
 
     line = {
-        "metric": "GLUPS of the fused stream-collide step (and fraction of HBM peak)",
+        "metric": METRIC,
         "value": glups_total, "unit": "GLUPS", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.form != "f64" else "f64", "data": "synthetic",
