@@ -46,14 +46,27 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
         if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
             if (p.nx % 2 != 0) return cudaErrorInvalidValue;
             const dim3 grid((p.nx / 2 + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
-#define RLBM_PAIR(MB)                                                        \
-    do {                                                                     \
-        if (forced) k_step_pair<TS, true, MB><<<grid, block, 0, s>>>(in, out, f, p);  \
-        else k_step_pair<TS, false, MB><<<grid, block, 0, s>>>(in, out, f, p);        \
+            const bool idx32p = (long long)NC * p.plane < (1ll << 31) - 1;
+#define RLBM_PAIR(MB)                                                                          \
+    do {                                                                                       \
+        if (idx32p) {                                                                          \
+            if (forced) k_step_pair<TS, true, MB, int><<<grid, block, 0, s>>>(in, out, f, p);  \
+            else k_step_pair<TS, false, MB, int><<<grid, block, 0, s>>>(in, out, f, p);        \
+        } else {                                                                               \
+            if (forced) k_step_pair<TS, true, MB><<<grid, block, 0, s>>>(in, out, f, p);       \
+            else k_step_pair<TS, false, MB><<<grid, block, 0, s>>>(in, out, f, p);             \
+        }                                                                                      \
     } while (0)
-            if (cfg.minb == 3) RLBM_PAIR(3);
-            else if (cfg.minb == 2) RLBM_PAIR(2);
-            else RLBM_PAIR(1);
+            if (cfg.minb == 5) {
+                if (cfg.bx * cfg.by > 128) return cudaErrorInvalidConfiguration;
+                RLBM_PAIR(5);
+            } else if (cfg.minb == 3) {
+                RLBM_PAIR(3);
+            } else if (cfg.minb == 2) {
+                RLBM_PAIR(2);
+            } else {
+                RLBM_PAIR(1);
+            }
 #undef RLBM_PAIR
             return cudaGetLastError();
         } else {

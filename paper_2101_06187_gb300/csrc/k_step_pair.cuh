@@ -10,40 +10,48 @@
 namespace rlbk {
 
 // The fused step of the node pair (x0, x0 + 1) of row y in packed lanes.
-template <typename TS, bool FORCED>
+// I is the index type of the element offsets: 32-bit when all 17 planes fit,
+// so each load address is one 32-bit sum and one widening add.
+template <typename TS, bool FORCED, typename I = long long>
 __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
                                           const float *__restrict__ F, const StepParams &p, int x0, int y) {
     const int ym = (y == 0) ? p.ny - 1 : y - 1;
     const int yp = (y == p.ny - 1) ? 0 : y + 1;
     const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
     const int xr = (x0 + 2 == p.nx) ? 0 : x0 + 2;
-    const long long rowoff[3] = {(long long)ym * p.pitch, (long long)y * p.pitch, (long long)yp * p.pitch};
+    const I rowoff[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
+    const I plane = (I)p.plane;
 
     pf2 q[NC];
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
         constexpr int ox = cls_ox(c), oy = cls_oy(c);
         constexpr double tx = cls_tx(c), ty = cls_ty(c);
-        const TS *plane = qin + (long long)c * p.plane;
+        auto row = [&](I r, float (&a)[4]) {
+            const I base = (I)c * plane + r;
+            load_run<TS, float, 2>(qin + (base + (I)x0), &a[1]);
+            if constexpr (ox == -1) a[0] = load_q<TS, float>(qin + (base + (I)xl));
+            if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[3] = load_q<TS, float>(qin + (base + (I)xr));
+        };
         float a[4];  // columns x0-1 .. x0+2
-        load_class_row<c, TS, float, 2>(plane + rowoff[oy + 1], x0, xl, xr, a);
+        row(rowoff[oy + 1], a);
         pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
         if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
         if constexpr (ty != 0.0) {
             float b[4];
-            load_class_row<c, TS, float, 2>(plane + rowoff[oy + 2], x0, xl, xr, b);
+            row(rowoff[oy + 2], b);
             v = fmadd(pf2((float)((1.0 - tx) * ty)), pf2(b[ox + 1], b[ox + 2]), v);
             if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
         }
         q[c] = v;
     });
 
-    const long long n0 = (long long)y * p.pitch + x0;
+    const I n0 = rowoff[1] + (I)x0;
     pf2 Fx = 0.0f, Fy = 0.0f;
     if constexpr (FORCED) {
         float fx[2], fy[2];
         load_run<float, float, 2>(F + n0, fx);
-        load_run<float, float, 2>(F + p.plane + n0, fy);
+        load_run<float, float, 2>(F + (plane + n0), fy);
         Fx = pf2(fx[0], fx[1]);
         Fy = pf2(fy[0], fy[1]);
     }
@@ -52,7 +60,7 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
         const float out[2] = {q[c].v.x, q[c].v.y};
-        store_run<TS, float, 2>(qout + (long long)c * p.plane + n0, out);
+        store_run<TS, float, 2>(qout + ((I)c * plane + n0), out);
     });
 }
 
@@ -138,13 +146,15 @@ __global__ void __launch_bounds__(256, MINB) k_step_pair2(const TS *__restrict__
 // MINB: minimum resident blocks of 256 threads per SM asked of the register
 // allocator (1: unconstrained; 2: <= 128 registers; 3: <= 80), so the
 // autotuner can trade registers for occupancy.
-template <typename TS, bool FORCED, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
-                                                         const float *__restrict__ F, StepParams p) {
+// MINB 5: blocks of at most 128 threads, five resident per SM (at most 102
+// registers per thread: 20 warps per SM).
+template <typename TS, bool FORCED, int MINB, typename I = long long>
+__global__ void __launch_bounds__(MINB == 5 ? 128 : 256, MINB)
+    k_step_pair(const TS *__restrict__ qin, TS *__restrict__ qout, const float *__restrict__ F, StepParams p) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= p.nx || y >= p.ny) return;
-    step_pair<TS, FORCED>(qin, qout, F, p, x0, y);
+    step_pair<TS, FORCED, I>(qin, qout, F, p, x0, y);
 }
 
 // Ensemble step with the packed body (see k_step_batch).
@@ -163,12 +173,13 @@ __global__ void __launch_bounds__(256, MINB) k_step_batch_pair(const BatchRun *_
         const int tx = local % r.tiles_x, ty = local / r.tiles_x;
         const int x0 = (tx * blockDim.x + threadIdx.x) * 2;
         const int y = ty * blockDim.y + threadIdx.y;
-        if (x0 < r.p.nx && y < r.p.ny) {
+        if (x0 < r.p.nx && y < r.p.ny) {  // members hold fewer than 2^31 / 17 elements per plane: 32-bit offsets
             if (r.F)
-                step_pair<TS, true>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout),
-                                    static_cast<const float *>(r.F), r.p, x0, y);
+                step_pair<TS, true, int>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout),
+                                         static_cast<const float *>(r.F), r.p, x0, y);
             else
-                step_pair<TS, false>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout), nullptr, r.p, x0, y);
+                step_pair<TS, false, int>(static_cast<const TS *>(r.qin), static_cast<TS *>(r.qout), nullptr, r.p, x0,
+                                          y);
         }
     }
 }

@@ -283,6 +283,7 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_PACKED, 64, 2, 2}, {RLBM_KERNEL_PACKED, 128, 1, 2}, {RLBM_KERNEL_PACKED, 128, 2, 2},
     {RLBM_KERNEL_PACKED, 64, 2, 3}, {RLBM_KERNEL_PACKED, 128, 1, 3}, {RLBM_KERNEL_PACKED, 128, 2, 3},
     {RLBM_KERNEL_PACKED, 64, 4, 3}, {RLBM_KERNEL_PACKED, 32, 8, 3},
+    {RLBM_KERNEL_PACKED, 64, 2, 5}, {RLBM_KERNEL_PACKED, 128, 1, 5}, {RLBM_KERNEL_PACKED, 32, 4, 5},
     {RLBM_KERNEL_TMA, 32, 8, 2}, {RLBM_KERNEL_TMA, 32, 8, 1},
     {RLBM_KERNEL_TWOPASS, 64, 2, 2}, {RLBM_KERNEL_TWOPASS, 128, 1, 2}, {RLBM_KERNEL_TWOPASS, 32, 8, 2},
     {RLBM_KERNEL_TWOPASS, 64, 2, 3}, {RLBM_KERNEL_TWOPASS, 128, 1, 3}, {RLBM_KERNEL_TWOPASS, 32, 8, 3},
@@ -1341,7 +1342,9 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *bl
     }
     static const int shapes[][2] = {{32, 4}, {64, 2}, {128, 1}, {32, 8}, {64, 4}, {128, 2}, {32, 2}, {64, 1}};
     // body: the vector kernel, or the packed-lane kernel (FP32 compute, FP32 Landau)
-    const bool packed_ok = b->opts.dtype != RLBM_F64 && b->opts.landau == RLBM_LANDAU_FP32;
+    bool packed_ok = b->opts.dtype != RLBM_F64 && b->opts.landau == RLBM_LANDAU_FP32;
+    for (const rlbm_t *h : b->runs)  // the packed ensemble body indexes with 32-bit offsets
+        if ((long long)NC * h->ny * h->pitch >= (1ll << 31) - 1) packed_ok = false;
     static const int bodies[][2] = {{RLBM_KERNEL_GATHER_VEC, 1}, {RLBM_KERNEL_PACKED, 1}, {RLBM_KERNEL_PACKED, 3}};
     const int sms = sm_count(b->device);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
