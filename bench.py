@@ -323,9 +323,13 @@ def measure_variants(torch, rl, oracle, flush, hbm_peak, steps=50, warmup=5):
     got = lat.moments()
     lat.close()
     f = oracle.ring.init(n, n, *fields)
+    t0 = time.perf_counter()
     oracle.ring.run(f, 0.6, nsteps, kmin=2, kmax=4, amp=2e-4, seed=7, redraw=25)
+    dt = time.perf_counter() - t0
     out["ring8_1024x1024_f32"]["max_rel_err_vs_oracle"] = _field_errors(oracle.ring.fields(f), got,
                                                                        "64x64, 50 forced steps")
+    out["ring8_1024x1024_f32"]["cpu_oracle"] = {"glups": n * n * nsteps / dt / 1e9, "cores": os.cpu_count(),
+                                               "sample": "64x64, 50 forced steps"}
     m = 20
     fields3 = workloads.random_smooth3d(m, m, m, seed=2024, deps=0.02, vmax=0.02)
     lat = rl.Lattice3D(m, m, m, 0.6, dtype="f32", forcing=dict(small, kmax=3))
@@ -334,9 +338,13 @@ def measure_variants(torch, rl, oracle, flush, hbm_peak, steps=50, warmup=5):
     got = lat.moments()
     lat.close()
     f = oracle.lattice3d.init(m, m, m, *fields3)
+    t0 = time.perf_counter()
     oracle.lattice3d.run(f, 0.6, nsteps, kmin=2, kmax=3, amp=2e-4, seed=7, redraw=25)
+    dt = time.perf_counter() - t0
     out["lattice3d_256x256x256_f32"]["max_rel_err_vs_oracle"] = _field_errors(oracle.lattice3d.fields(f), got,
                                                                              "20^3, 50 forced steps")
+    out["lattice3d_256x256x256_f32"]["cpu_oracle"] = {"glups": m ** 3 * nsteps / dt / 1e9, "cores": os.cpu_count(),
+                                                     "sample": "20^3, 50 forced steps"}
     return out
 
 
