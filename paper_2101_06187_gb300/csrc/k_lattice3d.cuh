@@ -190,7 +190,7 @@ __device__ __forceinline__ Frame3<TL> landau3(TL eps0, TL dE, const TL (&M)[3], 
         const TL c00 = b11 * b22 - b12 * b12, c01 = b02 * b12 - b01 * b22, c02 = b01 * b12 - b02 * b11;
         const TL c11 = b00 * b22 - b02 * b02, c12 = b01 * b02 - b00 * b12, c22 = b00 * b11 - b01 * b01;
         const TL det = b00 * c00 + b01 * c01 + b02 * c02;
-        const TL inv = exact ? recip(det) : fast_recip(det);
+        const TL inv = exact ? frame_recip(det) : fast_recip(det);
         v[0] = (c00 * M[0] + c01 * M[1] + c02 * M[2]) * inv;
         v[1] = (c01 * M[0] + c11 * M[1] + c12 * M[2]) * inv;
         v[2] = (c02 * M[0] + c12 * M[1] + c22 * M[2]) * inv;
@@ -218,8 +218,13 @@ __device__ __forceinline__ Frame3<TL> landau3(TL eps0, TL dE, const TL (&M)[3], 
     fr.eps = eps0 + fr.ddelta_eps;
     for (int a = 0; a < 3; ++a) fr.v[a] = v[a];
     fr.v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    fr.g2 = recip((TL)1 - fr.v2);
-    fr.gamma = sqrt_(fr.g2);
+    if constexpr (is_f32_lane<TL>::value) {
+        fr.gamma = frame_rsqrt((TL)1 - fr.v2);
+        fr.g2 = fr.gamma * fr.gamma;
+    } else {
+        fr.g2 = recip((TL)1 - fr.v2);
+        fr.gamma = sqrt_(fr.g2);
+    }
     return fr;
 }
 

@@ -32,6 +32,7 @@ __device__ __forceinline__ pf2 fmadd(pf2 a, pf2 b, pf2 c) { return pf2(__ffma2_r
 __device__ __forceinline__ pf2 recip(pf2 x) { return pf2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
 __device__ __forceinline__ pf2 fast_recip(pf2 x) { return pf2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
 __device__ __forceinline__ pf2 sqrt_(pf2 x) { return pf2(sqrtf(x.v.x), sqrtf(x.v.y)); }
+__device__ __forceinline__ pf2 fast_rsqrt(pf2 x) { return pf2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
 __device__ __forceinline__ pf2 absval(pf2 x) { return pf2(fabsf(x.v.x), fabsf(x.v.y)); }
 
 // Lane-wise comparison; !mask is true only when the comparison fails in

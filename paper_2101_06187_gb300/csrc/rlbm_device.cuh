@@ -336,6 +336,43 @@ RLBM_HD inline T fast_recip(T x) {
     return (T)1 / x;
 }
 
+template <typename T>
+RLBM_HD inline T fast_rsqrt(T x) {
+#ifdef __CUDA_ARCH__
+    if constexpr (std::is_same<T, float>::value) return rsqrtf(x);
+#endif
+    return (T)1 / std::sqrt(x);
+}
+
+// Reciprocal and reciprocal square root of the final Landau frame.  FP32
+// lanes: the hardware estimate refined by one step of Newton's method,
+// y <- y + y (1 - x y) for 1/x and y <- y + (y/2) (1 - x y^2) for x^(-1/2),
+// which squares the estimate's relative error, so the result is within
+// about one unit in the last place (checked against IEEE division and
+// square root by the numerics test); FP64 lanes: IEEE division and square
+// root.
+template <typename T>
+RLBM_HD inline T frame_recip(T x) {
+    if constexpr (is_f32_lane<T>::value) {
+        const T y = fast_recip(x);
+        const T e = fmadd((T)0 - x, y, T(1.0f));
+        return fmadd(y, e, y);
+    } else {
+        return (T)1 / x;
+    }
+}
+
+template <typename T>
+RLBM_HD inline T frame_rsqrt(T x) {
+    if constexpr (is_f32_lane<T>::value) {
+        const T y = fast_rsqrt(x);
+        const T e = fmadd((T)0 - x * y, y, T(1.0f));
+        return fmadd(y * T(0.5f), e, y);
+    } else {
+        return (T)1 / sqrt_(x);
+    }
+}
+
 // rest_a: (S + eps I) at rest in units of eps0 -- 4/3 for the spherical node
 // (P = eps/3), 3/2 for the 2D ring (P = eps/2).
 template <typename TL>
@@ -350,7 +387,7 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
         const TL a = a0 - d;
         const TL axx = a + dSxx, ayy = a + dSyy;
         const TL det = fmadd(axx, ayy, nSxy * dSxy);
-        const TL inv_det = exact ? recip(det) : fast_recip(det);
+        const TL inv_det = exact ? frame_recip(det) : fast_recip(det);
         vx = fmadd(ayy, Mx, nSxy * My) * inv_det;
         vy = fmadd(axx, My, nSxy * Mx) * inv_det;
     };
@@ -380,8 +417,13 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
     fr.vx = vx;
     fr.vy = vy;
     fr.v2 = fmadd(vx, vx, vy * vy);
-    fr.g2 = recip((TL)1 - fr.v2);
-    fr.gamma = sqrt_(fr.g2);
+    if constexpr (is_f32_lane<TL>::value) {
+        fr.gamma = frame_rsqrt((TL)1 - fr.v2);
+        fr.g2 = fr.gamma * fr.gamma;
+    } else {
+        fr.g2 = recip((TL)1 - fr.v2);
+        fr.gamma = sqrt_(fr.g2);
+    }
     return fr;
 }
 
