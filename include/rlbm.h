@@ -20,7 +20,11 @@
  *     projected driving term (Eq. forceTerm, App. B);
  *   - the stirring force of Sec. 5: random modes on a wavenumber shell,
  *     zero mean, redrawn every `redraw_period` steps.
- * Lattice units: Delta x = Delta t = 1; tau is the relaxation time in steps.
+ * Beyond the paper's one-layer lattice the same library runs the genuinely
+ * two-dimensional massless gas on an 8-direction ring (RLBM_STENCIL_RING8_2D)
+ * and the paper's node on a three-dimensional lattice (rlbm_create3d).
+ * Lattice units: Delta x = Delta t = 1 (rlbm_opts.cfl sets Delta t / Delta x
+ * otherwise); tau is the relaxation time in steps.
  * Signature (-,+,+,+).
  *
  * Conventions for every call:

@@ -491,6 +491,11 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     } else {
         h->cfg.kernel = o.kernel;
         if (o.kernel == RLBM_KERNEL_TMA) h->cfg.minb = 2;  // two CTAs per SM
+        if (o.kernel == RLBM_KERNEL_PACKED && !d3) {     // the shape the autotuner usually picks
+            h->cfg.bx = 128;
+            h->cfg.by = 1;
+            h->cfg.minb = 2;
+        }
         if (o.kernel == RLBM_KERNEL_TWOPASS) {
             h->cfg.bx = 64;
             h->cfg.by = 2;
