@@ -169,6 +169,12 @@ typedef struct {
      * 0 (default): the constant tau of rlbm_create. */
     double eta_s;
     double dt;            /* time step for eta/s mode (default 1) */
+    /* Failure-detection test hook (default 0).  1: the TMA kernel issues no
+     * tile copies, so its bounded waits run out after one second, the
+     * kernel leaves without touching memory it did not own, and the next
+     * synchronising call returns RLBM_ERR_TIMEOUT (sticky); the state of
+     * that step is undefined.  Nothing faults or hangs. */
+    int test_unarmed_wait;
 } rlbm_opts;
 
 typedef struct {

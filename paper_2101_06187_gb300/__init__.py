@@ -66,7 +66,7 @@ class Opts(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("eps0", ctypes.c_double), ("scale", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("cfl", ctypes.c_double), ("eta_s", ctypes.c_double),
-                ("dt", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("test_unarmed_wait", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -441,7 +441,8 @@ class Lattice:
     def __init__(self, nx: int, ny: int, tau: float, *, dtype: str = "f32", landau: str = "fp32",
                  forcing: Optional[dict] = None, eps0: float = 1.0, scale: float = 0.0, kernel: str = "auto",
                  use_graphs: bool = True, allocator: str = "torch", stream=None, device: Optional[int] = None,
-                 cfl: float = 1.0, eta_s: float = 0.0, dt: float = 1.0, stencil: str = "sph26"):
+                 cfl: float = 1.0, eta_s: float = 0.0, dt: float = 1.0, stencil: str = "sph26",
+                 test_unarmed_wait: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the RLBM library runs on the GPU only")
@@ -471,6 +472,7 @@ class Lattice:
         o.cfl = float(cfl)
         o.eta_s = float(eta_s)
         o.dt = float(dt)
+        o.test_unarmed_wait = 1 if test_unarmed_wait else 0
         self._alloc = None
         if allocator == "torch":
             self._alloc = _TorchAllocator(dev, s)

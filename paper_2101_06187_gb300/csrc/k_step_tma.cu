@@ -59,7 +59,7 @@ static int sm_count_of_current_device() {
 
 template <bool FORCED>
 static cudaError_t launch_tma_t(int ctas_per_sm, const CUtensorMap &mq, const CUtensorMap &mf, const float *qin,
-                                float *qout, const StepParams &p, cudaStream_t s) {
+                                float *qout, const StepParams &p, cudaStream_t s, int unarmed) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
@@ -70,18 +70,18 @@ static cudaError_t launch_tma_t(int ctas_per_sm, const CUtensorMap &mq, const CU
     if (sms <= 0) return cudaErrorInvalidDevice;
     const int tiles = ((p.nx + kTmaTW - 1) / kTmaTW) * ((p.ny + kTmaTH - 1) / kTmaTH);
     const int grid = std::max(1, std::min(tiles, ctas_per_sm * sms));
-    k_step_tma<FORCED><<<grid, dim3(kTmaTW / 2, kTmaTH, 1), kTmaSmemBytes, s>>>(mq, mf, qin, qout, p);
+    k_step_tma<FORCED><<<grid, dim3(kTmaTW / 2, kTmaTH, 1), kTmaSmemBytes, s>>>(mq, mf, qin, qout, p, unarmed);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_tma(const LaunchCfg &cfg, bool forced, const CUtensorMap &mq, const CUtensorMap &mf,
-                            const void *qin, void *qout, const StepParams &p, cudaStream_t s) {
+                            const void *qin, void *qout, const StepParams &p, cudaStream_t s, int unarmed) {
     if (p.nx % 2 != 0 || p.cfl != 1.0 || p.eta_k != 0.0) return cudaErrorInvalidValue;
     const int per_sm = cfg.minb == 1 ? 1 : 2;
     const float *in = static_cast<const float *>(qin);
     float *out = static_cast<float *>(qout);
-    return forced ? launch_tma_t<true>(per_sm, mq, mf, in, out, p, s)
-                  : launch_tma_t<false>(per_sm, mq, mf, in, out, p, s);
+    return forced ? launch_tma_t<true>(per_sm, mq, mf, in, out, p, s, unarmed)
+                  : launch_tma_t<false>(per_sm, mq, mf, in, out, p, s, unarmed);
 }
 
 }  // namespace rlbk

@@ -173,7 +173,7 @@ static cudaError_t launch_step_h(const rlbm_t *h, const LaunchCfg &cfg, const vo
     if (cfg.kernel == RLBM_KERNEL_TMA) {
         if (!h->tm_ready) return cudaErrorNotSupported;
         const CUtensorMap &mq = (qin == h->q[0]) ? h->tm_q[0] : h->tm_q[1];
-        return launch_step_tma(cfg, h->forced, mq, h->tm_F, qin, qout, p, h->stream);
+        return launch_step_tma(cfg, h->forced, mq, h->tm_F, qin, qout, p, h->stream, h->opts.test_unarmed_wait);
     }
     return launch_step(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
 }

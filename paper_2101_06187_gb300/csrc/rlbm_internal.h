@@ -53,7 +53,7 @@ int moments_blocks(const StepParams &p);
 cudaError_t tma_encode_state(CUtensorMap *map, const void *q, const StepParams &p);
 cudaError_t tma_encode_force(CUtensorMap *map, const void *F, const StepParams &p);
 cudaError_t launch_step_tma(const LaunchCfg &cfg, bool forced, const CUtensorMap &mq, const CUtensorMap &mf,
-                            const void *qin, void *qout, const StepParams &p, cudaStream_t s);
+                            const void *qin, void *qout, const StepParams &p, cudaStream_t s, int unarmed = 0);
 
 // The three-dimensional lattice (k_lattice3d.cu).
 cudaError_t launch_step3(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
