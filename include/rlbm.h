@@ -361,6 +361,24 @@ RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, int nx, int
                                          double scale, double *d_eps, double *d_vx, double *d_vy, double *d_totals,
                                          void *stream);
 
+/* Checkpoint and resume (no counterpart in the paper).  A checkpoint holds
+ * a header (lattice sizes, stencil, storage form, tau, eps0, scale, cfl,
+ * eta/s, dt, the forcing parameters and the step counter) and the current
+ * device state verbatim; because the stirring force is a counter-based
+ * function of (seed, epoch), a handle created with the same arguments,
+ * loaded from the checkpoint and stepped on reproduces the uninterrupted
+ * run bitwise (same launch configuration).
+ * rlbm_checkpoint_size: bytes a checkpoint of this handle takes.
+ * rlbm_checkpoint_save: writes it into the caller's host buffer buf of len
+ *   >= that size (synchronises; RLBM_ERR_ARG if len is short).
+ * rlbm_checkpoint_load: restores state and step counter from buf; the
+ *   header must match the handle's configuration exactly (RLBM_ERR_ARG
+ *   otherwise, state untouched); the force of the restored epoch is
+ *   re-synthesised by the next step.  Synchronises. */
+RLBM_API rlbm_status rlbm_checkpoint_size(rlbm_t *h, size_t *bytes);
+RLBM_API rlbm_status rlbm_checkpoint_save(rlbm_t *h, void *buf, size_t len);
+RLBM_API rlbm_status rlbm_checkpoint_load(rlbm_t *h, const void *buf, size_t len);
+
 /* Wait for all work queued on the handle's stream. */
 RLBM_API rlbm_status rlbm_synchronize(rlbm_t *h);
 

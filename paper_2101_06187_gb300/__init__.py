@@ -42,7 +42,7 @@ EXPORTS = (
     "rlbm_batch_energy_spectrum", "rlbm_batch_get_populations", "rlbm_batch_autotune", "rlbm_batch_get_info",
     "rlbm_batch_synchronize", "rlbm_batch_last_error", "rlbm_batch_destroy", "rlbm_filtered_velocity",
     "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset", "rlbm_create3d", "rlbm_init_fields3d",
-    "rlbm_moments3d", "rlbm_get_force3d",
+    "rlbm_moments3d", "rlbm_get_force3d", "rlbm_checkpoint_size", "rlbm_checkpoint_save", "rlbm_checkpoint_load",
 )
 
 
@@ -133,6 +133,11 @@ def _load():
         lib.rlbm_moments3d.argtypes = [h, _dp, _dp, _dp, _dp, _dp]
         lib.rlbm_get_force3d.argtypes = [h, _dp, _dp, _dp]
         for name in ("rlbm_create3d", "rlbm_init_fields3d", "rlbm_moments3d", "rlbm_get_force3d"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib.rlbm_checkpoint_size.argtypes = [h, ctypes.POINTER(ctypes.c_size_t)]
+        lib.rlbm_checkpoint_save.argtypes = [h, ctypes.c_void_p, ctypes.c_size_t]
+        lib.rlbm_checkpoint_load.argtypes = [h, ctypes.c_void_p, ctypes.c_size_t]
+        for name in ("rlbm_checkpoint_size", "rlbm_checkpoint_save", "rlbm_checkpoint_load"):
             getattr(lib, name).restype = ctypes.c_int
         b = ctypes.c_void_p
         ip = ctypes.POINTER(ctypes.c_int)
@@ -319,6 +324,20 @@ def rlbm_init_fields3d(h, eps=None, vx=None, vy=None, vz=None):
 
 def rlbm_moments3d(h, eps, vx, vy, vz, totals):
     _check(h, _load().rlbm_moments3d(h, _p(eps), _p(vx), _p(vy), _p(vz), _p(totals)), "rlbm_moments3d")
+
+
+def rlbm_checkpoint_size(h) -> int:
+    n = ctypes.c_size_t()
+    _check(h, _load().rlbm_checkpoint_size(h, ctypes.byref(n)), "rlbm_checkpoint_size")
+    return int(n.value)
+
+
+def rlbm_checkpoint_save(h, buf: np.ndarray):
+    _check(h, _load().rlbm_checkpoint_save(h, buf.ctypes.data, buf.nbytes), "rlbm_checkpoint_save")
+
+
+def rlbm_checkpoint_load(h, buf: np.ndarray):
+    _check(h, _load().rlbm_checkpoint_load(h, buf.ctypes.data, buf.nbytes), "rlbm_checkpoint_load")
 
 
 def rlbm_get_force3d(h, Fx, Fy, Fz):
@@ -565,6 +584,22 @@ class Lattice:
 
     def set_populations(self, f):
         rlbm_set_populations(self.handle, _f64(f, self.nclasses * self.nx * self.ny))
+
+    def checkpoint(self) -> np.ndarray:
+        """The state and step counter as a byte array (rlbm_checkpoint_save)."""
+        buf = np.empty(rlbm_checkpoint_size(self.handle), dtype=np.uint8)
+        rlbm_checkpoint_save(self.handle, buf)
+        return buf
+
+    def restore(self, buf):
+        """Resume from a checkpoint of a lattice created with the same arguments."""
+        rlbm_checkpoint_load(self.handle, np.ascontiguousarray(np.asarray(buf, dtype=np.uint8)))
+
+    def save(self, path: str):
+        self.checkpoint().tofile(path)
+
+    def load(self, path: str):
+        self.restore(np.fromfile(path, dtype=np.uint8))
 
     def force(self):
         Fx = np.empty((self.ny, self.nx))

@@ -14,6 +14,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rlbm_internal.h"
 #include "k_ring.cuh"
 
@@ -74,6 +76,13 @@ int moments_blocks(const StepParams &p) { return ((p.nx + 31) / 32) * ((p.ny + 7
 using namespace rlbk;
 
 // ---------------------------------------------------------------- helpers
+// NVTX range over a library call (visible in Nsight timelines; free when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 static rlbm_status fail(rlbm_t *h, rlbm_status st, const char *fmt, ...) {
     if (!h) return st;
     char buf[512];
@@ -196,6 +205,7 @@ static rlbm_status ensure_force(rlbm_t *h) {
     if (!h->forced) return RLBM_OK;
     const long long e = h->step / h->forcing.redraw_period;
     if (e == h->force_epoch) return RLBM_OK;
+    NvtxRange range("rlbm_force_epoch");
     const StepParams p = params_of(h);
     if (h->d3) {
         CUDA_TRY(h, launch_draw_modes3(h->opts.dtype, h->modes3, h->coef, h->nmodes, h->forcing.amp,
@@ -674,6 +684,7 @@ rlbm_status rlbm_init_fields3d(rlbm_t *h, const double *eps, const double *vx, c
 
 rlbm_status rlbm_step(rlbm_t *h, int n) {
     CHECK_HANDLE(h);
+    NvtxRange range("rlbm_step");
     if (n < 0) return fail(h, RLBM_ERR_ARG, "negative step count");
     while (n > 0) {
         int chunk = n;
@@ -739,6 +750,7 @@ rlbm_status rlbm_moments3d(rlbm_t *h, double *eps, double *vx, double *vy, doubl
 
 rlbm_status rlbm_moments(rlbm_t *h, double *eps, double *vx, double *vy, double totals[3]) {
     CHECK_HANDLE(h);
+    NvtxRange range("rlbm_moments");
     const size_t n = (size_t)h->nx * h->ny;
     rlbm_status st = rlbm_moments_device(h, eps ? h->fields : nullptr, vx ? h->fields + n : nullptr,
                                          vy ? h->fields + 2 * n : nullptr, totals ? h->totals : nullptr);
@@ -800,6 +812,7 @@ extern "C" {
 
 rlbm_status rlbm_energy_spectrum(rlbm_t *h, int nshells, double *Ek) {
     CHECK_HANDLE(h);
+    NvtxRange range("rlbm_energy_spectrum");
     if (nshells < 1 || nshells > 4096 || !Ek) return fail(h, RLBM_ERR_ARG, "nshells must be in [1, 4096]");
     rlbm_status st0 = ensure_spectrum_work(h);
     if (st0 != RLBM_OK) return st0;
@@ -1004,6 +1017,7 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
 
 rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x, int *block_y) {
     CHECK_HANDLE(h);
+    NvtxRange range("rlbm_autotune");
     if (reps < 1) reps = 20;
     rlbm_status st = ensure_force(h);
     if (st != RLBM_OK) return st;
@@ -1049,6 +1063,98 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     if (chosen_kernel) *chosen_kernel = best.kernel;
     if (block_x) *block_x = best.bx;
     if (block_y) *block_y = best.by;
+    return RLBM_OK;
+}
+
+}  // extern "C"
+
+// Checkpoint layout: this header, then the current state buffer verbatim
+// (ncls planes of nz * ny * pitch elements of the storage type).
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t nx, ny, nz, pitch, ncls, dtype, kind, forced;
+    double tau, eps0, scale, cfl, eta_s, dt;
+    int32_t kmin, kmax, redraw_period, pad;
+    double amp;
+    uint64_t seed;
+    int64_t step;
+    uint64_t state_bytes;
+};
+static const char kCkptMagic[8] = {'R', 'L', 'B', 'M', 'C', 'K', 'P', 'T'};
+
+static CkptHeader ckpt_header_of(const rlbm_t *h) {
+    CkptHeader c;
+    memset(&c, 0, sizeof c);
+    memcpy(c.magic, kCkptMagic, 8);
+    c.version = 1;
+    c.header_bytes = sizeof(CkptHeader);
+    c.nx = h->nx;
+    c.ny = h->ny;
+    c.nz = h->nz;
+    c.pitch = h->pitch;
+    c.ncls = h->ncls;
+    c.dtype = h->opts.dtype;
+    c.kind = h->ring ? 1 : (h->d3 ? 2 : 0);
+    c.forced = h->forced ? 1 : 0;
+    c.tau = h->tau;
+    c.eps0 = h->opts.eps0;
+    c.scale = h->opts.scale;
+    c.cfl = h->opts.cfl;
+    c.eta_s = h->opts.eta_s;
+    c.dt = h->opts.dt;
+    if (h->forced) {
+        c.kmin = h->forcing.kmin;
+        c.kmax = h->forcing.kmax;
+        c.redraw_period = h->forcing.redraw_period;
+        c.amp = h->forcing.amp;
+        c.seed = h->forcing.seed;
+    }
+    c.step = h->step;
+    c.state_bytes = q_bytes(h);
+    return c;
+}
+
+extern "C" {
+
+rlbm_status rlbm_checkpoint_size(rlbm_t *h, size_t *bytes) {
+    CHECK_HANDLE(h);
+    if (!bytes) return RLBM_ERR_ARG;
+    *bytes = sizeof(CkptHeader) + q_bytes(h);
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_checkpoint_save(rlbm_t *h, void *buf, size_t len) {
+    CHECK_HANDLE(h);
+    const size_t need = sizeof(CkptHeader) + q_bytes(h);
+    if (!buf || len < need) return fail(h, RLBM_ERR_ARG, "checkpoint needs %zu bytes, got %zu", need, len);
+    const CkptHeader c = ckpt_header_of(h);
+    memcpy(buf, &c, sizeof c);
+    CUDA_TRY(h, cudaMemcpyAsync(static_cast<char *>(buf) + sizeof c, h->q[h->cur], q_bytes(h), cudaMemcpyDeviceToHost,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return check_errword(h);
+}
+
+rlbm_status rlbm_checkpoint_load(rlbm_t *h, const void *buf, size_t len) {
+    CHECK_HANDLE(h);
+    if (!buf || len < sizeof(CkptHeader)) return fail(h, RLBM_ERR_ARG, "not a checkpoint (too short)");
+    CkptHeader c;
+    memcpy(&c, buf, sizeof c);
+    CkptHeader mine = ckpt_header_of(h);
+    if (memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 1 || c.header_bytes != sizeof(CkptHeader))
+        return fail(h, RLBM_ERR_ARG, "not a checkpoint of this library version");
+    mine.step = c.step;  // the only field that may differ
+    if (memcmp(&c, &mine, sizeof c) != 0)
+        return fail(h, RLBM_ERR_ARG, "checkpoint of a different lattice configuration");
+    if (len < sizeof c + c.state_bytes) return fail(h, RLBM_ERR_ARG, "checkpoint truncated");
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->q[0], static_cast<const char *>(buf) + sizeof c, c.state_bytes,
+                                cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    h->step = c.step;
+    h->force_epoch = -1;
     return RLBM_OK;
 }
 
