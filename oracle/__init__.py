@@ -14,9 +14,9 @@ Function status (pins live in ``tests/test_oracle_*.py``):
   stencil, moments, ideal_T, feq, landau, force_term, collide, stream,
   forcing field, totals, spectrum: pinned (closed forms, invariants,
   library eigen-solver, linear-mode analysis).
-  philox4x32_10: pinned by statistics only (no known-answer vectors are
-  available offline); its bit pattern is cross-checked against the CUDA
-  library's independent implementation by the parity tests.
+  philox4x32_10: parity unpinned (bit pattern) -- no known-answer vectors
+  are available offline, so the tests pin its statistics only; the CUDA
+  library's independent implementation agrees with it bit for bit.
 """
 from __future__ import annotations
 

@@ -60,3 +60,34 @@ def test_bounded_wait_runs_out_and_is_reported():
     E, VX, VY = oracle.fields(f)
     assert np.max(np.abs(e - E)) < 1e-5 * np.max(np.abs(E))
     assert max(np.max(np.abs(vx - VX)), np.max(np.abs(vy - VY))) < 1e-5 * max(np.max(np.abs(VX)), np.max(np.abs(VY)))
+
+
+def test_failed_allocation_is_reported_and_nothing_leaks():
+    """Host-side fault injection through the allocator hooks: the k-th
+    allocation fails; rlbm_create returns RLBM_ERR_ALLOC and frees every
+    block it obtained (the fake allocator counts them)."""
+    import ctypes
+    for fail_at in (0, 1, 3, 6):
+        live = {}
+        calls = [0]
+
+        def _alloc(nbytes, _ctx):
+            calls[0] += 1
+            if calls[0] - 1 == fail_at:
+                return None
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+            live[t.data_ptr()] = t
+            return t.data_ptr()
+
+        def _free(ptr, _nbytes, _ctx):
+            live.pop(int(ptr), None)
+
+        alloc_cb, free_cb = rl.ALLOC_FN(_alloc), rl.FREE_FN(_free)
+        o = rl.rlbm_opts_default()
+        o.alloc, o.free = alloc_cb, free_cb
+        out = ctypes.c_void_p()
+        forcing = rl.Forcing(2, 4, 1e-4, 1, 10)
+        st = rl.library().rlbm_create(64, 48, 0, 0.7, ctypes.byref(forcing), ctypes.byref(o), ctypes.byref(out))
+        assert st == rl.RLBM_ERR_ALLOC, (fail_at, st)
+        assert out.value is None
+        assert not live, (fail_at, len(live))

@@ -155,3 +155,28 @@ def test_full_size_force_at_sampled_nodes(w, dtype):
         assert np.max(np.abs(Fx[ys, xs] - ox)) < 2e-6 * scale
         assert np.max(np.abs(Fy[ys, xs] - oy)) < 2e-6 * scale
     lat.close()
+
+
+def test_lattice_beyond_32bit_offsets_stays_an_exact_tiling(tiled_reference):
+    """12032^2 FP32 (145 M nodes, 17 planes = 2.5 G elements: the packed
+    kernel's 64-bit offset path), started on the device from the tiled
+    fields; sampled rows of the moments against the oracle's 64^2 tile."""
+    period, tau, nsteps, ref = tiled_reference
+    n = 12032
+    rep = n // period
+    e, a, b = workloads.random_smooth(period, period, seed=77, deps=0.02, vmax=0.02)
+    dev = lambda g: torch.as_tensor(g, dtype=torch.float64, device="cuda").repeat(rep, rep).contiguous()
+    lat = rl.Lattice(n, n, tau, dtype="f32", kernel="packed")
+    fe, fa, fb = dev(e), dev(a), dev(b)
+    lat.init_fields_device(fe, fa, fb)
+    lat.step(nsteps)
+    out = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(3)]
+    lat.moments_device(*out)
+    lat.synchronize()
+    rows = [0, 1, 4095, 4096, 9000, n - 1]
+    got = [o[rows].cpu().numpy() for o in out]
+    lat.close()
+    del fe, fa, fb, out
+    want = [np.tile(r, (1, rep))[[y % period for y in rows]] for r in ref]
+    err_e, err_v = _errs(want, got)
+    assert err_e < TILED_TOL["f32"] and err_v < TILED_TOL["f32"], (err_e, err_v)
