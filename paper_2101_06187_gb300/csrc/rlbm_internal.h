@@ -23,18 +23,17 @@ struct Mode {
     double ax, bx, ay, by;
 };
 
-struct Launch {
-    cudaStream_t stream;
-    int kernel;  // rlbm_kernel actually used
-};
-
-// Step launchers (defined in the per-form translation units).
-// Launch shape of the fused step (kernel variant and thread-block shape).
+// Launch shape of the fused step: kernel variant, thread-block shape and a
+// launch budget -- for the packed kernels the minimum resident blocks per SM
+// asked of the register allocator (1, 2, 3; 5 = five 128-thread blocks),
+// for the two-pass kernel 2..4, for the TMA kernel the CTAs per SM.
 struct LaunchCfg {
     int kernel = RLBM_KERNEL_GATHER;
     int bx = 32, by = 8;
-    int minb = 1;  // packed kernel: register budget (blocks of 256 per SM: 1, 2 or 3); TMA kernel: CTAs per SM
+    int minb = 1;
 };
+
+// Step launchers (defined in the per-form translation units).
 
 cudaError_t launch_step(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                         const void *F, const StepParams &p, cudaStream_t s);
