@@ -36,6 +36,12 @@ import workloads  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "GLUPS of the fused stream-collide step (and fraction of HBM peak)"
+# FP64 form: FP64 flops per node of the forced step (ncu: adds + multiplies
+# + 2 x FMAs of one launch / nodes, profiles/k_step_gather_f64_stirred_1024.md)
+# and the FP64 peak derived from the unit count and clock (152 SMs x 2 FP64
+# FMA per clock x 2 flops x 2.07 GHz).
+FP64_FLOPS_PER_NODE = 627.0
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -530,13 +536,20 @@ def main():
                    "block": [info["block_x"], info["block_y"]], "launch_budget": info["launch_budget"], "tau": w.tau,
                    "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
                    "l2": "flushed between timed steps (256 MB write, then 256 MB read)", "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "roofline": {"bound": "hbm" if args.form != "f64" else "alu", "achieved": achieved, "peak": hbm_peak,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_node": bpn,
                      "kernel_ms": kernel_ms, "epoch_steps_in_timed_region": n_epoch},
         "clocks": clocks.summary(),
         "gpu_launches": int(K + 2 * n_epoch),
     }
+    if args.form == "f64" and not variant:
+        tf = FP64_FLOPS_PER_NODE * nodes / (kernel_ms / 1e3) / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+                            "peak_kind": "derived (FP64 units x clock)", "flops_per_node": FP64_FLOPS_PER_NODE,
+                            "hbm_frac": achieved / hbm_peak, "kernel_ms": kernel_ms,
+                            "epoch_steps_in_timed_region": n_epoch}
 
     if rank == 0 and not args.no_extras and not variant:
         import oracle
@@ -557,6 +570,10 @@ def main():
                 "glups": g, "hbm_gbs": bp * nodes / (km / 1e3) / 1e9,
                 "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak, "bytes_per_node": bp,
                 "max_rel_err_vs_oracle": err}
+            if form == "f64":
+                tf = FP64_FLOPS_PER_NODE * nodes / (km / 1e3) / 1e12
+                forms["f64/landau-fp64"]["fp64_alu"] = {"tflops": tf, "peak_tflops": FP64_PEAK_TFLOPS,
+                                                       "frac": tf / FP64_PEAK_TFLOPS}
         line["forms"] = forms
         line["ensemble"] = measure_ensemble(torch, rl, flush)
         line["variants"] = measure_variants(torch, rl, oracle, flush, hbm_peak)
