@@ -92,33 +92,44 @@ cudaError_t launch_check_fields(const double *eps, const double *vx, const doubl
 }
 
 // ---------------------------------------------------------------- conservation totals
-// Fixed-order FP64 reduction of the per-block partials: thread t sums
-// partials t, t+256, ..., then a tree over the 256 threads.
+// Fixed-order, compensated FP64 reduction of the per-block partials: thread
+// t sums partials t, t+256, ... with Neumaier's compensated summation (the
+// rounding error of every addition is carried in a second accumulator),
+// then a tree over the 256 threads on (sum, compensation) pairs.
+struct KSum {
+    double s, c;
+};
+
+__device__ __forceinline__ KSum ksum_add(KSum a, double x) {
+    const double t = a.s + x;
+    const double e = (fabs(a.s) >= fabs(x)) ? (a.s - t) + x : (x - t) + a.s;
+    return {t, a.c + e};
+}
+
+__device__ __forceinline__ KSum ksum_merge(KSum a, KSum b) {
+    KSum r = ksum_add(a, b.s);
+    r.c += b.c;
+    return r;
+}
+
 __global__ void k_reduce_partials(const double *partials, int nblocks, double base_E, double *totals) {
-    __shared__ double red[3][256];
+    __shared__ KSum red[3][256];
     const int t = threadIdx.x;
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int i = t; i < nblocks; i += 256) {
-        a += partials[3 * i + 0];
-        b += partials[3 * i + 1];
-        c += partials[3 * i + 2];
-    }
-    red[0][t] = a;
-    red[1][t] = b;
-    red[2][t] = c;
+    KSum a[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    for (int i = t; i < nblocks; i += 256)
+        for (int j = 0; j < 3; ++j) a[j] = ksum_add(a[j], partials[3 * i + j]);
+    for (int j = 0; j < 3; ++j) red[j][t] = a[j];
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
-        if (t < h) {
-            red[0][t] += red[0][t + h];
-            red[1][t] += red[1][t + h];
-            red[2][t] += red[2][t + h];
-        }
+        if (t < h)
+            for (int j = 0; j < 3; ++j) red[j][t] = ksum_merge(red[j][t], red[j][t + h]);
         __syncthreads();
     }
     if (t == 0) {
-        totals[0] = base_E + red[0][0];
-        totals[1] = red[1][0];
-        totals[2] = red[2][0];
+        const KSum e = ksum_add(red[0][0], base_E);
+        totals[0] = e.s + e.c;
+        totals[1] = red[1][0].s + red[1][0].c;
+        totals[2] = red[2][0].s + red[2][0].c;
     }
 }
 

@@ -7,23 +7,36 @@
 
 namespace rlbk {
 
-// Fixed-order FP64 reduction of the 4-wide block partials.
+// Fixed-order FP64 reduction of the 4-wide block partials, with Neumaier's
+// compensated summation (error of each addition carried separately).
+__device__ __forceinline__ void ksum4_add(double &s, double &c, double x) {
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
 __global__ void k_reduce_partials4(const double *partials, long long nblocks, double base_E, double *totals) {
-    __shared__ double red[4][256];
+    __shared__ double rs[4][256], rc[4][256];
     const int t = threadIdx.x;
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    double s[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0};
     for (long long i = t; i < nblocks; i += 256)
-        for (int j = 0; j < 4; ++j) a[j] += partials[4 * i + j];
-    for (int j = 0; j < 4; ++j) red[j][t] = a[j];
+        for (int j = 0; j < 4; ++j) ksum4_add(s[j], c[j], partials[4 * i + j]);
+    for (int j = 0; j < 4; ++j) {
+        rs[j][t] = s[j];
+        rc[j][t] = c[j];
+    }
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
         if (t < h)
-            for (int j = 0; j < 4; ++j) red[j][t] += red[j][t + h];
+            for (int j = 0; j < 4; ++j) {
+                ksum4_add(rs[j][t], rc[j][t], rs[j][t + h]);
+                rc[j][t] += rc[j][t + h];
+            }
         __syncthreads();
     }
     if (t == 0) {
-        totals[0] = base_E + red[0][0];
-        for (int j = 1; j < 4; ++j) totals[j] = red[j][0];
+        ksum4_add(rs[0][0], rc[0][0], base_E);
+        for (int j = 0; j < 4; ++j) totals[j] = rs[j][0] + rc[j][0];
     }
 }
 
