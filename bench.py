@@ -41,6 +41,7 @@ METRIC = "GLUPS of the fused stream-collide step (and fraction of HBM peak)"
 # and the FP64 peak derived from the unit count and clock (152 SMs x 2 FP64
 # FMA per clock x 2 flops x 2.07 GHz).
 FP64_FLOPS_PER_NODE = 627.0
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e nominal, for context beside the measured copy bandwidth
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
@@ -549,6 +550,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_node": bpn,
+                     "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
                      "kernel_ms": kernel_ms, "epoch_steps_in_timed_region": n_epoch},
         "clocks": clocks.summary(),
         "gpu_launches": int(K + 2 * n_epoch),
