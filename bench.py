@@ -309,7 +309,15 @@ def measure_variants(torch, rl, oracle, flush, hbm_peak, steps=50, warmup=5):
     cases = (("ring8_1024x1024_f32", lambda: rl.Lattice(1024, 1024, w.tau, dtype="f32", forcing=fz, stencil="ring8"),
               1024 * 1024),
              ("lattice3d_256x256x256_f32", lambda: rl.Lattice3D(256, 256, 256, w.tau, dtype="f32", forcing=fz),
-              256 ** 3))
+              256 ** 3),
+             # the paper's own time step on its lattice spacings 0.08 and 0.04 (Sec. 5): cfl 0.625 and
+             # 1.25, relaxation from eta/s = 0.01 and the local temperature
+             ("paper_cfl0.625_eta0.01_1024x1024_f32",
+              lambda: rl.Lattice(1024, 1024, w.tau, dtype="f32", forcing=fz, cfl=0.625, eta_s=0.01, dt=0.05),
+              1024 * 1024),
+             ("paper_cfl1.25_eta0.01_1024x1024_f32",
+              lambda: rl.Lattice(1024, 1024, w.tau, dtype="f32", forcing=fz, cfl=1.25, eta_s=0.01, dt=0.05),
+              1024 * 1024))
     for name, make, nodes in cases:
         lat = make()
         lat.init_fields()
@@ -323,6 +331,7 @@ def measure_variants(torch, rl, oracle, flush, hbm_peak, steps=50, warmup=5):
         bp = int(info["bytes_per_node"])
         out[name] = {"glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_node": bp,
                      "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak,
+                     "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]],
                      "block": [info["block_x"], info["block_y"]]}
     # parity on small cases (FP32 against the FP64 oracles)
     n, nsteps = 64, 50

@@ -108,7 +108,8 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * again and writes its update), so no thread keeps all 17 populations live
  * across the Landau solve: about half the registers, twice the resident
  * warps; same conditions as PACKED.
- * The vector, packed, TMA and two-pass variants stream at CFL 1 only.
+ * The vector, TMA and two-pass variants stream at CFL 1 only, the packed
+ * kernel at cfl <= 1.
  * AUTO: the autotuned choice if one is cached for this lattice, else
  * GATHER. */
 typedef enum {
@@ -161,7 +162,8 @@ typedef struct {
      * cells around x - cfl v_i (Sec. 3.2, Sec. 5: Delta t = 0.05 on lattice
      * spacings 0.32, 0.16, 0.08, 0.04, i.e. cfl 0.156 ... 1.25).  cfl > 1
      * reaches two cells (halo 2) for the classes with cfl |v_i,a| > 1.
-     * cfl != 1 uses the one-node-per-thread kernel (RLBM_KERNEL_GATHER). */
+     * cfl < 1 runs the one-node-per-thread (GATHER) or the packed kernel
+     * (PACKED); cfl > 1 the GATHER kernel. */
     double cfl;
     /* eta/s > 0 switches the relaxation time to the paper's
      * tau_R = 5 (eta/s) / T with eps = 3 T^4 / pi^2 (Sec. 3.1-3.2), node by

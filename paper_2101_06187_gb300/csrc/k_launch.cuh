@@ -21,9 +21,11 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
     const dim3 block(cfg.bx, cfg.by, 1);
     if ((cfg.kernel == RLBM_KERNEL_GATHER_VEC || cfg.kernel == RLBM_KERNEL_GATHER_VEC2 ||
-         cfg.kernel == RLBM_KERNEL_PACKED || cfg.kernel == RLBM_KERNEL_TWOPASS) &&
+         cfg.kernel == RLBM_KERNEL_TWOPASS) &&
         p.cfl != 1.0)
         return cudaErrorInvalidValue;  // the vector kernels stream at CFL 1 only
+    if (cfg.kernel == RLBM_KERNEL_PACKED && !(p.cfl <= 1.0))
+        return cudaErrorInvalidValue;  // the packed kernel streams at cfl <= 1
     if (cfg.kernel == RLBM_KERNEL_TWOPASS) {
         if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
             if (p.nx % 2 != 0) return cudaErrorInvalidValue;
@@ -47,6 +49,25 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
             if (p.nx % 2 != 0) return cudaErrorInvalidValue;
             const dim3 grid((p.nx / 2 + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
             const bool idx32p = (long long)NC * p.plane < (1ll << 31) - 1;
+            if (p.cfl != 1.0) {  // 0 < cfl < 1: runtime weights; budgets 1 (unconstrained) and 2 (<= 128 registers)
+#define RLBM_PAIR_SUB(MB)                                                                                   \
+    do {                                                                                                    \
+        if (idx32p) {                                                                                       \
+            if (forced) k_step_pair<TS, true, MB, int, kStreamSub1><<<grid, block, 0, s>>>(in, out, f, p);  \
+            else k_step_pair<TS, false, MB, int, kStreamSub1><<<grid, block, 0, s>>>(in, out, f, p);        \
+        } else {                                                                                            \
+            if (forced) k_step_pair<TS, true, MB, long long, kStreamSub1><<<grid, block, 0, s>>>(in, out, f, p); \
+            else k_step_pair<TS, false, MB, long long, kStreamSub1><<<grid, block, 0, s>>>(in, out, f, p);  \
+        }                                                                                                   \
+    } while (0)
+                if (cfg.minb == 1) RLBM_PAIR_SUB(1);
+                else {
+                    if (cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
+                    RLBM_PAIR_SUB(2);
+                }
+#undef RLBM_PAIR_SUB
+                return cudaGetLastError();
+            }
 #define RLBM_PAIR(MB)                                                                          \
     do {                                                                                       \
         if (idx32p) {                                                                          \

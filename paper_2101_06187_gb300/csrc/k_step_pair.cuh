@@ -1,7 +1,7 @@
 // k_step_pair.cuh -- fused stream + collide + force step for two x-adjacent
 // nodes per thread whose whole arithmetic runs in packed FP32 lanes
 // (packed.cuh): one instruction advances both nodes.  FP32 compute (FP32,
-// BF16, FP16 storage), FP32 Landau solve, CFL 1, nx even.
+// BF16, FP16 storage), FP32 Landau solve, 0 < cfl <= 1, nx even.
 #pragma once
 
 #include "k_step_vec.cuh"
@@ -11,8 +11,11 @@ namespace rlbk {
 
 // The fused step of the node pair (x0, x0 + 1) of row y in packed lanes.
 // I is the index type of the element offsets: 32-bit when all 17 planes fit,
-// so each load address is one 32-bit sum and one widening add.
-template <typename TS, bool FORCED, typename I = long long>
+// so each load address is one 32-bit sum and one widening add.  SM is the
+// streaming mode: kStreamCfl1 (corners and weights fixed at compile time)
+// or kStreamSub1 (0 < cfl < 1: each moving class interpolates between the
+// cell it streams from and its own, with the launch's per-class weights).
+template <typename TS, bool FORCED, typename I = long long, int SM = kStreamCfl1>
 __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
                                           const float *__restrict__ F, const StepParams &p, int x0, int y) {
     const int ym = (y == 0) ? p.ny - 1 : y - 1;
@@ -34,16 +37,43 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
             if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[3] = load_q<TS, float>(qin + (base + (I)xr));
         };
         float a[4];  // columns x0-1 .. x0+2
-        row(rowoff[oy + 1], a);
-        pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
-        if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
-        if constexpr (ty != 0.0) {
-            float b[4];
-            row(rowoff[oy + 2], b);
-            v = fmadd(pf2((float)((1.0 - tx) * ty)), pf2(b[ox + 1], b[ox + 2]), v);
-            if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
+        if constexpr (SM == kStreamCfl1) {
+            row(rowoff[oy + 1], a);
+            pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
+            if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
+            if constexpr (ty != 0.0) {
+                float b[4];
+                row(rowoff[oy + 2], b);
+                v = fmadd(pf2((float)((1.0 - tx) * ty)), pf2(b[ox + 1], b[ox + 2]), v);
+                if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
+            }
+            q[c] = v;
+        } else {
+            // near corner (the class's own cell on an axis where it does not move)
+            constexpr double cx = cls_cx(c), cy = cls_cy(c);
+            constexpr int nx_ = cx > 0 ? -1 : 0, ny_ = cy > 0 ? -1 : 0;
+            constexpr bool mx = cx != 0.0, my = cy != 0.0;
+            auto row2 = [&](I r, float (&d)[4]) {
+                const I base = (I)c * plane + r;
+                load_run<TS, float, 2>(qin + (base + (I)x0), &d[1]);
+                if constexpr (mx && nx_ == -1) d[0] = load_q<TS, float>(qin + (base + (I)xl));
+                if constexpr (mx && nx_ == 0) d[3] = load_q<TS, float>(qin + (base + (I)xr));
+            };
+            row2(rowoff[ny_ + 1], a);
+            if constexpr (!mx && !my) {
+                q[c] = pf2(a[1], a[2]);
+            } else {
+                pf2 v = pf2(par_wt<float>(p, c, 0)) * pf2(a[nx_ + 1], a[nx_ + 2]);
+                if constexpr (mx) v = fmadd(pf2(par_wt<float>(p, c, 1)), pf2(a[nx_ + 2], a[nx_ + 3]), v);
+                if constexpr (my) {
+                    float b[4];
+                    row2(rowoff[ny_ + 2], b);
+                    v = fmadd(pf2(par_wt<float>(p, c, 2)), pf2(b[nx_ + 1], b[nx_ + 2]), v);
+                    if constexpr (mx) v = fmadd(pf2(par_wt<float>(p, c, 3)), pf2(b[nx_ + 2], b[nx_ + 3]), v);
+                }
+                q[c] = v;
+            }
         }
-        q[c] = v;
     });
 
     const I n0 = rowoff[1] + (I)x0;
@@ -148,13 +178,13 @@ __global__ void __launch_bounds__(256, MINB) k_step_pair2(const TS *__restrict__
 // autotuner can trade registers for occupancy.
 // MINB 5: blocks of at most 128 threads, five resident per SM (at most 102
 // registers per thread: 20 warps per SM).
-template <typename TS, bool FORCED, int MINB, typename I = long long>
+template <typename TS, bool FORCED, int MINB, typename I = long long, int SM = kStreamCfl1>
 __global__ void __launch_bounds__(MINB == 5 ? 128 : 256, MINB)
     k_step_pair(const TS *__restrict__ qin, TS *__restrict__ qout, const float *__restrict__ F, StepParams p) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= p.nx || y >= p.ny) return;
-    step_pair<TS, FORCED, I>(qin, qout, F, p, x0, y);
+    step_pair<TS, FORCED, I, SM>(qin, qout, F, p, x0, y);
 }
 
 // Ensemble step with the packed body (see k_step_batch).
