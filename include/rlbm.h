@@ -109,7 +109,7 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * across the Landau solve: about half the registers, twice the resident
  * warps; same conditions as PACKED.
  * The vector, TMA and two-pass variants stream at CFL 1 only, the packed
- * kernel at cfl <= 1.
+ * kernel at any cfl (halo 2 above 1).
  * AUTO: the autotuned choice if one is cached for this lattice, else
  * GATHER. */
 typedef enum {
@@ -162,8 +162,8 @@ typedef struct {
      * cells around x - cfl v_i (Sec. 3.2, Sec. 5: Delta t = 0.05 on lattice
      * spacings 0.32, 0.16, 0.08, 0.04, i.e. cfl 0.156 ... 1.25).  cfl > 1
      * reaches two cells (halo 2) for the classes with cfl |v_i,a| > 1.
-     * cfl < 1 runs the one-node-per-thread (GATHER) or the packed kernel
-     * (PACKED); cfl > 1 the GATHER kernel. */
+     * cfl != 1 runs the one-node-per-thread (GATHER) or the packed kernel
+     * (PACKED). */
     double cfl;
     /* eta/s > 0 switches the relaxation time to the paper's
      * tau_R = 5 (eta/s) / T with eps = 3 T^4 / pi^2 (Sec. 3.1-3.2), node by

@@ -24,8 +24,6 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
          cfg.kernel == RLBM_KERNEL_TWOPASS) &&
         p.cfl != 1.0)
         return cudaErrorInvalidValue;  // the vector kernels stream at CFL 1 only
-    if (cfg.kernel == RLBM_KERNEL_PACKED && !(p.cfl <= 1.0))
-        return cudaErrorInvalidValue;  // the packed kernel streams at cfl <= 1
     if (cfg.kernel == RLBM_KERNEL_TWOPASS) {
         if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value) {
             if (p.nx % 2 != 0) return cudaErrorInvalidValue;
@@ -49,21 +47,27 @@ cudaError_t launch_step_t(const LaunchCfg &cfg, bool forced, const void *qin, vo
             if (p.nx % 2 != 0) return cudaErrorInvalidValue;
             const dim3 grid((p.nx / 2 + cfg.bx - 1) / cfg.bx, (p.ny + cfg.by - 1) / cfg.by, 1);
             const bool idx32p = (long long)NC * p.plane < (1ll << 31) - 1;
-            if (p.cfl != 1.0) {  // 0 < cfl < 1: runtime weights; budgets 1 (unconstrained) and 2 (<= 128 registers)
-#define RLBM_PAIR_SUB(MB)                                                                                   \
-    do {                                                                                                    \
-        if (idx32p) {                                                                                       \
-            if (forced) k_step_pair<TS, true, MB, int, kStreamSub1><<<grid, block, 0, s>>>(in, out, f, p);  \
-            else k_step_pair<TS, false, MB, int, kStreamSub1><<<grid, block, 0, s>>>(in, out, f, p);        \
-        } else {                                                                                            \
-            if (forced) k_step_pair<TS, true, MB, long long, kStreamSub1><<<grid, block, 0, s>>>(in, out, f, p); \
-            else k_step_pair<TS, false, MB, long long, kStreamSub1><<<grid, block, 0, s>>>(in, out, f, p);  \
-        }                                                                                                   \
+            if (p.cfl != 1.0) {
+                // runtime weights (0 < cfl < 1) or halo 2 (1 < cfl < 2); budgets 1 (unconstrained)
+                // and 2 (<= 128 registers)
+#define RLBM_PAIR_SUB(MB, SMV)                                                                         \
+    do {                                                                                               \
+        if (idx32p) {                                                                                  \
+            if (forced) k_step_pair<TS, true, MB, int, SMV><<<grid, block, 0, s>>>(in, out, f, p);     \
+            else k_step_pair<TS, false, MB, int, SMV><<<grid, block, 0, s>>>(in, out, f, p);           \
+        } else {                                                                                       \
+            if (forced) k_step_pair<TS, true, MB, long long, SMV><<<grid, block, 0, s>>>(in, out, f, p); \
+            else k_step_pair<TS, false, MB, long long, SMV><<<grid, block, 0, s>>>(in, out, f, p);     \
+        }                                                                                              \
     } while (0)
-                if (cfg.minb == 1) RLBM_PAIR_SUB(1);
-                else {
+                const bool halo2 = stream_mode(p.cfl) == kStreamHalo2;
+                if (cfg.minb == 1) {
+                    if (halo2) RLBM_PAIR_SUB(1, kStreamHalo2);
+                    else RLBM_PAIR_SUB(1, kStreamSub1);
+                } else {
                     if (cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
-                    RLBM_PAIR_SUB(2);
+                    if (halo2) RLBM_PAIR_SUB(2, kStreamHalo2);
+                    else RLBM_PAIR_SUB(2, kStreamSub1);
                 }
 #undef RLBM_PAIR_SUB
                 return cudaGetLastError();

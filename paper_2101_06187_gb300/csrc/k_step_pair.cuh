@@ -1,7 +1,7 @@
 // k_step_pair.cuh -- fused stream + collide + force step for two x-adjacent
 // nodes per thread whose whole arithmetic runs in packed FP32 lanes
 // (packed.cuh): one instruction advances both nodes.  FP32 compute (FP32,
-// BF16, FP16 storage), FP32 Landau solve, 0 < cfl <= 1, nx even.
+// BF16, FP16 storage), FP32 Landau solve, 0 < cfl < 2, nx even.
 #pragma once
 
 #include "k_step_vec.cuh"
@@ -12,9 +12,13 @@ namespace rlbk {
 // The fused step of the node pair (x0, x0 + 1) of row y in packed lanes.
 // I is the index type of the element offsets: 32-bit when all 17 planes fit,
 // so each load address is one 32-bit sum and one widening add.  SM is the
-// streaming mode: kStreamCfl1 (corners and weights fixed at compile time)
-// or kStreamSub1 (0 < cfl < 1: each moving class interpolates between the
-// cell it streams from and its own, with the launch's per-class weights).
+// streaming mode: kStreamCfl1 (corners and weights fixed at compile time),
+// kStreamSub1 (0 < cfl < 1: each moving class interpolates between the
+// cell it streams from and its own, with the launch's per-class weights) or
+// kStreamHalo2 (1 < cfl < 2: the corner of an axis with cfl |c| > 1 lies two
+// cells away; each x-moving class row is read as the two aligned column
+// pairs that cover both candidate corners, and a register select picks the
+// launch's corner).
 template <typename TS, bool FORCED, typename I = long long, int SM = kStreamCfl1>
 __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
                                           const float *__restrict__ F, const StepParams &p, int x0, int y) {
@@ -24,6 +28,19 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
     const int xr = (x0 + 2 == p.nx) ? 0 : x0 + 2;
     const I rowoff[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
     const I plane = (I)p.plane;
+    [[maybe_unused]] I rowoff5[5];
+    [[maybe_unused]] int xl2 = 0, xr2 = 0;
+    if constexpr (SM == kStreamHalo2) {
+        const int ym2 = (ym == 0) ? p.ny - 1 : ym - 1;
+        const int yp2 = (yp == p.ny - 1) ? 0 : yp + 1;
+        rowoff5[0] = (I)ym2 * (I)p.pitch;
+        rowoff5[1] = rowoff[0];
+        rowoff5[2] = rowoff[1];
+        rowoff5[3] = rowoff[2];
+        rowoff5[4] = (I)yp2 * (I)p.pitch;
+        xl2 = (x0 == 0) ? p.nx - 2 : x0 - 2;  // the aligned pair (x0-2, x0-1), periodic (nx even)
+        xr2 = (x0 + 2 == p.nx) ? 0 : x0 + 2;  // the aligned pair (x0+2, x0+3)
+    }
 
     pf2 q[NC];
     static_for<0, NC>([&](auto C) {
@@ -36,8 +53,8 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
             if constexpr (ox == -1) a[0] = load_q<TS, float>(qin + (base + (I)xl));
             if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[3] = load_q<TS, float>(qin + (base + (I)xr));
         };
-        float a[4];  // columns x0-1 .. x0+2
         if constexpr (SM == kStreamCfl1) {
+            float a[4];  // columns x0-1 .. x0+2
             row(rowoff[oy + 1], a);
             pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
             if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
@@ -48,6 +65,50 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
                 if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
             }
             q[c] = v;
+        } else if constexpr (SM == kStreamHalo2) {
+            constexpr double cx = cls_cx(c), cy = cls_cy(c);
+            constexpr int nx_ = cx > 0 ? -1 : 0, ny_ = cy > 0 ? -1 : 0;  // near corner
+            constexpr int fy = cy > 0 ? -1 : 1;                              // step to the far row
+            constexpr bool mx = cx != 0.0, my = cy != 0.0;
+            const bool farx = mx && ((p.far_x >> c) & 1u);
+            const bool fary = my && ((p.far_y >> c) & 1u);
+            // the three columns of the pair's bilinear taps: near or far corner
+            auto row3 = [&](I r, float (&t)[3]) {
+                const I base = (I)c * plane + r;
+                float mid[2], side[2];
+                load_run<TS, float, 2>(qin + (base + (I)x0), mid);
+                if constexpr (!mx) {
+                    t[0] = mid[0];
+                    t[1] = mid[1];
+                } else if constexpr (nx_ == -1) {  // columns x0-2 .. x0+1
+                    load_run<TS, float, 2>(qin + (base + (I)xl2), side);
+                    t[0] = farx ? side[0] : side[1];
+                    t[1] = farx ? side[1] : mid[0];
+                    t[2] = farx ? mid[0] : mid[1];
+                } else {  // columns x0 .. x0+3
+                    load_run<TS, float, 2>(qin + (base + (I)xr2), side);
+                    t[0] = farx ? mid[1] : mid[0];
+                    t[1] = farx ? side[0] : mid[1];
+                    t[2] = farx ? side[1] : side[0];
+                }
+            };
+            const I ra = fary ? rowoff5[ny_ + fy + 2] : rowoff5[ny_ + 2];
+            float t[3];
+            row3(ra, t);
+            if constexpr (!mx && !my) {
+                q[c] = pf2(t[0], t[1]);
+            } else {
+                pf2 v = pf2(par_wt<float>(p, c, 0)) * pf2(t[0], t[1]);
+                if constexpr (mx) v = fmadd(pf2(par_wt<float>(p, c, 1)), pf2(t[1], t[2]), v);
+                if constexpr (my) {
+                    const I rb = fary ? rowoff5[ny_ + fy + 3] : rowoff5[ny_ + 3];
+                    float u[3];
+                    row3(rb, u);
+                    v = fmadd(pf2(par_wt<float>(p, c, 2)), pf2(u[0], u[1]), v);
+                    if constexpr (mx) v = fmadd(pf2(par_wt<float>(p, c, 3)), pf2(u[1], u[2]), v);
+                }
+                q[c] = v;
+            }
         } else {
             // near corner (the class's own cell on an axis where it does not move)
             constexpr double cx = cls_cx(c), cy = cls_cy(c);
@@ -59,6 +120,7 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
                 if constexpr (mx && nx_ == -1) d[0] = load_q<TS, float>(qin + (base + (I)xl));
                 if constexpr (mx && nx_ == 0) d[3] = load_q<TS, float>(qin + (base + (I)xr));
             };
+            float a[4];  // columns x0-1 .. x0+2
             row2(rowoff[ny_ + 1], a);
             if constexpr (!mx && !my) {
                 q[c] = pf2(a[1], a[2]);

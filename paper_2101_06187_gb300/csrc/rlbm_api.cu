@@ -444,7 +444,6 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2 ||
                          o.kernel == RLBM_KERNEL_TMA || o.kernel == RLBM_KERNEL_TWOPASS))
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
-    if (o.cfl > 1.0 && o.kernel == RLBM_KERNEL_PACKED) return RLBM_ERR_ARG;  // the packed kernel: cfl <= 1
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
     if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER && o.kernel != RLBM_KERNEL_PACKED) ||
@@ -1030,7 +1029,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     for (const LaunchCfg &c : kCandidates) {
         if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
         if (h->opts.cfl != 1.0 && c.kernel != RLBM_KERNEL_GATHER &&
-            !(c.kernel == RLBM_KERNEL_PACKED && h->opts.cfl < 1.0 && c.minb <= 2 && !h->ring && !h->d3))
+            !(c.kernel == RLBM_KERNEL_PACKED && c.minb <= 2 && !h->ring && !h->d3))
             continue;
         if ((h->d3 || h->ring) && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED) continue;
         if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) continue;

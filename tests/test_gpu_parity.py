@@ -301,8 +301,6 @@ def test_cfl_and_eta_over_s_match_oracle(dtype, kernel, cfl, eta_s):
     dt = 0.05
     fields = workloads.random_smooth(nx, ny, seed=61, deps=0.05, vmax=0.05)
     forcing = dict(kmin=2, kmax=4, amp=2e-4, seed=17, redraw_period=9)
-    if kernel == "packed" and cfl > 1.0:
-        pytest.skip("the packed kernel streams at cfl <= 1")
     lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, forcing=forcing, cfl=cfl, eta_s=eta_s, dt=dt, kernel=kernel)
     assert lat.info()["kernel"] == rl.KERNELS[kernel]
     lat.init_fields(*fields)
