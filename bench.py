@@ -54,7 +54,10 @@ def parse():
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--landau", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2", "packed", "tma", "twopass"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2", "packed", "tma", "twopass",
+                                                               "fused2"])
+    ap.add_argument("--launch", default="", metavar="KERNEL,BX,BY,BUDGET",
+                    help="pin one launch shape of the autotuner's list instead of tuning (profiling runs)")
     ap.add_argument("--n", type=int, default=0, help="override lattice side (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-form table, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
@@ -78,6 +81,8 @@ def dist_env():
 _STEP_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_gather.cuh", "k_step_vec.cuh", "k_step_pair.cuh",
                  "k_launch.cuh", "k_step_f32.cu", "k_step_f64.cu", "k_step_h16.cu")
 _TMA_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_tma.cuh", "k_step_tma.cu")
+_FUSED2_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_pair.cuh", "k_step_fused2.cuh",
+                   "k_step_fused2.cu")
 
 
 def step_kernel_source_hash(kernel_id=4):
@@ -86,7 +91,7 @@ def step_kernel_source_hash(kernel_id=4):
     order: a stored DRAM-traffic figure counts only while it matches."""
     import hashlib
     src = os.path.join(ROOT, "paper_2101_06187_gb300", "csrc")
-    files = _TMA_SOURCES if kernel_id == 5 else _STEP_SOURCES
+    files = {5: _TMA_SOURCES, 7: _FUSED2_SOURCES}.get(kernel_id, _STEP_SOURCES)
     hsh = hashlib.sha256()
     for fn in sorted(files):
         with open(os.path.join(src, fn), "rb") as fh:
@@ -185,25 +190,39 @@ class L2Flush:
         self.sink.copy_(self.r.sum())
 
 
-def time_steps(torch, lat, steps, flush):
-    """Per-step CUDA-event timing on the lattice stream with an L2 flush in between."""
+def launch_units(lat, steps):
+    """Split `steps` into the step counts of single launches of the chosen
+    kernel: 2 for a two-step kernel (an odd remainder is a single step)."""
+    spl = max(1, int(lat.info()["steps_per_launch"]))
+    return [spl] * (steps // spl) + ([steps % spl] if steps % spl else [])
+
+
+def time_steps(torch, lat, steps, flush, with_units=False):
+    """CUDA-event timing on the lattice stream of each launch (one step, or
+    two for a two-step kernel) with an L2 flush in between.  Returns the
+    time of every step in ms (a launch's time shared by its steps) and, with
+    with_units, the launch unit of every step."""
     stream = lat._torch_stream
+    sizes = launch_units(lat, steps)
     evs = []
     with torch.cuda.stream(stream):
-        for _ in range(steps):
+        for size in sizes:
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             flush()
             a.record(stream)
-            lat.step(1)
+            lat.step(size)
             b.record(stream)
             evs.append((a, b))
     stream.synchronize()
-    return np.array([a.elapsed_time(b) for a, b in evs])  # ms
+    ms = np.concatenate([np.full(size, a.elapsed_time(b) / size) for (a, b), size in zip(evs, sizes)])
+    if not with_units:
+        return ms
+    return ms, np.repeat(np.arange(len(sizes)), sizes)
 
 
 def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, init=None, tune=True, stencil="sph26",
-                 nz=0):
+                 nz=0, launch=""):
     if nz > 0:
         lat = rl.Lattice3D(n, n, nz, w.tau, dtype=form, landau=landau, kernel=kernel, forcing=forcing_of(w))
     else:
@@ -212,19 +231,27 @@ def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, in
         lat.init_fields(*init)
     else:
         lat.init_fields()
-    if tune:
+    if launch:
+        k, bx, by, budget = launch.split(",")
+        lat.set_launch(k, int(bx), int(by), int(budget))
+    elif tune:
         lat.autotune(10)
+    spl = int(lat.info()["steps_per_launch"])
+    warmup += (-warmup) % spl  # timed launches start on a launch boundary (epochs are 100 steps)
     lat.step(warmup)
     lat.synchronize()
-    ms = time_steps(torch, lat, steps, flush)
+    ms, unit = time_steps(torch, lat, steps, flush, with_units=True)
     info = lat.info()
-    # steps that started a forcing epoch also carry the force re-synthesis
+    info["timed_launches"] = int(unit[-1]) + 1 if len(unit) else 0
+    # launches that started a forcing epoch also carry the force re-synthesis
     redraw = w.redraw
     first = warmup
-    is_epoch = np.array([((first + i) % redraw) == 0 for i in range(steps)])
+    starts = np.array([((first + i) % redraw) == 0 for i in range(steps)])
+    epoch_units = set(unit[starts].tolist())
+    is_epoch = np.isin(unit, list(epoch_units))
     kernel_ms = ms[~is_epoch].mean() if (~is_epoch).any() else ms.mean()
     lat.close()
-    return ms, kernel_ms, info, int(is_epoch.sum())
+    return ms, kernel_ms, info, len(epoch_units)
 
 
 def measure_ensemble(torch, rl, flush, steps=20, warmup=5, nruns=64, sides=None):
@@ -519,7 +546,8 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(smi_index) as clocks:
         ms, kernel_ms, info, n_epoch = measure_form(torch, rl, w, n, args.form, args.landau, args.kernel, K, W, flush,
-                                                    tune=not args.no_tune, stencil=args.stencil, nz=args.nz)
+                                                    tune=not args.no_tune, stencil=args.stencil, nz=args.nz,
+                                                    launch=args.launch)
     torch.cuda.synchronize()
     step_ms = float(ms.mean())
     nodes = n * n * max(1, args.nz)
@@ -560,9 +588,11 @@ def main():
                      "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_node": bpn,
                      "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
-                     "kernel_ms": kernel_ms, "epoch_steps_in_timed_region": n_epoch},
+                     "kernel_ms": kernel_ms, "steps_per_launch": int(info["steps_per_launch"]),
+                     "launch_ms": kernel_ms * int(info["steps_per_launch"]),
+                     "epoch_steps_in_timed_region": n_epoch},
         "clocks": clocks.summary(),
-        "gpu_launches": int(K + 2 * n_epoch),
+        "gpu_launches": int(info["timed_launches"] + 2 * n_epoch),
     }
     if args.form == "f64" and not variant:
         tf = FP64_FLOPS_PER_NODE * nodes / (kernel_ms / 1e3) / 1e12

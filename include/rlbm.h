@@ -108,8 +108,16 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * again and writes its update), so no thread keeps all 17 populations live
  * across the Landau solve: about half the registers, twice the resident
  * warps; same conditions as PACKED.
- * The vector, TMA and two-pass variants stream at CFL 1 only, the packed
- * kernel at any cfl (halo 2 above 1).
+ * FUSED2: two time steps per launch (temporal blocking): each CTA updates
+ * its tile plus a one-cell halo by one step into shared memory, then the
+ * tile by a second step from there, so the state crosses HBM once per two
+ * steps; the packed body, same conditions as PACKED.  Step counts are
+ * split into launch pairs inside each forcing epoch (the force is constant
+ * within one) and an odd remainder runs the packed single step; results
+ * equal those of PACKED bit for bit.  block_x x block_y of the launch shape
+ * is the output tile (64 x 16, 64 x 8 or 128 x 8 nodes).
+ * The vector, TMA, two-pass and two-step variants stream at CFL 1 only, the
+ * packed kernel at any cfl (halo 2 above 1).
  * AUTO: the autotuned choice if one is cached for this lattice, else
  * GATHER. */
 typedef enum {
@@ -119,7 +127,8 @@ typedef enum {
     RLBM_KERNEL_GATHER_VEC2 = 3,
     RLBM_KERNEL_PACKED = 4,
     RLBM_KERNEL_TMA = 5,
-    RLBM_KERNEL_TWOPASS = 6
+    RLBM_KERNEL_TWOPASS = 6,
+    RLBM_KERNEL_FUSED2 = 7
 } rlbm_kernel;
 
 /* Stirring force (Sec. 5).  Modes are the integer wavevectors k with
@@ -188,12 +197,14 @@ typedef struct {
     int nmodes;               /* forcing modes (0 = unforced) */
     int64_t step;             /* steps taken since init */
     double tau, eps0, scale;
-    size_t bytes_per_node;    /* algorithmic HBM bytes per lattice update */
+    size_t bytes_per_node;    /* algorithmic HBM bytes per lattice update (a two-step launch moves the
+                                 state once for two updates: half the single-step figure) */
     size_t device_bytes;      /* device memory held by the handle */
     const void *populations;  /* device pointer of the current state, [nclasses][nz][ny][pitch] of the storage type */
     int nz;                   /* layers: 1, or nz of a 3D lattice */
     int launch_budget;        /* register budget of the chosen launch: minimum resident 256-thread blocks
                                  per SM asked of the compiler (packed variants), CTAs per SM (TMA), else 1 */
+    int steps_per_launch;     /* lattice steps one launch of the chosen kernel advances: 2 (FUSED2) or 1 */
 } rlbm_info_t;
 
 /* Fill *opts with the defaults listed above. */
@@ -329,13 +340,25 @@ RLBM_API rlbm_status rlbm_get_force3d(rlbm_t *h, double *Fx, double *Fy, double 
 
 /* Time every launch configuration of the fused step (kernel variant and
  * thread-block shape) for `reps` launches each (reps < 1: 20) on the
- * handle's lattice and keep the fastest.  The trial launches read the
+ * handle's lattice and keep the fastest per lattice step (a two-step launch
+ * counts its time once for two steps).  The trial launches read the
  * current state and write only the spare buffer, so the simulation state is
- * unchanged.  The choice is cached per (nx, ny, dtype, landau, forced) for
- * handles created later in the process with RLBM_KERNEL_AUTO (separately
- * for each stencil).  Outputs may
+ * unchanged.  The choice is cached per (nx, ny, dtype, landau, forced,
+ * streaming mode) for handles created later in the process with
+ * RLBM_KERNEL_AUTO (separately for each stencil).  Outputs may
  * be NULL.  Synchronises. */
 RLBM_API rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *kernel, int *block_x, int *block_y);
+
+/* Pin the launch of the fused step to one of the configurations the
+ * autotuner tries: kernel variant (rlbm_kernel, not AUTO), block_x x
+ * block_y (the thread-block shape; the output tile for FUSED2) and
+ * launch_budget (as reported in rlbm_info_t).  A handle created for a
+ * fixed kernel accepts only that kernel.  One trial launch writes the spare
+ * buffer (the state is unchanged).  RLBM_ERR_ARG if the configuration is
+ * not on offer or does not fit the lattice (the handle stays usable).  Not
+ * part of the paper: a service for reproducible timing and for tests that
+ * cover every launch shape.  Synchronises. */
+RLBM_API rlbm_status rlbm_set_launch(rlbm_t *h, int kernel, int block_x, int block_y, int launch_budget);
 
 /* Allocation-free moments (no counterpart in the paper; a service for
  * callers that cannot allocate device memory, e.g. applications that run

@@ -30,7 +30,7 @@ RLBM_STENCIL_RING8_2D = 1
 STENCILS = {"sph26": RLBM_STENCIL_SPH26_SLAB, "ring8": RLBM_STENCIL_RING8_2D}
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 LANDAU = {"fp64": 0, "fp32": 1}
-KERNELS = {"auto": 0, "gather": 1, "vec": 2, "vec2": 3, "packed": 4, "tma": 5, "twopass": 6}
+KERNELS = {"auto": 0, "gather": 1, "vec": 2, "vec2": 3, "packed": 4, "tma": 5, "twopass": 6, "fused2": 7}
 NCLASSES = 17
 
 # Symbols declared in include/rlbm.h (checked by the ABI test).
@@ -43,6 +43,7 @@ EXPORTS = (
     "rlbm_batch_synchronize", "rlbm_batch_last_error", "rlbm_batch_destroy", "rlbm_filtered_velocity",
     "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset", "rlbm_create3d", "rlbm_init_fields3d",
     "rlbm_moments3d", "rlbm_get_force3d", "rlbm_checkpoint_size", "rlbm_checkpoint_save", "rlbm_checkpoint_load",
+    "rlbm_set_launch",
 )
 
 
@@ -75,7 +76,8 @@ class Info(ctypes.Structure):
                 ("block_y", ctypes.c_int), ("nmodes", ctypes.c_int),
                 ("step", ctypes.c_int64), ("tau", ctypes.c_double), ("eps0", ctypes.c_double),
                 ("scale", ctypes.c_double), ("bytes_per_node", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
-                ("populations", ctypes.c_void_p), ("nz", ctypes.c_int), ("launch_budget", ctypes.c_int)]
+                ("populations", ctypes.c_void_p), ("nz", ctypes.c_int), ("launch_budget", ctypes.c_int),
+                ("steps_per_launch", ctypes.c_int)]
 
 
 class RunDesc(ctypes.Structure):
@@ -160,6 +162,8 @@ def _load():
             getattr(lib, name).restype = ctypes.c_int
         lib.rlbm_autotune.argtypes = [h, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]
+        lib.rlbm_set_launch.argtypes = [h, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.rlbm_set_launch.restype = ctypes.c_int
         lib.rlbm_last_error.argtypes = [h, ctypes.c_char_p, ctypes.c_size_t]
         lib.rlbm_destroy.argtypes = [h]
         lib.rlbm_destroy.restype = None
@@ -355,6 +359,11 @@ def rlbm_autotune(h, reps: int = 20):
     _check(h, _load().rlbm_autotune(h, int(reps), ctypes.byref(k), ctypes.byref(bx), ctypes.byref(by)),
            "rlbm_autotune")
     return k.value, bx.value, by.value
+
+
+def rlbm_set_launch(h, kernel: int, block_x: int, block_y: int, launch_budget: int):
+    _check(h, _load().rlbm_set_launch(h, int(kernel), int(block_x), int(block_y), int(launch_budget)),
+           "rlbm_set_launch")
 
 
 def rlbm_moments_static(dtype: int, d_q: int, nx: int, ny: int, pitch: int, eps0: float, scale: float,
@@ -614,6 +623,10 @@ class Lattice:
     def autotune(self, reps: int = 20):
         """Pick the fastest launch configuration of the fused step (state unchanged)."""
         return rlbm_autotune(self.handle, reps)
+
+    def set_launch(self, kernel: str, block_x: int, block_y: int, launch_budget: int):
+        """Pin the fused step to one of the autotuner's launch configurations."""
+        rlbm_set_launch(self.handle, KERNELS[kernel], block_x, block_y, launch_budget)
 
     def synchronize(self):
         rlbm_synchronize(self.handle)

@@ -1,0 +1,169 @@
+// k_step_fused2.cuh -- two time steps per launch (temporal blocking) of the
+// fused stream + collide + force update, in packed FP32 lanes.
+//
+// A CTA owns a TW x TH tile of output nodes.  Step t -> t+1 is computed on
+// the tile grown by the one-cell pull halo of the next step (Sec. 3.2: at
+// CFL 1 a class pulls from the 3 x 3 neighbourhood), i.e. on (TW + 4) x
+// (TH + 2) nodes -- two extra columns a side, so every node pair starts on
+// an even column and loads stay 8-byte aligned -- and kept in shared memory
+// in the storage type; step t+1 -> t+2 then pulls from shared memory and
+// writes the tile.  Per two steps the state is read from and written to HBM
+// once: half the traffic of two single-step launches, for about 10% more
+// arithmetic (the halo nodes are updated by every tile that needs them).
+// Both steps run the same per-node arithmetic as k_step_pair at CFL 1, and
+// the intermediate state is rounded to the storage type exactly as a
+// single step stores it, so two steps here equal two single steps bit for
+// bit.  The force field is the same for both steps: the host launches this
+// kernel only for step pairs inside one forcing epoch.
+#pragma once
+
+#include "k_step_pair.cuh"
+
+namespace rlbk {
+
+// Shared-memory reads of the storage type (no read-only-cache path there).
+template <typename TS>
+__device__ __forceinline__ void lds_run2(const TS *p, float *o) {
+    if constexpr (std::is_same<TS, float>::value) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    } else if constexpr (std::is_same<TS, __half>::value) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    } else {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+}
+template <typename TS>
+__device__ __forceinline__ float lds1(const TS *p) {
+    if constexpr (std::is_same<TS, float>::value) return *p;
+    else if constexpr (std::is_same<TS, __half>::value) return __half2float(*p);
+    else return __bfloat162float(*p);
+}
+
+// CFL-1 pull of the node pair (x0, x0 + 1) from a state laid out as NC
+// planes of `plane` elements: rows[k] is the offset of row y - 1 + k, xl and
+// xr the columns x0 - 1 and x0 + 2.  SHARED selects shared-memory reads.
+// The same taps, weights and operation order as step_pair at CFL 1.
+template <typename TS, typename I, bool SHARED>
+__device__ __forceinline__ void pull_pair_cfl1(const TS *__restrict__ src, I plane, const I (&rows)[3], I x0, I xl,
+                                               I xr, pf2 (&q)[NC]) {
+    static_for<0, NC>([&](auto C) {
+        constexpr int c = decltype(C)::value;
+        constexpr int ox = cls_ox(c), oy = cls_oy(c);
+        constexpr double tx = cls_tx(c), ty = cls_ty(c);
+        auto row = [&](I r, float (&a)[4]) {
+            const TS *base = src + ((I)c * plane + r);
+            if constexpr (SHARED) {
+                lds_run2<TS>(base + x0, &a[1]);
+                if constexpr (ox == -1) a[0] = lds1<TS>(base + xl);
+                if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[3] = lds1<TS>(base + xr);
+            } else {
+                load_run<TS, float, 2>(base + x0, &a[1]);
+                if constexpr (ox == -1) a[0] = load_q<TS, float>(base + xl);
+                if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[3] = load_q<TS, float>(base + xr);
+            }
+        };
+        float a[4];  // columns x0-1 .. x0+2
+        row(rows[oy + 1], a);
+        pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
+        if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
+        if constexpr (ty != 0.0) {
+            float b[4];
+            row(rows[oy + 2], b);
+            v = fmadd(pf2((float)((1.0 - tx) * ty)), pf2(b[ox + 1], b[ox + 2]), v);
+            if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
+        }
+        q[c] = v;
+    });
+}
+
+template <typename I, bool FORCED>
+__device__ __forceinline__ void force_pair(const float *__restrict__ F, I plane, I n0, pf2 &Fx, pf2 &Fy) {
+    if constexpr (FORCED) {
+        float fx[2], fy[2];
+        load_run<float, float, 2>(F + n0, fx);
+        load_run<float, float, 2>(F + (plane + n0), fy);
+        Fx = pf2(fx[0], fx[1]);
+        Fy = pf2(fy[0], fy[1]);
+    } else {
+        Fx = 0.0f;
+        Fy = 0.0f;
+    }
+}
+
+// Shared-memory footprint of one tile's intermediate state.
+template <typename TS, int TW, int TH>
+constexpr int fused2_smem_bytes() {
+    return NC * (TW + 4) * (TH + 2) * (int)sizeof(TS);
+}
+
+__device__ __forceinline__ int wrap_mod(int a, int n) {
+    const int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// Two steps of the TW x TH tile (blockIdx.x, blockIdx.y) with NT threads.
+// Needs nx even and CFL 1; the grid covers the lattice with whole tiles
+// (nodes past the lattice edge in the last tiles are not written).
+template <typename TS, bool FORCED, int TW, int TH, int NT, int MINB, typename I>
+__global__ void __launch_bounds__(NT, MINB)
+    k_step_fused2(const TS *__restrict__ qin, TS *__restrict__ qout, const float *__restrict__ F, StepParams p) {
+    static_assert(TW % 2 == 0, "tiles hold whole node pairs");
+    constexpr int SW = TW + 4, SH = TH + 2, SPLANE = SW * SH;
+    constexpr int PW1 = SW / 2, NP1 = PW1 * SH;  // node pairs of the first step
+    constexpr int PW2 = TW / 2, NP2 = PW2 * TH;  // node pairs of the second step
+    extern __shared__ __align__(16) unsigned char fused2_smem[];
+    TS *S = reinterpret_cast<TS *>(fused2_smem);
+    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * TH;
+    const I plane = (I)p.plane;
+
+    // step t -> t+1 on the window: local (lr, lc) <-> node
+    // ((tx0 - 2 + lc) mod nx, (ty0 - 1 + lr) mod ny)
+    for (int i = threadIdx.x; i < NP1; i += NT) {
+        const int lr = i / PW1, lc = (i - lr * PW1) * 2;
+        const int x0 = wrap_mod(tx0 - 2 + lc, p.nx), y = wrap_mod(ty0 - 1 + lr, p.ny);
+        const int ym = (y == 0) ? p.ny - 1 : y - 1;
+        const int yp = (y == p.ny - 1) ? 0 : y + 1;
+        const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
+        const int xr = (x0 + 2 == p.nx) ? 0 : x0 + 2;
+        const I rows[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
+        pf2 q[NC];
+        pull_pair_cfl1<TS, I, false>(qin, plane, rows, (I)x0, (I)xl, (I)xr, q);
+        pf2 Fx, Fy;
+        force_pair<I, FORCED>(F, plane, rows[1] + (I)x0, Fx, Fy);
+        collide_node<pf2, pf2, FORCED>(q, Fx, Fy, p);
+        static_for<0, NC>([&](auto C) {
+            constexpr int c = decltype(C)::value;
+            const float out[2] = {q[c].v.x, q[c].v.y};
+            store_run<TS, float, 2>(S + (c * SPLANE + lr * SW + lc), out);
+        });
+    }
+    __syncthreads();
+
+    // step t+1 -> t+2 on the tile, pulling from the window
+    for (int i = threadIdx.x; i < NP2; i += NT) {
+        const int r = i / PW2, c2 = (i - r * PW2) * 2;
+        const int x0 = tx0 + c2, y = ty0 + r;
+        if (x0 >= p.nx || y >= p.ny) continue;
+        const int lr = r + 1, lc = c2 + 2;
+        const int rows[3] = {(lr - 1) * SW, lr * SW, (lr + 1) * SW};
+        pf2 q[NC];
+        pull_pair_cfl1<TS, int, true>(S, SPLANE, rows, lc, lc - 1, lc + 2, q);
+        const I n0 = (I)y * (I)p.pitch + (I)x0;
+        pf2 Fx, Fy;
+        force_pair<I, FORCED>(F, plane, n0, Fx, Fy);
+        collide_node<pf2, pf2, FORCED>(q, Fx, Fy, p);
+        static_for<0, NC>([&](auto C) {
+            constexpr int c = decltype(C)::value;
+            const float out[2] = {q[c].v.x, q[c].v.y};
+            store_run<TS, float, 2>(qout + ((I)c * plane + n0), out);
+        });
+    }
+}
+
+}  // namespace rlbk

@@ -179,6 +179,8 @@ static cudaError_t launch_step_h(const rlbm_t *h, const LaunchCfg &cfg, const vo
                                  const StepParams &p) {
     if (h->ring) return launch_ring_step(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
     if (h->d3) return launch_step3(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
+    if (cfg.kernel == RLBM_KERNEL_FUSED2)
+        return launch_step_fused2(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
     if (cfg.kernel == RLBM_KERNEL_TMA) {
         if (!h->tm_ready) return cudaErrorNotSupported;
         const CUtensorMap &mq = (qin == h->q[0]) ? h->tm_q[0] : h->tm_q[1];
@@ -222,17 +224,34 @@ static rlbm_status ensure_force(rlbm_t *h) {
     return RLBM_OK;
 }
 
+// Lattice steps one launch of `cfg` advances.
+static int steps_per_launch(const LaunchCfg &cfg) { return cfg.kernel == RLBM_KERNEL_FUSED2 ? 2 : 1; }
+
+// Launches that advance n steps: two-step launches, then single steps for
+// what is left (the packed single step after two-step launches).
+static int launches_for(const LaunchCfg &cfg, int n) { return steps_per_launch(cfg) == 2 ? n / 2 + n % 2 : n; }
+
 static rlbm_status launch_steps(rlbm_t *h, int n) {
     const StepParams p = params_of(h);
-    for (int i = 0; i < n; ++i) {
-        CUDA_TRY(h, launch_step_h(h, h->cfg, h->q[h->cur], h->q[h->cur ^ 1], p));
+    int i = 0;
+    LaunchCfg one = h->cfg;
+    if (steps_per_launch(h->cfg) == 2) {
+        for (; i + 2 <= n; i += 2) {
+            CUDA_TRY(h, launch_step_h(h, h->cfg, h->q[h->cur], h->q[h->cur ^ 1], p));
+            h->cur ^= 1;
+        }
+        one = LaunchCfg{RLBM_KERNEL_PACKED, 128, 1, 2};
+    }
+    for (; i < n; ++i) {
+        CUDA_TRY(h, launch_step_h(h, one, h->q[h->cur], h->q[h->cur ^ 1], p));
         h->cur ^= 1;
     }
     return RLBM_OK;
 }
 
-// Run `n` steps inside one epoch: replay a captured graph of n steps (n
-// even, so the ping-pong parity returns to where it started), or launch.
+// Run `n` steps inside one epoch: replay a captured graph of the even part
+// of n (keyed by that count and the buffer it starts from; it leaves the
+// state in the buffer its launch count implies), then a last single step.
 static rlbm_status run_chunk(rlbm_t *h, int n) {
     const bool graphs = h->opts.use_graphs && h->stream != nullptr && n >= 2;
     if (!graphs) return launch_steps(h, n);
@@ -258,6 +277,7 @@ static rlbm_status run_chunk(rlbm_t *h, int n) {
         it = h->graphs.emplace(key, ge).first;
     }
     CUDA_TRY(h, cudaGraphLaunch(it->second, h->stream));
+    h->cur ^= launches_for(h->cfg, even) & 1;
     if (even != n) return launch_steps(h, 1);
     return RLBM_OK;
 }
@@ -301,13 +321,25 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_TWOPASS, 32, 8, 4},
     {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
     {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
+    {RLBM_KERNEL_FUSED2, 64, 16, 2}, {RLBM_KERNEL_FUSED2, 64, 8, 4}, {RLBM_KERNEL_FUSED2, 128, 8, 2},
 };
-static std::map<std::tuple<int, int, int, int, int, int>, LaunchCfg> g_tuned;
+// Whether launch shape c can run this lattice (the launchers reject the
+// remaining misfits: storage form, Landau precision, nx parity).
+static bool candidate_applies(const rlbm_t *h, const LaunchCfg &c) {
+    if (h->opts.cfl != 1.0 && c.kernel != RLBM_KERNEL_GATHER &&
+        !(c.kernel == RLBM_KERNEL_PACKED && c.minb <= 2 && !h->ring && !h->d3))
+        return false;
+    if ((h->d3 || h->ring) && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED) return false;
+    if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) return false;
+    return true;
+}
+
+static std::map<std::tuple<int, int, int, int, int, int, int>, LaunchCfg> g_tuned;
 static std::mutex g_tuned_mu;
 
-static std::tuple<int, int, int, int, int, int> tune_key(const rlbm_t *h) {
+static std::tuple<int, int, int, int, int, int, int> tune_key(const rlbm_t *h) {
     return std::make_tuple(h->nx, h->ny, h->opts.dtype, h->opts.landau, h->forced ? 1 : 0,
-                           h->ring ? 1 : (h->d3 ? 2 + h->nz : 0));
+                           h->ring ? 1 : (h->d3 ? 2 + h->nz : 0), stream_mode(h->opts.cfl));
 }
 
 
@@ -424,10 +456,10 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (opts) o = *opts;
     if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
     if (o.landau != RLBM_LANDAU_FP64 && o.landau != RLBM_LANDAU_FP32) return RLBM_ERR_ARG;
-    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_TWOPASS) return RLBM_ERR_ARG;
+    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_FUSED2) return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_TMA && (nx % 2 != 0 || o.dtype != RLBM_F32 || o.landau != RLBM_LANDAU_FP32))
         return RLBM_ERR_ARG;
-    if ((o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_TWOPASS) &&
+    if ((o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_TWOPASS || o.kernel == RLBM_KERNEL_FUSED2) &&
         (nx % 2 != 0 || o.dtype == RLBM_F64 || o.landau != RLBM_LANDAU_FP32))
         return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_GATHER_VEC && nx % (o.dtype == RLBM_F64 ? 2 : 4) != 0) return RLBM_ERR_ARG;
@@ -442,7 +474,8 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (!(o.cfl > 0.0 && o.cfl < 2.0) || !(o.eta_s >= 0.0) || !isfinite(o.eta_s) || !(o.dt > 0.0) || !isfinite(o.dt))
         return RLBM_ERR_ARG;
     if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2 ||
-                         o.kernel == RLBM_KERNEL_TMA || o.kernel == RLBM_KERNEL_TWOPASS))
+                         o.kernel == RLBM_KERNEL_TMA || o.kernel == RLBM_KERNEL_TWOPASS ||
+                         o.kernel == RLBM_KERNEL_FUSED2))
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
@@ -490,6 +523,14 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
         return RLBM_ERR_CUDA;
     }
     h->stream = static_cast<cudaStream_t>(o.stream);
+    // the two-step kernels keep more than 48 KB of shared memory per CTA
+    if (!ring && !d3 && o.dtype != RLBM_F64 && o.landau == RLBM_LANDAU_FP32 && fused2_prepare() != cudaSuccess) {
+        cudaGetLastError();
+        if (o.kernel == RLBM_KERNEL_FUSED2) {
+            delete h;
+            return RLBM_ERR_CUDA;
+        }
+    }
     if (o.kernel == RLBM_KERNEL_AUTO) {
         std::lock_guard<std::mutex> lk(g_tuned_mu);
         auto it = g_tuned.find(tune_key(h));
@@ -509,6 +550,11 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
             h->cfg.bx = 64;
             h->cfg.by = 2;
             h->cfg.minb = 3;
+        }
+        if (o.kernel == RLBM_KERNEL_FUSED2) {  // 64 x 16 output tiles, two CTAs per SM
+            h->cfg.bx = 64;
+            h->cfg.by = 16;
+            h->cfg.minb = 2;
         }
     }
     if (!h->tuned && o.kernel == RLBM_KERNEL_AUTO) {
@@ -1007,8 +1053,10 @@ rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {
     info->tau = h->tau;
     info->eps0 = h->opts.eps0;
     info->scale = h->opts.scale;
-    info->bytes_per_node = (size_t)2 * h->ncls * storage_bytes(h->opts.dtype) +
-                           (h->forced ? (h->d3 ? 3 : 2) * compute_bytes(h->opts.dtype) : 0);
+    info->steps_per_launch = steps_per_launch(h->cfg);
+    info->bytes_per_node = ((size_t)2 * h->ncls * storage_bytes(h->opts.dtype) +
+                            (h->forced ? (h->d3 ? 3 : 2) * compute_bytes(h->opts.dtype) : 0)) /
+                           (size_t)info->steps_per_launch;
     info->device_bytes = h->device_bytes;
     info->populations = h->q[h->cur];
     return RLBM_OK;
@@ -1028,11 +1076,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     LaunchCfg best = h->cfg;
     for (const LaunchCfg &c : kCandidates) {
         if (h->opts.kernel != RLBM_KERNEL_AUTO && c.kernel != h->opts.kernel) continue;
-        if (h->opts.cfl != 1.0 && c.kernel != RLBM_KERNEL_GATHER &&
-            !(c.kernel == RLBM_KERNEL_PACKED && c.minb <= 2 && !h->ring && !h->d3))
-            continue;
-        if ((h->d3 || h->ring) && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED) continue;
-        if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) continue;
+        if (!candidate_applies(h, c)) continue;
         // the trial steps read the current state and overwrite only the spare buffer
         bool ok = true;
         for (int i = 0; i < 2 + reps && ok; ++i) {
@@ -1047,6 +1091,7 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
         CUDA_TRY(h, cudaEventSynchronize(b));
         float ms = 0.f;
         CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
+        ms /= (float)steps_per_launch(c);  // per lattice step
         if (ms < best_ms) {
             best_ms = ms;
             best = c;
@@ -1067,6 +1112,31 @@ rlbm_status rlbm_autotune(rlbm_t *h, int reps, int *chosen_kernel, int *block_x,
     return RLBM_OK;
 }
 
+}  // extern "C"
+
+extern "C" {
+rlbm_status rlbm_set_launch(rlbm_t *h, int kernel, int block_x, int block_y, int launch_budget) {
+    CHECK_HANDLE(h);
+    if (h->opts.kernel != RLBM_KERNEL_AUTO && kernel != h->opts.kernel)
+        return fail(h, RLBM_ERR_ARG, "the handle was created for kernel %d", h->opts.kernel);
+    for (const LaunchCfg &c : kCandidates) {
+        if (c.kernel != kernel || c.bx != block_x || c.by != block_y || c.minb != launch_budget) continue;
+        if (!candidate_applies(h, c)) break;
+        // one trial launch into the spare buffer: the launcher's own checks
+        const StepParams p = params_of(h);
+        rlbm_status st = ensure_force(h);
+        if (st != RLBM_OK) return st;
+        if (launch_step_h(h, c, h->q[h->cur], h->q[h->cur ^ 1], p) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, RLBM_ERR_ARG, "launch shape does not fit this lattice");
+        }
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        h->cfg = c;
+        drop_graphs(h);
+        return RLBM_OK;
+    }
+    return fail(h, RLBM_ERR_ARG, "no such launch shape for this lattice");
+}
 }  // extern "C"
 
 // Checkpoint layout: this header, then the current state buffer verbatim

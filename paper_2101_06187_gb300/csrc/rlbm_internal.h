@@ -54,6 +54,14 @@ cudaError_t tma_encode_force(CUtensorMap *map, const void *F, const StepParams &
 cudaError_t launch_step_tma(const LaunchCfg &cfg, bool forced, const CUtensorMap &mq, const CUtensorMap &mf,
                             const void *qin, void *qout, const StepParams &p, cudaStream_t s, int unarmed = 0);
 
+// Two steps per launch (k_step_fused2.cu): cfg.bx x cfg.by is the output
+// tile; FP32 / BF16 / FP16 storage with the FP32 Landau solve, CFL 1, nx
+// even.  fused2_prepare raises the shared-memory limit of its kernels on the
+// current device (once per device, before any launch or stream capture).
+cudaError_t fused2_prepare();
+cudaError_t launch_step_fused2(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
+                               const void *F, const StepParams &p, cudaStream_t s);
+
 // The three-dimensional lattice (k_lattice3d.cu).
 cudaError_t launch_step3(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                          const void *F, const StepParams &p, cudaStream_t s);
