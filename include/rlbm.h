@@ -115,7 +115,7 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * split into launch pairs inside each forcing epoch (the force is constant
  * within one) and an odd remainder runs the packed single step; results
  * equal those of PACKED bit for bit.  block_x x block_y of the launch shape
- * is the output tile (64 x 16, 64 x 8 or 128 x 8 nodes).
+ * is the output tile (64 x 16, 64 x 8, 32 x 16 or 128 x 8 nodes).
  * The vector, TMA, two-pass and two-step variants stream at CFL 1 only, the
  * packed kernel at any cfl (halo 2 above 1).
  * AUTO: the autotuned choice if one is cached for this lattice, else

@@ -46,6 +46,7 @@ struct Fused2 {
 #define RLBM_FUSED2_SHAPES(X) \
     X(64, 16, 256, 2)         \
     X(64, 8, 128, 4)          \
+    X(32, 16, 128, 4)         \
     X(128, 8, 256, 2)
 
 template <typename TS>

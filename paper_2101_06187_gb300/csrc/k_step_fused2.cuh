@@ -102,7 +102,13 @@ constexpr int fused2_smem_bytes() {
     return NC * (TW + 4) * (TH + 2) * (int)sizeof(TS);
 }
 
-__device__ __forceinline__ int wrap_mod(int a, int n) {
+// a mod n for the window coordinates: one conditional add or subtract for
+// a in [-n, 2n), the integer remainder only for lattices narrower than the
+// window (where the window wraps more than once).
+__device__ __forceinline__ int wrap_window(int a, int n) {
+    if (a < 0) a += n;
+    else if (a >= n) a -= n;
+    if ((unsigned)a < (unsigned)n) return a;
     const int r = a % n;
     return r < 0 ? r + n : r;
 }
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(NT, MINB)
     // ((tx0 - 2 + lc) mod nx, (ty0 - 1 + lr) mod ny)
     for (int i = threadIdx.x; i < NP1; i += NT) {
         const int lr = i / PW1, lc = (i - lr * PW1) * 2;
-        const int x0 = wrap_mod(tx0 - 2 + lc, p.nx), y = wrap_mod(ty0 - 1 + lr, p.ny);
+        const int x0 = wrap_window(tx0 - 2 + lc, p.nx), y = wrap_window(ty0 - 1 + lr, p.ny);
         const int ym = (y == 0) ? p.ny - 1 : y - 1;
         const int yp = (y == p.ny - 1) ? 0 : y + 1;
         const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;

@@ -321,7 +321,8 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_TWOPASS, 32, 8, 4},
     {RLBM_KERNEL_GATHER, 32, 8}, {RLBM_KERNEL_GATHER, 64, 4}, {RLBM_KERNEL_GATHER, 128, 2},
     {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
-    {RLBM_KERNEL_FUSED2, 64, 16, 2}, {RLBM_KERNEL_FUSED2, 64, 8, 4}, {RLBM_KERNEL_FUSED2, 128, 8, 2},
+    {RLBM_KERNEL_FUSED2, 64, 16, 2}, {RLBM_KERNEL_FUSED2, 64, 8, 4}, {RLBM_KERNEL_FUSED2, 32, 16, 4},
+    {RLBM_KERNEL_FUSED2, 128, 8, 2},
 };
 // Whether launch shape c can run this lattice (the launchers reject the
 // remaining misfits: storage form, Landau precision, nx parity).

@@ -26,7 +26,7 @@ import paper_2101_06187_gb300 as rl  # noqa: E402
 
 oracle.set_threads(os.cpu_count() or 4)
 
-TILES = [(64, 16, 2), (64, 8, 4), (128, 8, 2)]
+TILES = [(64, 16, 2), (64, 8, 4), (32, 16, 4), (128, 8, 2)]
 FORCING = dict(kmin=1, kmax=2, amp=2e-4, seed=987654321, redraw_period=7)
 FORCING_TINY = dict(kmin=1, kmax=1, amp=2e-3, seed=5, redraw_period=3)  # 4x4: kmax < n/2
 CHUNKS = (1, 6, 13, 2, 41, 4)  # odd and even chunks, across epoch boundaries (67 steps)
