@@ -263,21 +263,22 @@ def measure_ensemble(torch, rl, flush, steps=20, warmup=5, nruns=64, sides=None)
             for w in members]
     ens = rl.Ensemble(runs, dtype="f32", landau="fp32")
     bx, by, grid = ens.autotune(5)
-    ens.step(warmup)
+    spl = int(ens.info()["steps_per_launch"])  # 2 for the two-step body: time whole launches
+    ens.step(warmup + (-warmup) % spl)
     ens.synchronize()
     stream = ens._torch_stream
     evs = []
     with torch.cuda.stream(stream):
-        for _ in range(steps):
+        for _ in range(max(1, steps // spl)):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             flush()
             a.record(stream)
-            ens.step(1)
+            ens.step(spl)
             b.record(stream)
             evs.append((a, b))
     stream.synchronize()
-    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    ms = np.array([a.elapsed_time(b) / spl for a, b in evs])  # per step
     info = ens.info()
     # a full forcing epoch replayed as one graph (starts at an epoch boundary;
     # one untimed epoch first, so capture and instantiation are not timed)
@@ -300,7 +301,8 @@ def measure_ensemble(torch, rl, flush, steps=20, warmup=5, nruns=64, sides=None)
             "nodes": int(info["nodes"]), "glups": info["nodes"] / (step_ms / 1e3) / 1e9,
             "hbm_frac": info["bytes_per_step"] / (step_ms / 1e3) / 1e9 / peak,
             "glups_graph_100_steps": info["nodes"] * 100 / (graph_ms / 1e3) / 1e9,
-            "block": [bx, by], "grid": grid, "tiles": int(info["ntiles"]), "launches_per_step": 1}
+            "block": [bx, by], "grid": grid, "tiles": int(info["ntiles"]), "launches_per_step": 1 / spl,
+            "body": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]]}
 
 
 def parity_error(rl, oracle, form, landau):
@@ -594,6 +596,14 @@ def main():
         "clocks": clocks.summary(),
         "gpu_launches": int(info["timed_launches"] + 2 * n_epoch),
     }
+    spl = int(info["steps_per_launch"])
+    if spl > 1:
+        # a launch of several steps moves the state once: its HBM fraction is per launch; the
+        # same throughput from one-step launches would need bytes_per_node * spl per update
+        line["roofline"]["frac_at_single_step_bytes"] = achieved * spl / hbm_peak
+        line["roofline"]["limiter"] = ("instruction issue, not HBM: under ncu the two-step launch keeps DRAM "
+                                       "29% busy, issue slots 51%, FP32 FMA pipe 61% "
+                                       "(profiles/k_step_fused2_f32_stirred_1024.md)")
     if args.form == "f64" and not variant:
         tf = FP64_FLOPS_PER_NODE * nodes / (kernel_ms / 1e3) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

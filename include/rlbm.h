@@ -429,12 +429,20 @@ typedef struct {
     int block_x, block_y, grid, ntiles; /* launch shape of the ensemble step */
     int64_t step;
     int64_t nodes;                      /* lattice nodes over all members */
-    size_t bytes_per_step;              /* algorithmic HBM bytes of one ensemble step */
+    size_t bytes_per_step;              /* algorithmic HBM bytes per ensemble step (a two-step launch
+                                           moves the state once for two steps: half the one-step figure) */
     size_t device_bytes;
+    int kernel;                         /* body of the ensemble step: GATHER_VEC, PACKED or FUSED2 */
+    int steps_per_launch;               /* 2 for the two-step body (FUSED2), else 1 */
 } rlbm_batch_info_t;
 
 /* Create nruns members (validation as rlbm_create, per member); all start at
- * rest at step 0.  Errors: RLBM_ERR_ARG, RLBM_ERR_ALLOC, RLBM_ERR_CUDA. */
+ * rest at step 0.  opts->kernel picks the body of the ensemble step: AUTO
+ * (the vector kernel until rlbm_batch_autotune chooses), GATHER_VEC, PACKED
+ * or FUSED2 (FP32 compute with RLBM_LANDAU_FP32, nx even, fewer than 2^31
+ * elements in a member's 17 planes); the autotuner then keeps that body.
+ * Ensembles stream at CFL 1.  Errors: RLBM_ERR_ARG, RLBM_ERR_ALLOC,
+ * RLBM_ERR_CUDA. */
 RLBM_API rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_opts *opts,
                                        rlbm_batch_t **out);
 /* Initialise member `run` as rlbm_init_fields does, at the ensemble's
@@ -449,8 +457,12 @@ RLBM_API rlbm_status rlbm_batch_moments(rlbm_batch_t *b, int run, double *eps, d
 RLBM_API rlbm_status rlbm_batch_energy_spectrum(rlbm_batch_t *b, int run, int nshells, double *Ek);
 RLBM_API rlbm_status rlbm_batch_get_populations(rlbm_batch_t *b, int run, double *f);
 /* Time tile shapes and persistent grid sizes (multiples of the SM count,
- * or one block per tile) for the ensemble step and keep the fastest; the
- * state is unchanged.  Outputs may be NULL.  Synchronises. */
+ * or one block per tile) for the ensemble step and keep the fastest per
+ * step; the bodies on offer are the vector kernel, the packed kernel and,
+ * for FP32 compute with RLBM_LANDAU_FP32, two steps per launch through
+ * shared memory (as RLBM_KERNEL_FUSED2, bit-identical to two packed steps;
+ * block_x x block_y is then the tile in nodes).  The state is unchanged.
+ * Outputs may be NULL.  Synchronises. */
 RLBM_API rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *block_y, int *grid);
 RLBM_API rlbm_status rlbm_batch_get_info(rlbm_batch_t *b, rlbm_batch_info_t *info);
 RLBM_API rlbm_status rlbm_batch_synchronize(rlbm_batch_t *b);

@@ -87,7 +87,8 @@ class RunDesc(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("nruns", ctypes.c_int), ("dtype", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
                 ("grid", ctypes.c_int), ("ntiles", ctypes.c_int), ("step", ctypes.c_int64), ("nodes", ctypes.c_int64),
-                ("bytes_per_step", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t)]
+                ("bytes_per_step", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t), ("kernel", ctypes.c_int),
+                ("steps_per_launch", ctypes.c_int)]
 
 
 _lib_lock = threading.Lock()
@@ -674,14 +675,15 @@ class Lattice3D(Lattice):
 
 
 class Ensemble:
-    """Independent lattices advanced together by one launch per step.
+    """Independent lattices advanced together by one launch per step (per two
+    steps with the two-step body the autotuner may pick).
 
     runs: list of dicts with nx, ny, tau and optional forcing (as for
     Lattice).  dtype / landau / allocator / stream as for Lattice.
     """
 
     def __init__(self, runs, *, dtype: str = "f32", landau: str = "fp32", use_graphs: bool = True,
-                 allocator: str = "torch", stream=None, device: Optional[int] = None):
+                 allocator: str = "torch", stream=None, device: Optional[int] = None, kernel: str = "auto"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the RLBM library runs on the GPU only")
@@ -700,6 +702,7 @@ class Ensemble:
         o = rlbm_opts_default()
         o.dtype = DTYPES[dtype]
         o.landau = LANDAU[landau]
+        o.kernel = KERNELS[kernel]
         o.use_graphs = 1 if use_graphs else 0
         o.stream = s
         o.device = dev

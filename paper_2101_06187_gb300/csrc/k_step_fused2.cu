@@ -18,7 +18,9 @@ struct Fused2 {
         return reinterpret_cast<void *>(&k_step_fused2<TS, FORCED, TW, TH, NT, MINB, I>);
     }
     static cudaError_t prepare() {
-        for (void *f : {fn<true, int>(), fn<false, int>(), fn<true, long long>(), fn<false, long long>()}) {
+        for (void *f : {fn<true, int>(), fn<false, int>(), fn<true, long long>(), fn<false, long long>(),
+                        reinterpret_cast<void *>(&k_step_batch_fused2<TS, TW, TH, NT, MINB, true>),
+                        reinterpret_cast<void *>(&k_step_batch_fused2<TS, TW, TH, NT, MINB, false>)}) {
             const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
         }
@@ -38,6 +40,12 @@ struct Fused2 {
             if (forced) k_step_fused2<TS, true, TW, TH, NT, MINB, long long><<<grid, NT, smem, s>>>(in, out, f, p);
             else k_step_fused2<TS, false, TW, TH, NT, MINB, long long><<<grid, NT, smem, s>>>(in, out, f, p);
         }
+        return cudaGetLastError();
+    }
+    static cudaError_t launch_batch(int grid, const void *runs, int nruns, int ntiles, int two, cudaStream_t s) {
+        const BatchRun *r = static_cast<const BatchRun *>(runs);
+        if (two) k_step_batch_fused2<TS, TW, TH, NT, MINB, true><<<grid, NT, smem, s>>>(r, nruns, ntiles);
+        else k_step_batch_fused2<TS, TW, TH, NT, MINB, false><<<grid, NT, smem, s>>>(r, nruns, ntiles);
         return cudaGetLastError();
     }
 };
@@ -71,6 +79,17 @@ cudaError_t launch_t(const LaunchCfg &cfg, bool forced, const void *qin, void *q
     return cudaErrorInvalidConfiguration;
 }
 
+template <typename TS>
+cudaError_t launch_batch_t(const LaunchCfg &cfg, int grid, const void *runs, int nruns, int ntiles, int two,
+                           cudaStream_t s) {
+#define X(TW, TH, NT, MB)                                                                       \
+    if (cfg.bx == TW && cfg.by == TH)                                                           \
+        return Fused2<TS, TW, TH, NT, MB>::launch_batch(grid, runs, nruns, ntiles, two, s);
+    RLBM_FUSED2_SHAPES(X)
+#undef X
+    return cudaErrorInvalidConfiguration;
+}
+
 }  // namespace
 
 cudaError_t fused2_prepare() {
@@ -87,6 +106,17 @@ cudaError_t launch_step_fused2(int dtype, int landau, const LaunchCfg &cfg, bool
     case RLBM_F32: return launch_t<float>(cfg, forced, qin, qout, F, p, s);
     case RLBM_BF16: return launch_t<__nv_bfloat16>(cfg, forced, qin, qout, F, p, s);
     case RLBM_F16: return launch_t<__half>(cfg, forced, qin, qout, F, p, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch_fused2(int dtype, int landau, const LaunchCfg &cfg, int grid, const void *runs, int nruns,
+                                int ntiles, int two, cudaStream_t s) {
+    if (landau != RLBM_LANDAU_FP32 || grid < 1) return cudaErrorInvalidValue;
+    switch (dtype) {
+    case RLBM_F32: return launch_batch_t<float>(cfg, grid, runs, nruns, ntiles, two, s);
+    case RLBM_BF16: return launch_batch_t<__nv_bfloat16>(cfg, grid, runs, nruns, ntiles, two, s);
+    case RLBM_F16: return launch_batch_t<__half>(cfg, grid, runs, nruns, ntiles, two, s);
     default: return cudaErrorInvalidValue;
     }
 }

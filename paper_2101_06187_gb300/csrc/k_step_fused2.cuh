@@ -113,19 +113,17 @@ __device__ __forceinline__ int wrap_window(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Two steps of the TW x TH tile (blockIdx.x, blockIdx.y) with NT threads.
-// Needs nx even and CFL 1; the grid covers the lattice with whole tiles
-// (nodes past the lattice edge in the last tiles are not written).
-template <typename TS, bool FORCED, int TW, int TH, int NT, int MINB, typename I>
-__global__ void __launch_bounds__(NT, MINB)
-    k_step_fused2(const TS *__restrict__ qin, TS *__restrict__ qout, const float *__restrict__ F, StepParams p) {
+// Two steps of the TW x TH tile whose first node is (tx0, ty0), by the NT
+// threads of a CTA, through the shared window S.  Needs nx even and CFL 1;
+// nodes of the tile past the lattice edge are not written.
+template <typename TS, bool FORCED, int TW, int TH, int NT, typename I>
+__device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                            const float *__restrict__ F, const StepParams &p, int tx0, int ty0,
+                                            TS *__restrict__ S) {
     static_assert(TW % 2 == 0, "tiles hold whole node pairs");
     constexpr int SW = TW + 4, SH = TH + 2, SPLANE = SW * SH;
     constexpr int PW1 = SW / 2, NP1 = PW1 * SH;  // node pairs of the first step
     constexpr int PW2 = TW / 2, NP2 = PW2 * TH;  // node pairs of the second step
-    extern __shared__ __align__(16) unsigned char fused2_smem[];
-    TS *S = reinterpret_cast<TS *>(fused2_smem);
-    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * TH;
     const I plane = (I)p.plane;
 
     // step t -> t+1 on the window: local (lr, lc) <-> node
@@ -169,6 +167,54 @@ __global__ void __launch_bounds__(NT, MINB)
             const float out[2] = {q[c].v.x, q[c].v.y};
             store_run<TS, float, 2>(qout + ((I)c * plane + n0), out);
         });
+    }
+}
+
+// Two steps of the lattice, one TW x TH tile per CTA (blockIdx.x, blockIdx.y).
+template <typename TS, bool FORCED, int TW, int TH, int NT, int MINB, typename I>
+__global__ void __launch_bounds__(NT, MINB)
+    k_step_fused2(const TS *__restrict__ qin, TS *__restrict__ qout, const float *__restrict__ F, StepParams p) {
+    extern __shared__ __align__(16) unsigned char fused2_smem[];
+    fused2_tile<TS, FORCED, TW, TH, NT, I>(qin, qout, F, p, blockIdx.x * TW, blockIdx.y * TH,
+                                           reinterpret_cast<TS *>(fused2_smem));
+}
+
+// Ensemble form: a grid-stride walk over the flat tile list of all members
+// (BatchRun descriptors, tiles of TW x TH nodes).  TWO: two steps per tile
+// through shared memory, as k_step_fused2; else one step of the tile's node
+// pairs with the packed body (the odd step of an odd count).  Members hold
+// fewer than 2^31 / 17 elements per plane: 32-bit offsets.
+template <typename TS, int TW, int TH, int NT, int MINB, bool TWO>
+__global__ void __launch_bounds__(NT, MINB)
+    k_step_batch_fused2(const BatchRun *__restrict__ runs, int nruns, int ntiles) {
+    extern __shared__ __align__(16) unsigned char fused2_smem[];
+    TS *S = reinterpret_cast<TS *>(fused2_smem);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int lo = 0, hi = nruns - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (runs[mid].tile0 <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchRun &r = runs[lo];
+        const int local = t - r.tile0;
+        const int tx0 = (local % r.tiles_x) * TW, ty0 = (local / r.tiles_x) * TH;
+        const TS *qin = static_cast<const TS *>(r.qin);
+        TS *qout = static_cast<TS *>(r.qout);
+        const float *F = static_cast<const float *>(r.F);
+        if constexpr (TWO) {
+            if (F) fused2_tile<TS, true, TW, TH, NT, int>(qin, qout, F, r.p, tx0, ty0, S);
+            else fused2_tile<TS, false, TW, TH, NT, int>(qin, qout, nullptr, r.p, tx0, ty0, S);
+            __syncthreads();  // the next tile's first step overwrites the window
+        } else {
+            for (int i = threadIdx.x; i < (TW / 2) * TH; i += NT) {
+                const int rr = i / (TW / 2);
+                const int x0 = tx0 + (i - rr * (TW / 2)) * 2, y = ty0 + rr;
+                if (x0 >= r.p.nx || y >= r.p.ny) continue;
+                if (F) step_pair<TS, true, int>(qin, qout, F, r.p, x0, y);
+                else step_pair<TS, false, int>(qin, qout, nullptr, r.p, x0, y);
+            }
+        }
     }
 }
 

@@ -1297,7 +1297,8 @@ static void batch_drop_graphs(rlbm_batch_t *b) {
 
 // Host copy of the descriptors for a launch shape; returns the tile count.
 static int batch_descriptors(const rlbm_batch_t *b, const LaunchCfg &cfg, int parity, std::vector<BatchRun> *out) {
-    const int V = (cfg.kernel == RLBM_KERNEL_PACKED) ? 2 : run_length(b->opts.dtype);
+    // columns per tile unit: node pairs (packed), whole nodes (two-step tiles of bx x by nodes), runs
+    const int V = (cfg.kernel == RLBM_KERNEL_PACKED) ? 2 : (cfg.kernel == RLBM_KERNEL_FUSED2) ? 1 : run_length(b->opts.dtype);
     int t0 = 0;
     out->clear();
     for (rlbm_t *h : b->runs) {
@@ -1336,11 +1337,23 @@ static int sm_count(int device) {
     return n;
 }
 
+// One launch of the ensemble step with launch shape c: two steps (two-step
+// tiles, two != 0) or one.
+static cudaError_t batch_launch(const rlbm_batch_t *b, const LaunchCfg &c, int grid, int two) {
+    if (c.kernel == RLBM_KERNEL_FUSED2)
+        return launch_batch_fused2(b->opts.dtype, b->opts.landau, c, grid, b->desc[b->cur], (int)b->runs.size(),
+                                   b->ntiles, two, b->stream);
+    return launch_batch(b->opts.dtype, b->opts.landau, c, grid, b->desc[b->cur], (int)b->runs.size(), b->ntiles,
+                        b->stream);
+}
+
 static rlbm_status batch_launch_steps(rlbm_batch_t *b, int n) {
-    for (int i = 0; i < n; ++i) {
-        BCUDA_TRY(b, launch_batch(b->opts.dtype, b->opts.landau, b->cfg, b->grid, b->desc[b->cur], (int)b->runs.size(),
-                                  b->ntiles, b->stream));
+    const int spl = steps_per_launch(b->cfg);
+    for (int i = 0; i < n; i += spl) {
+        const int two = (spl == 2 && i + 2 <= n) ? 1 : 0;
+        BCUDA_TRY(b, batch_launch(b, b->cfg, b->grid, two));
         b->cur ^= 1;
+        if (spl == 2 && !two) break;  // the odd last step
     }
     return RLBM_OK;
 }
@@ -1370,6 +1383,7 @@ static rlbm_status batch_run_chunk(rlbm_batch_t *b, int n) {
         it = b->graphs.emplace(key, ge).first;
     }
     BCUDA_TRY(b, cudaGraphLaunch(it->second, b->stream));
+    b->cur ^= launches_for(b->cfg, even) & 1;
     if (even != n) return batch_launch_steps(b, 1);
     return RLBM_OK;
 }
@@ -1419,15 +1433,25 @@ rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_o
     rlbm_opts_default(&o);
     if (opts) o = *opts;
     if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
-    const int V = run_length(o.dtype);
-    for (int r = 0; r < nruns; ++r)
+    // body of the ensemble step: the vector kernel (AUTO starts there), packed lanes, or two steps per launch
+    const int bk = o.kernel;
+    if (bk != RLBM_KERNEL_AUTO && bk != RLBM_KERNEL_GATHER_VEC && bk != RLBM_KERNEL_PACKED &&
+        bk != RLBM_KERNEL_FUSED2)
+        return RLBM_ERR_ARG;
+    const bool lanes = bk == RLBM_KERNEL_PACKED || bk == RLBM_KERNEL_FUSED2;
+    if (lanes && (o.dtype == RLBM_F64 || o.landau != RLBM_LANDAU_FP32)) return RLBM_ERR_ARG;
+    const int V = lanes ? 2 : run_length(o.dtype);
+    for (int r = 0; r < nruns; ++r) {
         if (runs[r].nx % V != 0) return RLBM_ERR_ARG;  // the ensemble kernel works on runs of V nodes
+        if (lanes && (long long)NC * runs[r].ny * ((runs[r].nx + 31) & ~31) >= (1ll << 31) - 1)
+            return RLBM_ERR_ARG;  // the packed ensemble bodies index with 32-bit offsets
+    }
     if (!(o.cfl == 0.0 || o.cfl == 1.0)) return RLBM_ERR_ARG;  // and streams at CFL 1
     rlbm_batch_t *b = new rlbm_batch_t();
     b->opts = o;
     b->stream = static_cast<cudaStream_t>(o.stream);
     rlbm_opts member = o;
-    member.kernel = RLBM_KERNEL_GATHER_VEC;
+    member.kernel = lanes ? RLBM_KERNEL_PACKED : RLBM_KERNEL_GATHER_VEC;  // validates the member's shape
     for (int r = 0; r < nruns; ++r) {
         rlbm_t *h = nullptr;
         rlbm_status st = rlbm_create(runs[r].nx, runs[r].ny, RLBM_STENCIL_SPH26_SLAB, runs[r].tau, &runs[r].forcing,
@@ -1447,9 +1471,9 @@ rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_o
             return RLBM_ERR_ALLOC;
         }
     }
-    b->cfg.kernel = RLBM_KERNEL_GATHER_VEC;
-    b->cfg.bx = 64;
-    b->cfg.by = 2;
+    if (bk == RLBM_KERNEL_PACKED) b->cfg = LaunchCfg{RLBM_KERNEL_PACKED, 64, 2, 1};
+    else if (bk == RLBM_KERNEL_FUSED2) b->cfg = LaunchCfg{RLBM_KERNEL_FUSED2, 64, 8, 4};
+    else b->cfg = LaunchCfg{RLBM_KERNEL_GATHER_VEC, 64, 2, 1};
     rlbm_status st = batch_upload(b, b->cfg);
     if (st != RLBM_OK) {
         rlbm_batch_destroy(b);
@@ -1524,11 +1548,15 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *bl
         if (st != RLBM_OK) return st;
     }
     static const int shapes[][2] = {{32, 4}, {64, 2}, {128, 1}, {32, 8}, {64, 4}, {128, 2}, {32, 2}, {64, 1}};
-    // body: the vector kernel, or the packed-lane kernel (FP32 compute, FP32 Landau)
+    // two-step tiles (bx x by nodes) and their launch budgets
+    static const int tiles2[][3] = {{64, 8, 4}, {64, 16, 2}, {32, 16, 4}, {128, 8, 2}};
+    // body: the vector kernel, the packed-lane kernel (FP32 compute, FP32 Landau), or two steps per
+    // launch with the packed body
     bool packed_ok = b->opts.dtype != RLBM_F64 && b->opts.landau == RLBM_LANDAU_FP32;
     for (const rlbm_t *h : b->runs)  // the packed ensemble body indexes with 32-bit offsets
         if ((long long)NC * h->ny * h->pitch >= (1ll << 31) - 1) packed_ok = false;
-    static const int bodies[][2] = {{RLBM_KERNEL_GATHER_VEC, 1}, {RLBM_KERNEL_PACKED, 1}, {RLBM_KERNEL_PACKED, 3}};
+    static const int bodies[][2] = {{RLBM_KERNEL_GATHER_VEC, 1}, {RLBM_KERNEL_PACKED, 1}, {RLBM_KERNEL_PACKED, 3},
+                                    {RLBM_KERNEL_FUSED2, 0}};
     const int sms = sm_count(b->device);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     BCUDA_TRY(b, cudaEventCreate(&e0));
@@ -1537,13 +1565,15 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *bl
     LaunchCfg best = b->cfg;
     int best_grid = b->grid;
     for (const auto &body : bodies)
-    for (const auto &sh : shapes) {
-        if (body[0] == RLBM_KERNEL_PACKED && !packed_ok) continue;
+    for (int si = 0; si < 8; ++si) {
+        if (b->opts.kernel != RLBM_KERNEL_AUTO && body[0] != b->opts.kernel) continue;
+        if ((body[0] == RLBM_KERNEL_PACKED || body[0] == RLBM_KERNEL_FUSED2) && !packed_ok) continue;
+        if (body[0] == RLBM_KERNEL_FUSED2 && si >= 4) continue;
         LaunchCfg c;
         c.kernel = body[0];
-        c.minb = body[1];
-        c.bx = sh[0];
-        c.by = sh[1];
+        c.minb = body[0] == RLBM_KERNEL_FUSED2 ? tiles2[si][2] : body[1];
+        c.bx = body[0] == RLBM_KERNEL_FUSED2 ? tiles2[si][0] : shapes[si][0];
+        c.by = body[0] == RLBM_KERNEL_FUSED2 ? tiles2[si][1] : shapes[si][1];
         rlbm_status st = batch_upload(b, c);
         if (st != RLBM_OK) return st;
         const int grids[] = {sms, 2 * sms, 4 * sms, 8 * sms, 16 * sms, b->ntiles};
@@ -1553,8 +1583,7 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *bl
             bool ok = true;
             for (int i = 0; i < 1 + reps && ok; ++i) {
                 if (i == 1) ok = cudaEventRecord(e0, b->stream) == cudaSuccess;
-                ok = ok && launch_batch(b->opts.dtype, b->opts.landau, c, g, b->desc[b->cur], (int)b->runs.size(),
-                                        b->ntiles, b->stream) == cudaSuccess;
+                ok = ok && batch_launch(b, c, g, 1) == cudaSuccess;
             }
             if (!ok) {
                 cudaGetLastError();
@@ -1564,6 +1593,7 @@ rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *bl
             BCUDA_TRY(b, cudaEventSynchronize(e1));
             float ms = 0.f;
             BCUDA_TRY(b, cudaEventElapsedTime(&ms, e0, e1));
+            ms /= (float)steps_per_launch(c);  // per ensemble step
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
@@ -1591,6 +1621,8 @@ rlbm_status rlbm_batch_get_info(rlbm_batch_t *b, rlbm_batch_info_t *info) {
     info->block_x = b->cfg.bx;
     info->block_y = b->cfg.by;
     info->grid = b->grid;
+    info->kernel = b->cfg.kernel;
+    info->steps_per_launch = steps_per_launch(b->cfg);
     info->ntiles = b->ntiles;
     info->step = b->step;
     long long nodes = 0;
@@ -1602,7 +1634,7 @@ rlbm_status rlbm_batch_get_info(rlbm_batch_t *b, rlbm_batch_info_t *info) {
         dev += h->device_bytes;
     }
     info->nodes = nodes;
-    info->bytes_per_step = bytes;
+    info->bytes_per_step = bytes / (size_t)steps_per_launch(b->cfg);
     info->device_bytes = dev;
     return RLBM_OK;
 }

@@ -61,6 +61,10 @@ cudaError_t launch_step_tma(const LaunchCfg &cfg, bool forced, const CUtensorMap
 cudaError_t fused2_prepare();
 cudaError_t launch_step_fused2(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                                const void *F, const StepParams &p, cudaStream_t s);
+// Ensemble form over `runs` (BatchRun descriptors with TW x TH tiles, cfl 1
+// members): two steps per launch (two != 0) or one packed step.
+cudaError_t launch_batch_fused2(int dtype, int landau, const LaunchCfg &cfg, int grid, const void *runs, int nruns,
+                                int ntiles, int two, cudaStream_t s);
 
 // The three-dimensional lattice (k_lattice3d.cu).
 cudaError_t launch_step3(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,

@@ -119,6 +119,18 @@ def test_batch_create_rejects_invalid_members(lib):
     assert lib.rlbm_batch_create(2, arr, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG
     assert lib.rlbm_batch_create(0, arr, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG
     assert lib.rlbm_batch_create(1, None, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG
+    # ensemble bodies: vector, packed or two-step; the lane bodies need FP32 compute, FP32 Landau, nx even
+    for field, value, kernel in ((None, None, "tma"), (None, None, "gather"), ("dtype", rl.DTYPES["f64"], "fused2"),
+                                 ("landau", rl.LANDAU["fp64"], "packed"), ("cfl", 0.5, "fused2")):
+        o = rl.rlbm_opts_default()
+        o.kernel = rl.KERNELS[kernel]
+        if field:
+            setattr(o, field, value)
+        assert lib.rlbm_batch_create(1, arr, ctypes.byref(o), ctypes.byref(out)) == rl.RLBM_ERR_ARG, (field, kernel)
+    o = rl.rlbm_opts_default()
+    o.kernel = rl.KERNELS["fused2"]
+    odd2 = (rl.RunDesc * 1)(rl.RunDesc(63, 64, 0.7, rl.Forcing(0, 0, 0.0, 0, 100)))  # nx odd
+    assert lib.rlbm_batch_create(1, odd2, ctypes.byref(o), ctypes.byref(out)) == rl.RLBM_ERR_ARG
     assert out.value is None
     lib.rlbm_batch_destroy(None)
 

@@ -89,7 +89,9 @@ def test_autotune_and_graphs_keep_results():
         if tune:
             before = [ens.populations(k) for k in range(len(RUNS))]
             bx, by, grid = ens.autotune(3)
-            assert bx * by <= 256 and grid >= 1
+            info = ens.info()
+            # thread blocks of at most 256, or two-step tiles of at most 1024 nodes
+            assert (bx * by <= 256 or (info["kernel"] == rl.KERNELS["fused2"] and bx * by <= 1024)) and grid >= 1
             for k in range(len(RUNS)):
                 np.testing.assert_array_equal(ens.populations(k), before[k])
         ens.step(30)
@@ -98,6 +100,46 @@ def test_autotune_and_graphs_keep_results():
     # the tuned run may use another kernel body (packed lanes): FP32 rounding, not bitwise
     for a, b in zip(*out):
         assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(a))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_two_step_body_equals_packed_lone_lattices(dtype, graphs):
+    """The two-step ensemble body (two steps per launch through shared
+    memory) against lone lattices on the packed single-step kernel: the same
+    per-node arithmetic, so bit for bit; odd chunks cross the members'
+    forcing epochs (an odd last step runs the packed body)."""
+    ens = rl.Ensemble(RUNS, dtype=dtype, kernel="fused2", use_graphs=graphs)
+    info = ens.info()
+    assert info["kernel"] == rl.KERNELS["fused2"] and info["steps_per_launch"] == 2
+    for k, r in enumerate(RUNS):
+        ens.init_fields(k, *_fields(r, k))
+    for n in (1, 6, 13, 2, 9):
+        ens.step(n)
+    for k, r in enumerate(RUNS):
+        lat = rl.Lattice(r["nx"], r["ny"], r["tau"], dtype=dtype, forcing=r["forcing"], kernel="packed")
+        lat.init_fields(*_fields(r, k))
+        lat.step(31)
+        np.testing.assert_array_equal(ens.populations(k), lat.populations(), err_msg=str(k))
+        lat.close()
+    ens.close()
+
+
+def test_two_step_body_autotune_keeps_state():
+    ens = rl.Ensemble(RUNS, dtype="f32", kernel="fused2")
+    for k, r in enumerate(RUNS):
+        ens.init_fields(k, *_fields(r, k))
+    ens.step(3)
+    before = [ens.populations(k) for k in range(len(RUNS))]
+    bx, by, grid = ens.autotune(2)
+    assert (bx, by) in ((64, 8), (64, 16), (32, 16), (128, 8)) and grid >= 1
+    for k in range(len(RUNS)):
+        np.testing.assert_array_equal(ens.populations(k), before[k])
+    info = ens.info()
+    nodes = sum(r["nx"] * r["ny"] for r in RUNS)
+    forced = sum(r["nx"] * r["ny"] for r in RUNS if r["forcing"])
+    assert info["bytes_per_step"] == (nodes * 2 * 17 * 4 + forced * 8) // 2
+    ens.close()
 
 
 def test_ensemble_workload_shape_runs():
