@@ -428,19 +428,25 @@ def cpu_oracle_glups(oracle, w, n, budget_s):
 
 
 def e2e_glups(rl, w, n, form, landau, reps=3, steps_per_call=100):
-    """Through the public API with host buffers: upload the initial fields
-    from host memory, advance steps_per_call steps, read the fields back."""
-    eps, vx, vy = workloads.random_smooth(n, n, seed=5, deps=0.01, vmax=0.01)
+    """Through the public API with host buffers in pinned memory: upload the
+    initial fields, advance steps_per_call steps, read the fields back."""
+    import torch
+    fields = workloads.random_smooth(n, n, seed=5, deps=0.01, vmax=0.01)
+    pinned = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    inp = [pinned((n * n,)) for _ in range(3)]
+    for dst, src in zip(inp, fields):
+        dst[:] = np.ravel(src)
+    res = (pinned((n, n)), pinned((n, n)), pinned((n, n)), pinned((3,)))
     lat = rl.Lattice(n, n, w.tau, dtype=form, landau=landau, forcing=forcing_of(w))
-    lat.init_fields(eps, vx, vy)
+    lat.init_fields(*inp)
     lat.step(steps_per_call)
-    lat.moments()
+    lat.moments(out=res)
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        lat.init_fields(eps, vx, vy)
+        lat.init_fields(*inp)
         lat.step(steps_per_call)
-        out = lat.moments()
+        out = lat.moments(out=res)
         times.append(time.perf_counter() - t0)
     lat.close()
     dt = float(np.median(times))

@@ -555,12 +555,17 @@ class Lattice:
     def step(self, n: int = 1):
         rlbm_step(self.handle, n)
 
-    def moments(self):
-        """(eps, vx, vy, totals): (ny, nx) FP64 fields and totals[3]."""
-        eps = np.empty((self.ny, self.nx))
-        vx = np.empty((self.ny, self.nx))
-        vy = np.empty((self.ny, self.nx))
-        tot = np.empty(3)
+    def moments(self, out=None):
+        """(eps, vx, vy, totals): (ny, nx) FP64 fields and totals[3].  out:
+        optional (eps, vx, vy, totals) C-contiguous FP64 arrays to fill (for
+        example views of pinned host memory), returned as given."""
+        if out is None:
+            out = (np.empty((self.ny, self.nx)), np.empty((self.ny, self.nx)), np.empty((self.ny, self.nx)),
+                   np.empty(3))
+        eps, vx, vy, tot = out
+        for a, n in ((eps, self.nx * self.ny), (vx, self.nx * self.ny), (vy, self.nx * self.ny), (tot, 3)):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+                raise ValueError("moments(out=...) needs C-contiguous FP64 arrays of the lattice's size")
         rlbm_moments(self.handle, eps, vx, vy, tot)
         return eps, vx, vy, tot
 

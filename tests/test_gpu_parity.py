@@ -221,6 +221,25 @@ def test_step_zero_and_info():
     lat.close()
 
 
+def test_moments_into_caller_buffers():
+    """moments(out=...) fills caller arrays (here pinned host memory) with the
+    same values as the allocating form, and rejects arrays of the wrong kind."""
+    nx, ny = 48, 40
+    lat = rl.Lattice(nx, ny, 0.7, dtype="f32", forcing=FORCING_SMALL)
+    lat.init_fields(*workloads.random_smooth(nx, ny, seed=3))
+    lat.step(9)
+    ref = lat.moments()
+    pinned = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    out = (pinned((ny, nx)), pinned((ny, nx)), pinned((ny, nx)), pinned((3,)))
+    got = lat.moments(out=out)
+    assert all(g is o for g, o in zip(got, out))
+    for a, b in zip(ref, got):
+        np.testing.assert_array_equal(a, b)
+    with pytest.raises(ValueError):
+        lat.moments(out=(np.empty((ny, nx), dtype=np.float32),) + out[1:])
+    lat.close()
+
+
 def test_invalid_initial_fields_rejected():
     lat = rl.Lattice(8, 8, 0.8, dtype="f64")
     with pytest.raises(rl.RLBMError):
