@@ -82,7 +82,7 @@ _STEP_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_gather.cuh", "k_step_v
                  "k_launch.cuh", "k_step_f32.cu", "k_step_f64.cu", "k_step_h16.cu")
 _TMA_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_tma.cuh", "k_step_tma.cu")
 _FUSED2_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_pair.cuh", "k_step_fused2.cuh",
-                   "k_step_fused2.cu")
+                   "k_fused2_launch.cuh", "k_step_fused2.cu", "k_step_fused2_sub.cu")
 
 
 def step_kernel_source_hash(kernel_id=4):

@@ -116,8 +116,8 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * within one) and an odd remainder runs the packed single step; results
  * equal those of PACKED bit for bit.  block_x x block_y of the launch shape
  * is the output tile (64 x 16, 64 x 8, 32 x 16 or 128 x 8 nodes).
- * The vector, TMA, two-pass and two-step variants stream at CFL 1 only, the
- * packed kernel at any cfl (halo 2 above 1).
+ * The vector, TMA and two-pass variants stream at CFL 1 only, the two-step
+ * kernel at cfl <= 1 (halo 1), the packed kernel at any cfl (halo 2 above 1).
  * AUTO: the autotuned choice if one is cached for this lattice, else
  * GATHER. */
 typedef enum {
@@ -172,7 +172,7 @@ typedef struct {
      * spacings 0.32, 0.16, 0.08, 0.04, i.e. cfl 0.156 ... 1.25).  cfl > 1
      * reaches two cells (halo 2) for the classes with cfl |v_i,a| > 1.
      * cfl != 1 runs the one-node-per-thread (GATHER) or the packed kernel
-     * (PACKED). */
+     * (PACKED), and cfl < 1 also the two-step kernel (FUSED2). */
     double cfl;
     /* eta/s > 0 switches the relaxation time to the paper's
      * tau_R = 5 (eta/s) / T with eps = 3 T^4 / pi^2 (Sec. 3.1-3.2), node by

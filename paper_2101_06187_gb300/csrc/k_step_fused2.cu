@@ -1,48 +1,24 @@
 // Two-steps-per-launch (temporally blocked) form of the packed step:
-// instantiations and launcher.  FP32 arithmetic with the FP32 Landau
-// solve, FP32 / BF16 / FP16 storage, CFL 1, nx even.
-#include "k_step_fused2.cuh"
-#include "rlbm_internal.h"
+// CFL-1 and ensemble instantiations, and the launchers.  FP32 arithmetic
+// with the FP32 Landau solve, FP32 / BF16 / FP16 storage, cfl <= 1, nx even.
+#include "k_fused2_launch.cuh"
 
 namespace rlbk {
 namespace {
 
-// Tile shapes: output tile TW x TH, NT threads, MINB resident CTAs per SM
-// (shared memory per CTA: 17 (TW + 4)(TH + 2) stored values).
+// The ensemble kernels of tile shape TW x TH (CFL 1).
 template <typename TS, int TW, int TH, int NT, int MINB>
-struct Fused2 {
+struct Fused2Batch {
     static constexpr int smem = fused2_smem_bytes<TS, TW, TH>();
-
-    template <bool FORCED, typename I>
-    static void *fn() {
-        return reinterpret_cast<void *>(&k_step_fused2<TS, FORCED, TW, TH, NT, MINB, I>);
-    }
     static cudaError_t prepare() {
-        for (void *f : {fn<true, int>(), fn<false, int>(), fn<true, long long>(), fn<false, long long>(),
-                        reinterpret_cast<void *>(&k_step_batch_fused2<TS, TW, TH, NT, MINB, true>),
+        for (void *f : {reinterpret_cast<void *>(&k_step_batch_fused2<TS, TW, TH, NT, MINB, true>),
                         reinterpret_cast<void *>(&k_step_batch_fused2<TS, TW, TH, NT, MINB, false>)}) {
             const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     }
-    static cudaError_t launch(bool forced, const void *qin, void *qout, const void *F, const StepParams &p,
-                              cudaStream_t s) {
-        const TS *in = static_cast<const TS *>(qin);
-        TS *out = static_cast<TS *>(qout);
-        const float *f = static_cast<const float *>(F);
-        const dim3 grid((p.nx + TW - 1) / TW, (p.ny + TH - 1) / TH, 1);
-        const bool idx32 = (long long)NC * p.plane < (1ll << 31) - 1;
-        if (idx32) {
-            if (forced) k_step_fused2<TS, true, TW, TH, NT, MINB, int><<<grid, NT, smem, s>>>(in, out, f, p);
-            else k_step_fused2<TS, false, TW, TH, NT, MINB, int><<<grid, NT, smem, s>>>(in, out, f, p);
-        } else {
-            if (forced) k_step_fused2<TS, true, TW, TH, NT, MINB, long long><<<grid, NT, smem, s>>>(in, out, f, p);
-            else k_step_fused2<TS, false, TW, TH, NT, MINB, long long><<<grid, NT, smem, s>>>(in, out, f, p);
-        }
-        return cudaGetLastError();
-    }
-    static cudaError_t launch_batch(int grid, const void *runs, int nruns, int ntiles, int two, cudaStream_t s) {
+    static cudaError_t launch(int grid, const void *runs, int nruns, int ntiles, int two, cudaStream_t s) {
         const BatchRun *r = static_cast<const BatchRun *>(runs);
         if (two) k_step_batch_fused2<TS, TW, TH, NT, MINB, true><<<grid, NT, smem, s>>>(r, nruns, ntiles);
         else k_step_batch_fused2<TS, TW, TH, NT, MINB, false><<<grid, NT, smem, s>>>(r, nruns, ntiles);
@@ -50,19 +26,12 @@ struct Fused2 {
     }
 };
 
-// The tile shapes on offer, by (bx, by) = (TW, TH) of the launch shape.
-#define RLBM_FUSED2_SHAPES(X) \
-    X(64, 16, 256, 2)         \
-    X(64, 8, 128, 4)          \
-    X(32, 16, 128, 4)         \
-    X(128, 8, 256, 2)
-
 template <typename TS>
-cudaError_t prepare_t() {
-#define X(TW, TH, NT, MB)                                              \
-    {                                                                  \
-        const cudaError_t e = Fused2<TS, TW, TH, NT, MB>::prepare();   \
-        if (e != cudaSuccess) return e;                                \
+cudaError_t batch_prepare_t() {
+#define X(TW, TH, NT, MB)                                                  \
+    {                                                                      \
+        const cudaError_t e = Fused2Batch<TS, TW, TH, NT, MB>::prepare();  \
+        if (e != cudaSuccess) return e;                                    \
     }
     RLBM_FUSED2_SHAPES(X)
 #undef X
@@ -70,21 +39,11 @@ cudaError_t prepare_t() {
 }
 
 template <typename TS>
-cudaError_t launch_t(const LaunchCfg &cfg, bool forced, const void *qin, void *qout, const void *F,
-                     const StepParams &p, cudaStream_t s) {
-#define X(TW, TH, NT, MB) \
-    if (cfg.bx == TW && cfg.by == TH) return Fused2<TS, TW, TH, NT, MB>::launch(forced, qin, qout, F, p, s);
-    RLBM_FUSED2_SHAPES(X)
-#undef X
-    return cudaErrorInvalidConfiguration;
-}
-
-template <typename TS>
 cudaError_t launch_batch_t(const LaunchCfg &cfg, int grid, const void *runs, int nruns, int ntiles, int two,
                            cudaStream_t s) {
 #define X(TW, TH, NT, MB)                                                                       \
     if (cfg.bx == TW && cfg.by == TH)                                                           \
-        return Fused2<TS, TW, TH, NT, MB>::launch_batch(grid, runs, nruns, ntiles, two, s);
+        return Fused2Batch<TS, TW, TH, NT, MB>::launch(grid, runs, nruns, ntiles, two, s);
     RLBM_FUSED2_SHAPES(X)
 #undef X
     return cudaErrorInvalidConfiguration;
@@ -93,21 +52,19 @@ cudaError_t launch_batch_t(const LaunchCfg &cfg, int grid, const void *runs, int
 }  // namespace
 
 cudaError_t fused2_prepare() {
-    cudaError_t e = prepare_t<float>();
-    if (e == cudaSuccess) e = prepare_t<__nv_bfloat16>();
-    if (e == cudaSuccess) e = prepare_t<__half>();
+    cudaError_t e = fused2_prepare_mode<kStreamCfl1>();
+    if (e == cudaSuccess) e = fused2_prepare_sub1();
+    if (e == cudaSuccess) e = batch_prepare_t<float>();
+    if (e == cudaSuccess) e = batch_prepare_t<__nv_bfloat16>();
+    if (e == cudaSuccess) e = batch_prepare_t<__half>();
     return e;
 }
 
 cudaError_t launch_step_fused2(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                                const void *F, const StepParams &p, cudaStream_t s) {
-    if (landau != RLBM_LANDAU_FP32 || p.cfl != 1.0 || p.nx % 2 != 0) return cudaErrorInvalidValue;
-    switch (dtype) {
-    case RLBM_F32: return launch_t<float>(cfg, forced, qin, qout, F, p, s);
-    case RLBM_BF16: return launch_t<__nv_bfloat16>(cfg, forced, qin, qout, F, p, s);
-    case RLBM_F16: return launch_t<__half>(cfg, forced, qin, qout, F, p, s);
-    default: return cudaErrorInvalidValue;
-    }
+    if (landau != RLBM_LANDAU_FP32 || p.nx % 2 != 0 || !(p.cfl > 0.0 && p.cfl <= 1.0)) return cudaErrorInvalidValue;
+    if (p.cfl == 1.0) return fused2_launch_mode<kStreamCfl1>(dtype, cfg, forced, qin, qout, F, p, s);
+    return fused2_launch_sub1(dtype, cfg, forced, qin, qout, F, p, s);
 }
 
 cudaError_t launch_batch_fused2(int dtype, int landau, const LaunchCfg &cfg, int grid, const void *runs, int nruns,

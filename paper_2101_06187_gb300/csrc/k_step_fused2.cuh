@@ -45,40 +45,72 @@ __device__ __forceinline__ float lds1(const TS *p) {
     else return __bfloat162float(*p);
 }
 
-// CFL-1 pull of the node pair (x0, x0 + 1) from a state laid out as NC
-// planes of `plane` elements: rows[k] is the offset of row y - 1 + k, xl and
-// xr the columns x0 - 1 and x0 + 2.  SHARED selects shared-memory reads.
-// The same taps, weights and operation order as step_pair at CFL 1.
-template <typename TS, typename I, bool SHARED>
-__device__ __forceinline__ void pull_pair_cfl1(const TS *__restrict__ src, I plane, const I (&rows)[3], I x0, I xl,
-                                               I xr, pf2 (&q)[NC]) {
+// Pull of the node pair (x0, x0 + 1) from a state laid out as NC planes of
+// `plane` elements: rows[k] is the offset of row y - 1 + k, xl and xr the
+// columns x0 - 1 and x0 + 2.  SHARED selects shared-memory reads.  SM is
+// kStreamCfl1 (corners and weights fixed at compile time) or kStreamSub1
+// (0 < cfl < 1: each moving class between its near corner and the cell it
+// streams from, with the launch's weights); the same taps, weights and
+// operation order as step_pair in that mode.
+template <typename TS, typename I, bool SHARED, int SM>
+__device__ __forceinline__ void pull_pair(const TS *__restrict__ src, const StepParams &p, I plane,
+                                          const I (&rows)[3], I x0, I xl, I xr, pf2 (&q)[NC]) {
+    static_assert(SM == kStreamCfl1 || SM == kStreamSub1, "halo-1 streaming modes only");
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
-        constexpr int ox = cls_ox(c), oy = cls_oy(c);
-        constexpr double tx = cls_tx(c), ty = cls_ty(c);
-        auto row = [&](I r, float (&a)[4]) {
+        // the class row around the pair: a[1], a[2] = columns x0, x0 + 1; a[0] = x0 - 1 if LEFT;
+        // a[3] = x0 + 2 if RIGHT
+        auto row = [&](I r, float (&a)[4], auto left, auto right) {
             const TS *base = src + ((I)c * plane + r);
             if constexpr (SHARED) {
                 lds_run2<TS>(base + x0, &a[1]);
-                if constexpr (ox == -1) a[0] = lds1<TS>(base + xl);
-                if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[3] = lds1<TS>(base + xr);
+                if constexpr (decltype(left)::value) a[0] = lds1<TS>(base + xl);
+                if constexpr (decltype(right)::value) a[3] = lds1<TS>(base + xr);
             } else {
                 load_run<TS, float, 2>(base + x0, &a[1]);
-                if constexpr (ox == -1) a[0] = load_q<TS, float>(base + xl);
-                if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[3] = load_q<TS, float>(base + xr);
+                if constexpr (decltype(left)::value) a[0] = load_q<TS, float>(base + xl);
+                if constexpr (decltype(right)::value) a[3] = load_q<TS, float>(base + xr);
             }
         };
-        float a[4];  // columns x0-1 .. x0+2
-        row(rows[oy + 1], a);
-        pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
-        if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
-        if constexpr (ty != 0.0) {
-            float b[4];
-            row(rows[oy + 2], b);
-            v = fmadd(pf2((float)((1.0 - tx) * ty)), pf2(b[ox + 1], b[ox + 2]), v);
-            if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
+        if constexpr (SM == kStreamCfl1) {
+            constexpr int ox = cls_ox(c), oy = cls_oy(c);
+            constexpr double tx = cls_tx(c), ty = cls_ty(c);
+            using L = std::integral_constant<bool, ox == -1>;
+            using R = std::integral_constant<bool, ox == 1 || (ox == 0 && tx != 0.0)>;
+            float a[4];  // columns x0-1 .. x0+2
+            row(rows[oy + 1], a, L{}, R{});
+            pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
+            if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
+            if constexpr (ty != 0.0) {
+                float b[4];
+                row(rows[oy + 2], b, L{}, R{});
+                v = fmadd(pf2((float)((1.0 - tx) * ty)), pf2(b[ox + 1], b[ox + 2]), v);
+                if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * ty)), pf2(b[ox + 2], b[ox + 3]), v);
+            }
+            q[c] = v;
+        } else {
+            // near corner (the class's own cell on an axis where it does not move)
+            constexpr double cx = cls_cx(c), cy = cls_cy(c);
+            constexpr int nx_ = cx > 0 ? -1 : 0, ny_ = cy > 0 ? -1 : 0;
+            constexpr bool mx = cx != 0.0, my = cy != 0.0;
+            using L = std::integral_constant<bool, mx && nx_ == -1>;
+            using R = std::integral_constant<bool, mx && nx_ == 0>;
+            float a[4];  // columns x0-1 .. x0+2
+            row(rows[ny_ + 1], a, L{}, R{});
+            if constexpr (!mx && !my) {
+                q[c] = pf2(a[1], a[2]);
+            } else {
+                pf2 v = pf2(par_wt<float>(p, c, 0)) * pf2(a[nx_ + 1], a[nx_ + 2]);
+                if constexpr (mx) v = fmadd(pf2(par_wt<float>(p, c, 1)), pf2(a[nx_ + 2], a[nx_ + 3]), v);
+                if constexpr (my) {
+                    float b[4];
+                    row(rows[ny_ + 2], b, L{}, R{});
+                    v = fmadd(pf2(par_wt<float>(p, c, 2)), pf2(b[nx_ + 1], b[nx_ + 2]), v);
+                    if constexpr (mx) v = fmadd(pf2(par_wt<float>(p, c, 3)), pf2(b[nx_ + 2], b[nx_ + 3]), v);
+                }
+                q[c] = v;
+            }
         }
-        q[c] = v;
     });
 }
 
@@ -114,9 +146,10 @@ __device__ __forceinline__ int wrap_window(int a, int n) {
 }
 
 // Two steps of the TW x TH tile whose first node is (tx0, ty0), by the NT
-// threads of a CTA, through the shared window S.  Needs nx even and CFL 1;
-// nodes of the tile past the lattice edge are not written.
-template <typename TS, bool FORCED, int TW, int TH, int NT, typename I>
+// threads of a CTA, through the shared window S.  Needs nx even and a
+// halo-1 streaming mode SM (cfl <= 1); nodes of the tile past the lattice
+// edge are not written.
+template <typename TS, bool FORCED, int TW, int TH, int NT, typename I, int SM = kStreamCfl1>
 __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__restrict__ qout,
                                             const float *__restrict__ F, const StepParams &p, int tx0, int ty0,
                                             TS *__restrict__ S) {
@@ -137,7 +170,7 @@ __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__re
         const int xr = (x0 + 2 == p.nx) ? 0 : x0 + 2;
         const I rows[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
         pf2 q[NC];
-        pull_pair_cfl1<TS, I, false>(qin, plane, rows, (I)x0, (I)xl, (I)xr, q);
+        pull_pair<TS, I, false, SM>(qin, p, plane, rows, (I)x0, (I)xl, (I)xr, q);
         pf2 Fx, Fy;
         force_pair<I, FORCED>(F, plane, rows[1] + (I)x0, Fx, Fy);
         collide_node<pf2, pf2, FORCED>(q, Fx, Fy, p);
@@ -157,7 +190,7 @@ __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__re
         const int lr = r + 1, lc = c2 + 2;
         const int rows[3] = {(lr - 1) * SW, lr * SW, (lr + 1) * SW};
         pf2 q[NC];
-        pull_pair_cfl1<TS, int, true>(S, SPLANE, rows, lc, lc - 1, lc + 2, q);
+        pull_pair<TS, int, true, SM>(S, p, SPLANE, rows, lc, lc - 1, lc + 2, q);
         const I n0 = (I)y * (I)p.pitch + (I)x0;
         pf2 Fx, Fy;
         force_pair<I, FORCED>(F, plane, n0, Fx, Fy);
@@ -171,12 +204,12 @@ __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__re
 }
 
 // Two steps of the lattice, one TW x TH tile per CTA (blockIdx.x, blockIdx.y).
-template <typename TS, bool FORCED, int TW, int TH, int NT, int MINB, typename I>
+template <typename TS, bool FORCED, int TW, int TH, int NT, int MINB, typename I, int SM = kStreamCfl1>
 __global__ void __launch_bounds__(NT, MINB)
     k_step_fused2(const TS *__restrict__ qin, TS *__restrict__ qout, const float *__restrict__ F, StepParams p) {
     extern __shared__ __align__(16) unsigned char fused2_smem[];
-    fused2_tile<TS, FORCED, TW, TH, NT, I>(qin, qout, F, p, blockIdx.x * TW, blockIdx.y * TH,
-                                           reinterpret_cast<TS *>(fused2_smem));
+    fused2_tile<TS, FORCED, TW, TH, NT, I, SM>(qin, qout, F, p, blockIdx.x * TW, blockIdx.y * TH,
+                                               reinterpret_cast<TS *>(fused2_smem));
 }
 
 // Ensemble form: a grid-stride walk over the flat tile list of all members

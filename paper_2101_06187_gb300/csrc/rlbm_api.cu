@@ -328,7 +328,8 @@ static const LaunchCfg kCandidates[] = {
 // remaining misfits: storage form, Landau precision, nx parity).
 static bool candidate_applies(const rlbm_t *h, const LaunchCfg &c) {
     if (h->opts.cfl != 1.0 && c.kernel != RLBM_KERNEL_GATHER &&
-        !(c.kernel == RLBM_KERNEL_PACKED && c.minb <= 2 && !h->ring && !h->d3))
+        !(c.kernel == RLBM_KERNEL_PACKED && c.minb <= 2 && !h->ring && !h->d3) &&
+        !(c.kernel == RLBM_KERNEL_FUSED2 && h->opts.cfl < 1.0 && !h->ring && !h->d3))
         return false;
     if ((h->d3 || h->ring) && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED) return false;
     if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) return false;
@@ -475,9 +476,9 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (!(o.cfl > 0.0 && o.cfl < 2.0) || !(o.eta_s >= 0.0) || !isfinite(o.eta_s) || !(o.dt > 0.0) || !isfinite(o.dt))
         return RLBM_ERR_ARG;
     if (o.cfl != 1.0 && (o.kernel == RLBM_KERNEL_GATHER_VEC || o.kernel == RLBM_KERNEL_GATHER_VEC2 ||
-                         o.kernel == RLBM_KERNEL_TMA || o.kernel == RLBM_KERNEL_TWOPASS ||
-                         o.kernel == RLBM_KERNEL_FUSED2))
+                         o.kernel == RLBM_KERNEL_TMA || o.kernel == RLBM_KERNEL_TWOPASS))
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
+    if (o.cfl > 1.0 && o.kernel == RLBM_KERNEL_FUSED2) return RLBM_ERR_ARG;  // two steps per launch: halo 1
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
     if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER && o.kernel != RLBM_KERNEL_PACKED) ||

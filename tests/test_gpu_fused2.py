@@ -73,6 +73,21 @@ def test_graphs_and_direct_launches_agree():
     np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("cfl", [0.625, 0.15625, 0.9])
+def test_sub_unit_cfl_equals_packed(cfl, dtype, tile):
+    """0 < cfl < 1 (the paper's time steps on its coarser lattices, Sec. 5):
+    runtime bilinear weights, halo 1; bit for bit against the packed kernel."""
+    nx, ny = 130, 27
+    fields = workloads.random_smooth(nx, ny, seed=17, deps=0.05, vmax=0.05)
+    kw = dict(cfl=cfl, eta_s=0.01, dt=0.05)
+    ref, _ = _run("packed", nx, ny, dtype, fields, **kw)
+    got, info = _run("fused2", nx, ny, dtype, fields, tile=tile, **kw)
+    assert info["kernel"] == rl.KERNELS["fused2"] and info["steps_per_launch"] == 2
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_eta_over_s_relaxation_equals_packed():
     nx, ny = 96, 40
     fields = workloads.random_smooth(nx, ny, seed=9, deps=0.05, vmax=0.05)

@@ -309,7 +309,7 @@ def test_spectrum_statistics_match_oracle_samples():
     lat.close()
 
 
-@pytest.mark.parametrize("dtype,kernel", [("f64", "gather"), ("f32", "gather"), ("f32", "packed")])
+@pytest.mark.parametrize("dtype,kernel", [("f64", "gather"), ("f32", "gather"), ("f32", "packed"), ("f32", "fused2")])
 @pytest.mark.parametrize("cfl,eta_s", [(0.5, 0.0), (0.15625, 0.01), (0.625, 0.01), (1.0, 0.01), (1.25, 0.01),
                                        (1.25, 0.0), (1.75, 0.0)])
 def test_cfl_and_eta_over_s_match_oracle(dtype, kernel, cfl, eta_s):
@@ -320,6 +320,8 @@ def test_cfl_and_eta_over_s_match_oracle(dtype, kernel, cfl, eta_s):
     dt = 0.05
     fields = workloads.random_smooth(nx, ny, seed=61, deps=0.05, vmax=0.05)
     forcing = dict(kmin=2, kmax=4, amp=2e-4, seed=17, redraw_period=9)
+    if kernel == "fused2" and cfl > 1.0:
+        pytest.skip("two steps per launch keep a halo of 1: cfl <= 1")
     lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, forcing=forcing, cfl=cfl, eta_s=eta_s, dt=dt, kernel=kernel)
     assert lat.info()["kernel"] == rl.KERNELS[kernel]
     lat.init_fields(*fields)
