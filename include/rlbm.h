@@ -210,7 +210,9 @@ typedef struct {
 /* Fill *opts with the defaults listed above. */
 RLBM_API void rlbm_opts_default(rlbm_opts *opts);
 
-/* Create a lattice of nx x ny nodes (nx, ny >= 4) with relaxation time
+/* Create a lattice of nx x ny nodes (nx, ny >= 4, nx * ny <= 2^31,
+ * ny <= 65535: the kernels put rows on the y dimension of the launch grid)
+ * with relaxation time
  * tau > 1/2 (Eq. boltzmanneq_rel; eta = tau (eps + P)/5, Sec. 3.1) and
  * optional forcing (NULL = none; needs kmax < min(nx, ny)/2, amp >= 0,
  * 1 <= kmin <= kmax).  opts may be NULL (defaults).  The state starts as the
@@ -321,7 +323,7 @@ RLBM_API rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info);
  * (rlbm_energy_spectrum, rlbm_filtered_velocity, rlbm_spectrum_*), which
  * then bin |k| = (kx^2 + ky^2 + kz^2)^{1/2} over the three velocity
  * components; rlbm_init_fields, rlbm_moments[_device] and rlbm_get_force
- * return RLBM_ERR_STATE.  Errors as rlbm_create; nz >= 4, nx*ny*nz <= 2^31,
+ * return RLBM_ERR_STATE.  Errors as rlbm_create; nz >= 4, nx*ny*nz <= 2^31, nz <= 65535,
  * 2 kmax < min(nx, ny, nz). */
 RLBM_API rlbm_status rlbm_create3d(int nx, int ny, int nz, double tau, const rlbm_forcing *forcing,
                                    const rlbm_opts *opts, rlbm_t **out);

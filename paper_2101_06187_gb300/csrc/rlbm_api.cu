@@ -452,6 +452,7 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (d3 && (ring || nz < 4)) return RLBM_ERR_ARG;
     if (!d3) nz = 1;
     if (nx < 4 || ny < 4 || (long long)nx * ny * nz > (1ll << 31)) return RLBM_ERR_ARG;
+    if (ny > 65535 || nz > 65535) return RLBM_ERR_ARG;  // rows and layers span launch-grid y and z
     if (!(tau > 0.5) || !isfinite(tau)) return RLBM_ERR_ARG;
     rlbm_opts o;
     rlbm_opts_default(&o);

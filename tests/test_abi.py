@@ -58,6 +58,7 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
 
     assert create(3, 16, 0.8) == rl.RLBM_ERR_ARG          # nx < 4
     assert create(16, 2, 0.8) == rl.RLBM_ERR_ARG          # ny < 4
+    assert create(16, 65536, 0.8) == rl.RLBM_ERR_ARG      # ny beyond the launch grid's y dimension
     assert create(16, 16, 0.5) == rl.RLBM_ERR_ARG         # tau must exceed 1/2
     assert create(16, 16, float("nan")) == rl.RLBM_ERR_ARG
     assert create(16, 16, 0.8, st=2) == rl.RLBM_ERR_ARG   # unknown stencil

@@ -95,7 +95,8 @@ def stirred_1024_oracle():
 
 
 @pytest.mark.parametrize("dtype,tol,kernel", [("f32", 1e-5, "auto"), ("f64", 1e-12, "auto"), ("f32", 1e-5, "tma"),
-                                             ("f32", 1e-5, "packed"), ("f32", 1e-5, "twopass")])
+                                             ("f32", 1e-5, "packed"), ("f32", 1e-5, "twopass"),
+                                             ("f32", 1e-5, "fused2")])
 def test_stirred_1024_full_size_matches_oracle(stirred_1024_oracle, dtype, tol, kernel):
     w = workloads.STIRRED_1024
     lat = rl.Lattice(w.nx, w.ny, w.tau, dtype=dtype, forcing=_forcing(w), kernel=kernel)
@@ -122,7 +123,8 @@ def tiled_reference():
 
 
 @pytest.mark.parametrize("n,dtype,kernel", [(4096, "bf16", "auto"), (4096, "f16", "auto"), (4096, "f32", "auto"),
-                                           (8192, "f32", "auto"), (8192, "f32", "tma")])
+                                           (8192, "f32", "auto"), (8192, "f32", "tma"), (8192, "f32", "fused2"),
+                                           (4096, "bf16", "fused2")])
 def test_full_size_lattice_stays_an_exact_tiling(tiled_reference, n, dtype, kernel):
     period, tau, nsteps, ref = tiled_reference
     e, a, b = workloads.random_tiled(n, n, period, seed=77, deps=0.02, vmax=0.02)
@@ -157,16 +159,18 @@ def test_full_size_force_at_sampled_nodes(w, dtype):
     lat.close()
 
 
-def test_lattice_beyond_32bit_offsets_stays_an_exact_tiling(tiled_reference):
-    """12032^2 FP32 (145 M nodes, 17 planes = 2.5 G elements: the packed
-    kernel's 64-bit offset path), started on the device from the tiled
-    fields; sampled rows of the moments against the oracle's 64^2 tile."""
+@pytest.mark.parametrize("kernel", ["packed", "fused2"])
+def test_lattice_beyond_32bit_offsets_stays_an_exact_tiling(tiled_reference, kernel):
+    """12032^2 FP32 (145 M nodes, 17 planes = 2.5 G elements: the 64-bit
+    offset path of the packed and two-step kernels), started on the device
+    from the tiled fields; sampled rows of the moments against the oracle's
+    64^2 tile."""
     period, tau, nsteps, ref = tiled_reference
     n = 12032
     rep = n // period
     e, a, b = workloads.random_smooth(period, period, seed=77, deps=0.02, vmax=0.02)
     dev = lambda g: torch.as_tensor(g, dtype=torch.float64, device="cuda").repeat(rep, rep).contiguous()
-    lat = rl.Lattice(n, n, tau, dtype="f32", kernel="packed")
+    lat = rl.Lattice(n, n, tau, dtype="f32", kernel=kernel)
     fe, fa, fb = dev(e), dev(a), dev(b)
     lat.init_fields_device(fe, fa, fb)
     lat.step(nsteps)
