@@ -73,9 +73,11 @@ typedef enum {
  *   with its quasi-2D one (Sec. 3.1): 8 unit momenta in the plane at 45
  *   degree steps, weight 1/8, P = eps/2, c_s^2 = 1/2; the same step with the
  *   circle's angular polynomials (norms 1, 2, 4).  It runs the one node per
- *   thread kernel (GATHER) or the packed-lane kernel (PACKED: FP32 compute
- *   with RLBM_LANDAU_FP32, nx even), at cfl 1 and fixed tau (eta_s 0), and
- *   is not available to ensembles.  rlbm_info_t.nclasses is 8 and the
+ *   thread kernel (GATHER), the packed-lane kernel (PACKED: FP32 compute
+ *   with RLBM_LANDAU_FP32, nx even) or two steps per launch with the packed
+ *   body (FUSED2, same conditions; its tiles run at a fixed 3 (256-thread)
+ *   or 6 (128-thread) CTAs per SM whatever launch_budget says), at cfl 1 and
+ *   fixed tau (eta_s 0), and is not available to ensembles.  rlbm_info_t.nclasses is 8 and the
  *   population arrays have 8 planes, in ring order k = 0..7 (angle k*45deg). */
 typedef enum { RLBM_STENCIL_SPH26_SLAB = 0, RLBM_STENCIL_RING8_2D = 1 } rlbm_stencil;
 

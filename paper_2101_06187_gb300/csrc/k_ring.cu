@@ -1,12 +1,43 @@
 // Launchers of the 2D ring variant (k_ring.cuh) for every storage form.
 #include "k_ring.cuh"
+#include "k_ring_fused2.cuh"
 #include "rlbm_internal.h"
 
 namespace rlbk {
 
+// Two ring steps per launch: tile TW x TH of cfg.bx x cfg.by, with the
+// thread count and resident CTAs per SM fixed per tile (<= 85 registers).
+template <typename TS>
+static cudaError_t ring_fused2_t(const LaunchCfg &cfg, bool forced, const void *qin, void *qout, const void *F,
+                                 const StepParams &p, cudaStream_t s) {
+    if (p.nx % 2 != 0 || p.cfl != 1.0) return cudaErrorInvalidValue;
+    const TS *in = static_cast<const TS *>(qin);
+    TS *out = static_cast<TS *>(qout);
+    const float *f = static_cast<const float *>(F);
+#define RLBM_RING_TILE(TW, TH, NT, MB)                                                                  \
+    if (cfg.bx == TW && cfg.by == TH) {                                                                 \
+        const dim3 grid((p.nx + TW - 1) / TW, (p.ny + TH - 1) / TH, 1);                                \
+        if (forced) k_ring_fused2<TS, true, TW, TH, NT, MB><<<grid, NT, 0, s>>>(in, out, f, p);         \
+        else k_ring_fused2<TS, false, TW, TH, NT, MB><<<grid, NT, 0, s>>>(in, out, f, p);               \
+        return cudaGetLastError();                                                                      \
+    }
+    RLBM_RING_TILE(64, 16, 256, 3)
+    RLBM_RING_TILE(64, 8, 128, 6)
+    RLBM_RING_TILE(32, 16, 128, 6)
+    RLBM_RING_TILE(128, 8, 256, 3)
+#undef RLBM_RING_TILE
+    return cudaErrorInvalidConfiguration;
+}
+
 template <typename TS, typename TC, typename TL>
 static cudaError_t ring_step_t(const LaunchCfg &cfg, bool forced, const void *qin, void *qout, const void *F,
                                const StepParams &p, cudaStream_t s) {
+    if (cfg.kernel == RLBM_KERNEL_FUSED2) {
+        if constexpr (std::is_same<TC, float>::value && std::is_same<TL, float>::value)
+            return ring_fused2_t<TS>(cfg, forced, qin, qout, F, p, s);
+        else
+            return cudaErrorInvalidValue;  // packed lanes: FP32 compute with the FP32 Landau solve
+    }
     if (cfg.bx < 1 || cfg.by < 1 || cfg.bx * cfg.by > 256) return cudaErrorInvalidConfiguration;
     const dim3 block(cfg.bx, cfg.by, 1);
     if (cfg.kernel == RLBM_KERNEL_PACKED) {

@@ -331,7 +331,9 @@ static bool candidate_applies(const rlbm_t *h, const LaunchCfg &c) {
         !(c.kernel == RLBM_KERNEL_PACKED && c.minb <= 2 && !h->ring && !h->d3) &&
         !(c.kernel == RLBM_KERNEL_FUSED2 && h->opts.cfl < 1.0 && !h->ring && !h->d3))
         return false;
-    if ((h->d3 || h->ring) && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED) return false;
+    if ((h->d3 || h->ring) && c.kernel != RLBM_KERNEL_GATHER && c.kernel != RLBM_KERNEL_PACKED &&
+        !(h->ring && c.kernel == RLBM_KERNEL_FUSED2))
+        return false;
     if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) return false;
     return true;
 }
@@ -482,7 +484,8 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (o.cfl > 1.0 && o.kernel == RLBM_KERNEL_FUSED2) return RLBM_ERR_ARG;  // two steps per launch: halo 1
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
-    if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER && o.kernel != RLBM_KERNEL_PACKED) ||
+    if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER && o.kernel != RLBM_KERNEL_PACKED &&
+                  o.kernel != RLBM_KERNEL_FUSED2) ||
                  o.cfl != 1.0 || o.eta_s != 0.0))
         return RLBM_ERR_ARG;
     // the 3D lattice runs the one-node-per-thread or the packed-lane kernel at CFL 1

@@ -95,7 +95,9 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
         assert create(nx, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG, (field, value, nx)
     o = rl.rlbm_opts_default()
     o.kernel = rl.KERNELS["fused2"]
-    assert create(16, 16, 0.8, opts=o, st=rl.RLBM_STENCIL_RING8_2D) == rl.RLBM_ERR_ARG
+    o.dtype = rl.DTYPES["f64"]
+    assert create(16, 16, 0.8, opts=o, st=rl.RLBM_STENCIL_RING8_2D) == rl.RLBM_ERR_ARG   # ring: FP32 lanes
+    o.dtype = rl.DTYPES["f32"]
     assert lib.rlbm_create3d(16, 16, 16, ctypes.c_double(0.8), None, ctypes.byref(o),
                              ctypes.byref(out)) == rl.RLBM_ERR_ARG   # not on the 3D lattice
     o.kernel = 8

@@ -62,7 +62,8 @@ def oracle_run(nx, ny, tau, nsteps, fields, forcing):
 
 
 @pytest.mark.parametrize("dtype,landau,kernel", [("f64", "fp64", "gather"), ("f32", "fp64", "gather"),
-                                                 ("f32", "fp32", "gather"), ("f32", "fp32", "packed")])
+                                                 ("f32", "fp32", "gather"), ("f32", "fp32", "packed"),
+                                                 ("f32", "fp32", "fused2")])
 @pytest.mark.parametrize("shape", [(38, 29), (64, 48), (300, 20), (4, 4)])
 def test_ring_forced_run_matches_oracle(dtype, landau, kernel, shape):
     nx, ny = shape
@@ -144,9 +145,37 @@ def test_ring_set_populations_round_trip_and_graphs():
     np.testing.assert_allclose(out[0], ref, rtol=0, atol=1e-12 * np.max(np.abs(ref - 0.125)))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("tile", [(64, 16, 2), (64, 8, 4), (32, 16, 4), (128, 8, 2)])
+@pytest.mark.parametrize("shape", [(130, 27), (4, 4), (200, 34)])
+def test_ring_two_step_launches_equal_packed_single_steps(dtype, tile, shape):
+    """Two ring steps per launch through shared memory: the packed ring
+    body for both steps, so bit for bit against k_ring_step_pair, for every
+    tile, ragged lattices, the 4x4 minimum, odd chunks across epochs and
+    graphs on and off."""
+    nx, ny = shape
+    forcing = FORCING_SMALL if min(nx, ny) > 8 else dict(kmin=1, kmax=1, amp=2e-3, seed=5, redraw_period=3)
+    fields = workloads.random_smooth(nx, ny, seed=31 * nx + ny, deps=0.05, vmax=0.05)
+    out = []
+    for kernel, graphs in (("packed", True), ("fused2", True), ("fused2", False)):
+        lat = rl.Lattice(nx, ny, 0.7, dtype=dtype, forcing=forcing, stencil="ring8", kernel=kernel,
+                         use_graphs=graphs)
+        lat.init_fields(*fields)
+        if kernel == "fused2":
+            lat.set_launch("fused2", *tile)
+            assert lat.info()["steps_per_launch"] == 2
+        for n in (1, 6, 13, 2, 9):
+            lat.step(n)
+        out.append(lat.populations())
+        lat.close()
+    np.testing.assert_array_equal(out[1], out[0])
+    np.testing.assert_array_equal(out[2], out[0])
+
+
 def test_ring_rejects_what_it_does_not_run():
     for kw in (dict(kernel="vec"), dict(kernel="tma"), dict(kernel="twopass"), dict(cfl=0.5), dict(eta_s=0.1),
-               dict(kernel="packed", dtype="f64")):
+               dict(kernel="packed", dtype="f64"), dict(kernel="fused2", dtype="f64"),
+               dict(kernel="fused2", landau="fp64")):
         with pytest.raises(rl.RLBMError):
             rl.Lattice(32, 32, 0.7, stencil="ring8", **kw)
 
