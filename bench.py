@@ -327,6 +327,28 @@ def parity_error(rl, oracle, form, landau):
     return {"eps": err_e, "v": err_v, "case": "128x128, 100 forced steps from seeded smooth fields"}
 
 
+def measure_configs(torch, rl, flush, hbm_peak, steps=40, warmup=6):
+    """The suite's other configurations at their own sizes and parameters,
+    each autotuned and timed like the headline (per-launch CUDA events, L2
+    flushed between launches): the 128^2 shear wave (FP64 form, unforced),
+    the 4096^2 precision run in BF16 and FP16 storage (tau 0.51, shell
+    8..10) and the 8192^2 FP32 run (tau 0.505, shell 16..18)."""
+    out = {}
+    cases = ((workloads.SHEAR_128, "f64", "fp64"), (workloads.PRECISION_4096, "bf16", "fp32"),
+             (workloads.PRECISION_4096, "f16", "fp32"), (workloads.LARGE_8192, "f32", "fp32"))
+    for w, form, landau in cases:
+        init = workloads.shear_wave(w.nx, w.ny, w.extra["u0"]) if w.init == "shear" else None
+        _, km, info, _ = measure_form(torch, rl, w, w.nx, form, landau, "auto", steps, warmup, flush, init=init)
+        nodes = w.nx * w.ny
+        bp = int(info["bytes_per_node"])
+        out["%s/%s" % (w.name, form)] = {
+            "glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_node": bp,
+            "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak,
+            "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]], "block": [info["block_x"], info["block_y"]],
+            "steps_per_launch": int(info["steps_per_launch"])}
+    return out
+
+
 def measure_variants(torch, rl, oracle, flush, hbm_peak, steps=50, warmup=5):
     """The lattice variants beyond the paper's one-layer node, each timed
     like the headline (per-step CUDA events, L2 flushed between steps) and
@@ -644,6 +666,7 @@ def main():
         line["forms"] = forms
         line["ensemble"] = measure_ensemble(torch, rl, flush)
         line["variants"] = measure_variants(torch, rl, oracle, flush, hbm_peak)
+        line["configs"] = measure_configs(torch, rl, flush, hbm_peak)
         line["e2e"] = e2e_glups(rl, w, n, args.form, args.landau)
         g, desc, th = cpu_oracle_glups(oracle, w, n, args.cpu_seconds)
         line["cpu_baseline"] = {"value": g, "unit": "GLUPS", "cores": th, "kind": "oracle", "sample": desc}
