@@ -332,16 +332,18 @@ def measure_configs(torch, rl, flush, hbm_peak, steps=40, warmup=6):
     each autotuned and timed like the headline (per-launch CUDA events, L2
     flushed between launches): the 128^2 shear wave (FP64 form, unforced),
     the 4096^2 precision run in BF16 and FP16 storage (tau 0.51, shell
-    8..10) and the 8192^2 FP32 run (tau 0.505, shell 16..18)."""
+    8..10; FP32 Landau solve, and BF16 with the FP64 solve that run names)
+    and the 8192^2 FP32 run (tau 0.505, shell 16..18)."""
     out = {}
     cases = ((workloads.SHEAR_128, "f64", "fp64"), (workloads.PRECISION_4096, "bf16", "fp32"),
-             (workloads.PRECISION_4096, "f16", "fp32"), (workloads.LARGE_8192, "f32", "fp32"))
+             (workloads.PRECISION_4096, "f16", "fp32"), (workloads.PRECISION_4096, "bf16", "fp64"),
+             (workloads.LARGE_8192, "f32", "fp32"))
     for w, form, landau in cases:
         init = workloads.shear_wave(w.nx, w.ny, w.extra["u0"]) if w.init == "shear" else None
         _, km, info, _ = measure_form(torch, rl, w, w.nx, form, landau, "auto", steps, warmup, flush, init=init)
         nodes = w.nx * w.ny
         bp = int(info["bytes_per_node"])
-        out["%s/%s" % (w.name, form)] = {
+        out["%s/%s/landau-%s" % (w.name, form, landau)] = {
             "glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_node": bp,
             "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak,
             "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]], "block": [info["block_x"], info["block_y"]],
