@@ -3,18 +3,20 @@
 //
 // A CTA owns a TW x TH tile of output nodes.  Step t -> t+1 is computed on
 // the tile grown by the one-cell pull halo of the next step (Sec. 3.2: at
-// CFL 1 a class pulls from the 3 x 3 neighbourhood), i.e. on (TW + 4) x
+// cfl <= 1 a class pulls from the 3 x 3 neighbourhood), i.e. on (TW + 4) x
 // (TH + 2) nodes -- two extra columns a side, so every node pair starts on
 // an even column and loads stay 8-byte aligned -- and kept in shared memory
 // in the storage type; step t+1 -> t+2 then pulls from shared memory and
 // writes the tile.  Per two steps the state is read from and written to HBM
-// once: half the traffic of two single-step launches, for about 10% more
-// arithmetic (the halo nodes are updated by every tile that needs them).
-// Both steps run the same per-node arithmetic as k_step_pair at CFL 1, and
-// the intermediate state is rounded to the storage type exactly as a
-// single step stores it, so two steps here equal two single steps bit for
-// bit.  The force field is the same for both steps: the host launches this
-// kernel only for step pairs inside one forcing epoch.
+// once: half the traffic of two single-step launches, for 10-20% more
+// arithmetic (the halo nodes are updated by every tile that needs them: 16%
+// for 64 x 8 tiles).  Both steps run the same per-node arithmetic as
+// k_step_pair in the same streaming mode (CFL 1, or 0 < cfl < 1 with the
+// launch's weights), and the intermediate state is rounded to the storage
+// type exactly as a single step stores it, so two steps here equal two
+// single steps bit for bit.  The force field is the same for both steps:
+// the host launches this kernel only for step pairs inside one forcing
+// epoch.
 #pragma once
 
 #include "k_step_pair.cuh"
