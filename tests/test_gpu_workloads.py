@@ -159,6 +159,32 @@ def test_full_size_force_at_sampled_nodes(w, dtype):
     lat.close()
 
 
+def test_full_size_8192_spectrum_of_two_modes():
+    """E(k) at the 8192^2 workload's size (the radix-2 transform at its
+    largest side): fields set on the device to a shear mode v_x = a sin(2 pi
+    y/N) and a mode v_y = b cos(2 pi 37 x/N) put their energies a^2/4 and
+    b^2/4 in shells 1 and 37 and nothing elsewhere (Parseval, a single mode
+    lands in its shell), read back through the FP32 populations.  The
+    diagnostic reports the state the next collision sees (after one pull
+    stream), whose bilinear interpolation damps a mode by O((k dx)^2):
+    2e-7 at k = 1, 8e-4 at k = 37 -- hence the looser bound there."""
+    w = workloads.LARGE_8192
+    n, k1, a, b = w.nx, 37, 1e-3, 2e-3
+    lat = rl.Lattice(n, n, w.tau, dtype="f32")
+    c = torch.arange(n, dtype=torch.float64, device="cuda")
+    vx = (a * torch.sin(2 * np.pi * c / n)).unsqueeze(1).expand(n, n).contiguous()
+    vy = (b * torch.cos(2 * np.pi * k1 * c / n)).unsqueeze(0).expand(n, n).contiguous()
+    eps = torch.ones((n, n), dtype=torch.float64, device="cuda")
+    lat.init_fields_device(eps, vx, vy)
+    E = lat.energy_spectrum(64)
+    lat.close()
+    del eps, vx, vy
+    assert abs(E[1] - a * a / 4) < 1e-5 * a * a / 4, E[1]
+    assert abs(E[k1] - b * b / 4) < 1e-3 * b * b / 4, E[k1]
+    others = np.delete(E, [1, k1])
+    assert np.max(others) < 1e-9 * E[k1], np.max(others)
+
+
 @pytest.mark.parametrize("kernel", ["packed", "fused2"])
 def test_lattice_beyond_32bit_offsets_stays_an_exact_tiling(tiled_reference, kernel):
     """12032^2 FP32 (145 M nodes, 17 planes = 2.5 G elements: the 64-bit
