@@ -254,15 +254,21 @@ def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, in
     return ms, kernel_ms, info, len(epoch_units)
 
 
-def measure_ensemble(torch, rl, flush, steps=20, warmup=5, nruns=64, sides=None):
+def measure_ensemble(torch, rl, flush, steps=20, warmup=5, nruns=64, sides=None, kernel="auto", tune=True):
     """The 64-member ensemble (sides 256..1024): per-step timing with an L2
-    flush between steps, and the throughput of a replayed 100-step graph."""
+    flush between steps, and the throughput of a replayed 100-step graph.
+    kernel / tune: pin the ensemble body and skip the autotuner (profiling
+    runs)."""
     members = workloads.ensemble(nruns) if sides is None else workloads.ensemble(nruns, sides=sides)
     runs = [dict(nx=w.nx, ny=w.ny, tau=w.tau,
                  forcing=dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw))
             for w in members]
-    ens = rl.Ensemble(runs, dtype="f32", landau="fp32")
-    bx, by, grid = ens.autotune(5)
+    ens = rl.Ensemble(runs, dtype="f32", landau="fp32", kernel=kernel)
+    if tune:
+        bx, by, grid = ens.autotune(5)
+    else:
+        i0 = ens.info()
+        bx, by, grid = i0["block_x"], i0["block_y"], i0["grid"]
     spl = int(ens.info()["steps_per_launch"])  # 2 for the two-step body: time whole launches
     ens.step(warmup + (-warmup) % spl)
     ens.synchronize()
@@ -564,7 +570,8 @@ def main():
     K, W = args.steps, max(3, args.warmup)
     flush = L2Flush(torch, L2_FLUSH_BYTES)
     if args.ensemble_only > 0:
-        res = measure_ensemble(torch, rl, flush, steps=K, warmup=W, nruns=args.ensemble_only, sides=(256, 384, 512))
+        res = measure_ensemble(torch, rl, flush, steps=K, warmup=W, nruns=args.ensemble_only, sides=(256, 384, 512),
+                               kernel=args.kernel, tune=not args.no_tune)
         print(json.dumps({"metric": METRIC, "value": res["glups"], "unit": "GLUPS", "n_gpus": 1, "steps": K,
                           "warmup": W, "higher_is_better": True, "config": {"workload": res["workload"]},
                           "ensemble": res}), flush=True)
