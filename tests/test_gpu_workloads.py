@@ -5,7 +5,9 @@ launch configuration the benchmark uses (autotuned).
   steps; decay over 2000 steps against the linear-mode analysis; totals
   conserved; rest state fixed.
 * 1024^2 stirred run (tau = 0.52, shell 4..6, amplitude 1e-5): 100 steps
-  against the oracle at full size, FP32 and FP64 forms.
+  against the oracle at full size, FP32 and FP64 forms, each kernel
+  variant, and the bench's variants at that size (the paper's time step
+  cfl 0.625 with eta/s; the 2D ring).
 * 4096^2 (16-bit forms) and 8192^2 (FP32): too large for the oracle, so
   (a) a lattice started from a field periodic with period 64 must stay an
   exact tiling of the oracle's 64^2 run (a property that holds at any size),
@@ -107,6 +109,42 @@ def test_stirred_1024_full_size_matches_oracle(stirred_1024_oracle, dtype, tol, 
     err_e, err_v = _errs(stirred_1024_oracle, lat.moments())
     assert err_e < tol and err_v < tol, (err_e, err_v)
     lat.close()
+
+
+def test_paper_time_step_full_size_matches_oracle():
+    """The paper's own time step on the 1024^2 workload (cfl 0.625, eta/s =
+    0.01, dt = 0.05: the bench's variant), autotuned as the bench runs it
+    (two steps per launch with runtime weights), 100 steps against the
+    oracle at full size."""
+    w = workloads.STIRRED_1024
+    kw = dict(cfl=0.625, eta_s=0.01, dt=0.05)
+    lat = rl.Lattice(w.nx, w.ny, w.tau, dtype="f32", forcing=_forcing(w), **kw)
+    lat.autotune(5)
+    lat.init_fields()
+    lat.step(100)
+    got = lat.moments()
+    lat.close()
+    f = oracle.init(w.nx, w.ny)
+    oracle.run(f, w.tau, 100, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw, **kw)
+    err_e, err_v = _errs(oracle.fields(f, kw["cfl"]), got)
+    assert err_e < 1e-5 and err_v < 1e-5, (err_e, err_v)
+
+
+def test_ring_full_size_matches_oracle():
+    """The 2D ring at the bench's variant size (1024^2, stirred), autotuned
+    as the bench runs it (two steps per launch), 100 steps against the ring
+    oracle at full size."""
+    w = workloads.STIRRED_1024
+    lat = rl.Lattice(w.nx, w.ny, w.tau, dtype="f32", forcing=_forcing(w), stencil="ring8")
+    lat.autotune(5)
+    lat.init_fields()
+    lat.step(100)
+    got = lat.moments()
+    lat.close()
+    f = oracle.ring.init(w.nx, w.ny)
+    oracle.ring.run(f, w.tau, 100, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+    err_e, err_v = _errs(oracle.ring.fields(f), got)
+    assert err_e < 1e-5 and err_v < 1e-5, (err_e, err_v)
 
 
 # --------------------------------------------------------------------------- 4096^2 / 8192^2
