@@ -239,7 +239,8 @@ def test_3d_rejects_what_it_does_not_run():
     lat.close()
 
 
-@pytest.mark.parametrize("n,dtype,kernel", [(128, "f32", "auto"), (128, "f32", "packed"), (96, "f64", "auto")])
+@pytest.mark.parametrize("n,dtype,kernel", [(128, "f32", "auto"), (128, "f32", "packed"), (96, "f64", "auto"),
+                                           (256, "f32", "auto")])
 def test_full_size_3d_lattice_stays_an_exact_tiling(n, dtype, kernel):
     period, tau, nsteps = 16, 0.55, 12
     fields = smooth3(period, period, period, seed=77, deps=0.02, vmax=0.02)
