@@ -159,6 +159,36 @@ def test_ensemble_workload_shape_runs():
     ens.close()
 
 
+def test_ensemble_workload_members_match_oracle():
+    """The 64-member workload (sides 256..1024), autotuned as the benchmark
+    runs it, 100 steps from seeded smooth fields; one member of each side up
+    to 512 against the FP64 oracle at the FP32 bar."""
+    members = workloads.ensemble()
+    runs = [dict(nx=w.nx, ny=w.ny, tau=w.tau,
+                 forcing=dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw))
+            for w in members]
+    ens = rl.Ensemble(runs, dtype="f32")
+    ens.autotune(2)
+    picks = {}
+    for k, w in enumerate(members):
+        ens.init_fields(k, *workloads.random_smooth(w.nx, w.ny, seed=900 + k, deps=0.02, vmax=0.02))
+        if w.nx <= 512 and w.nx not in picks:
+            picks[w.nx] = k
+    ens.step(100)
+    assert len(picks) == 3
+    for k in picks.values():
+        w = members[k]
+        f = oracle.init(w.nx, w.ny, *workloads.random_smooth(w.nx, w.ny, seed=900 + k, deps=0.02, vmax=0.02))
+        oracle.run(f, w.tau, 100, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+        e_o, vx_o, vy_o = oracle.fields(f)
+        e_g, vx_g, vy_g, _ = ens.moments(k)
+        err_e = np.max(np.abs(e_g - e_o)) / np.max(np.abs(e_o))
+        vn = max(np.max(np.abs(vx_o)), np.max(np.abs(vy_o)))
+        err_v = max(np.max(np.abs(vx_g - vx_o)), np.max(np.abs(vy_g - vy_o))) / vn
+        assert err_e < 1e-5 and err_v < 1e-5, (k, w.nx, err_e, err_v)
+    ens.close()
+
+
 def test_bad_member_index_rejected():
     ens = rl.Ensemble(RUNS[:2], dtype="f32")
     buf = np.empty(64 * 64)
