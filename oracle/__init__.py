@@ -14,9 +14,10 @@ Function status (pins live in ``tests/test_oracle_*.py``):
   stencil, moments, ideal_T, feq, landau, force_term, collide, stream,
   forcing field, totals, spectrum: pinned (closed forms, invariants,
   library eigen-solver, linear-mode analysis).
-  philox4x32_10: parity unpinned (bit pattern) -- no known-answer vectors
-  are available offline, so the tests pin its statistics only; the CUDA
-  library's independent implementation agrees with it bit for bit.
+  philox4x32_10: pinned word for word against Triton's Philox4x32
+  (CPU interpreter, tests/test_oracle_philox.py) and cuRAND's
+  Philox4x32-10 (GPU, tests/test_gpu_philox.py) on the forcing's counters
+  and seeded random words; its statistics are pinned too.
 """
 from __future__ import annotations
 

@@ -369,8 +369,9 @@ void oracle_stream(const double *fin, double *fout, int nx, int ny) { oracle_str
  * as 1, 2, 3", SC'11): 10 rounds of two 32x32->64 multiplications by
  * 0xD2511F53 and 0xCD9E8D57, the S-box/P-box word exchange, and a key
  * schedule bumped by the Weyl constants 0x9E3779B9 and 0xBB67AE85.
- * Parity unpinned (bit pattern): no known-answer vectors are available
- * offline; the tests pin its statistics only.
+ * Pinned word for word against two implementations it shares nothing
+ * with (Triton's Philox4x32 on the CPU, cuRAND's Philox4x32-10 on the
+ * GPU), and statistically.
  * ------------------------------------------------------------------------- */
 void oracle_philox4x32_10(const uint32_t *ctr_in, const uint32_t *key_in, uint32_t *out)
 {

@@ -195,8 +195,9 @@ def test_force_redraw_changes_with_epoch_and_seed():
 
 
 def test_philox_output_statistics():
-    """Statistical sanity of the counter-based generator (no known-answer
-    vectors are available offline): uniform words, uncorrelated counters."""
+    """Statistical sanity of the counter-based generator (its bit pattern is
+    pinned in tests/test_oracle_philox.py): uniform words, uncorrelated
+    counters."""
     words = np.array([oracle.philox4x32_10([e, m, s, 0], [0xDEADBEEF, 0x12345678])
                       for e in range(40) for m in range(50) for s in range(2)], dtype=np.uint64)
     u = words.astype(np.float64) / 2.0 ** 32

@@ -150,3 +150,28 @@ def ensemble(nruns: int = 64, seed: int = SEED + 3, sides=ENSEMBLE_SIDES):
         runs.append(Workload("ens%02d" % r, n, n, tau, "f32", kmin=kmin, kmax=kmax, amp=1e-5,
                              seed=int(seed * 1000 + r), redraw=100, steps=100))
     return runs
+
+
+def philox_pin_inputs(n_random: int = 4096, seed: int = 11):
+    """Counter and key words (uint32, shapes (n, 4) and (n, 2)) on which a
+    Philox4x32-10 implementation is compared with an independent one: the
+    counters the stirring force draws with ({epoch, mode, stream, 0} for
+    epochs 0..3, modes 0..255, streams 0..2) under the keys of the
+    workloads' seeds (low word, high word), the all-zero and all-one words,
+    and n_random seeded uniform draws."""
+    ctr, key = [], []
+    for s in (SEED, SEED + 1, SEED + 2):
+        k = (s & 0xFFFFFFFF, (s >> 32) & 0xFFFFFFFF)
+        for epoch in range(4):
+            for mode in range(256):
+                for stream in range(3):
+                    ctr.append((epoch, mode, stream, 0))
+                    key.append(k)
+    ctr += [(0, 0, 0, 0), (0xFFFFFFFF,) * 4]
+    key += [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF)]
+    rng = np.random.default_rng(seed)
+    c = np.concatenate([np.array(ctr, dtype=np.uint64),
+                        rng.integers(0, 1 << 32, size=(n_random, 4), dtype=np.uint64)]).astype(np.uint32)
+    k = np.concatenate([np.array(key, dtype=np.uint64),
+                        rng.integers(0, 1 << 32, size=(n_random, 2), dtype=np.uint64)]).astype(np.uint32)
+    return c, k
