@@ -2,17 +2,22 @@
 """Benchmark of the fused RLBM stream-collide step on GB300.
 
 Metric: GLUPS (10^9 lattice-node updates per second) of the stream-collide
-step, and its fraction of the measured HBM bandwidth.  Default workload:
-1024 x 1024 periodic lattice, FP32 populations, tau = 0.52, stirring force on
-the shell 4 <= |k| <= 6 (amplitude 1e-5, redrawn every 100 steps), started
-at rest -- the paper's stirred-turbulence runs (Sec. 5) at N = 1024.
+step, and its fraction of the measured HBM bandwidth.  Default workload: the
+largest single-GPU configuration of the suite, an 8192 x 8192 periodic
+lattice, FP32 populations, tau = 0.505, stirring force on the shell
+16 <= |k| <= 18 (amplitude 2e-6, redrawn every 100 steps), started at rest
+-- the paper's stirred-turbulence runs (Sec. 5) scaled to a GB300.  The
+1024^2, 4096^2, 128^2 and ensemble configurations are timed in `configs`.
 
-Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
-on the lattice's stream; between timed steps a 256 MB buffer (larger than
-the 129 MB L2) is rewritten on the same stream so each step starts with a
-cold L2.  Multi-GPU (torchrun): each rank advances its own independent
-replica (no data exchange; weak scaling); value = sum over ranks, time =
-max over ranks.
+Timing: W untimed warm-up steps made of the same calls as the timed ones
+(so every CUDA graph the timed calls replay exists before the first event),
+then K steps, launch by launch, each launch bracketed by CUDA events on the
+lattice's stream, and the whole region by one more pair.  Lattices whose
+state is smaller than twice the 129 MB L2 get an L2 flush (a 256 MB write,
+then a 256 MB read) between launches; larger ones (the 8192^2 headline:
+9.7 GB) need none.  Multi-GPU (torchrun): each rank advances its own
+independent replica (no data exchange; weak scaling); value = sum over
+ranks, time = max over ranks.
 
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on the host cores, on a bounded sample of the same workload.
@@ -35,9 +40,16 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20
+L2_BYTES = 129 << 20
+# Algorithmic bytes per node update (one read and one write of the 17 stored
+# classes plus the force read), whatever the kernel actually moves.
+ALGO_BYTES_PER_UPDATE = {"f64": 288, "f32": 144, "bf16": 76, "f16": 76}
+# The CPU sample of the oracle: the workload's node, relaxation time and
+# forcing on a 2048^2 lattice (the oracle lattice of the 8192^2 run).
+CPU_SAMPLE_SIDE = 2048
 METRIC = "GLUPS of the fused stream-collide step (and fraction of HBM peak)"
 # FP64 form: FP64 flops per node of the forced step (ncu: adds + multiplies
-# + 2 x FMAs of one launch / nodes, profiles/k_step_gather_f64_stirred_1024.md)
+# + 2 x FMAs of one launch / nodes, one-node-per-thread kernel, 1024^2 stirred)
 # and the FP64 peak derived from the unit count and clock (152 SMs x 2 FP64
 # FMA per clock x 2 flops x 2.07 GHz).
 FP64_FLOPS_PER_NODE = 627.0
@@ -58,6 +70,8 @@ def parse():
                                                                "fused2"])
     ap.add_argument("--launch", default="", metavar="KERNEL,BX,BY,BUDGET",
                     help="pin one launch shape of the autotuner's list instead of tuning (profiling runs)")
+    ap.add_argument("--workload", default="large8192", choices=sorted(WORKLOADS),
+                    help="workload of the headline line (profiling runs use the smaller ones)")
     ap.add_argument("--n", type=int, default=0, help="override lattice side (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-form table, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
@@ -164,10 +178,37 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+WORKLOADS = {"large8192": workloads.LARGE_8192, "stirred1024": workloads.STIRRED_1024,
+             "precision4096": workloads.PRECISION_4096}
+
+
 def workload_for(args):
-    w = workloads.STIRRED_1024
+    w = WORKLOADS[getattr(args, "workload", "large8192")]
     n = args.n or w.nx
     return w, n
+
+
+def workload_config(w, n, form):
+    """The workload as both arms name it (identical keys and values)."""
+    return {"workload": w.name if n == w.nx else "%s (side %d)" % (w.name, n), "nx": n, "ny": n, "form": form,
+            "tau": w.tau, "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
+            "l2": l2_policy(n, form)}
+
+
+def state_bytes(n, form):
+    return ALGO_BYTES_PER_UPDATE[form] * n * n
+
+
+def needs_flush(n, form):
+    """The L2 is flushed between timed launches unless the lattice state is
+    larger than twice the L2."""
+    return state_bytes(n, form) < 2 * L2_BYTES
+
+
+def l2_policy(n, form):
+    if needs_flush(n, form):
+        return "flushed between timed launches (256 MB write, then 256 MB read)"
+    return "not flushed: the state (%.1f GB) is larger than L2 (129 MB)" % (state_bytes(n, form) / 1e9)
 
 
 def forcing_of(w):
@@ -197,28 +238,55 @@ def launch_units(lat, steps):
     return [spl] * (steps // spl) + ([steps % spl] if steps % spl else [])
 
 
-def time_steps(torch, lat, steps, flush, with_units=False):
+def time_steps(torch, lat, steps, flush, with_units=False, region=None):
     """CUDA-event timing on the lattice stream of each launch (one step, or
-    two for a two-step kernel) with an L2 flush in between.  Returns the
-    time of every step in ms (a launch's time shared by its steps) and, with
-    with_units, the launch unit of every step."""
+    two for a two-step kernel), with an L2 flush in between when `flush` is
+    given.  Returns the time of every step in ms (a launch's time shared by
+    its steps) and, with with_units, the launch unit of every step.  region:
+    a list that receives the elapsed ms of the whole timed region (one event
+    pair around all launches; without flushes it includes the gaps between
+    launches)."""
     stream = lat._torch_stream
     sizes = launch_units(lat, steps)
     evs = []
     with torch.cuda.stream(stream):
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
         for size in sizes:
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            flush()
+            if flush is not None:
+                flush()
             a.record(stream)
             lat.step(size)
             b.record(stream)
             evs.append((a, b))
+        r1.record(stream)
     stream.synchronize()
+    if region is not None:
+        region.append(r0.elapsed_time(r1))
     ms = np.concatenate([np.full(size, a.elapsed_time(b) / size) for (a, b), size in zip(evs, sizes)])
     if not with_units:
         return ms
     return ms, np.repeat(np.arange(len(sizes)), sizes)
+
+
+def warm_up(lat, warmup, flush=None):
+    """Untimed warm-up with the timed calls themselves: at least two
+    launch-sized calls, so the CUDA graphs of both buffer parities that the
+    timed calls replay are captured and instantiated here (graphs are keyed
+    by step count and starting buffer).  Returns the steps advanced (a
+    whole number of launches, so timed launches start on a launch
+    boundary)."""
+    spl = max(1, int(lat.info()["steps_per_launch"]))
+    calls = max(2, -(-warmup // spl))
+    for _ in range(calls):
+        if flush is not None:
+            flush()
+        lat.step(spl)
+    lat.synchronize()
+    return calls * spl
 
 
 def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, init=None, tune=True, stencil="sph26",
@@ -236,13 +304,13 @@ def measure_form(torch, rl, w, n, form, landau, kernel, steps, warmup, flush, in
         lat.set_launch(k, int(bx), int(by), int(budget))
     elif tune:
         lat.autotune(10)
-    spl = int(lat.info()["steps_per_launch"])
-    warmup += (-warmup) % spl  # timed launches start on a launch boundary (epochs are 100 steps)
-    lat.step(warmup)
-    lat.synchronize()
-    ms, unit = time_steps(torch, lat, steps, flush, with_units=True)
+    fl = flush if needs_flush(n, form) else None
+    warmup = warm_up(lat, warmup, fl)
+    region = []
+    ms, unit = time_steps(torch, lat, steps, fl, with_units=True, region=region)
     info = lat.info()
     info["timed_launches"] = int(unit[-1]) + 1 if len(unit) else 0
+    info["region_ms"] = region[0]
     # launches that started a forcing epoch also carry the force re-synthesis
     redraw = w.redraw
     first = warmup
@@ -270,7 +338,9 @@ def measure_ensemble(torch, rl, flush, steps=20, warmup=5, nruns=64, sides=None,
         i0 = ens.info()
         bx, by, grid = i0["block_x"], i0["block_y"], i0["grid"]
     spl = int(ens.info()["steps_per_launch"])  # 2 for the two-step body: time whole launches
-    ens.step(warmup + (-warmup) % spl)
+    for _ in range(max(2, -(-warmup // spl))):  # the timed calls themselves: both graph parities captured
+        flush()
+        ens.step(spl)
     ens.synchronize()
     stream = ens._torch_stream
     evs = []
@@ -336,24 +406,30 @@ def parity_error(rl, oracle, form, landau):
 def measure_configs(torch, rl, flush, hbm_peak, steps=40, warmup=6):
     """The suite's other configurations at their own sizes and parameters,
     each autotuned and timed like the headline (per-launch CUDA events, L2
-    flushed between launches): the 128^2 shear wave (FP64 form, unforced),
-    the 4096^2 precision run in BF16 and FP16 storage (tau 0.51, shell
-    8..10; FP32 Landau solve, and BF16 with the FP64 solve that run names)
-    and the 8192^2 FP32 run (tau 0.505, shell 16..18)."""
+    flushed between launches where the state fits twice in L2): the 128^2
+    shear wave (FP64 form, unforced), the 1024^2 stirred run (FP32, tau
+    0.52, shell 4..6) and the 4096^2 precision run in BF16 and FP16 storage
+    (tau 0.51, shell 8..10; FP32 Landau solve, and BF16 with the FP64 solve
+    that run names).  hbm_frac counts the algorithmic bytes of a node update
+    (one read and one write of the 17 classes plus the force) per update,
+    whatever the kernel moves."""
     out = {}
-    cases = ((workloads.SHEAR_128, "f64", "fp64"), (workloads.PRECISION_4096, "bf16", "fp32"),
-             (workloads.PRECISION_4096, "f16", "fp32"), (workloads.PRECISION_4096, "bf16", "fp64"),
-             (workloads.LARGE_8192, "f32", "fp32"))
+    cases = ((workloads.SHEAR_128, "f64", "fp64"), (workloads.STIRRED_1024, "f32", "fp32"),
+             (workloads.PRECISION_4096, "bf16", "fp32"), (workloads.PRECISION_4096, "f16", "fp32"),
+             (workloads.PRECISION_4096, "bf16", "fp64"))
     for w, form, landau in cases:
         init = workloads.shear_wave(w.nx, w.ny, w.extra["u0"]) if w.init == "shear" else None
-        _, km, info, _ = measure_form(torch, rl, w, w.nx, form, landau, "auto", steps, warmup, flush, init=init)
+        ms, km, info, _ = measure_form(torch, rl, w, w.nx, form, landau, "auto", steps, warmup, flush, init=init)
         nodes = w.nx * w.ny
-        bp = int(info["bytes_per_node"])
+        bp = ALGO_BYTES_PER_UPDATE[form]
+        spl = int(info["steps_per_launch"])
         out["%s/%s/landau-%s" % (w.name, form, landau)] = {
-            "glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_node": bp,
+            "glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_update": bp,
             "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak,
+            "moved_bytes_per_update": int(info["bytes_per_node"]) / spl,
             "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]], "block": [info["block_x"], info["block_y"]],
-            "steps_per_launch": int(info["steps_per_launch"])}
+            "steps_per_launch": spl, "l2": l2_policy(w.nx, form),
+            "glups_whole_region": nodes * len(ms) / (info["region_ms"] / 1e3) / 1e9}
     return out
 
 
@@ -381,8 +457,7 @@ def measure_variants(torch, rl, oracle, flush, hbm_peak, steps=50, warmup=5):
         lat = make()
         lat.init_fields()
         lat.autotune(5)
-        lat.step(warmup)
-        lat.synchronize()
+        warm_up(lat, warmup, flush)
         ms = time_steps(torch, lat, steps, flush)
         info = lat.info()
         lat.close()
@@ -442,6 +517,7 @@ def cpu_oracle_glups(oracle, w, n, budget_s):
     (same shape per node); returns (GLUPS, description, threads)."""
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
+    n = min(n, CPU_SAMPLE_SIDE)
     rows = n
     f = oracle.init(n, rows)
     tmp_steps = 1
@@ -454,7 +530,8 @@ def cpu_oracle_glups(oracle, w, n, budget_s):
                redraw=w.redraw)
     dt = time.perf_counter() - t0
     glups = n * rows * nsteps / dt / 1e9
-    return glups, "%dx%d lattice, %d forced steps (FP64 oracle, OpenMP)" % (n, rows, nsteps), threads
+    return glups, ("%dx%d lattice with the workload's tau and forcing, %d forced steps (FP64 oracle, OpenMP)"
+                   % (n, rows, nsteps)), threads
 
 
 def e2e_glups(rl, w, n, form, landau, reps=3, steps_per_call=100):
@@ -505,45 +582,67 @@ def aggregate_replicas(torch, local_seconds, local_updates, world):
 
 
 def reference_arm(args):
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    headline workload: its node, relaxation time and forcing on a lattice of
+    side min(n, 2048), each timed step a few lattice steps of it."""
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return
     import oracle
     oracle.build()
     w, n = workload_for(args)
+    m = min(n, CPU_SAMPLE_SIDE)
     total_steps = max(1, args.steps)
     warm = max(0, args.warmup)
     oracle.set_threads(os.cpu_count() or 1)
-    # bounded sample: the full lattice, steps scaled so the run ends in minutes
-    f = oracle.init(n, n)
+    f = oracle.init(m, m)
     t0 = time.perf_counter()
     oracle.run(f, w.tau, 1, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
     one = time.perf_counter() - t0
     per_step_budget = 60.0 / max(1, total_steps + warm)
-    nsub = max(1, int(per_step_budget / max(one, 1e-6)))
-    nsub = min(nsub, 50)
+    nsub = max(1, min(50, int(per_step_budget / max(one, 1e-6))))
+    done = 1
     for _ in range(min(warm, 3)):
-        oracle.run(f, w.tau, 1, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+        oracle.run(f, w.tau, 1, step0=done, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+        done += 1
     t0 = time.perf_counter()
     steps_done = 0
     for _ in range(total_steps):
-        oracle.run(f, w.tau, nsub, step0=steps_done, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed,
-                   redraw=w.redraw)
+        oracle.run(f, w.tau, nsub, step0=done, kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw=w.redraw)
+        done += nsub
         steps_done += nsub
         if time.perf_counter() - t0 > 150:
             break
     dt = time.perf_counter() - t0
-    glups = n * n * steps_done / dt / 1e9
+    glups = m * m * steps_done / dt / 1e9
+    sample = "%dx%d lattice with the workload's tau and forcing, %d forced steps (FP64 oracle, OpenMP)" % (
+        m, m, steps_done)
     line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS",
             "n_gpus": args.gpus, "steps": total_steps, "warmup": args.warmup,
-            "ms_per_step": dt / steps_done * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "nx": n, "ny": n, "form": "f64 (CPU oracle)", "tau": w.tau,
-                       "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw)},
+            "ms_per_step": dt / steps_done * 1e3 * (n * n) / (m * m), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, n, args.form),
             "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "%dx%d lattice, %d forced steps" % (n, n, steps_done)},
+                             "sample": sample},
             "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def traffic_entry(form, landau, kernel_id, n, variant_key=""):
+    """The stored ncu DRAM figure (profiles/traffic.json) of this kernel and
+    lattice, if it was taken on the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as fh:
+            tj = json.load(fh)
+        ent = tj.get("%s_%s_%d_%d%s" % (form, landau, kernel_id, n, variant_key))
+        if ent and ent.get("source_sha256") == step_kernel_source_hash(kernel_id):
+            return ent
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
 
 
 def main():
@@ -588,86 +687,81 @@ def main():
                                                     tune=not args.no_tune, stencil=args.stencil, nz=args.nz,
                                                     launch=args.launch)
     torch.cuda.synchronize()
-    step_ms = float(ms.mean())
     nodes = n * n * max(1, args.nz)
     variant = args.stencil != "sph26" or args.nz > 0
-    total_s, glups_total = aggregate_replicas(torch, float(ms.sum()) / 1e3, nodes * K, world)
+    # whole timed region: one event pair around all launches when nothing runs between them, else the sum of
+    # the launches (the L2 flushes between launches are not the job's work)
+    region_s = (info["region_ms"] if not needs_flush(n, args.form) else float(ms.sum())) / 1e3
+    total_s, glups_total = aggregate_replicas(torch, region_s, nodes * K, world)
+    step_ms = total_s * 1e3 / K
 
     hbm_peak, peak_kind = load_peaks()
-    bpn = int(info["bytes_per_node"])
-    achieved = bpn * nodes / (kernel_ms / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as fh:
-                tj = json.load(fh)
-            key = "%s_%s_%s_%d" % (args.form, args.landau, info["kernel"], n)
-            if variant:
-                key += "_%s_nz%d" % (args.stencil, args.nz)
-            ent = tj.get(key)
-            if ent and ent.get("source_sha256") == step_kernel_source_hash(info["kernel"]):
-                traffic = ent["bytes_per_launch"]
-        except (OSError, ValueError, KeyError):
-            traffic = None
+    spl = int(info["steps_per_launch"])
+    launch_ms = kernel_ms * spl
+    moved = int(info["bytes_per_node"])  # bytes the chosen kernel moves per node per launch
+    algo = moved if variant else ALGO_BYTES_PER_UPDATE[args.form]  # per node update (SURVEY-style count)
+    achieved = algo * nodes * spl / (launch_ms / 1e3) / 1e9
+    vkey = "_%s_nz%d" % (args.stencil, args.nz) if variant else ""
+    ent = traffic_entry(args.form, args.landau, info["kernel"], n, vkey)
+    kname = {v: k for k, v in rl.KERNELS.items()}[info["kernel"]]
 
+    config = workload_config(w, n, args.form)
+    if variant:
+        config["workload"] += " (3D lattice %dx%dx%d)" % (n, n, args.nz) if args.nz else " (2D ring)"
     line = {
         "metric": METRIC,
         "value": glups_total, "unit": "GLUPS", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.form != "f64" else "f64", "data": "synthetic",
-        "config": {"workload": w.name + ("" if not variant else
-                                          (" (3D lattice %dx%dx%d)" % (n, n, args.nz) if args.nz else " (2D ring)")),
-                   "nx": n, "ny": n, "form": args.form, "landau": args.landau,
-                   "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]],
-                   "block": [info["block_x"], info["block_y"]], "launch_budget": info["launch_budget"], "tau": w.tau,
-                   "forcing": "shell %d..%d amp %g redraw %d" % (w.kmin, w.kmax, w.amp, w.redraw),
-                   "l2": "flushed between timed steps (256 MB write, then 256 MB read)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "config": config,
+        "launch": {"kernel": kname, "block": [info["block_x"], info["block_y"]],
+                   "launch_budget": info["launch_budget"], "steps_per_launch": spl, "landau": args.landau,
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                     "peak_kind": peak_kind, "bytes_per_node": bpn,
+                     "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": ent["bytes_per_launch"] if ent else None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_update": algo,
+                     "moved_bytes_per_update": moved / spl,
+                     "frac_of_moved_bytes": moved * nodes / (launch_ms / 1e3) / 1e9 / hbm_peak,
                      "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
-                     "kernel_ms": kernel_ms, "steps_per_launch": int(info["steps_per_launch"]),
-                     "launch_ms": kernel_ms * int(info["steps_per_launch"]),
-                     "epoch_steps_in_timed_region": n_epoch},
+                     "kernel": kname, "launch_ms": launch_ms, "updates_per_launch": nodes * spl,
+                     "epoch_launches_in_timed_region": n_epoch},
         "clocks": clocks.summary(),
         "gpu_launches": int(info["timed_launches"] + 2 * n_epoch),
     }
-    spl = int(info["steps_per_launch"])
-    if spl > 1:
-        # a launch of several steps moves the state once: its HBM fraction is per launch; the
-        # same throughput from one-step launches would need bytes_per_node * spl per update
-        line["roofline"]["frac_at_single_step_bytes"] = achieved * spl / hbm_peak
-        line["roofline"]["limiter"] = ("instruction issue, not HBM: under ncu the two-step launch keeps DRAM "
-                                       "29% busy, issue slots 51%, FP32 FMA pipe 61% "
-                                       "(profiles/k_step_fused2_f32_stirred_1024.md)")
+    if ent:
+        line["roofline"]["traffic_source"] = ent.get("from")
+        if ent.get("scaled_from"):
+            line["roofline"]["traffic_scaled_from"] = ent["scaled_from"]
+        if ent.get("limiter"):
+            line["roofline"]["limiter"] = ent["limiter"]
     if args.form == "f64" and not variant:
         tf = FP64_FLOPS_PER_NODE * nodes / (kernel_ms / 1e3) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+                            "frac": tf / FP64_PEAK_TFLOPS, "traffic": ent["bytes_per_launch"] if ent else None,
                             "peak_kind": "derived (FP64 units x clock)", "flops_per_node": FP64_FLOPS_PER_NODE,
-                            "hbm_frac": achieved / hbm_peak, "kernel_ms": kernel_ms,
-                            "epoch_steps_in_timed_region": n_epoch}
+                            "hbm_frac": achieved / hbm_peak, "launch_ms": launch_ms,
+                            "epoch_launches_in_timed_region": n_epoch}
 
     if rank == 0 and not args.no_extras and not variant:
         import oracle
         oracle.build()
         oracle.set_threads(os.cpu_count() or 1)
         forms = {}
-        for form, landau in (("f32", "fp32"), ("f32", "fp64"), ("f64", "fp64"), ("bf16", "fp32"), ("f16", "fp32")):
+        for form, landau in (("f32", "fp32"), ("f32", "fp64"), ("f64", "fp64"), ("bf16", "fp32"), ("f16", "fp32"),
+                             ("bf16", "fp64")):
             if form == args.form and landau == args.landau:
-                g = glups_total / world
-                km = kernel_ms
-                bp = bpn
+                g, km, spl_f = glups_total / world, kernel_ms, spl
             else:
                 msf, km, inf, _ = measure_form(torch, rl, w, n, form, landau, args.kernel, min(K, 100), 5, flush)
                 g = nodes * len(msf) / (msf.sum() / 1e3) / 1e9
-                bp = int(inf["bytes_per_node"])
+                spl_f = int(inf["steps_per_launch"])
+            bp = ALGO_BYTES_PER_UPDATE[form]
             err = parity_error(rl, oracle, form, landau)
             forms["%s/landau-%s" % (form, landau)] = {
                 "glups": g, "hbm_gbs": bp * nodes / (km / 1e3) / 1e9,
-                "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak, "bytes_per_node": bp,
-                "max_rel_err_vs_oracle": err}
+                "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak, "bytes_per_update": bp,
+                "steps_per_launch": spl_f, "max_rel_err_vs_oracle": err}
             if form == "f64":
                 tf = FP64_FLOPS_PER_NODE * nodes / (km / 1e3) / 1e12
                 forms["f64/landau-fp64"]["fp64_alu"] = {"tflops": tf, "peak_tflops": FP64_PEAK_TFLOPS,

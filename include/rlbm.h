@@ -369,26 +369,39 @@ RLBM_API rlbm_status rlbm_set_launch(rlbm_t *h, int kernel, int block_x, int blo
  * on a memory budget fixed up front, loops that must not take the implicit
  * synchronisation of cudaMalloc, or hosts whose device memory belongs to
  * another framework's pool).  Computes what rlbm_moments_device computes
- * from a caller-owned SPH26_SLAB population array: d_q is the device state
- * [17][ny][pitch] of storage type `dtype` (for example rlbm_info_t.populations
- * and .pitch of a handle), eps0 and scale its deviation parameters; d_eps,
- * d_vx, d_vy (nx*ny FP64 each, any may be NULL) and d_totals (3 FP64, may be
- * NULL) are caller-owned device outputs.  Async on `stream` (NULL = legacy
- * default stream).  No device or host memory is allocated: the scratch (FP64
- * per-block partial sums and a failed-node counter) lives in one static
- * device array of 1.5 MiB that every GPU loading the library holds until the
- * process exits.  The lattice must satisfy ceil(nx/32) * ceil(ny/8) <=
- * RLBM_STATIC_MAX_BLOCKS (e.g. 4096 x 4096); larger lattices get
- * RLBM_ERR_ARG.  The first call on a device looks the scratch address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the scratch and
- * clear the counter they need, so calls that overlap on the GPU (different
- * streams, no ordering) race: order them on one stream.  Errors:
- * RLBM_ERR_ARG, RLBM_ERR_CUDA (no handle, so no message). */
+ * from a caller-owned population array of the paper's one-layer node:
+ * stencil must be RLBM_STENCIL_SPH26_SLAB (anything else, e.g. the ring's
+ * 8 planes or a 3D lattice's 26, is refused with RLBM_ERR_ARG: the call
+ * cannot tell a layout from the pointer); d_q is the device state
+ * [17][ny][pitch] of storage type `dtype` (for example
+ * rlbm_info_t.populations and .pitch of a handle), eps0 and scale its
+ * deviation parameters, and cfl the CFL number the lattice streams with
+ * (rlbm_opts.cfl; 0 < cfl < 2; 1 for the default lattice), because the
+ * moments are those of the streamed state and the pull depends on it.
+ * d_eps, d_vx, d_vy (nx*ny FP64 each, any may be NULL) and d_totals (3
+ * FP64, may be NULL) are caller-owned device outputs; d_bad (one int, may
+ * be NULL) receives the number of nodes whose frame is not physical (their
+ * outputs are NaN).  Async on `stream` (NULL = legacy default stream).
+ * No device or host memory is allocated: the scratch (FP64 per-block
+ * partial sums and the failed-node counter) lives in one static device
+ * array of 1.5 MiB, held until the process exits by every GPU on which the
+ * library's module is loaded.  With CUDA's default lazy module loading
+ * that happens on the first use of the module on a device, which may
+ * itself reserve device memory and synchronise: make the first call on a
+ * device during set-up, before any stream capture (or load eagerly with
+ * CUDA_MODULE_LOADING=EAGER).  That first call also looks the scratch
+ * address up (cudaGetSymbolAddress) with that device current.  The lattice
+ * must satisfy ceil(nx/32) * ceil(ny/8) <= RLBM_STATIC_MAX_BLOCKS (e.g.
+ * 4096 x 4096); larger lattices get RLBM_ERR_ARG.  All calls on a device
+ * share the scratch, which keeps the previous call's contents; each call
+ * clears the counter and overwrites the partial sums it reads, so calls
+ * that overlap on the GPU (different streams, no ordering) race: order
+ * them on one stream.  Errors: RLBM_ERR_ARG, RLBM_ERR_CUDA (no handle, so
+ * no message). */
 #define RLBM_STATIC_MAX_BLOCKS 65536
-RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, int nx, int ny, int pitch, double eps0,
-                                         double scale, double *d_eps, double *d_vx, double *d_vy, double *d_totals,
-                                         void *stream);
+RLBM_API rlbm_status rlbm_moments_static(int stencil, int dtype, const void *d_q, int nx, int ny, int pitch,
+                                         double eps0, double scale, double cfl, double *d_eps, double *d_vx,
+                                         double *d_vy, double *d_totals, int *d_bad, void *stream);
 
 /* Checkpoint and resume (no counterpart in the paper).  A checkpoint holds
  * a header (lattice sizes, stencil, storage form, tau, eps0, scale, cfl,
@@ -448,6 +461,11 @@ typedef struct {
  * Ensembles stream at CFL 1.  Errors: RLBM_ERR_ARG, RLBM_ERR_ALLOC,
  * RLBM_ERR_CUDA. */
 RLBM_API rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_opts *opts,
+                                       rlbm_batch_t **out);
+/* The same call under the name rlbm_create_batch (identical arguments,
+ * behaviour and errors), for callers that spell the constructors
+ * rlbm_create*. */
+RLBM_API rlbm_status rlbm_create_batch(int nruns, const rlbm_run_desc *runs, const rlbm_opts *opts,
                                        rlbm_batch_t **out);
 /* Initialise member `run` as rlbm_init_fields does, at the ensemble's
  * current step (the step counter is shared and not reset). */

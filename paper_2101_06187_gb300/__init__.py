@@ -43,7 +43,7 @@ EXPORTS = (
     "rlbm_batch_synchronize", "rlbm_batch_last_error", "rlbm_batch_destroy", "rlbm_filtered_velocity",
     "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset", "rlbm_create3d", "rlbm_init_fields3d",
     "rlbm_moments3d", "rlbm_get_force3d", "rlbm_checkpoint_size", "rlbm_checkpoint_save", "rlbm_checkpoint_load",
-    "rlbm_set_launch",
+    "rlbm_set_launch", "rlbm_create_batch",
 )
 
 
@@ -120,9 +120,10 @@ def _load():
         lib.rlbm_get_force.argtypes = [h, _dp, _dp]
         lib.rlbm_get_info.argtypes = [h, ctypes.POINTER(Info)]
         lib.rlbm_synchronize.argtypes = [h]
-        lib.rlbm_moments_static.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                            ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
-                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.rlbm_moments_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]
         lib.rlbm_moments_static.restype = ctypes.c_int
         lib.rlbm_filtered_velocity.argtypes = [h, ctypes.c_double, _dp]
         lib.rlbm_spectrum_sample.argtypes = [h, ctypes.c_int]
@@ -367,12 +368,14 @@ def rlbm_set_launch(h, kernel: int, block_x: int, block_y: int, launch_budget: i
            "rlbm_set_launch")
 
 
-def rlbm_moments_static(dtype: int, d_q: int, nx: int, ny: int, pitch: int, eps0: float, scale: float,
-                        d_eps: int = 0, d_vx: int = 0, d_vy: int = 0, d_totals: int = 0, stream: int = 0):
+def rlbm_moments_static(stencil: int, dtype: int, d_q: int, nx: int, ny: int, pitch: int, eps0: float, scale: float,
+                        cfl: float = 1.0, d_eps: int = 0, d_vx: int = 0, d_vy: int = 0, d_totals: int = 0,
+                        d_bad: int = 0, stream: int = 0):
     """Allocation-free moments from a caller-owned device population array
     (see include/rlbm.h); all pointers are device addresses as ints."""
-    st = _load().rlbm_moments_static(int(dtype), d_q or None, int(nx), int(ny), int(pitch), float(eps0), float(scale),
-                                     d_eps or None, d_vx or None, d_vy or None, d_totals or None, stream or None)
+    st = _load().rlbm_moments_static(int(stencil), int(dtype), d_q or None, int(nx), int(ny), int(pitch), float(eps0),
+                                     float(scale), float(cfl), d_eps or None, d_vx or None, d_vy or None,
+                                     d_totals or None, d_bad or None, stream or None)
     _check(None, st, "rlbm_moments_static")
 
 

@@ -1489,6 +1489,10 @@ rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_o
     return RLBM_OK;
 }
 
+rlbm_status rlbm_create_batch(int nruns, const rlbm_run_desc *runs, const rlbm_opts *opts, rlbm_batch_t **out) {
+    return rlbm_batch_create(nruns, runs, opts, out);
+}
+
 rlbm_status rlbm_batch_init_fields(rlbm_batch_t *b, int run, const double *eps, const double *vx, const double *vy) {
     CHECK_BATCH(b);
     rlbm_t *h = nullptr;

@@ -18,12 +18,17 @@ namespace {
 
 // Scratch: RLBM_STATIC_MAX_BLOCKS moments blocks (32 x 8 nodes each) of three
 // FP64 partial sums, plus one int counter at the end.  1.5 MiB per device,
-// held by every GPU that loads the library until the process exits.
+// held until the process exits by every GPU on which this module is loaded
+// (with CUDA's lazy module loading, the default, on the first use of the
+// module on that device: the first call of rlbm_moments_static, or any
+// earlier kernel launch of the library there).
 constexpr int kMaxBlocks = RLBM_STATIC_MAX_BLOCKS;
 constexpr size_t kScratchBytes = (size_t)3 * kMaxBlocks * sizeof(double) + 256;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Host-side address of g_scratch per device, filled once per device.
+// Device address of g_scratch per device, looked up once per device with
+// that device current (in host code the name g_scratch is only a host-side
+// stand-in; a kernel handed it would read the wrong memory).
 constexpr int kMaxDevices = 64;
 static void *g_scratch_ptr[kMaxDevices] = {nullptr};
 static std::mutex g_scratch_mu;
@@ -49,11 +54,15 @@ rlbm_status scratch_for_current_device(void **out) {
 
 }  // namespace
 
-extern "C" RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, int nx, int ny, int pitch, double eps0,
-                                                    double scale, double *d_eps, double *d_vx, double *d_vy,
-                                                    double *d_totals, void *stream) {
+extern "C" RLBM_API rlbm_status rlbm_moments_static(int stencil, int dtype, const void *d_q, int nx, int ny,
+                                                    int pitch, double eps0, double scale, double cfl, double *d_eps,
+                                                    double *d_vx, double *d_vy, double *d_totals, int *d_bad,
+                                                    void *stream) {
+    // only the 17-class one-layer state of the paper's node: the ring's 8
+    // planes or the 3D lattice's 26 would be read as something they are not
+    if (stencil != RLBM_STENCIL_SPH26_SLAB) return RLBM_ERR_ARG;
     if (!d_q || nx < 4 || ny < 4 || pitch < nx || dtype < RLBM_F64 || dtype > RLBM_F16) return RLBM_ERR_ARG;
-    if (!(eps0 > 0.0) || !(scale > 0.0)) return RLBM_ERR_ARG;
+    if (!(eps0 > 0.0) || !(scale > 0.0) || !(cfl > 0.0 && cfl < 2.0)) return RLBM_ERR_ARG;
     rlbk::StepParams p{};
     p.nx = nx;
     p.ny = ny;
@@ -65,7 +74,7 @@ extern "C" RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, 
     p.eps0 = eps0;
     p.scale = scale;
     p.eta_k = 0.0;
-    p.cfl = 1.0;  // the moments of a CFL-1 lattice
+    p.cfl = cfl;  // the pull of the last stream before the moments: cfl v_i cells
     p.err = nullptr;
     rlbk::finish_params(p);
     const int nblocks = rlbk::moments_blocks(p);
@@ -81,6 +90,8 @@ extern "C" RLBM_API rlbm_status rlbm_moments_static(int dtype, const void *d_q, 
         return RLBM_ERR_CUDA;
     if (d_totals &&
         rlbk::launch_reduce_partials(partials, nblocks, eps0 * (double)nx * ny, d_totals, s) != cudaSuccess)
+        return RLBM_ERR_CUDA;
+    if (d_bad && cudaMemcpyAsync(d_bad, bad, sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return RLBM_ERR_CUDA;
     return RLBM_OK;
 }
