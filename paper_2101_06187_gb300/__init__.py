@@ -147,6 +147,8 @@ def _load():
         ip = ctypes.POINTER(ctypes.c_int)
         lib.rlbm_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(RunDesc), ctypes.POINTER(Opts),
                                           ctypes.POINTER(ctypes.c_void_p)]
+        lib.rlbm_create_batch.argtypes = lib.rlbm_batch_create.argtypes
+        lib.rlbm_create_batch.restype = ctypes.c_int
         lib.rlbm_batch_init_fields.argtypes = [b, ctypes.c_int, _dp, _dp, _dp]
         lib.rlbm_batch_step.argtypes = [b, ctypes.c_int]
         lib.rlbm_batch_moments.argtypes = [b, ctypes.c_int, _dp, _dp, _dp, _dp]
@@ -398,6 +400,15 @@ def rlbm_batch_create(runs, opts: Optional[Opts]):
     out = ctypes.c_void_p()
     st = _load().rlbm_batch_create(len(runs), arr, ctypes.byref(opts) if opts else None, ctypes.byref(out))
     _check(None, st, "rlbm_batch_create")
+    return out
+
+
+def rlbm_create_batch(runs, opts: Optional[Opts]):
+    """rlbm_batch_create under its other name."""
+    arr = (RunDesc * len(runs))(*runs)
+    out = ctypes.c_void_p()
+    st = _load().rlbm_create_batch(len(runs), arr, ctypes.byref(opts) if opts else None, ctypes.byref(out))
+    _check(None, st, "rlbm_create_batch")
     return out
 
 
