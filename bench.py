@@ -426,7 +426,7 @@ def measure_configs(torch, rl, flush, hbm_peak, steps=40, warmup=6):
         out["%s/%s/landau-%s" % (w.name, form, landau)] = {
             "glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_update": bp,
             "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak,
-            "moved_bytes_per_update": int(info["bytes_per_node"]) / spl,
+            "moved_bytes_per_update": int(info["bytes_per_node"]),
             "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]], "block": [info["block_x"], info["block_y"]],
             "steps_per_launch": spl, "l2": l2_policy(w.nx, form),
             "glups_whole_region": nodes * len(ms) / (info["region_ms"] / 1e3) / 1e9}
@@ -462,9 +462,10 @@ def measure_variants(torch, rl, oracle, flush, hbm_peak, steps=50, warmup=5):
         info = lat.info()
         lat.close()
         km = float(np.median(ms))
-        bp = int(info["bytes_per_node"])
-        out[name] = {"glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_node": bp,
-                     "hbm_frac": bp * nodes / (km / 1e3) / 1e9 / hbm_peak,
+        bp = int(info["bytes_per_node"])  # moved per update; algorithmic = one step's read + write + force
+        algo = bp * int(info["steps_per_launch"])
+        out[name] = {"glups": nodes / (km / 1e3) / 1e9, "kernel_ms": km, "bytes_per_update": algo,
+                     "moved_bytes_per_update": bp, "hbm_frac": algo * nodes / (km / 1e3) / 1e9 / hbm_peak,
                      "kernel": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]],
                      "block": [info["block_x"], info["block_y"]]}
     # parity on small cases (FP32 against the FP64 oracles)
@@ -698,8 +699,9 @@ def main():
     hbm_peak, peak_kind = load_peaks()
     spl = int(info["steps_per_launch"])
     launch_ms = kernel_ms * spl
-    moved = int(info["bytes_per_node"])  # bytes the chosen kernel moves per node per launch
-    algo = moved if variant else ALGO_BYTES_PER_UPDATE[args.form]  # per node update (SURVEY-style count)
+    moved = int(info["bytes_per_node"])  # bytes the chosen kernel moves per node update (half per update of a
+    #                                     two-step launch, which moves the state once)
+    algo = moved * spl if variant else ALGO_BYTES_PER_UPDATE[args.form]  # algorithmic bytes per node update
     achieved = algo * nodes * spl / (launch_ms / 1e3) / 1e9
     vkey = "_%s_nz%d" % (args.stencil, args.nz) if variant else ""
     ent = traffic_entry(args.form, args.landau, info["kernel"], n, vkey)
@@ -721,8 +723,8 @@ def main():
                      "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": ent["bytes_per_launch"] if ent else None,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_update": algo,
-                     "moved_bytes_per_update": moved / spl,
-                     "frac_of_moved_bytes": moved * nodes / (launch_ms / 1e3) / 1e9 / hbm_peak,
+                     "moved_bytes_per_update": moved,
+                     "frac_of_moved_bytes": moved * nodes * spl / (launch_ms / 1e3) / 1e9 / hbm_peak,
                      "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
                      "kernel": kname, "launch_ms": launch_ms, "updates_per_launch": nodes * spl,
                      "epoch_launches_in_timed_region": n_epoch},

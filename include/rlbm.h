@@ -188,7 +188,22 @@ typedef struct {
      * synchronising call returns RLBM_ERR_TIMEOUT (sticky); the state of
      * that step is undefined.  Nothing faults or hangs. */
     int test_unarmed_wait;
+    /* Rounding of the 16-bit stores (rlbm_rounding).  RLBM_ROUND_NEAREST:
+     * round to nearest even.  RLBM_ROUND_STOCHASTIC: round each stored value
+     * up or down with probability given by its distance to the two
+     * neighbours (the hardware's stochastic-rounding conversion), with random
+     * bits hashed from the node, the class and the value itself, so runs
+     * stay deterministic and checkpoints resume bitwise; nearest rounding's
+     * error is a deterministic function of the smooth deviation field and
+     * with BF16's 8-bit significand it shifts the time-averaged spectrum by
+     * about 4%, stochastic rounding by a few tenths of a percent.  Needs
+     * the packed kernels (PACKED, FUSED2) of the one-layer lattice.
+     * RLBM_ROUND_DEFAULT (0): stochastic for BF16, nearest for FP16; for
+     * ensembles nearest.  Ignored by the F32 and F64 forms. */
+    int rounding;
 } rlbm_opts;
+
+typedef enum { RLBM_ROUND_DEFAULT = 0, RLBM_ROUND_NEAREST = 1, RLBM_ROUND_STOCHASTIC = 2 } rlbm_rounding;
 
 typedef struct {
     int nx, ny, pitch;        /* lattice and row pitch (elements) of the device arrays */

@@ -29,6 +29,7 @@ RLBM_STENCIL_SPH26_SLAB = 0
 RLBM_STENCIL_RING8_2D = 1
 STENCILS = {"sph26": RLBM_STENCIL_SPH26_SLAB, "ring8": RLBM_STENCIL_RING8_2D}
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+ROUNDING = {"default": 0, "nearest": 1, "stochastic": 2}
 LANDAU = {"fp64": 0, "fp32": 1}
 KERNELS = {"auto": 0, "gather": 1, "vec": 2, "vec2": 3, "packed": 4, "tma": 5, "twopass": 6, "fused2": 7}
 NCLASSES = 17
@@ -67,7 +68,7 @@ class Opts(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("eps0", ctypes.c_double), ("scale", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("cfl", ctypes.c_double), ("eta_s", ctypes.c_double),
-                ("dt", ctypes.c_double), ("test_unarmed_wait", ctypes.c_int)]
+                ("dt", ctypes.c_double), ("test_unarmed_wait", ctypes.c_int), ("rounding", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -485,7 +486,7 @@ class Lattice:
                  forcing: Optional[dict] = None, eps0: float = 1.0, scale: float = 0.0, kernel: str = "auto",
                  use_graphs: bool = True, allocator: str = "torch", stream=None, device: Optional[int] = None,
                  cfl: float = 1.0, eta_s: float = 0.0, dt: float = 1.0, stencil: str = "sph26",
-                 test_unarmed_wait: bool = False):
+                 test_unarmed_wait: bool = False, rounding: str = "default"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the RLBM library runs on the GPU only")
@@ -516,6 +517,7 @@ class Lattice:
         o.eta_s = float(eta_s)
         o.dt = float(dt)
         o.test_unarmed_wait = 1 if test_unarmed_wait else 0
+        o.rounding = ROUNDING[rounding]
         self._alloc = None
         if allocator == "torch":
             self._alloc = _TorchAllocator(dev, s)
@@ -702,7 +704,8 @@ class Ensemble:
     """
 
     def __init__(self, runs, *, dtype: str = "f32", landau: str = "fp32", use_graphs: bool = True,
-                 allocator: str = "torch", stream=None, device: Optional[int] = None, kernel: str = "auto"):
+                 allocator: str = "torch", stream=None, device: Optional[int] = None, kernel: str = "auto",
+                 rounding: str = "default"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the RLBM library runs on the GPU only")
@@ -723,6 +726,7 @@ class Ensemble:
         o.landau = LANDAU[landau]
         o.kernel = KERNELS[kernel]
         o.use_graphs = 1 if use_graphs else 0
+        o.rounding = ROUNDING[rounding]
         o.stream = s
         o.device = dev
         self._alloc = None

@@ -237,39 +237,66 @@ cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, i
     return cudaGetLastError();
 }
 
-// F(x) = sum_m [a cos psi - b sin psi], psi = 2 pi (kx x/nx + ky y/ny), with
-// e^{i psi} = X[m][x] * Y[m][y].
+// F(x) = sum_m [a cos psi - b sin psi] = Re sum_m (a + i b) e^{i psi},
+// psi = 2 pi (kx x/nx + ky y/ny), e^{i psi} = X[m][x] Y[m][y].  The modes
+// come in runs of equal ky (enumerated ky ascending), which share Y, so the
+// synthesis is separable: per run j and column x the row sums
+//     G_j(x) = sum_{m in run j} (a_m + i b_m) X[m][x]      (k_force_rows)
+// and per node F = Re sum_j G_j(x) Y_j(y)                   (k_synth_force):
+// 4 multiply-adds per run and node instead of 12 per mode and node.
 template <typename TC>
-__global__ void k_synth_force(TC *F, const C4<TC> *__restrict__ coef, int nmodes, const C2<TC> *__restrict__ X,
+__global__ void k_force_rows(C4<TC> *G, const C4<TC> *__restrict__ coef, const int *__restrict__ run_start,
+                             const C2<TC> *__restrict__ X, int nx) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (x >= nx) return;
+    TC xr = 0, xi = 0, yr = 0, yi = 0;
+    for (int m = run_start[j]; m < run_start[j + 1]; ++m) {
+        const C4<TC> c = coef[m];
+        const C2<TC> a = X[(long long)m * nx + x];
+        xr += c.ax * a.c - c.bx * a.s;
+        xi += c.ax * a.s + c.bx * a.c;
+        yr += c.ay * a.c - c.by * a.s;
+        yi += c.ay * a.s + c.by * a.c;
+    }
+    G[(long long)j * nx + x] = C4<TC>{xr, xi, yr, yi};
+}
+
+template <typename TC>
+__global__ void k_synth_force(TC *F, const C4<TC> *__restrict__ G, const int *__restrict__ run_start, int nruns,
                               const C2<TC> *__restrict__ Y, StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     TC fx = 0, fy = 0;
-    for (int m = 0; m < nmodes; ++m) {
-        const C4<TC> c = coef[m];
-        const C2<TC> a = X[(long long)m * p.nx + x];
-        const C2<TC> b = Y[(long long)m * p.ny + y];
-        const TC cpsi = a.c * b.c - a.s * b.s;
-        const TC spsi = a.s * b.c + a.c * b.s;
-        fx += c.ax * cpsi - c.bx * spsi;
-        fy += c.ay * cpsi - c.by * spsi;
+    for (int j = 0; j < nruns; ++j) {
+        const C4<TC> g = G[(long long)j * p.nx + x];
+        const C2<TC> b = Y[(long long)run_start[j] * p.ny + y];
+        fx += g.ax * b.c - g.bx * b.s;
+        fy += g.ay * b.c - g.by * b.s;
     }
     const long long n = (long long)y * p.pitch + x;
     F[n] = fx;
     F[p.plane + n] = fy;
 }
 
-cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const void *X, const void *Y,
-                               const StepParams &p, cudaStream_t s) {
-    dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
-    if (dtype == RLBM_F64)
-        k_synth_force<double><<<g, b, 0, s>>>(static_cast<double *>(F), static_cast<const C4<double> *>(coef), nmodes,
-                                              static_cast<const C2<double> *>(X), static_cast<const C2<double> *>(Y),
-                                              p);
-    else
-        k_synth_force<float><<<g, b, 0, s>>>(static_cast<float *>(F), static_cast<const C4<float> *>(coef), nmodes,
-                                             static_cast<const C2<float> *>(X), static_cast<const C2<float> *>(Y), p);
+cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const int *run_start, int nruns,
+                               void *G, const void *X, const void *Y, const StepParams &p, cudaStream_t s) {
+    if (nmodes <= 0 || nruns <= 0) return cudaSuccess;
+    const dim3 gr((p.nx + 255) / 256, nruns, 1);
+    const dim3 block(32, 8, 1);
+    const dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, 1);
+    if (dtype == RLBM_F64) {
+        k_force_rows<double><<<gr, 256, 0, s>>>(static_cast<C4<double> *>(G), static_cast<const C4<double> *>(coef),
+                                                run_start, static_cast<const C2<double> *>(X), p.nx);
+        k_synth_force<double><<<grid, block, 0, s>>>(static_cast<double *>(F), static_cast<const C4<double> *>(G),
+                                                     run_start, nruns, static_cast<const C2<double> *>(Y), p);
+    } else {
+        k_force_rows<float><<<gr, 256, 0, s>>>(static_cast<C4<float> *>(G), static_cast<const C4<float> *>(coef),
+                                               run_start, static_cast<const C2<float> *>(X), p.nx);
+        k_synth_force<float><<<grid, block, 0, s>>>(static_cast<float *>(F), static_cast<const C4<float> *>(G),
+                                                    run_start, nruns, static_cast<const C2<float> *>(Y), p);
+    }
     return cudaGetLastError();
 }
 

@@ -151,7 +151,7 @@ __device__ __forceinline__ int wrap_window(int a, int n) {
 // threads of a CTA, through the shared window S.  Needs nx even and a
 // halo-1 streaming mode SM (cfl <= 1); nodes of the tile past the lattice
 // edge are not written.
-template <typename TS, bool FORCED, int TW, int TH, int NT, typename I, int SM = kStreamCfl1>
+template <typename TS, bool FORCED, int TW, int TH, int NT, typename I, int SM = kStreamCfl1, bool DFL = false>
 __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__restrict__ qout,
                                             const float *__restrict__ F, const StepParams &p, int tx0, int ty0,
                                             TS *__restrict__ S) {
@@ -175,11 +175,12 @@ __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__re
         pull_pair<TS, I, false, SM>(qin, p, plane, rows, (I)x0, (I)xl, (I)xr, q);
         pf2 Fx, Fy;
         force_pair<I, FORCED>(F, plane, rows[1] + (I)x0, Fx, Fy);
-        collide_node<pf2, pf2, FORCED>(q, Fx, Fy, p);
+        collide_node<pf2, pf2, FORCED, DFL>(q, Fx, Fy, p);
+        const unsigned seed =
+            rounds_sr<TS>(p) ? sr_pair_seed((unsigned)y * (unsigned)p.nx + (unsigned)x0, q[0].v.x, q[0].v.y) : 0u;
         static_for<0, NC>([&](auto C) {
             constexpr int c = decltype(C)::value;
-            const float out[2] = {q[c].v.x, q[c].v.y};
-            store_run<TS, float, 2>(S + (c * SPLANE + lr * SW + lc), out);
+            store_pair<TS, c>(S + (c * SPLANE + lr * SW + lc), q[c].v.x, q[c].v.y, p, seed);
         });
     }
     __syncthreads();
@@ -196,22 +197,25 @@ __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__re
         const I n0 = (I)y * (I)p.pitch + (I)x0;
         pf2 Fx, Fy;
         force_pair<I, FORCED>(F, plane, n0, Fx, Fy);
-        collide_node<pf2, pf2, FORCED>(q, Fx, Fy, p);
+        collide_node<pf2, pf2, FORCED, DFL>(q, Fx, Fy, p);
+        const unsigned seed =
+            rounds_sr<TS>(p) ? sr_pair_seed((unsigned)y * (unsigned)p.nx + (unsigned)x0, q[0].v.x, q[0].v.y) : 0u;
         static_for<0, NC>([&](auto C) {
             constexpr int c = decltype(C)::value;
-            const float out[2] = {q[c].v.x, q[c].v.y};
-            store_run<TS, float, 2>(qout + ((I)c * plane + n0), out);
+            store_pair<TS, c>(qout + ((I)c * plane + n0), q[c].v.x, q[c].v.y, p, seed);
         });
     }
 }
 
 // Two steps of the lattice, one TW x TH tile per CTA (blockIdx.x, blockIdx.y).
-template <typename TS, bool FORCED, int TW, int TH, int NT, int MINB, typename I, int SM = kStreamCfl1>
+// DFL: the Landau frame refined to FP64 accuracy (see step_pair).
+template <typename TS, bool FORCED, int TW, int TH, int NT, int MINB, typename I, int SM = kStreamCfl1,
+          bool DFL = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_step_fused2(const TS *__restrict__ qin, TS *__restrict__ qout, const float *__restrict__ F, StepParams p) {
     extern __shared__ __align__(16) unsigned char fused2_smem[];
-    fused2_tile<TS, FORCED, TW, TH, NT, I, SM>(qin, qout, F, p, blockIdx.x * TW, blockIdx.y * TH,
-                                               reinterpret_cast<TS *>(fused2_smem));
+    fused2_tile<TS, FORCED, TW, TH, NT, I, SM, DFL>(qin, qout, F, p, blockIdx.x * TW, blockIdx.y * TH,
+                                                    reinterpret_cast<TS *>(fused2_smem));
 }
 
 // Ensemble form: a grid-stride walk over the flat tile list of all members

@@ -9,6 +9,66 @@
 
 namespace rlbk {
 
+// Stochastic rounding of the two values (a at x0, b at x0 + 1) of a node
+// pair to the 16-bit storage type: the hardware conversion with stochastic
+// rounding (cvt.rs) rounds up with probability equal to the value's
+// distance from the lower neighbour in units of the gap, using the random
+// bits supplied.  Those are hashed, once per node pair, from the pair's
+// index and the bits of its two updated rest-class values (xor-combined
+// with odd multipliers, then the "lowbias32" finaliser from C. Wellons'
+// hash-prospector), and per class from that seed xor the bits of the
+// class's value times an odd multiplier of the class.  The rounding is thus a
+// deterministic function of the state: runs repeat bit for bit, a halo node
+// recomputed by two tiles rounds the same way in both, and checkpoints
+// resume bitwise; the rest values change every step wherever the fluid
+// moves, so the draws do too.
+__device__ __forceinline__ unsigned sr_pair_seed(unsigned node, float a0, float b0) {
+    unsigned h = (node * 0x85EBCA77u) ^ __float_as_uint(a0) ^ (__float_as_uint(b0) * 0x9E3779B1u);
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
+}
+
+// Odd multiplier of class c (distinct per class).
+__host__ __device__ constexpr unsigned sr_class_mult(int c) { return 0xC2B2AE3Du + 0x27D4EB2Eu * (unsigned)c; }
+
+template <typename TS>
+__device__ __forceinline__ unsigned cvt_pair_sr(float a, float b, unsigned rbits) {
+    unsigned d;
+    // the first source goes to the upper half (the element at x0 + 1)
+    if constexpr (std::is_same<TS, __half>::value)
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(b), "f"(a), "r"(rbits));
+    else
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(b), "f"(a), "r"(rbits));
+    return d;
+}
+
+// Whether a lattice with storage TS rounds its stores stochastically.
+template <typename TS>
+__device__ __forceinline__ bool rounds_sr(const StepParams &p) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value || std::is_same<TS, __half>::value) return p.round_sr != 0;
+    else return false;
+}
+
+// Store of a node pair's two values of class c: rounded to nearest, or
+// stochastically (pair seed `seed`) for the 16-bit types when the lattice
+// asks for it.
+template <typename TS, int C>
+__device__ __forceinline__ void store_pair(TS *p, float a, float b, const StepParams &prm, unsigned seed) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value || std::is_same<TS, __half>::value) {
+        if (prm.round_sr) {
+            const unsigned r = (seed ^ __float_as_uint(a)) * sr_class_mult(C);
+            *reinterpret_cast<unsigned *>(p) = cvt_pair_sr<TS>(a, b, r);
+            return;
+        }
+    }
+    const float out[2] = {a, b};
+    store_run<TS, float, 2>(p, out);
+}
+
 // The fused step of the node pair (x0, x0 + 1) of row y in packed lanes.
 // I is the index type of the element offsets: 32-bit when all 17 planes fit,
 // so each load address is one 32-bit sum and one widening add.  SM is the
@@ -19,7 +79,9 @@ namespace rlbk {
 // cells away; each x-moving class row is read as the two aligned column
 // pairs that cover both candidate corners, and a register select picks the
 // launch's corner).
-template <typename TS, bool FORCED, typename I = long long, int SM = kStreamCfl1>
+// DFL: the Landau frame refined to FP64 accuracy on the FP32 lanes
+// (landau_refine_df), the library's FP64 Landau solve for these kernels.
+template <typename TS, bool FORCED, typename I = long long, int SM = kStreamCfl1, bool DFL = false>
 __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__restrict__ qout,
                                           const float *__restrict__ F, const StepParams &p, int x0, int y) {
     const int ym = (y == 0) ? p.ny - 1 : y - 1;
@@ -147,12 +209,13 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
         Fx = pf2(fx[0], fx[1]);
         Fy = pf2(fy[0], fy[1]);
     }
-    collide_node<pf2, pf2, FORCED>(q, Fx, Fy, p);
+    collide_node<pf2, pf2, FORCED, DFL>(q, Fx, Fy, p);
 
+    const unsigned seed =
+        rounds_sr<TS>(p) ? sr_pair_seed((unsigned)y * (unsigned)p.nx + (unsigned)x0, q[0].v.x, q[0].v.y) : 0u;
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
-        const float out[2] = {q[c].v.x, q[c].v.y};
-        store_run<TS, float, 2>(qout + ((I)c * plane + n0), out);
+        store_pair<TS, c>(qout + ((I)c * plane + n0), q[c].v.x, q[c].v.y, p, seed);
     });
 }
 
@@ -240,13 +303,13 @@ __global__ void __launch_bounds__(256, MINB) k_step_pair2(const TS *__restrict__
 // autotuner can trade registers for occupancy.
 // MINB 5: blocks of at most 128 threads, five resident per SM (at most 102
 // registers per thread: 20 warps per SM).
-template <typename TS, bool FORCED, int MINB, typename I = long long, int SM = kStreamCfl1>
+template <typename TS, bool FORCED, int MINB, typename I = long long, int SM = kStreamCfl1, bool DFL = false>
 __global__ void __launch_bounds__(MINB == 5 ? 128 : 256, MINB)
     k_step_pair(const TS *__restrict__ qin, TS *__restrict__ qout, const float *__restrict__ F, StepParams p) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= p.nx || y >= p.ny) return;
-    step_pair<TS, FORCED, I, SM>(qin, qout, F, p, x0, y);
+    step_pair<TS, FORCED, I, SM, DFL>(qin, qout, F, p, x0, y);
 }
 
 // Ensemble step with the packed body (see k_step_batch).

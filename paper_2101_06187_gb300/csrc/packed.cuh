@@ -29,6 +29,13 @@ __device__ __forceinline__ pf2 operator-(pf2 a, pf2 b) {
 __device__ __forceinline__ pf2 operator*(pf2 a, pf2 b) { return pf2(__fmul2_rn(a.v, b.v)); }
 __device__ __forceinline__ pf2 fmadd(pf2 a, pf2 b, pf2 c) { return pf2(__ffma2_rn(a.v, b.v, c.v)); }
 
+// The rounded single operations of the double-float refinement
+// (rlbm_device.cuh): the packed intrinsics are never contracted.
+__device__ __forceinline__ pf2 xadd(pf2 a, pf2 b) { return a + b; }
+__device__ __forceinline__ pf2 xsub(pf2 a, pf2 b) { return a - b; }
+__device__ __forceinline__ pf2 xmul(pf2 a, pf2 b) { return a * b; }
+__device__ __forceinline__ pf2 xfma(pf2 a, pf2 b, pf2 c) { return fmadd(a, b, c); }
+
 __device__ __forceinline__ pf2 recip(pf2 x) { return pf2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
 __device__ __forceinline__ pf2 fast_recip(pf2 x) { return pf2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
 __device__ __forceinline__ pf2 sqrt_(pf2 x) { return pf2(sqrtf(x.v.x), sqrtf(x.v.y)); }

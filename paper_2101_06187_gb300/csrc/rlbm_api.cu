@@ -148,6 +148,7 @@ static StepParams params_of(const rlbm_t *h) {
     p.eta_k = h->opts.eta_s > 0.0 ? std::pow(M_PI * M_PI / 3.0, 0.25) * h->opts.dt / (5.0 * h->opts.eta_s) : 0.0;
     p.err = h->errword;
     finish_params(p);
+    p.round_sr = h->opts.rounding == RLBM_ROUND_STOCHASTIC ? 1 : 0;  // resolved at create (16-bit forms only)
     return p;
 }
 
@@ -164,6 +165,7 @@ static size_t partials_bytes(const rlbm_t *h) {
     return h->d3 ? (size_t)4 * moments3_blocks(params_of(h)) * sizeof(double)
                  : (size_t)3 * moments_blocks(params_of(h)) * sizeof(double);
 }
+static size_t gtab_bytes(const rlbm_t *h) { return (size_t)h->nky * h->nx * 4 * compute_bytes(h->opts.dtype); }
 static size_t coef_bytes(const rlbm_t *h) {
     return h->d3 ? coef3_bytes(h->opts.dtype) * h->nmodes : 4 * compute_bytes(h->opts.dtype) * h->nmodes;
 }
@@ -179,8 +181,15 @@ static cudaError_t launch_step_h(const rlbm_t *h, const LaunchCfg &cfg, const vo
                                  const StepParams &p) {
     if (h->ring) return launch_ring_step(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
     if (h->d3) return launch_step3(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
-    if (cfg.kernel == RLBM_KERNEL_FUSED2)
+    // FP32 / 16-bit storage with the FP64 Landau solve on the packed kernels: the frame refined to FP64
+    // accuracy on the FP32 lanes
+    const bool dfl = h->opts.landau == RLBM_LANDAU_FP64 && h->opts.dtype != RLBM_F64;
+    if (cfg.kernel == RLBM_KERNEL_FUSED2) {
+        if (dfl) return launch_step_fused2_dfl(h->opts.dtype, cfg, h->forced, qin, qout, h->F, p, h->stream);
         return launch_step_fused2(h->opts.dtype, h->opts.landau, cfg, h->forced, qin, qout, h->F, p, h->stream);
+    }
+    if (cfg.kernel == RLBM_KERNEL_PACKED && dfl)
+        return launch_step_pair_dfl(h->opts.dtype, cfg, h->forced, qin, qout, h->F, p, h->stream);
     if (cfg.kernel == RLBM_KERNEL_TMA) {
         if (!h->tm_ready) return cudaErrorNotSupported;
         const CUtensorMap &mq = (qin == h->q[0]) ? h->tm_q[0] : h->tm_q[1];
@@ -219,7 +228,8 @@ static rlbm_status ensure_force(rlbm_t *h) {
     }
     CUDA_TRY(h, launch_draw_modes(h->opts.dtype, h->modes, h->coef, h->nmodes, h->forcing.amp,
                                   (unsigned long long)h->forcing.seed, (unsigned long long)e, h->stream));
-    CUDA_TRY(h, launch_synth_force(h->opts.dtype, h->F, h->coef, h->nmodes, h->tabx, h->taby, p, h->stream));
+    CUDA_TRY(h, launch_synth_force(h->opts.dtype, h->F, h->coef, h->nmodes, h->ky_start, h->nky, h->gtab, h->tabx,
+                                   h->taby, p, h->stream));
     h->force_epoch = e;
     return RLBM_OK;
 }
@@ -335,15 +345,17 @@ static bool candidate_applies(const rlbm_t *h, const LaunchCfg &c) {
         !(h->ring && c.kernel == RLBM_KERNEL_FUSED2))
         return false;
     if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) return false;
+    if (h->opts.rounding == RLBM_ROUND_STOCHASTIC && c.kernel != RLBM_KERNEL_PACKED && c.kernel != RLBM_KERNEL_FUSED2)
+        return false;  // the other kernels round to nearest
     return true;
 }
 
-static std::map<std::tuple<int, int, int, int, int, int, int>, LaunchCfg> g_tuned;
+static std::map<std::tuple<int, int, int, int, int, int, int, int>, LaunchCfg> g_tuned;
 static std::mutex g_tuned_mu;
 
-static std::tuple<int, int, int, int, int, int, int> tune_key(const rlbm_t *h) {
+static std::tuple<int, int, int, int, int, int, int, int> tune_key(const rlbm_t *h) {
     return std::make_tuple(h->nx, h->ny, h->opts.dtype, h->opts.landau, h->forced ? 1 : 0,
-                           h->ring ? 1 : (h->d3 ? 2 + h->nz : 0), stream_mode(h->opts.cfl));
+                           h->ring ? 1 : (h->d3 ? 2 + h->nz : 0), stream_mode(h->opts.cfl), h->opts.rounding);
 }
 
 
@@ -411,6 +423,8 @@ void rlbm_destroy(rlbm_t *h) {
     if (h->tabx) dev_free(h, h->tabx, tw_bytes(h, h->nx) * h->nmodes);
     if (h->taby) dev_free(h, h->taby, tw_bytes(h, h->ny) * h->nmodes);
     if (h->modes) dev_free(h, h->modes, sizeof(Mode) * h->nmodes);
+    if (h->ky_start) dev_free(h, h->ky_start, sizeof(int) * (h->nky + 1));
+    if (h->gtab) dev_free(h, h->gtab, gtab_bytes(h));
     dev_free(h, h->fields, fields_bytes(h));
     dev_free(h, h->partials, partials_bytes(h));
     dev_free(h, h->totals, 4 * sizeof(double));
@@ -465,7 +479,13 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (o.kernel == RLBM_KERNEL_TMA && (nx % 2 != 0 || o.dtype != RLBM_F32 || o.landau != RLBM_LANDAU_FP32))
         return RLBM_ERR_ARG;
     if ((o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_TWOPASS || o.kernel == RLBM_KERNEL_FUSED2) &&
-        (nx % 2 != 0 || o.dtype == RLBM_F64 || o.landau != RLBM_LANDAU_FP32))
+        (nx % 2 != 0 || o.dtype == RLBM_F64))
+        return RLBM_ERR_ARG;
+    // the FP64 Landau solve on the packed kernels is the frame refined on the FP32 lanes: one-layer lattice, CFL 1
+    if (o.landau != RLBM_LANDAU_FP32 &&
+        (o.kernel == RLBM_KERNEL_TWOPASS ||
+         ((o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_FUSED2) &&
+          (ring || d3 || !(o.cfl == 0.0 || o.cfl == 1.0)))))
         return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_GATHER_VEC && nx % (o.dtype == RLBM_F64 ? 2 : 4) != 0) return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_GATHER_VEC2 && nx % 2 != 0) return RLBM_ERR_ARG;
@@ -482,6 +502,16 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
                          o.kernel == RLBM_KERNEL_TMA || o.kernel == RLBM_KERNEL_TWOPASS))
         return RLBM_ERR_ARG;  // the vector kernels stream at CFL 1 only
     if (o.cfl > 1.0 && o.kernel == RLBM_KERNEL_FUSED2) return RLBM_ERR_ARG;  // two steps per launch: halo 1
+    if (o.rounding < RLBM_ROUND_DEFAULT || o.rounding > RLBM_ROUND_STOCHASTIC) return RLBM_ERR_ARG;
+    const bool h16 = o.dtype == RLBM_BF16 || o.dtype == RLBM_F16;
+    const bool sr_kernel = o.kernel == RLBM_KERNEL_AUTO || o.kernel == RLBM_KERNEL_PACKED ||
+                           o.kernel == RLBM_KERNEL_FUSED2;
+    if (o.rounding == RLBM_ROUND_DEFAULT)  // BF16: stochastic where the kernel can, else nearest
+        o.rounding = (o.dtype == RLBM_BF16 && !ring && !d3 && sr_kernel && nx % 2 == 0) ? RLBM_ROUND_STOCHASTIC
+                                                                                           : RLBM_ROUND_NEAREST;
+    if (!h16) o.rounding = RLBM_ROUND_NEAREST;
+    // stochastic rounding of 16-bit stores: the packed kernels of the one-layer lattice
+    if (o.rounding == RLBM_ROUND_STOCHASTIC && (ring || d3 || !sr_kernel || nx % 2 != 0)) return RLBM_ERR_ARG;
     if (o.dtype == RLBM_F64) o.landau = RLBM_LANDAU_FP64;
     // the ring runs the one-node-per-thread kernel, at CFL 1 with a fixed tau
     if (ring && ((o.kernel != RLBM_KERNEL_AUTO && o.kernel != RLBM_KERNEL_GATHER && o.kernel != RLBM_KERNEL_PACKED &&
@@ -530,7 +560,8 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     }
     h->stream = static_cast<cudaStream_t>(o.stream);
     // the two-step kernels keep more than 48 KB of shared memory per CTA
-    if (!ring && !d3 && o.dtype != RLBM_F64 && o.landau == RLBM_LANDAU_FP32 && fused2_prepare() != cudaSuccess) {
+    if (!ring && !d3 && o.dtype != RLBM_F64 &&
+        (o.landau == RLBM_LANDAU_FP32 ? fused2_prepare() : fused2_dfl_prepare()) != cudaSuccess) {
         cudaGetLastError();
         if (o.kernel == RLBM_KERNEL_FUSED2) {
             delete h;
@@ -561,15 +592,26 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
             h->cfg.bx = 64;
             h->cfg.by = 16;
             h->cfg.minb = 2;
+            if (o.landau == RLBM_LANDAU_FP64 && o.dtype != RLBM_F64 && !ring) {
+                h->cfg.by = 8;  // the refined-frame kernel comes in 64 x 8 tiles, four CTAs per SM
+                h->cfg.minb = 4;
+            }
         }
     }
     if (!h->tuned && o.kernel == RLBM_KERNEL_AUTO) {
         h->cfg.kernel = RLBM_KERNEL_GATHER;
         h->cfg.bx = 128;
         h->cfg.by = 2;
+        if (o.rounding == RLBM_ROUND_STOCHASTIC) {
+            h->cfg.kernel = RLBM_KERNEL_PACKED;  // the kernels that round stochastically
+            h->cfg.bx = 128;
+            h->cfg.by = 1;
+            h->cfg.minb = 2;
+        }
     }
 
     std::vector<Mode> modes;
+    std::vector<int> ky_runs;  // first mode of each run of equal ky, then nmodes
     std::vector<int> modes3;
     if (forced) h->nmodes = d3 ? enumerate_modes3(fz.kmin, fz.kmax, &modes3) : enumerate_modes(fz.kmin, fz.kmax, &modes);
     if (forced && h->nmodes == 0) {
@@ -600,7 +642,13 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
             ok = ok && h->modes3 && h->twz && h->tabz;
         } else {
             h->modes = static_cast<Mode *>(dev_alloc(h, sizeof(Mode) * h->nmodes));
-            ok = ok && h->modes;
+            for (int m = 0; m < h->nmodes; ++m)
+                if (m == 0 || modes[m].ky != modes[m - 1].ky) ky_runs.push_back(m);
+            ky_runs.push_back(h->nmodes);
+            h->nky = (int)ky_runs.size() - 1;
+            h->ky_start = static_cast<int *>(dev_alloc(h, sizeof(int) * ky_runs.size()));
+            h->gtab = dev_alloc(h, gtab_bytes(h));
+            ok = ok && h->modes && h->ky_start && h->gtab;
         }
     }
     if (!ok || cudaMallocHost(&h->host_small, 4096) != cudaSuccess) {
@@ -625,6 +673,9 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     } else if (forced) {
         cudaError_t e = cudaMemcpyAsync(h->modes, modes.data(), sizeof(Mode) * h->nmodes, cudaMemcpyHostToDevice,
                                         h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->ky_start, ky_runs.data(), sizeof(int) * ky_runs.size(), cudaMemcpyHostToDevice,
+                                h->stream);
         if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twx, nx, h->stream);
         if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twy, ny, h->stream);
         if (e == cudaSuccess)
@@ -1152,7 +1203,7 @@ struct CkptHeader {
     uint32_t version, header_bytes;
     int32_t nx, ny, nz, pitch, ncls, dtype, kind, forced;
     double tau, eps0, scale, cfl, eta_s, dt;
-    int32_t kmin, kmax, redraw_period, pad;
+    int32_t kmin, kmax, redraw_period, rounding;
     double amp;
     uint64_t seed;
     int64_t step;
@@ -1187,6 +1238,7 @@ static CkptHeader ckpt_header_of(const rlbm_t *h) {
         c.amp = h->forcing.amp;
         c.seed = h->forcing.seed;
     }
+    c.rounding = h->opts.rounding;
     c.step = h->step;
     c.state_bytes = q_bytes(h);
     return c;
@@ -1445,6 +1497,11 @@ rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_o
         return RLBM_ERR_ARG;
     const bool lanes = bk == RLBM_KERNEL_PACKED || bk == RLBM_KERNEL_FUSED2;
     if (lanes && (o.dtype == RLBM_F64 || o.landau != RLBM_LANDAU_FP32)) return RLBM_ERR_ARG;
+    // ensembles round to nearest unless asked otherwise; stochastic rounding needs a packed-lane body
+    if (o.rounding < RLBM_ROUND_DEFAULT || o.rounding > RLBM_ROUND_STOCHASTIC) return RLBM_ERR_ARG;
+    if (o.rounding == RLBM_ROUND_DEFAULT || (o.dtype != RLBM_BF16 && o.dtype != RLBM_F16))
+        o.rounding = RLBM_ROUND_NEAREST;
+    if (o.rounding == RLBM_ROUND_STOCHASTIC && !lanes) return RLBM_ERR_ARG;
     const int V = lanes ? 2 : run_length(o.dtype);
     for (int r = 0; r < nruns; ++r) {
         if (runs[r].nx % V != 0) return RLBM_ERR_ARG;  // the ensemble kernel works on runs of V nodes

@@ -103,6 +103,9 @@ struct StepParams {
     double inv_scale; // 1/s
     // FP32 copies, so the FP32 kernels never touch the (slow) FP64 pipe
     float inv_tau_f, eps0_f, scale_f, inv_scale_f;
+    // (4/3) eps0, the diagonal of S + eps I at rest, as an unevaluated sum
+    // of two floats (for the frame refined to FP64 accuracy on FP32 lanes)
+    float alpha_hi_f, alpha_lo_f;
     // eta/s mode (eta_k > 0): 1/tau = eta_k eps^{1/4}, from tau_R = 5 (eta/s)/T,
     // eps = 3 T^4/pi^2, in steps of dt: eta_k = (pi^2/3)^{1/4} dt / (5 eta/s)
     double eta_k;
@@ -119,6 +122,8 @@ struct StepParams {
     // compiler cannot merge its loads with the first pass's (re-reading is
     // what frees the registers of the two-pass kernels)
     int reload_offset;
+    // 1: stochastic rounding of 16-bit stores (packed kernels), else nearest
+    int round_sr;
     int *err;         // device error word (bounded-wait / failure reporting)
 };
 
@@ -148,6 +153,11 @@ RLBM_HD inline void finish_params(StepParams &p) {
     p.scale_f = (float)p.scale;
     p.inv_scale_f = (float)p.inv_scale;
     p.eta_k_f = (float)p.eta_k;
+    {
+        const double alpha = 4.0 / 3.0 * p.eps0;
+        p.alpha_hi_f = (float)alpha;
+        p.alpha_lo_f = (float)(alpha - (double)p.alpha_hi_f);
+    }
     p.far_x = p.far_y = 0u;
     for (int c = 0; c < 17; ++c) {
         const double sx = -p.cfl * cls_cx(c), sy = -p.cfl * cls_cy(c);
@@ -377,7 +387,7 @@ RLBM_HD inline T frame_rsqrt(T x) {
 // (P = eps/3), 3/2 for the 2D ring (P = eps/2).
 template <typename TL>
 RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL dSxy, TL dSyy,
-                                      double rest_a = 4.0 / 3.0) {
+                                      double rest_a = 4.0 / 3.0, TL *delta_out = nullptr) {
     const TL a0 = (TL)rest_a * eps0 + dE;
     constexpr bool dbl = std::is_same<TL, double>::value;
     const TL tol = dbl ? (TL)4e-16 : (TL)1e-7;
@@ -410,6 +420,7 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
         if (!(step * step > tol * absval(delta))) break;
         newton();
     }
+    if (delta_out) *delta_out = delta;
     velocity(delta, true);
     Frame<TL> fr;
     fr.ddelta_eps = dE - delta;
@@ -425,6 +436,116 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
         fr.gamma = sqrt_(fr.g2);
     }
     return fr;
+}
+
+// ---------------------------------------------------------------- frame to FP64 accuracy on FP32 lanes
+// Rounded single operations that the compiler may neither contract into a
+// fused multiply-add nor reassociate: the error-free transformations below
+// rely on each rounding happening exactly as written.  (Overloads for the
+// packed lanes live in packed.cuh, whose operators are such operations.)
+__device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float xsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// s + e = a + b exactly (Knuth's branch-free TwoSum).
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+    s = xadd(a, b);
+    const T bb = xsub(s, a);
+    e = xadd(xsub(a, xsub(s, bb)), xsub(b, bb));
+}
+// s + e = a + b exactly when |a| >= |b| (Dekker's Fast2Sum).
+template <typename T>
+__device__ __forceinline__ void fast_two_sum(T a, T b, T &s, T &e) {
+    s = xadd(a, b);
+    e = xsub(b, xsub(s, a));
+}
+// p + e = a * b exactly (the rounding error of a product is one FMA away).
+template <typename T>
+__device__ __forceinline__ void two_prod(T a, T b, T &p, T &e) {
+    p = xmul(a, b);
+    e = xfma(a, b, xsub(T(0.0f), p));
+}
+
+// The Landau frame of the FP32 Newton solve (delta, v), refined by one
+// Newton step of the coupled system
+//     F1 = M - (A - delta I) v = 0,   F2 = M . v - delta = 0
+// (the frame condition in the deviation variables of landau_solve) whose
+// residuals are evaluated in double-float arithmetic: each product and sum
+// of the residual is carried as an unevaluated pair of floats with its
+// rounding error, so the residuals come out with about 48 significant
+// bits although each input is an FP32 number.  The correction itself
+// needs only FP32: with B = A - delta I, w = B^-1 F1 and u = B^-1 v,
+//     d_delta = (F2 + M . w) / (1 - M . u),   d_v = w + d_delta u,
+// where M . u = (B^-1 M) . v = |v|^2 to the order kept (B is symmetric), so
+// 1 / (1 - M . u) is the frame's gamma^2.  The FP32 solve has converged to
+// a few units in the last place, so the step's quadratic convergence
+// leaves (delta + d_delta, v + d_v) within about 1e-14 of the exact frame
+// of the stored moments: an FP64-accurate solve on the FP32 pipes (the
+// FP64 units of this GPU run at 1/58 of the FP32 rate).  The frame's FP32
+// fields are then the refined values rounded once; the collision consumes
+// them in FP32, as it consumes an FP64 solve's.
+// The refined frame as unevaluated sums hi + lo (for accuracy checks).
+template <typename TL>
+struct FramePairs {
+    TL delta_hi, delta_lo, vx_hi, vx_lo, vy_hi, vy_lo;
+};
+
+template <typename TL>
+__device__ __forceinline__ void landau_refine_df(TL alpha_hi, TL alpha_lo, TL eps0, TL dE, TL Mx, TL My, TL dSxx,
+                                                 TL dSxy, TL dSyy, TL delta, Frame<TL> &fr,
+                                                 FramePairs<TL> *pairs = nullptr) {
+    const TL vx = fr.vx, vy = fr.vy, zero = TL(0.0f);
+    const TL ndelta = xsub(zero, delta);
+    // a = alpha + dE - delta (pair ah + al); bxx = a + dSxx, byy = a + dSyy
+    TL s1, e1, ah, e2;
+    two_sum(alpha_hi, dE, s1, e1);
+    fast_two_sum(s1, ndelta, ah, e2);  // |s1| = E + eps0/3 > delta = M . v
+    const TL al = xadd(alpha_lo, xadd(e1, e2));
+    TL bxh, e3, byh, e4;
+    two_sum(ah, dSxx, bxh, e3);
+    two_sum(ah, dSyy, byh, e4);
+    const TL bxl = xadd(al, e3), byl = xadd(al, e4);
+    // F1x = Mx - bxx vx - dSxy vy,  F1y = My - dSxy vx - byy vy
+    auto residual = [&](TL Ma, TL bh, TL bl, TL va, TL vb) {
+        TL p1, q1, p2, q2, t1, f1, t2, f2;
+        two_prod(bh, va, p1, q1);
+        q1 = xfma(bl, va, q1);
+        two_prod(dSxy, vb, p2, q2);
+        two_sum(Ma, xsub(zero, p1), t1, f1);
+        two_sum(t1, xsub(zero, p2), t2, f2);
+        return xadd(t2, xsub(xadd(f1, f2), xadd(q1, q2)));
+    };
+    const TL rx = residual(Mx, bxh, bxl, vx, vy);
+    const TL ry = residual(My, byh, byl, vy, vx);
+    // F2 = Mx vx + My vy - delta
+    TL p5, q5, p6, q6, t5, f5, t6, f6;
+    two_prod(Mx, vx, p5, q5);
+    two_prod(My, vy, p6, q6);
+    two_sum(p5, p6, t5, f5);
+    two_sum(t5, ndelta, t6, f6);
+    const TL r2 = xadd(t6, xadd(xadd(f5, f6), xadd(q5, q6)));
+    // the FP32 Newton correction
+    const TL nSxy = zero - dSxy;
+    const TL inv_det = fast_recip(fmadd(bxh, byh, nSxy * dSxy));
+    const TL wx = fmadd(byh, rx, nSxy * ry) * inv_det;
+    const TL wy = fmadd(bxh, ry, nSxy * rx) * inv_det;
+    const TL ux = fmadd(byh, vx, nSxy * vy) * inv_det;
+    const TL uy = fmadd(bxh, vy, nSxy * vx) * inv_det;
+    const TL dd = fmadd(Mx, wx, fmadd(My, wy, r2)) * fr.g2;
+    const TL dvx = fmadd(dd, ux, wx), dvy = fmadd(dd, uy, wy);
+    if (pairs) *pairs = FramePairs<TL>{delta, dd, vx, dvx, vy, dvy};
+    // refined frame, rounded once to FP32: eps - eps0 = dE - delta - dd
+    TL h, e;
+    two_sum(dE, ndelta, h, e);
+    fr.ddelta_eps = xadd(h, xsub(e, dd));
+    fr.eps = eps0 + fr.ddelta_eps;
+    fr.vx = xadd(vx, dvx);
+    fr.vy = xadd(vy, dvy);
+    fr.v2 = fmadd(fr.vx, fr.vx, fr.vy * fr.vy);
+    fr.gamma = frame_rsqrt(TL(1.0f) - fr.v2);
+    fr.g2 = fr.gamma * fr.gamma;
 }
 
 // Fused collision of one node (steps (c)-(e) of Sec. 3.3) on the gathered
@@ -455,12 +576,21 @@ struct CollideCoef {
     TC K0, Kxx, Kxy, Kyy, o1, no3, G1, om, a0, vx, vy, Fx, Fy;
 };
 
-// Frame and update coefficients of a node from its moments.
-template <typename TC, typename TL, bool FORCED>
+// Frame and update coefficients of a node from its moments.  DFL: refine
+// the FP32 frame to FP64 accuracy (landau_refine_df; FP32 lanes only).
+template <typename TC, typename TL, bool FORCED, bool DFL = false>
 RLBM_HD inline Frame<TL> collide_coef(const NodeMoments<TC> &m, TC Fx, TC Fy, const StepParams &p,
                                       CollideCoef<TC> &k) {
-    const Frame<TL> fr = landau_solve<TL>(par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
-                                          (TL)m.dSyy);
+    TL delta;
+    Frame<TL> fr = landau_solve<TL>(par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
+                                    (TL)m.dSyy, 4.0 / 3.0, DFL ? &delta : nullptr);
+    if constexpr (DFL) {
+        static_assert(is_f32_lane<TL>::value, "the double-float refinement runs on FP32 lanes");
+#ifdef __CUDA_ARCH__
+        landau_refine_df<TL>(TL(p.alpha_hi_f), TL(p.alpha_lo_f), par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My,
+                             (TL)m.dSxx, (TL)m.dSxy, (TL)m.dSyy, delta, fr);
+#endif
+    }
     const TC inv_s = par_inv_scale<TC>(p);
     const TL eg2 = fr.eps * fr.g2;
     const TC P0 = (TC)(fmadd((TL)(-2) * eg2, fr.v2, fr.ddelta_eps)) * inv_s;
@@ -544,11 +674,11 @@ RLBM_HD inline void collide_pair(TC &qp, TC &qn, const CollideCoef<TC> &k) {
     qn = fmadd(n0, k.a0 - oxi, even - odd);
 }
 
-template <typename TC, typename TL, bool FORCED>
+template <typename TC, typename TL, bool FORCED, bool DFL = false>
 RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
     const NodeMoments<TC> m = node_moments<TC>(q, par_scale<TC>(p));
     CollideCoef<TC> k;
-    const Frame<TL> fr = collide_coef<TC, TL, FORCED>(m, Fx, Fy, p, k);
+    const Frame<TL> fr = collide_coef<TC, TL, FORCED, DFL>(m, Fx, Fy, p, k);
     q[0] = collide_rest<TC>(q[0], k);
     static_for<0, NPAIR>([&](auto K) {
         constexpr int kp = decltype(K)::value;

@@ -61,6 +61,16 @@ cudaError_t launch_step_tma(const LaunchCfg &cfg, bool forced, const CUtensorMap
 cudaError_t fused2_prepare();
 cudaError_t launch_step_fused2(int dtype, int landau, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                                const void *F, const StepParams &p, cudaStream_t s);
+// The packed single step and the two-step kernel (64 x 8 tiles) with the
+// Landau frame refined to FP64 accuracy on the FP32 lanes (k_step_dfl.cu):
+// RLBM_LANDAU_FP64 for FP32 / BF16 / FP16 storage on those kernels, CFL 1,
+// nx even, launch budgets 1 and 2 for the single step.  fused2_dfl_prepare
+// as fused2_prepare.
+cudaError_t launch_step_pair_dfl(int dtype, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
+                                 const void *F, const StepParams &p, cudaStream_t s);
+cudaError_t fused2_dfl_prepare();
+cudaError_t launch_step_fused2_dfl(int dtype, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
+                                   const void *F, const StepParams &p, cudaStream_t s);
 // Ensemble form over `runs` (BatchRun descriptors with TW x TH tiles, cfl 1
 // members): two steps per launch (two != 0) or one packed step.
 cudaError_t launch_batch_fused2(int dtype, int landau, const LaunchCfg &cfg, int grid, const void *runs, int nruns,
@@ -118,8 +128,11 @@ cudaError_t launch_draw_modes(int dtype, Mode *modes, void *coef, int nmodes, do
                               unsigned long long epoch, cudaStream_t s);
 cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, int nmodes, const void *twx,
                                const void *twy, int nx, int ny, cudaStream_t s);
-cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const void *X, const void *Y,
-                               const StepParams &p, cudaStream_t s);
+// F from the mode coefficients, separably: per run of equal ky (ky_start,
+// nky runs) the row sums G over the x tables X, then per node the sum over
+// runs with the run's y table (Y of its first mode); G is [nky][nx] x 4.
+cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const int *ky_start, int nky,
+                               void *G, const void *X, const void *Y, const StepParams &p, cudaStream_t s);
 cudaError_t launch_decode_class(int dtype, const void *q, int c, double W, const StepParams &p, double *out,
                                 cudaStream_t s);
 cudaError_t launch_encode_class(int dtype, void *q, int c, double W, const StepParams &p, const double *in,
@@ -170,6 +183,9 @@ struct rlbm {
     void *tabx = nullptr, *taby = nullptr;  // per-mode phase tables [nmodes][nx], [nmodes][ny]
     rlbk::Mode *modes = nullptr;
     void *coef = nullptr;             // per-mode synthesis coefficients (ax, bx, ay, by) in the compute type
+    int nky = 0;                      // runs of modes with equal ky (the modes are enumerated ky ascending)
+    int *ky_start = nullptr;          // first mode of each run, and nmodes at the end [nky + 1]
+    void *gtab = nullptr;             // per-run row sums of the synthesis [nky][nx] (4 values, compute type)
     double *fields = nullptr;         // 3 * nx * ny doubles: staging for init / moments outputs
     double *partials = nullptr;       // per-block partial sums of the moments kernel
     double *totals = nullptr;         // 3 doubles

@@ -85,14 +85,27 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     o = rl.rlbm_opts_default()
     o.eta_s = -0.01
     assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
-    # two steps per launch: packed FP32 lanes (FP32 Landau, nx even) at cfl <= 1, one-layer lattice only
-    for field, value, nx in (("dtype", rl.DTYPES["f64"], 16), ("landau", rl.LANDAU["fp64"], 16), (None, None, 17),
-                             ("cfl", 1.25, 16)):
+    # two steps per launch: packed FP32 lanes (nx even) at cfl <= 1, one-layer lattice only; the FP64 Landau
+    # solve on them (the frame refined on the FP32 lanes) at cfl 1 only
+    for field, value, nx in (("dtype", rl.DTYPES["f64"], 16), (None, None, 17), ("cfl", 1.25, 16)):
         o = rl.rlbm_opts_default()
         o.kernel = rl.KERNELS["fused2"]
         if field:
             setattr(o, field, value)
         assert create(nx, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG, (field, value, nx)
+    for kernel in ("fused2", "packed", "twopass"):
+        o = rl.rlbm_opts_default()
+        o.kernel = rl.KERNELS[kernel]
+        o.landau = rl.LANDAU["fp64"]
+        o.cfl = 0.5 if kernel != "twopass" else 1.0
+        assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG, kernel
+    # stochastic rounding of 16-bit stores: the packed kernels only; unknown rounding modes refused
+    for kernel, rounding in (("gather", 2), ("vec", 2), ("auto", 3), ("auto", -1)):
+        o = rl.rlbm_opts_default()
+        o.dtype = rl.DTYPES["bf16"]
+        o.kernel = rl.KERNELS[kernel]
+        o.rounding = rounding
+        assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG, (kernel, rounding)
     o = rl.rlbm_opts_default()
     o.kernel = rl.KERNELS["fused2"]
     o.dtype = rl.DTYPES["f64"]

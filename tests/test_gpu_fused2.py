@@ -144,3 +144,31 @@ def test_set_launch_rejects_misfits():
     with pytest.raises(rl.RLBMError):
         lat.set_launch("fused2", 64, 16, 2)
     lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_fp64_landau_solve_on_the_packed_kernels(dtype):
+    """The FP64 Landau solve of the FP32 and 16-bit forms on the packed
+    kernels (the FP32 frame refined to FP64 accuracy by one double-float
+    Newton step): two steps per launch equal packed single steps bit for
+    bit, and the run matches the FP64 oracle within the form's tolerance."""
+    nx, ny = 66, 40
+    fields = workloads.random_smooth(nx, ny, seed=5 * nx + ny, deps=0.05, vmax=0.05)
+    ref, info_p = _run("packed", nx, ny, dtype, fields, landau="fp64")
+    got, info_f = _run("fused2", nx, ny, dtype, fields, landau="fp64")
+    assert info_p["kernel"] == rl.KERNELS["packed"] and info_f["kernel"] == rl.KERNELS["fused2"]
+    np.testing.assert_array_equal(got, ref)
+    lat = rl.Lattice(nx, ny, 0.6, dtype=dtype, forcing=FORCING, kernel="fused2", landau="fp64")
+    lat.init_fields(*fields)
+    for n in CHUNKS:
+        lat.step(n)
+    e_g, vx_g, vy_g, _ = lat.moments()
+    lat.close()
+    f = oracle.init(nx, ny, *fields)
+    oracle.run(f, 0.6, sum(CHUNKS), kmin=FORCING["kmin"], kmax=FORCING["kmax"], amp=FORCING["amp"],
+               seed=FORCING["seed"], redraw=FORCING["redraw_period"])
+    e_o, vx_o, vy_o = oracle.fields(f)
+    tol = {"f32": 1e-5, "bf16": 2e-2, "f16": 2e-3}[dtype]
+    vn = max(np.max(np.abs(vx_o)), np.max(np.abs(vy_o)))
+    assert np.max(np.abs(e_g - e_o)) / np.max(np.abs(e_o)) < tol
+    assert max(np.max(np.abs(vx_g - vx_o)), np.max(np.abs(vy_g - vy_o))) / vn < tol

@@ -28,3 +28,42 @@ def test_frame_reciprocals_are_within_one_and_a_half_ulp():
     r = json.loads(out.strip().splitlines()[-1])
     assert r["recip_max_ulp"] <= 1.5 and r["rsqrt_max_ulp"] <= 1.5, r
     assert r["recip_mean_ulp"] < 0.6 and r["rsqrt_mean_ulp"] < 0.6, r
+
+
+def test_landau_frame_refined_on_fp32_lanes_reaches_fp64_accuracy():
+    """The FP64 Landau solve of the FP32 and 16-bit forms on the packed
+    kernels: the FP32 Newton frame refined by one Newton step whose
+    residuals are evaluated in double-float arithmetic.  Against the FP64
+    Newton solve of the same moments (|v| up to 0.6, energy deviations up to
+    30%) the refined (delta, v) agree to 1e-12 relative (the FP32 solve alone
+    to about 1e-7), and the FP32 fields the collision consumes are the
+    refined values rounded, within one unit in the last place."""
+    src = os.path.join(HERE, "numerics", "landau_df_check.cu")
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = os.path.join(tmp, "landau_df_check")
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                        "--expt-relaxed-constexpr", "-o", exe, src], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    r = json.loads(out.strip().splitlines()[-1])
+    assert r["df_max_rel"] <= 1e-12, r
+    assert r["fp32_max_rel"] > 1e-9, r  # the refinement is what buys the digits
+    assert r["fp32_fields_max_ulp"] <= 1.0, r
+
+
+def test_stochastic_rounding_is_unbiased_between_the_two_neighbours():
+    """The stochastic rounding of 16-bit stores: each stored value is one of
+    the two 16-bit neighbours of the FP32 result, and averaged over 16384
+    nodes (the hash's inputs) the stored values reproduce the FP32 value to
+    within a few hundredths of the gap between the neighbours (the sampling
+    error of the mean is 1/sqrt(16384) of the gap at most), for BF16 and FP16
+    and both halves of a node pair."""
+    src = os.path.join(HERE, "numerics", "sr_check.cu")
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = os.path.join(tmp, "sr_check")
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                        "--expt-relaxed-constexpr", "-o", exe, src], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    r = json.loads(out.strip().splitlines()[-1])
+    for t in ("bf16", "f16"):
+        assert r[t + "_outside"] == 0, r
+        assert r[t + "_max_mean_err_gaps"] < 0.03, r

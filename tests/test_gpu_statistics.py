@@ -11,8 +11,11 @@ driven shell), 2% per shell:
   steps are pinned to the oracle at 1e-12 by the parity tests (the oracle
   itself cannot run 20k steps of a 1024^2 lattice in test time);
 * 1024 x 1024 with the precision workload's band (shell 8..10, tau = 0.51):
-  BF16 and FP16 deviation storage against the FP64 form (FP16 2%, BF16 6%:
-  its 8-bit mantissa costs about 4% on the low-k shells).
+  BF16 and FP16 deviation storage against the FP64 form, 2% per shell, each
+  with its default rounding (BF16 stochastic, FP16 nearest).  BF16 with
+  round-to-nearest misses the bar: its rounding error is a deterministic
+  function of the smooth deviation field and shifts every low-k shell by
+  about 4% (checked below as a property of that rounding, not hidden).
 """
 import os
 
@@ -39,8 +42,8 @@ def _built():
     __graft_entry__.build()
 
 
-def gpu_mean_spectrum(n, tau, forcing, dtype, steps, start, every, nshells):
-    lat = rl.Lattice(n, n, tau, dtype=dtype, forcing=forcing)
+def gpu_mean_spectrum(n, tau, forcing, dtype, steps, start, every, nshells, rounding="default"):
+    lat = rl.Lattice(n, n, tau, dtype=dtype, forcing=forcing, rounding=rounding)
     lat.init_fields()
     lat.step(start)
     acc = np.zeros(nshells)
@@ -81,18 +84,27 @@ def test_time_averaged_spectrum_fp32_vs_fp64_1024():
     assert np.all(rel < 0.02), rel
 
 
-# Measured on GB300 (10k steps, spectra averaged over the second half):
-# FP16 storage stays within 2% per shell; BF16's 8-bit mantissa shifts the
-# low-k spectrum by about 4% (stated per form rather than hidden).
-SPECTRUM_TOL = {"f16": 0.02, "bf16": 0.06}
-
-
-@pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_time_averaged_spectrum_16bit_vs_fp64_1024(dtype):
+@pytest.fixture(scope="module")
+def precision_fp64_spectrum():
     w = workloads.PRECISION_4096
     fz = dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw)
-    n = 1024
-    E64 = gpu_mean_spectrum(n, w.tau, fz, "f64", 10000, 5000, 500, 10)
-    E16 = gpu_mean_spectrum(n, w.tau, fz, dtype, 10000, 5000, 500, 10)
+    return w, fz, gpu_mean_spectrum(1024, w.tau, fz, "f64", 10000, 5000, 500, 10)
+
+
+@pytest.mark.parametrize("dtype,rounding", [("bf16", "default"), ("f16", "default"), ("bf16", "stochastic"),
+                                            ("f16", "stochastic")])
+def test_time_averaged_spectrum_16bit_vs_fp64_1024(precision_fp64_spectrum, dtype, rounding):
+    w, fz, E64 = precision_fp64_spectrum
+    E16 = gpu_mean_spectrum(1024, w.tau, fz, dtype, 10000, 5000, 500, 10, rounding=rounding)
     rel = np.abs(E16[1:8] - E64[1:8]) / E64[1:8]
-    assert np.all(rel < SPECTRUM_TOL[dtype]), rel
+    assert np.all(rel < 0.02), rel
+
+
+def test_nearest_rounding_biases_the_bf16_spectrum(precision_fp64_spectrum):
+    """Why BF16 rounds stochastically by default: with round-to-nearest the
+    time-averaged low-k spectrum is shifted by several percent, beyond the
+    2% bar."""
+    w, fz, E64 = precision_fp64_spectrum
+    E16 = gpu_mean_spectrum(1024, w.tau, fz, "bf16", 10000, 5000, 500, 10, rounding="nearest")
+    rel = (E16[1:8] - E64[1:8]) / E64[1:8]
+    assert np.max(np.abs(rel)) > 0.02, rel
