@@ -118,7 +118,9 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
         if constexpr (SM == kStreamCfl1) {
             float a[4];  // columns x0-1 .. x0+2
             row(rowoff[oy + 1], a);
-            pf2 v = pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
+            // a whole-cell shift (weight 1) needs no multiply: 1 * a is a exactly
+            pf2 v = (tx == 0.0 && ty == 0.0) ? pf2(a[ox + 1], a[ox + 2])
+                                              : pf2((float)((1.0 - tx) * (1.0 - ty))) * pf2(a[ox + 1], a[ox + 2]);
             if constexpr (tx != 0.0) v = fmadd(pf2((float)(tx * (1.0 - ty))), pf2(a[ox + 2], a[ox + 3]), v);
             if constexpr (ty != 0.0) {
                 float b[4];

@@ -37,9 +37,9 @@ __device__ __forceinline__ pf2 xmul(pf2 a, pf2 b) { return a * b; }
 __device__ __forceinline__ pf2 xfma(pf2 a, pf2 b, pf2 c) { return fmadd(a, b, c); }
 
 __device__ __forceinline__ pf2 recip(pf2 x) { return pf2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
-__device__ __forceinline__ pf2 fast_recip(pf2 x) { return pf2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+__device__ __forceinline__ pf2 fast_recip(pf2 x) { return pf2(rcp_approx(x.v.x), rcp_approx(x.v.y)); }
 __device__ __forceinline__ pf2 sqrt_(pf2 x) { return pf2(sqrtf(x.v.x), sqrtf(x.v.y)); }
-__device__ __forceinline__ pf2 fast_rsqrt(pf2 x) { return pf2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
+__device__ __forceinline__ pf2 fast_rsqrt(pf2 x) { return pf2(rsqrt_approx(x.v.x), rsqrt_approx(x.v.y)); }
 __device__ __forceinline__ pf2 absval(pf2 x) { return pf2(fabsf(x.v.x), fabsf(x.v.y)); }
 
 // Lane-wise comparison; !mask is true only when the comparison fails in

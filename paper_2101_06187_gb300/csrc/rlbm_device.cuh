@@ -338,10 +338,26 @@ struct Frame {
     TL gamma;
 };
 
+// The hardware's approximate reciprocal and reciprocal square root (PTX
+// rcp.approx.ftz.f32, rsqrt.approx.ftz.f32: one instruction each, a few
+// units in the last place; arguments here are normal, positive numbers, so
+// flushing subnormals changes nothing).  The Landau iteration corrects
+// their error, and the final frame refines them by one Newton step.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <typename T>
 RLBM_HD inline T fast_recip(T x) {
 #ifdef __CUDA_ARCH__
-    if constexpr (std::is_same<T, float>::value) return __fdividef(1.0f, x);
+    if constexpr (std::is_same<T, float>::value) return rcp_approx(x);
 #endif
     return (T)1 / x;
 }
@@ -349,7 +365,7 @@ RLBM_HD inline T fast_recip(T x) {
 template <typename T>
 RLBM_HD inline T fast_rsqrt(T x) {
 #ifdef __CUDA_ARCH__
-    if constexpr (std::is_same<T, float>::value) return rsqrtf(x);
+    if constexpr (std::is_same<T, float>::value) return rsqrt_approx(x);
 #endif
     return (T)1 / std::sqrt(x);
 }
