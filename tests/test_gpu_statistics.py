@@ -108,3 +108,23 @@ def test_nearest_rounding_biases_the_bf16_spectrum(precision_fp64_spectrum):
     E16 = gpu_mean_spectrum(1024, w.tau, fz, "bf16", 10000, 5000, 500, 10, rounding="nearest")
     rel = (E16[1:8] - E64[1:8]) / E64[1:8]
     assert np.max(np.abs(rel)) > 0.02, rel
+
+
+def test_large_workload_compensated_spectrum_fp32_vs_fp64_2048():
+    """The 8192^2 workload's parameters (tau = 0.505, shell 16..18, amplitude
+    2e-6, redraw every 100 steps) on its 2048^2 oracle lattice: the
+    compensated spectrum k^{5/3} E(k), time-averaged over steps 5000..10000
+    and normalised over 1 <= k < 16, of the FP32 form against the FP64 form
+    (whose every 100 steps the parity tests pin to the oracle at 1e-12),
+    2% per shell; the shell energies themselves agree to 2% as well."""
+    from paper_2101_06187_gb300 import analysis
+    w = workloads.LARGE_8192
+    fz = dict(kmin=w.kmin, kmax=w.kmax, amp=w.amp, seed=w.seed, redraw_period=w.redraw)
+    n, nsh = 2048, 17
+    E64 = gpu_mean_spectrum(n, w.tau, fz, "f64", 10000, 5000, 1000, nsh)
+    E32 = gpu_mean_spectrum(n, w.tau, fz, "f32", 10000, 5000, 1000, nsh)
+    c64, c32 = analysis.compensated(E64)[:15], analysis.compensated(E32)[:15]
+    c64, c32 = c64 / c64.mean(), c32 / c32.mean()
+    assert np.all(np.abs(c32 - c64) / c64 < 0.02), (c32, c64)
+    rel = np.abs(E32[1:16] - E64[1:16]) / E64[1:16]
+    assert np.all(rel < 0.02), rel
