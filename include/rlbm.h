@@ -357,6 +357,28 @@ RLBM_API rlbm_status rlbm_moments3d(rlbm_t *h, double *eps, double *vx, double *
 /* Force of the current epoch, host FP64 nx*ny*nz each (any may be NULL). */
 RLBM_API rlbm_status rlbm_get_force3d(rlbm_t *h, double *Fx, double *Fy, double *Fz);
 
+/* Domain decomposition (no counterpart in the paper, which runs one
+ * lattice per process; its step is local in space, so a lattice split into
+ * slabs of rows with halo rows advances exactly like the whole lattice).
+ * A slab is an ordinary lattice of ny_local + 2 H rows whose first and last
+ * H rows are halo copies of the neighbouring slabs' edge rows, refreshed
+ * before every H steps; the periodic pull inside the slab then gives the
+ * interior rows exactly the whole lattice's values.
+ * rlbm_set_force_frame: draw the stirring force (Sec. 5) in the frame of the
+ *   whole nx_global x ny_global lattice, this lattice's node (x, y) being
+ *   the global node (x + x0, y + y0) modulo the global sizes (y0 may be
+ *   negative for halo rows).  The forcing shell must satisfy
+ *   kmax < min(nx_global, ny_global)/2 (RLBM_ERR_ARG otherwise).  Not stored
+ *   in checkpoints.  Synchronises.  RLBM_ERR_STATE for 3D lattices.
+ * rlbm_halo_pack / rlbm_halo_unpack: copy rows [row, row + nrows) of the
+ *   current state, every class with its pitch padding, to / from the
+ *   caller's device buffer d_buf of nclasses * nrows * pitch elements of the
+ *   storage type, laid out [class][row][pitch] (async on the handle's
+ *   stream; RLBM_ERR_ARG for rows outside the lattice). */
+RLBM_API rlbm_status rlbm_set_force_frame(rlbm_t *h, int nx_global, int ny_global, int x0, int y0);
+RLBM_API rlbm_status rlbm_halo_pack(rlbm_t *h, int row, int nrows, void *d_buf);
+RLBM_API rlbm_status rlbm_halo_unpack(rlbm_t *h, int row, int nrows, const void *d_buf);
+
 /* Time every launch configuration of the fused step (kernel variant and
  * thread-block shape) for `reps` launches each (reps < 1: 20) on the
  * handle's lattice and keep the fastest per lattice step (a two-step launch

@@ -44,7 +44,7 @@ EXPORTS = (
     "rlbm_batch_synchronize", "rlbm_batch_last_error", "rlbm_batch_destroy", "rlbm_filtered_velocity",
     "rlbm_spectrum_sample", "rlbm_spectrum_stats", "rlbm_spectrum_reset", "rlbm_create3d", "rlbm_init_fields3d",
     "rlbm_moments3d", "rlbm_get_force3d", "rlbm_checkpoint_size", "rlbm_checkpoint_save", "rlbm_checkpoint_load",
-    "rlbm_set_launch", "rlbm_create_batch",
+    "rlbm_set_launch", "rlbm_create_batch", "rlbm_set_force_frame", "rlbm_halo_pack", "rlbm_halo_unpack",
 )
 
 
@@ -150,6 +150,11 @@ def _load():
                                           ctypes.POINTER(ctypes.c_void_p)]
         lib.rlbm_create_batch.argtypes = lib.rlbm_batch_create.argtypes
         lib.rlbm_create_batch.restype = ctypes.c_int
+        lib.rlbm_set_force_frame.argtypes = [h, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.rlbm_halo_pack.argtypes = [h, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        lib.rlbm_halo_unpack.argtypes = [h, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        for name in ("rlbm_set_force_frame", "rlbm_halo_pack", "rlbm_halo_unpack"):
+            getattr(lib, name).restype = ctypes.c_int
         lib.rlbm_batch_init_fields.argtypes = [b, ctypes.c_int, _dp, _dp, _dp]
         lib.rlbm_batch_step.argtypes = [b, ctypes.c_int]
         lib.rlbm_batch_moments.argtypes = [b, ctypes.c_int, _dp, _dp, _dp, _dp]
@@ -382,6 +387,19 @@ def rlbm_moments_static(stencil: int, dtype: int, d_q: int, nx: int, ny: int, pi
     _check(None, st, "rlbm_moments_static")
 
 
+def rlbm_set_force_frame(h, nx_global: int, ny_global: int, x0: int, y0: int):
+    _check(h, _load().rlbm_set_force_frame(h, int(nx_global), int(ny_global), int(x0), int(y0)),
+           "rlbm_set_force_frame")
+
+
+def rlbm_halo_pack(h, row: int, nrows: int, d_buf: int):
+    _check(h, _load().rlbm_halo_pack(h, int(row), int(nrows), d_buf), "rlbm_halo_pack")
+
+
+def rlbm_halo_unpack(h, row: int, nrows: int, d_buf: int):
+    _check(h, _load().rlbm_halo_unpack(h, int(row), int(nrows), d_buf), "rlbm_halo_unpack")
+
+
 def rlbm_synchronize(h):
     _check(h, _load().rlbm_synchronize(h), "rlbm_synchronize")
 
@@ -584,6 +602,17 @@ class Lattice:
                 raise ValueError("moments(out=...) needs C-contiguous FP64 arrays of the lattice's size")
         rlbm_moments(self.handle, eps, vx, vy, tot)
         return eps, vx, vy, tot
+
+    def set_force_frame(self, nx_global: int, ny_global: int, x0: int, y0: int):
+        """Draw the stirring force in the frame of a larger lattice (a slab of
+        a decomposed lattice; see slab.py)."""
+        rlbm_set_force_frame(self.handle, nx_global, ny_global, x0, y0)
+
+    def halo_pack(self, row: int, nrows: int, d_buf: int):
+        rlbm_halo_pack(self.handle, row, nrows, d_buf)
+
+    def halo_unpack(self, row: int, nrows: int, d_buf: int):
+        rlbm_halo_unpack(self.handle, row, nrows, d_buf)
 
     def moments_device(self, eps=None, vx=None, vy=None, totals=None):
         ptr = lambda t: 0 if t is None else int(t.data_ptr())

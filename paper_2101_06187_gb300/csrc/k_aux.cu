@@ -202,38 +202,44 @@ cudaError_t launch_twiddles(int dtype, void *tw, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Per-mode phase tables: X[m][x] = e^{2 pi i kx_m x / nx} and
-// Y[m][y] = e^{2 pi i ky_m y / ny}, read from the twiddle tables with the
-// phase index reduced in integers ((k x) mod n), so the argument is exact at
-// any lattice size.  Built once per lattice.
+// Per-mode phase tables: X[m][x] = e^{2 pi i kx_m (x + x0) / nxg} and
+// Y[m][y] = e^{2 pi i ky_m (y + y0) / nyg}, read from the twiddle tables of
+// the global sizes nxg, nyg with the phase index reduced in integers
+// ((k (x + x0)) mod nxg), so the argument is exact at any lattice size.  A
+// whole lattice has x0 = y0 = 0 and nxg, nyg its own sizes; a slab of a
+// decomposed lattice its global offset (y0 may be negative: halo rows) and
+// the global sizes.  Built once per lattice (or force frame).
 template <typename TC>
 __global__ void k_mode_tables(C2<TC> *X, C2<TC> *Y, const Mode *__restrict__ modes, int nmodes,
-                              const C2<TC> *__restrict__ twx, const C2<TC> *__restrict__ twy, int nx, int ny) {
+                              const C2<TC> *__restrict__ twx, const C2<TC> *__restrict__ twy, int nx, int ny,
+                              int nxg, int nyg, int x0, int y0) {
     const int m = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= nmodes) return;
     if (i < nx) {
-        const long long k = ((long long)modes[m].kx % nx + nx) % nx;
-        X[(long long)m * nx + i] = twx[(k * i) % nx];
+        const long long k = ((long long)modes[m].kx % nxg + nxg) % nxg;
+        const long long g = (((long long)i + x0) % nxg + nxg) % nxg;
+        X[(long long)m * nx + i] = twx[(k * g) % nxg];
     }
     if (i < ny) {
-        const long long k = ((long long)modes[m].ky % ny + ny) % ny;
-        Y[(long long)m * ny + i] = twy[(k * i) % ny];
+        const long long k = ((long long)modes[m].ky % nyg + nyg) % nyg;
+        const long long g = (((long long)i + y0) % nyg + nyg) % nyg;
+        Y[(long long)m * ny + i] = twy[(k * g) % nyg];
     }
 }
 
 cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, int nmodes, const void *twx,
-                               const void *twy, int nx, int ny, cudaStream_t s) {
+                               const void *twy, int nx, int ny, int nxg, int nyg, int x0, int y0, cudaStream_t s) {
     if (nmodes <= 0) return cudaSuccess;
     const dim3 g((std::max(nx, ny) + 255) / 256, nmodes, 1);
     if (dtype == RLBM_F64)
         k_mode_tables<double><<<g, 256, 0, s>>>(static_cast<C2<double> *>(X), static_cast<C2<double> *>(Y), modes,
                                                 nmodes, static_cast<const C2<double> *>(twx),
-                                                static_cast<const C2<double> *>(twy), nx, ny);
+                                                static_cast<const C2<double> *>(twy), nx, ny, nxg, nyg, x0, y0);
     else
         k_mode_tables<float><<<g, 256, 0, s>>>(static_cast<C2<float> *>(X), static_cast<C2<float> *>(Y), modes,
                                                nmodes, static_cast<const C2<float> *>(twx),
-                                               static_cast<const C2<float> *>(twy), nx, ny);
+                                               static_cast<const C2<float> *>(twy), nx, ny, nxg, nyg, x0, y0);
     return cudaGetLastError();
 }
 
@@ -262,22 +268,40 @@ __global__ void k_force_rows(C4<TC> *G, const C4<TC> *__restrict__ coef, const i
     G[(long long)j * nx + x] = C4<TC>{xr, xi, yr, yi};
 }
 
+// One thread per column x and SYNTH_ROWS consecutive rows: the row sums
+// G_j(x) are read once per run and reused for every row of the strip.
+constexpr int SYNTH_ROWS = 8;
+
 template <typename TC>
 __global__ void k_synth_force(TC *F, const C4<TC> *__restrict__ G, const int *__restrict__ run_start, int nruns,
                               const C2<TC> *__restrict__ Y, StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= p.nx || y >= p.ny) return;
-    TC fx = 0, fy = 0;
+    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * SYNTH_ROWS;
+    if (x >= p.nx || y0 >= p.ny) return;
+    const int rows = min(SYNTH_ROWS, p.ny - y0);
+    TC fx[SYNTH_ROWS], fy[SYNTH_ROWS];
+#pragma unroll
+    for (int r = 0; r < SYNTH_ROWS; ++r) fx[r] = fy[r] = 0;
     for (int j = 0; j < nruns; ++j) {
         const C4<TC> g = G[(long long)j * p.nx + x];
-        const C2<TC> b = Y[(long long)run_start[j] * p.ny + y];
-        fx += g.ax * b.c - g.bx * b.s;
-        fy += g.ay * b.c - g.by * b.s;
+        const C2<TC> *Yj = Y + (long long)run_start[j] * p.ny + y0;
+#pragma unroll
+        for (int r = 0; r < SYNTH_ROWS; ++r) {
+            if (r < rows) {
+                const C2<TC> b = Yj[r];
+                fx[r] += g.ax * b.c - g.bx * b.s;
+                fy[r] += g.ay * b.c - g.by * b.s;
+            }
+        }
     }
-    const long long n = (long long)y * p.pitch + x;
-    F[n] = fx;
-    F[p.plane + n] = fy;
+#pragma unroll
+    for (int r = 0; r < SYNTH_ROWS; ++r) {
+        if (r < rows) {
+            const long long n = (long long)(y0 + r) * p.pitch + x;
+            F[n] = fx[r];
+            F[p.plane + n] = fy[r];
+        }
+    }
 }
 
 cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const int *run_start, int nruns,
@@ -285,7 +309,7 @@ cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes,
     if (nmodes <= 0 || nruns <= 0) return cudaSuccess;
     const dim3 gr((p.nx + 255) / 256, nruns, 1);
     const dim3 block(32, 8, 1);
-    const dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, 1);
+    const dim3 grid((p.nx + 31) / 32, (p.ny + 8 * SYNTH_ROWS - 1) / (8 * SYNTH_ROWS), 1);
     if (dtype == RLBM_F64) {
         k_force_rows<double><<<gr, 256, 0, s>>>(static_cast<C4<double> *>(G), static_cast<const C4<double> *>(coef),
                                                 run_start, static_cast<const C2<double> *>(X), p.nx);

@@ -414,8 +414,8 @@ void rlbm_destroy(rlbm_t *h) {
     dev_free(h, h->q[0], q_bytes(h));
     dev_free(h, h->q[1], q_bytes(h));
     if (h->F) dev_free(h, h->F, F_bytes(h));
-    if (h->twx) dev_free(h, h->twx, tw_bytes(h, h->nx));
-    if (h->twy) dev_free(h, h->twy, tw_bytes(h, h->ny));
+    if (h->twx) dev_free(h, h->twx, tw_bytes(h, h->fnx));
+    if (h->twy) dev_free(h, h->twy, tw_bytes(h, h->fny));
     if (h->coef) dev_free(h, h->coef, coef_bytes(h));
     if (h->twz) dev_free(h, h->twz, tw_bytes(h, h->nz));
     if (h->tabz) dev_free(h, h->tabz, tw_bytes(h, h->nz) * h->nmodes);
@@ -629,6 +629,8 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     bool ok = h->q[0] && h->q[1] && h->fields && h->partials && h->totals && h->bad && h->errword;
     if (forced) {
         h->F = dev_alloc(h, F_bytes(h));
+        h->fnx = nx;
+        h->fny = ny;
         h->twx = dev_alloc(h, tw_bytes(h, nx));
         h->twy = dev_alloc(h, tw_bytes(h, ny));
         h->coef = dev_alloc(h, coef_bytes(h));
@@ -679,7 +681,8 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
         if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twx, nx, h->stream);
         if (e == cudaSuccess) e = launch_twiddles(o.dtype, h->twy, ny, h->stream);
         if (e == cudaSuccess)
-            e = launch_mode_tables(o.dtype, h->tabx, h->taby, h->modes, h->nmodes, h->twx, h->twy, nx, ny, h->stream);
+            e = launch_mode_tables(o.dtype, h->tabx, h->taby, h->modes, h->nmodes, h->twx, h->twy, nx, ny, nx, ny, 0,
+                                   0, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) st = RLBM_ERR_CUDA;
     }
@@ -1091,6 +1094,65 @@ rlbm_status rlbm_get_force(rlbm_t *h, double *Fx, double *Fy) {
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     }
     return RLBM_OK;
+}
+
+rlbm_status rlbm_set_force_frame(rlbm_t *h, int nx_global, int ny_global, int x0, int y0) {
+    CHECK_HANDLE(h);
+    if (h->d3) return fail(h, RLBM_ERR_STATE, "3D lattice: no force frame");
+    if (nx_global < 4 || ny_global < 4 || x0 <= -nx_global || x0 >= nx_global || y0 <= -ny_global ||
+        y0 >= ny_global)
+        return fail(h, RLBM_ERR_ARG, "force frame %dx%d at (%d, %d) is not valid", nx_global, ny_global, x0, y0);
+    if (h->forced && !(h->forcing.kmax < std::min(nx_global, ny_global) / 2))
+        return fail(h, RLBM_ERR_ARG, "forcing shell kmax %d needs a frame wider than %d", h->forcing.kmax,
+                    2 * h->forcing.kmax);
+    if (!h->forced) return RLBM_OK;  // nothing is drawn
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (nx_global != h->fnx || ny_global != h->fny) {
+        void *tx = dev_alloc(h, tw_bytes(h, nx_global)), *ty = dev_alloc(h, tw_bytes(h, ny_global));
+        if (!tx || !ty) {
+            if (tx) dev_free(h, tx, tw_bytes(h, nx_global));
+            if (ty) dev_free(h, ty, tw_bytes(h, ny_global));
+            return fail(h, RLBM_ERR_ALLOC, "force frame twiddles");
+        }
+        dev_free(h, h->twx, tw_bytes(h, h->fnx));
+        dev_free(h, h->twy, tw_bytes(h, h->fny));
+        h->twx = tx;
+        h->twy = ty;
+        h->fnx = nx_global;
+        h->fny = ny_global;
+        CUDA_TRY(h, launch_twiddles(h->opts.dtype, h->twx, nx_global, h->stream));
+        CUDA_TRY(h, launch_twiddles(h->opts.dtype, h->twy, ny_global, h->stream));
+    }
+    h->fx0 = x0;
+    h->fy0 = y0;
+    CUDA_TRY(h, launch_mode_tables(h->opts.dtype, h->tabx, h->taby, h->modes, h->nmodes, h->twx, h->twy, h->nx, h->ny,
+                                   h->fnx, h->fny, x0, y0, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->force_epoch = -1;  // the next step synthesises the force in the new frame
+    return RLBM_OK;
+}
+
+// Rows [row, row + nrows) of every class plane, with their pitch padding:
+// one 2D copy of ncls blocks of nrows * pitch elements.
+static rlbm_status halo_copy(rlbm_t *h, int row, int nrows, void *d_buf, bool pack) {
+    CHECK_HANDLE(h);
+    if (h->d3) return fail(h, RLBM_ERR_STATE, "3D lattice: no halo rows");
+    if (!d_buf || nrows < 1 || row < 0 || row + nrows > h->ny)
+        return fail(h, RLBM_ERR_ARG, "halo rows [%d, %d) outside 0..%d", row, row + nrows, h->ny);
+    const size_t es = storage_bytes(h->opts.dtype);
+    const size_t width = (size_t)nrows * h->pitch * es, plane = (size_t)h->ny * h->pitch * es;
+    char *state = static_cast<char *>(h->q[h->cur]) + (size_t)row * h->pitch * es;
+    if (pack)
+        CUDA_TRY(h, cudaMemcpy2DAsync(d_buf, width, state, plane, width, h->ncls, cudaMemcpyDeviceToDevice, h->stream));
+    else
+        CUDA_TRY(h, cudaMemcpy2DAsync(state, plane, d_buf, width, width, h->ncls, cudaMemcpyDeviceToDevice, h->stream));
+    return RLBM_OK;
+}
+
+rlbm_status rlbm_halo_pack(rlbm_t *h, int row, int nrows, void *d_buf) { return halo_copy(h, row, nrows, d_buf, true); }
+
+rlbm_status rlbm_halo_unpack(rlbm_t *h, int row, int nrows, const void *d_buf) {
+    return halo_copy(h, row, nrows, const_cast<void *>(d_buf), false);
 }
 
 rlbm_status rlbm_get_info(rlbm_t *h, rlbm_info_t *info) {

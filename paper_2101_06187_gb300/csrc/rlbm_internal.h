@@ -127,7 +127,7 @@ cudaError_t launch_twiddles(int dtype, void *tw, int n, cudaStream_t s);
 cudaError_t launch_draw_modes(int dtype, Mode *modes, void *coef, int nmodes, double amp, unsigned long long seed,
                               unsigned long long epoch, cudaStream_t s);
 cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, int nmodes, const void *twx,
-                               const void *twy, int nx, int ny, cudaStream_t s);
+                               const void *twy, int nx, int ny, int nxg, int nyg, int x0, int y0, cudaStream_t s);
 // F from the mode coefficients, separably: per run of equal ky (ky_start,
 // nky runs) the row sums G over the x tables X, then per node the sum over
 // runs with the run's y table (Y of its first mode); G is [nky][nx] x 4.
@@ -179,7 +179,8 @@ struct rlbm {
     void *q[2] = {nullptr, nullptr};  // ping-pong population buffers [17][ny][pitch]
     int cur = 0;                      // index of the current (post-collision) state
     void *F = nullptr;                // force field [2][ny][pitch] (compute type)
-    void *twx = nullptr, *twy = nullptr;
+    void *twx = nullptr, *twy = nullptr;  // twiddles of the force frame's global sizes [fnx], [fny]
+    int fnx = 0, fny = 0, fx0 = 0, fy0 = 0;  // force frame: global sizes and this lattice's offset in it
     void *tabx = nullptr, *taby = nullptr;  // per-mode phase tables [nmodes][nx], [nmodes][ny]
     rlbk::Mode *modes = nullptr;
     void *coef = nullptr;             // per-mode synthesis coefficients (ax, bx, ay, by) in the compute type

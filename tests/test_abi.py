@@ -136,6 +136,10 @@ def test_batch_create_rejects_invalid_members(lib):
     assert lib.rlbm_batch_create(0, arr, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG
     assert lib.rlbm_batch_create(1, None, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG
     assert lib.rlbm_create_batch(2, arr, None, ctypes.byref(out)) == rl.RLBM_ERR_ARG  # the same call, other name
+    # decomposition calls refuse a missing handle
+    assert lib.rlbm_set_force_frame(None, 64, 64, 0, 0) == rl.RLBM_ERR_ARG
+    assert lib.rlbm_halo_pack(None, 0, 1, None) == rl.RLBM_ERR_ARG
+    assert lib.rlbm_halo_unpack(None, 0, 1, None) == rl.RLBM_ERR_ARG
     # ensemble bodies: vector, packed or two-step; the lane bodies need FP32 compute, FP32 Landau, nx even
     for field, value, kernel in ((None, None, "tma"), (None, None, "gather"), ("dtype", rl.DTYPES["f64"], "fused2"),
                                  ("landau", rl.LANDAU["fp64"], "packed"), ("cfl", 0.5, "fused2")):
