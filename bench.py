@@ -535,7 +535,7 @@ def cpu_oracle_glups(oracle, w, n, budget_s):
                    % (n, rows, nsteps)), threads
 
 
-def e2e_glups(rl, w, n, form, landau, reps=3, steps_per_call=100):
+def e2e_glups(rl, w, n, form, landau, reps=5, steps_per_call=100):
     """Through the public API with host buffers in pinned memory: upload the
     initial fields, advance steps_per_call steps, read the fields back."""
     import torch
