@@ -162,7 +162,7 @@ typedef struct {
     int kernel;           /* rlbm_kernel (default RLBM_KERNEL_AUTO) */
     int use_graphs;       /* 1: replay the step loop as CUDA graphs (default 1) */
     double eps0;          /* reference energy density of the deviation (default 1) */
-    double scale;         /* s of the deviation; 0 = default: 1 (F64/F32), 2^-6 (16-bit) */
+    double scale;         /* s of the deviation; 0 = default: 1 (F64/F32, which accept only 1), 2^-6 (16-bit) */
     void *stream;         /* cudaStream_t the handle works on; NULL = legacy default stream */
     int device;           /* CUDA device ordinal; -1 = current device (default) */
     rlbm_alloc_fn alloc;  /* optional device allocator */

@@ -177,7 +177,7 @@ __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__re
         pull_pair<TS, I, false, SM>(qin, p, plane, rows, (I)x0, (I)xl, (I)xr, q);
         pf2 Fx, Fy;
         force_pair<I, FORCED>(F, plane, rows[1] + (I)x0, Fx, Fy);
-        collide_node<pf2, pf2, FORCED, DFL>(q, Fx, Fy, p);
+        collide_node<pf2, pf2, FORCED, DFL, std::is_same<TS, float>::value>(q, Fx, Fy, p);
         const unsigned seed =
             rounds_sr<TS>(p) ? sr_pair_seed((unsigned)y * (unsigned)p.nx + (unsigned)x0, q[0].v.x, q[0].v.y) : 0u;
         static_for<0, NC>([&](auto C) {
@@ -199,7 +199,7 @@ __device__ __forceinline__ void fused2_tile(const TS *__restrict__ qin, TS *__re
         const I n0 = (I)y * (I)p.pitch + (I)x0;
         pf2 Fx, Fy;
         force_pair<I, FORCED>(F, plane, n0, Fx, Fy);
-        collide_node<pf2, pf2, FORCED, DFL>(q, Fx, Fy, p);
+        collide_node<pf2, pf2, FORCED, DFL, std::is_same<TS, float>::value>(q, Fx, Fy, p);
         const unsigned seed =
             rounds_sr<TS>(p) ? sr_pair_seed((unsigned)y * (unsigned)p.nx + (unsigned)x0, q[0].v.x, q[0].v.y) : 0u;
         static_for<0, NC>([&](auto C) {

@@ -211,7 +211,8 @@ __device__ __forceinline__ void step_pair(const TS *__restrict__ qin, TS *__rest
         Fx = pf2(fx[0], fx[1]);
         Fy = pf2(fy[0], fy[1]);
     }
-    collide_node<pf2, pf2, FORCED, DFL>(q, Fx, Fy, p);
+    // FP32 storage keeps the deviation unscaled (s = 1)
+    collide_node<pf2, pf2, FORCED, DFL, std::is_same<TS, float>::value>(q, Fx, Fy, p);
 
     const unsigned seed =
         rounds_sr<TS>(p) ? sr_pair_seed((unsigned)y * (unsigned)p.nx + (unsigned)x0, q[0].v.x, q[0].v.y) : 0u;

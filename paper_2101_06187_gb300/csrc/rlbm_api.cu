@@ -493,6 +493,8 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (!(o.eps0 > 0.0) || !isfinite(o.eps0)) return RLBM_ERR_ARG;
     if (o.scale == 0.0) o.scale = (o.dtype == RLBM_BF16 || o.dtype == RLBM_F16) ? 1.0 / 64.0 : 1.0;
     if (!(o.scale > 0.0) || !isfinite(o.scale)) return RLBM_ERR_ARG;
+    // FP32 and FP64 storage keep the deviation unscaled (a scale buys floating point nothing)
+    if ((o.dtype == RLBM_F32 || o.dtype == RLBM_F64) && o.scale != 1.0) return RLBM_ERR_ARG;
     if (o.alloc && !o.free) return RLBM_ERR_ARG;
     if (o.cfl == 0.0) o.cfl = 1.0;
     if (o.dt == 0.0) o.dt = 1.0;

@@ -277,8 +277,14 @@ RLBM_HD inline void moments_add_pair(MomentSums<TC> &a, TC qp, TC qn) {
     }
 }
 
-template <typename TC>
+// UNIT: the deviation scale s is 1 (FP32 and FP64 storage), so the sums
+// are the moments and the multiplies are skipped (multiplying by 1 is exact:
+// the results are the same bits either way).
+template <typename TC, bool UNIT = false>
 RLBM_HD inline NodeMoments<TC> moments_end(const MomentSums<TC> &a, TC s) {
+    if constexpr (UNIT) {
+        return NodeMoments<TC>{a.e, a.mx, a.my, a.sxx, a.sxy, a.syy, a.qxxx, a.qxxy, a.qxyy, a.qyyy};
+    }
     NodeMoments<TC> m;
     m.dE = s * a.e;
     m.Mx = s * a.mx;
@@ -293,14 +299,14 @@ RLBM_HD inline NodeMoments<TC> moments_end(const MomentSums<TC> &a, TC s) {
     return m;
 }
 
-template <typename TC>
+template <typename TC, bool UNIT = false>
 RLBM_HD inline NodeMoments<TC> node_moments(const TC (&q)[NC], TC s) {
     MomentSums<TC> a = moments_begin<TC>(q[0]);
     static_for<0, NPAIR>([&](auto K) {
         constexpr int k = decltype(K)::value;
         moments_add_pair<k, TC>(a, q[pair_pos(k)], q[pair_neg(k)]);
     });
-    return moments_end<TC>(a, s);
+    return moments_end<TC, UNIT>(a, s);
 }
 
 template <typename T>
@@ -409,13 +415,15 @@ RLBM_HD inline Frame<TL> landau_solve(TL eps0, TL dE, TL Mx, TL My, TL dSxx, TL 
     const TL tol = dbl ? (TL)4e-16 : (TL)1e-7;
     TL vx, vy;
     const TL nMx = (TL)0 - Mx, nMy = (TL)0 - My, nSxy = (TL)0 - dSxy;
+    // the delta-independent products of the 2 x 2 solve, formed once
+    const TL nSxy2 = nSxy * dSxy, nSxyMy = nSxy * My, nSxyMx = nSxy * Mx;
     auto velocity = [&](TL d, bool exact) {
         const TL a = a0 - d;
         const TL axx = a + dSxx, ayy = a + dSyy;
-        const TL det = fmadd(axx, ayy, nSxy * dSxy);
+        const TL det = fmadd(axx, ayy, nSxy2);
         const TL inv_det = exact ? frame_recip(det) : fast_recip(det);
-        vx = fmadd(ayy, Mx, nSxy * My) * inv_det;
-        vy = fmadd(axx, My, nSxy * Mx) * inv_det;
+        vx = fmadd(ayy, Mx, nSxyMy) * inv_det;
+        vy = fmadd(axx, My, nSxyMx) * inv_det;
     };
     velocity((TL)0, false);
     const TL m1 = fmadd(Mx, vx, My * vy);
@@ -589,12 +597,12 @@ __device__ __forceinline__ void landau_refine_df(TL alpha_hi, TL alpha_lo, TL ep
 // Coefficients of the per-class update of one node (below).
 template <typename TC>
 struct CollideCoef {
-    TC K0, Kxx, Kxy, Kyy, o1, no3, G1, om, a0, vx, vy, Fx, Fy;
+    TC K0, Kxx, Kxy, Kyy, o1, no3, G1, om, nom, a0, vx, vy, Fx, Fy;
 };
 
 // Frame and update coefficients of a node from its moments.  DFL: refine
 // the FP32 frame to FP64 accuracy (landau_refine_df; FP32 lanes only).
-template <typename TC, typename TL, bool FORCED, bool DFL = false>
+template <typename TC, typename TL, bool FORCED, bool DFL = false, bool UNIT = false>
 RLBM_HD inline Frame<TL> collide_coef(const NodeMoments<TC> &m, TC Fx, TC Fy, const StepParams &p,
                                       CollideCoef<TC> &k) {
     TL delta;
@@ -608,10 +616,15 @@ RLBM_HD inline Frame<TL> collide_coef(const NodeMoments<TC> &m, TC Fx, TC Fy, co
 #endif
     }
     const TC inv_s = par_inv_scale<TC>(p);
+    // times 1/s, skipped where s = 1 (exact either way)
+    auto unscale = [&](TC x) {
+        if constexpr (UNIT) return x;
+        else return x * inv_s;
+    };
     const TL eg2 = fr.eps * fr.g2;
-    const TC P0 = (TC)(fmadd((TL)(-2) * eg2, fr.v2, fr.ddelta_eps)) * inv_s;
-    const TC P1 = (TC)((TL)4 * eg2) * inv_s;
-    const TC P2 = (TC)((TL)10 * eg2) * inv_s;
+    const TC P0 = unscale((TC)(fmadd((TL)(-2) * eg2, fr.v2, fr.ddelta_eps)));
+    const TC P1 = unscale((TC)((TL)4 * eg2));
+    const TC P2 = unscale((TC)((TL)10 * eg2));
     const TC vx = (TC)fr.vx, vy = (TC)fr.vy;
     // relaxation rate: 1/tau, or in eta/s mode T(eps) dt / (5 eta/s)
     TL inv_tau = par_inv_tau<TL>(p);
@@ -625,7 +638,7 @@ RLBM_HD inline Frame<TL> collide_coef(const NodeMoments<TC> &m, TC Fx, TC Fy, co
     TC G1 = 0;
     if constexpr (FORCED) {
         const TC E = par_eps0<TC>(p) + m.dE;
-        const TC c6 = (TC)(-6.0) * inv_s;
+        const TC c6 = unscale((TC)(-6.0));
         const TC G0 = c6 * (TC)0.25 * fmadd(Fx, m.Mx, Fy * m.My);
         G1 = c6 * (TC)(-0.5) * E;
         const TC G3 = c6 * (TC)(-2.5);
@@ -649,6 +662,7 @@ RLBM_HD inline Frame<TL> collide_coef(const NodeMoments<TC> &m, TC Fx, TC Fy, co
     k.no3 = no3;
     k.G1 = G1;
     k.om = om;
+    k.nom = (TC)0 - om;
     k.a0 = (TC)1 - om;
     k.vx = vx;
     k.vy = vy;
@@ -663,7 +677,9 @@ RLBM_HD inline TC collide_rest(TC q0, const CollideCoef<TC> &k) {
     return fmadd(q0, k.a0, k.K0);
 }
 
-// Opposite pair k: (q_c, q_-c) -> updated values.
+// Opposite pair k: (q_c, q_-c) -> updated values.  The relaxation factors
+// a0 +- om xi are single fused multiply-adds; components of c equal to 1
+// (the axis classes) enter without a multiply.
 template <int kp, typename TC, bool FORCED>
 RLBM_HD inline void collide_pair(TC &qp, TC &qn, const CollideCoef<TC> &k) {
     constexpr int c = pair_pos(kp);
@@ -672,29 +688,41 @@ RLBM_HD inline void collide_pair(TC &qp, TC &qn, const CollideCoef<TC> &k) {
     [[maybe_unused]] TC Fc = 0;
     TC even = k.K0;
     if constexpr (cx != 0.0) {
-        xi = (TC)cx * k.vx;
-        even = fmadd((TC)(cx * cx), k.Kxx, even);
-        if constexpr (FORCED) Fc = (TC)cx * k.Fx;
+        if constexpr (cx == 1.0) {
+            xi = k.vx;
+            even = even + k.Kxx;
+            if constexpr (FORCED) Fc = k.Fx;
+        } else {
+            xi = (TC)cx * k.vx;
+            even = fmadd((TC)(cx * cx), k.Kxx, even);
+            if constexpr (FORCED) Fc = (TC)cx * k.Fx;
+        }
     }
     if constexpr (cy != 0.0) {
-        xi = fmadd((TC)cy, k.vy, xi);
-        even = fmadd((TC)(cy * cy), k.Kyy, even);
-        if constexpr (FORCED) Fc = fmadd((TC)cy, k.Fy, Fc);
+        if constexpr (cy == 1.0 && cx == 0.0) {
+            xi = k.vy;
+            even = even + k.Kyy;
+            if constexpr (FORCED) Fc = k.Fy;
+        } else {
+            xi = fmadd((TC)cy, k.vy, xi);
+            even = fmadd((TC)(cy * cy), k.Kyy, even);
+            if constexpr (FORCED) Fc = fmadd((TC)cy, k.Fy, Fc);
+        }
     }
     if constexpr (cx != 0.0 && cy != 0.0) even = fmadd((TC)(cx * cy), k.Kxy, even);
     TC odd = xi * fmadd(k.no3, xi * xi, k.o1);
     if constexpr (FORCED) odd = fmadd(k.G1, Fc, odd);
-    const TC oxi = k.om * xi;
+    const TC ap = fmadd(k.om, xi, k.a0), an = fmadd(k.nom, xi, k.a0);
     const TC p0 = qp, n0 = qn;
-    qp = fmadd(p0, k.a0 + oxi, even + odd);
-    qn = fmadd(n0, k.a0 - oxi, even - odd);
+    qp = fmadd(p0, ap, even + odd);
+    qn = fmadd(n0, an, even - odd);
 }
 
-template <typename TC, typename TL, bool FORCED, bool DFL = false>
+template <typename TC, typename TL, bool FORCED, bool DFL = false, bool UNIT = false>
 RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
-    const NodeMoments<TC> m = node_moments<TC>(q, par_scale<TC>(p));
+    const NodeMoments<TC> m = node_moments<TC, UNIT>(q, par_scale<TC>(p));
     CollideCoef<TC> k;
-    const Frame<TL> fr = collide_coef<TC, TL, FORCED, DFL>(m, Fx, Fy, p, k);
+    const Frame<TL> fr = collide_coef<TC, TL, FORCED, DFL, UNIT>(m, Fx, Fy, p, k);
     q[0] = collide_rest<TC>(q[0], k);
     static_for<0, NPAIR>([&](auto K) {
         constexpr int kp = decltype(K)::value;

@@ -74,6 +74,11 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     o.scale = -1.0
     assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
     o = rl.rlbm_opts_default()
+    o.scale = 2.0   # FP32 and FP64 storage keep the deviation unscaled
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
+    o.dtype = rl.DTYPES["f64"]
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG
+    o = rl.rlbm_opts_default()
     o.kernel = rl.KERNELS["vec"]
     assert create(37, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # vector kernel needs nx % 4 == 0
     o = rl.rlbm_opts_default()
