@@ -88,9 +88,14 @@ typedef enum { RLBM_STENCIL_SPH26_SLAB = 0, RLBM_STENCIL_RING8_2D = 1 } rlbm_ste
 typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16 = 2, RLBM_F16 = 3 } rlbm_dtype;
 
 /* Precision of the per-node Landau-frame solve in the fused step of the
- * F32/16-bit forms (the F64 form always solves in FP64; rlbm_moments always
- * solves in FP64).  The solve is a Newton iteration on the small deviation
- * delta = E - eps, so FP32 keeps full FP32 accuracy of eps and v. */
+ * F32/16-bit forms (the F64 form always solves in FP64).  The solve is a
+ * Newton iteration on the small deviation delta = E - eps, so FP32 keeps
+ * full FP32 accuracy of eps and v.  RLBM_LANDAU_FP64 gives an FP64-accurate
+ * frame: the FP64 Newton solve on the one-node-per-thread kernels, the FP32
+ * frame refined by one double-float Newton step (residuals carried as pairs
+ * of floats, within about 1e-12 of the FP64 solve) on the packed kernels.
+ * rlbm_moments always returns an FP64-accurate frame (the refined one for
+ * the F32/16-bit forms). */
 typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
 
 /* Kernel variant of the fused step.  GATHER: one node per thread.

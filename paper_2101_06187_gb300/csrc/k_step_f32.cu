@@ -9,8 +9,8 @@ cudaError_t launch_step_f32(const LaunchCfg &cfg, int landau, bool forced, const
 }
 cudaError_t launch_moments_f32(int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                                double *vy, double *partials, int *bad, cudaStream_t s) {
-    (void)landau;  // diagnostics always solve the frame in FP64
-    return launch_moments_t<float, float, double>(qin, p, eps, vx, vy, partials, bad, s);
+    (void)landau;  // diagnostics always solve the frame to FP64 accuracy (refined FP32 frame)
+    return launch_moments_t<float, float, float>(qin, p, eps, vx, vy, partials, bad, s);
 }
 cudaError_t launch_batch_f32(const LaunchCfg &cfg, int landau, int grid, const void *runs, int nruns, int ntiles,
                              cudaStream_t s) {

@@ -114,7 +114,11 @@ __global__ void __launch_bounds__(256) k_step_gather(const TS *__restrict__ qin,
 // Moments of the state the next collision sees: eps, v (FP64, compact
 // nx*ny), and per-block FP64 partial sums of (T^00, T^0x, T^0y) for the
 // global conservation totals (warp shuffles, then one partial per block in
-// `partials`, reduced in a fixed order by k_reduce_partials).
+// `partials`, reduced in a fixed order by k_reduce_partials).  The frame is
+// FP64-accurate: TL = double solves it by FP64 Newton; TL = float (the FP32
+// and 16-bit forms, whose moments are FP32 sums) solves it by FP32 Newton
+// refined by one double-float Newton step (landau_refine_df), and forms
+// eps and v from the refined pairs in FP64.
 template <typename TS, typename TC, typename TL, int SM>
 __global__ void __launch_bounds__(256) k_moments(const TS *__restrict__ qin, StepParams p, double *__restrict__ eps,
                                                  double *__restrict__ vx, double *__restrict__ vy,
@@ -126,14 +130,33 @@ __global__ void __launch_bounds__(256) k_moments(const TS *__restrict__ qin, Ste
         TC q[NC];
         gather_node<TS, TC, long long, SM>(qin, p, x, y, q);
         const NodeMoments<TC> m = node_moments<TC>(q, par_scale<TC>(p));
-        const Frame<TL> fr = landau_solve<TL>(par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx, (TL)m.dSxy,
-                                              (TL)m.dSyy);
+        double e64, vx64, vy64;
+        bool ok;
+        if constexpr (std::is_same<TL, float>::value) {
+            float delta;
+            Frame<float> fr = landau_solve<float>(p.eps0_f, m.dE, m.Mx, m.My, m.dSxx, m.dSxy, m.dSyy, 4.0 / 3.0,
+                                                  &delta);
+            FramePairs<float> pr;
+            landau_refine_df<float>(p.alpha_hi_f, p.alpha_lo_f, p.eps0_f, m.dE, m.Mx, m.My, m.dSxx, m.dSxy, m.dSyy,
+                                    delta, fr, &pr);
+            e64 = p.eps0 + ((double)m.dE - ((double)pr.delta_hi + (double)pr.delta_lo));
+            vx64 = (double)pr.vx_hi + (double)pr.vx_lo;
+            vy64 = (double)pr.vy_hi + (double)pr.vy_lo;
+            ok = (fmadd(vx64, vx64, vy64 * vy64) < 1.0) && (e64 > 0.0) && isfinite(e64) && isfinite(vx64) &&
+                 isfinite(vy64);
+        } else {
+            const Frame<TL> fr = landau_solve<TL>(par_eps0<TL>(p), (TL)m.dE, (TL)m.Mx, (TL)m.My, (TL)m.dSxx,
+                                                  (TL)m.dSxy, (TL)m.dSyy);
+            e64 = (double)fr.eps;
+            vx64 = (double)fr.vx;
+            vy64 = (double)fr.vy;
+            ok = (fr.v2 < (TL)1) && (fr.eps > (TL)0) && isfinite((double)fr.eps);
+        }
         const long long n = (long long)y * p.nx + x;
-        const bool ok = (fr.v2 < (TL)1) && (fr.eps > (TL)0) && isfinite((double)fr.eps);
         if (!ok) atomicAdd(bad, 1);
-        if (eps) eps[n] = ok ? (double)fr.eps : __longlong_as_double(0x7ff8000000000000LL);
-        if (vx) vx[n] = ok ? (double)fr.vx : __longlong_as_double(0x7ff8000000000000LL);
-        if (vy) vy[n] = ok ? (double)fr.vy : __longlong_as_double(0x7ff8000000000000LL);
+        if (eps) eps[n] = ok ? e64 : __longlong_as_double(0x7ff8000000000000LL);
+        if (vx) vx[n] = ok ? vx64 : __longlong_as_double(0x7ff8000000000000LL);
+        if (vy) vy[n] = ok ? vy64 : __longlong_as_double(0x7ff8000000000000LL);
         sE = (double)m.dE;  // eps0 * nodes is added on the host side of the reduction
         sMx = (double)m.Mx;
         sMy = (double)m.My;

@@ -15,10 +15,10 @@ cudaError_t launch_step_h16(int dtype, const LaunchCfg &cfg, int landau, bool fo
 }
 cudaError_t launch_moments_h16(int dtype, int landau, const void *qin, const StepParams &p, double *eps, double *vx,
                                double *vy, double *partials, int *bad, cudaStream_t s) {
-    (void)landau;  // diagnostics always solve the frame in FP64
+    (void)landau;  // diagnostics always solve the frame to FP64 accuracy (refined FP32 frame)
     if (dtype == RLBM_BF16)
-        return launch_moments_t<__nv_bfloat16, float, double>(qin, p, eps, vx, vy, partials, bad, s);
-    return launch_moments_t<__half, float, double>(qin, p, eps, vx, vy, partials, bad, s);
+        return launch_moments_t<__nv_bfloat16, float, float>(qin, p, eps, vx, vy, partials, bad, s);
+    return launch_moments_t<__half, float, float>(qin, p, eps, vx, vy, partials, bad, s);
 }
 cudaError_t launch_batch_h16(int dtype, const LaunchCfg &cfg, int landau, int grid, const void *runs, int nruns,
                              int ntiles, cudaStream_t s) {

@@ -34,6 +34,8 @@ def _make(kind, **kw):
         return rl.Lattice(64, 48, 0.6, dtype="f32", kernel="packed", forcing=FORCING, **kw)
     if kind == "slab-fused2":  # two steps per launch: saves land between launch pairs and on odd steps
         return rl.Lattice(64, 48, 0.6, dtype="f32", kernel="fused2", forcing=FORCING, **kw)
+    if kind == "slab-bf16":  # stochastic rounding of the stores: its draws are a function of the state
+        return rl.Lattice(64, 48, 0.6, dtype="bf16", kernel="fused2", forcing=FORCING, rounding="stochastic", **kw)
     if kind == "ring":
         return rl.Lattice(64, 48, 0.6, dtype="f32", kernel="packed", forcing=FORCING, stencil="ring8", **kw)
     if kind == "ring-fused2":
@@ -47,7 +49,7 @@ def _fields(kind):
     return workloads.random_smooth(64, 48, seed=5)
 
 
-@pytest.mark.parametrize("kind", ["slab", "slab-fused2", "ring", "ring-fused2", "3d"])
+@pytest.mark.parametrize("kind", ["slab", "slab-fused2", "slab-bf16", "ring", "ring-fused2", "3d"])
 def test_resumed_run_is_bitwise_the_uninterrupted_run(kind):
     a = _make(kind)
     a.init_fields(*_fields(kind))

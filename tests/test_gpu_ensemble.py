@@ -199,3 +199,21 @@ def test_bad_member_index_rejected():
     with pytest.raises(rl.RLBMError):
         rl.rlbm_batch_moments(ens.handle, -1, buf, buf, buf, np.empty(3))
     ens.close()
+
+
+def test_stochastic_rounding_members_equal_lone_lattices():
+    """BF16 members rounding their stores stochastically (the random bits
+    are hashed from each member's own node index and state) evolve bit for
+    bit like lone lattices with the same rounding."""
+    ens = rl.Ensemble(RUNS, dtype="bf16", kernel="fused2", rounding="stochastic")
+    for k, r in enumerate(RUNS):
+        ens.init_fields(k, *_fields(r, k))
+    ens.step(14)
+    for k, r in enumerate(RUNS):
+        lat = rl.Lattice(r["nx"], r["ny"], r["tau"], dtype="bf16", forcing=r["forcing"], kernel="packed",
+                         rounding="stochastic")
+        lat.init_fields(*_fields(r, k))
+        lat.step(14)
+        np.testing.assert_array_equal(ens.populations(k), lat.populations(), err_msg=str(k))
+        lat.close()
+    ens.close()
