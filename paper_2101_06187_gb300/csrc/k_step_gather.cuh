@@ -139,9 +139,23 @@ __global__ void __launch_bounds__(256) k_moments(const TS *__restrict__ qin, Ste
             FramePairs<float> pr;
             landau_refine_df<float>(p.alpha_hi_f, p.alpha_lo_f, p.eps0_f, m.dE, m.Mx, m.My, m.dSxx, m.dSxy, m.dSyy,
                                     delta, fr, &pr);
-            e64 = p.eps0 + ((double)m.dE - ((double)pr.delta_hi + (double)pr.delta_lo));
-            vx64 = (double)pr.vx_hi + (double)pr.vx_lo;
-            vy64 = (double)pr.vy_hi + (double)pr.vy_lo;
+            // one refinement squares the FP32 solve's relative error (a few ulp, about 1e-13 after);
+            // close to the light cone (|v| above about 0.95) the FP32 solve is off by more than
+            // 1e-6 and the refined frame would be too: solve those nodes by FP64 Newton instead
+            const float tol = 1e-6f;
+            const bool fine = fabsf(pr.delta_lo) <= tol * fabsf(pr.delta_hi) + 1e-30f &&
+                              fabsf(pr.vx_lo) + fabsf(pr.vy_lo) <= tol * (fabsf(pr.vx_hi) + fabsf(pr.vy_hi)) + 1e-30f;
+            if (fine) {
+                e64 = p.eps0 + ((double)m.dE - ((double)pr.delta_hi + (double)pr.delta_lo));
+                vx64 = (double)pr.vx_hi + (double)pr.vx_lo;
+                vy64 = (double)pr.vy_hi + (double)pr.vy_lo;
+            } else {
+                const Frame<double> f64 = landau_solve<double>(p.eps0, (double)m.dE, (double)m.Mx, (double)m.My,
+                                                               (double)m.dSxx, (double)m.dSxy, (double)m.dSyy);
+                e64 = f64.eps;
+                vx64 = f64.vx;
+                vy64 = f64.vy;
+            }
             ok = (fmadd(vx64, vx64, vy64 * vy64) < 1.0) && (e64 > 0.0) && isfinite(e64) && isfinite(vx64) &&
                  isfinite(vy64);
         } else {

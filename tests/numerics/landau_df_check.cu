@@ -1,12 +1,13 @@
 // Accuracy of the Landau frame refined to FP64 accuracy on FP32 lanes
 // (landau_refine_df in rlbm_device.cuh, packed lanes of packed.cuh) against
 // the library's FP64 Newton solve of the same FP32 moments, over moments of
-// fluid states with |v| up to 0.6 and energy deviations up to 30%: the
-// refined pairs (delta, v) must agree with the FP64 frame to about 1e-13,
-// the FP32 Newton solve alone to about 1e-7.  Prints one JSON line.  Test
-// infrastructure only.
+// fluid states with |v| up to argv[1] (default 0.6) and energy deviations
+// up to 30%: the refined pairs (delta, v) agree with the FP64 frame to about
+// 1e-13 at |v| <= 0.6, the FP32 Newton solve alone to about 1e-7.  Prints
+// one JSON line.  Test infrastructure only.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include "../../paper_2101_06187_gb300/csrc/packed.cuh"
 
@@ -14,10 +15,11 @@ using namespace rlbk;
 
 // a deterministic spread of node moments: an ideal fluid (eps, v) in the
 // deviation variables of the moments kernel, plus a non-equilibrium part
-__device__ void sample_moments(int i, int n, float &dE, float &Mx, float &My, float &Sxx, float &Sxy, float &Syy) {
+__device__ void sample_moments(int i, int n, double vmax, float &dE, float &Mx, float &My, float &Sxx, float &Sxy,
+                               float &Syy) {
     const double t = (double)i / n;
     const double eps = 0.7 + 0.6 * fmod(t * 7.31, 1.0);
-    const double sp = 0.6 * fmod(t * 3.17 + 0.13, 1.0);
+    const double sp = vmax * fmod(t * 3.17 + 0.13, 1.0);
     const double th = 6.283185307179586 * fmod(t * 11.7, 1.0);
     const double vx = sp * cos(th), vy = sp * sin(th);
     const double g2 = 1.0 / (1.0 - vx * vx - vy * vy);
@@ -31,11 +33,11 @@ __device__ void sample_moments(int i, int n, float &dE, float &Mx, float &My, fl
     Syy = (float)(w * vy * vy + eps / 3.0 - 1.0 / 3.0 - ne);
 }
 
-__global__ void k_check(int n, double *err) {
+__global__ void k_check(int n, double vmax, double *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float dE, Mx, My, Sxx, Sxy, Syy;
-    sample_moments(i, n, dE, Mx, My, Sxx, Sxy, Syy);
+    sample_moments(i, n, vmax, dE, Mx, My, Sxx, Sxy, Syy);
     double d64;
     const Frame<double> f64 = landau_solve<double>(1.0, dE, Mx, My, Sxx, Sxy, Syy, 4.0 / 3.0, &d64);
     float d32;
@@ -70,18 +72,19 @@ __global__ void k_check(int n, double *err) {
     err[3 * i + 2] = e_round;
 }
 
-int main() {
+int main(int argc, char **argv) {
     const int n = 1 << 16;
+    const double vmax = argc > 1 ? std::atof(argv[1]) : 0.6;  // largest |v| of the sampled fluid states
     double *d = nullptr;
     if (cudaMalloc(&d, sizeof(double) * 3 * n) != cudaSuccess) return 1;
-    k_check<<<(n + 127) / 128, 128>>>(n, d);
+    k_check<<<(n + 127) / 128, 128>>>(n, vmax, d);
     double *h = new double[3 * n];
     if (cudaMemcpy(h, d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
     double m[3] = {0, 0, 0};
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) m[k] = fmax(m[k], h[3 * i + k]);
-    std::printf("{\"df_max_rel\": %.3e, \"fp32_max_rel\": %.3e, \"fp32_fields_max_ulp\": %.3f, \"n\": %d}\n", m[0],
-                m[1], m[2], n);
+    std::printf("{\"vmax\": %.3f, \"df_max_rel\": %.3e, \"fp32_max_rel\": %.3e, \"fp32_fields_max_ulp\": %.3f, "
+                "\"n\": %d}\n", vmax, m[0], m[1], m[2], n);
     cudaFree(d);
     delete[] h;
     return 0;
