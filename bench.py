@@ -93,10 +93,13 @@ def dist_env():
 
 # Sources each fused-step variant compiles from (kernel id -> files).
 _STEP_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_gather.cuh", "k_step_vec.cuh", "k_step_pair.cuh",
-                 "k_launch.cuh", "k_step_f32.cu", "k_step_f64.cu", "k_step_h16.cu", "k_step_dfl.cu")
+                 "k_launch.cuh", "k_step_f32.cu", "k_step_f64.cu", "k_step_h16.cu", "k_step_bf16.cu", "k_step_f16.cu",
+                 "k_step_dfl.cu")
 _TMA_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_tma.cuh", "k_step_tma.cu")
 _FUSED2_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_pair.cuh", "k_step_fused2.cuh",
-                   "k_fused2_launch.cuh", "k_step_fused2.cu", "k_step_fused2_sub.cu", "k_step_dfl.cu")
+                   "k_fused2_launch.cuh", "k_fused2_inst.cuh", "k_step_fused2.cu", "k_fused2_f32.cu", "k_fused2_bf16.cu",
+                   "k_fused2_f16.cu", "k_fused2_sub_f32.cu", "k_fused2_sub_bf16.cu", "k_fused2_sub_f16.cu",
+                   "k_step_dfl.cu")
 
 
 def step_kernel_source_hash(kernel_id=4):

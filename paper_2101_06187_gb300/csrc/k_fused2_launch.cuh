@@ -76,29 +76,65 @@ cudaError_t fused2_launch_t(const LaunchCfg &cfg, bool forced, const void *qin, 
     return cudaErrorInvalidConfiguration;
 }
 
-// Every storage form in streaming mode SM: prepare, and launch by dtype.
-template <int SM>
-cudaError_t fused2_prepare_mode() {
-    cudaError_t e = fused2_prepare_t<float, SM>();
-    if (e == cudaSuccess) e = fused2_prepare_t<__nv_bfloat16, SM>();
-    if (e == cudaSuccess) e = fused2_prepare_t<__half, SM>();
-    return e;
-}
-
-template <int SM>
-cudaError_t fused2_launch_mode(int dtype, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
-                               const void *F, const StepParams &p, cudaStream_t s) {
-    switch (dtype) {
-    case RLBM_F32: return fused2_launch_t<float, SM>(cfg, forced, qin, qout, F, p, s);
-    case RLBM_BF16: return fused2_launch_t<__nv_bfloat16, SM>(cfg, forced, qin, qout, F, p, s);
-    case RLBM_F16: return fused2_launch_t<__half, SM>(cfg, forced, qin, qout, F, p, s);
-    default: return cudaErrorInvalidValue;
+// The ensemble kernels of tile shape TW x TH (CFL 1).
+template <typename TS, int TW, int TH, int NT, int MINB>
+struct Fused2Batch {
+    static constexpr int smem = fused2_smem_bytes<TS, TW, TH>();
+    static cudaError_t prepare() {
+        for (void *f : {reinterpret_cast<void *>(&k_step_batch_fused2<TS, TW, TH, NT, MINB, true>),
+                        reinterpret_cast<void *>(&k_step_batch_fused2<TS, TW, TH, NT, MINB, false>)}) {
+            const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
+    static cudaError_t launch(int grid, const void *runs, int nruns, int ntiles, int two, cudaStream_t s) {
+        const BatchRun *r = static_cast<const BatchRun *>(runs);
+        if (two) k_step_batch_fused2<TS, TW, TH, NT, MINB, true><<<grid, NT, smem, s>>>(r, nruns, ntiles);
+        else k_step_batch_fused2<TS, TW, TH, NT, MINB, false><<<grid, NT, smem, s>>>(r, nruns, ntiles);
+        return cudaGetLastError();
+    }
+};
+
+template <typename TS>
+cudaError_t batch_prepare_t() {
+#define X(TW, TH, NT, MB)                                                  \
+    {                                                                      \
+        const cudaError_t e = Fused2Batch<TS, TW, TH, NT, MB>::prepare();  \
+        if (e != cudaSuccess) return e;                                    \
+    }
+    RLBM_FUSED2_SHAPES(X)
+#undef X
+    return cudaSuccess;
 }
 
-// The cfl < 1 instantiations (k_step_fused2_sub.cu).
-cudaError_t fused2_prepare_sub1();
-cudaError_t fused2_launch_sub1(int dtype, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
-                               const void *F, const StepParams &p, cudaStream_t s);
+template <typename TS>
+cudaError_t batch_launch_t(const LaunchCfg &cfg, int grid, const void *runs, int nruns, int ntiles, int two,
+                           cudaStream_t s) {
+#define X(TW, TH, NT, MB)                                                                       \
+    if (cfg.bx == TW && cfg.by == TH)                                                           \
+        return Fused2Batch<TS, TW, TH, NT, MB>::launch(grid, runs, nruns, ntiles, two, s);
+    RLBM_FUSED2_SHAPES(X)
+#undef X
+    return cudaErrorInvalidConfiguration;
+}
+
+// Per storage type and streaming mode, one translation unit each
+// (k_fused2_inst.cuh), so the many kernel instantiations compile in
+// parallel: the single-lattice kernels at CFL 1 with the ensemble kernels,
+// and the single-lattice kernels at 0 < cfl < 1.
+#define RLBM_FUSED2_TYPE_ENTRIES(SFX)                                                                          \
+    cudaError_t fused2_prepare_cfl1_##SFX();                                                                   \
+    cudaError_t fused2_launch_cfl1_##SFX(const LaunchCfg &cfg, bool forced, const void *qin, void *qout,        \
+                                         const void *F, const StepParams &p, cudaStream_t s);                  \
+    cudaError_t fused2_launch_batch_##SFX(const LaunchCfg &cfg, int grid, const void *runs, int nruns,         \
+                                          int ntiles, int two, cudaStream_t s);                                \
+    cudaError_t fused2_prepare_sub1_##SFX();                                                                   \
+    cudaError_t fused2_launch_sub1_##SFX(const LaunchCfg &cfg, bool forced, const void *qin, void *qout,        \
+                                         const void *F, const StepParams &p, cudaStream_t s);
+RLBM_FUSED2_TYPE_ENTRIES(f32)
+RLBM_FUSED2_TYPE_ENTRIES(bf16)
+RLBM_FUSED2_TYPE_ENTRIES(f16)
+#undef RLBM_FUSED2_TYPE_ENTRIES
 
 }  // namespace rlbk
