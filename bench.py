@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--landau", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--kernel", default="auto", choices=["auto", "gather", "vec", "vec2", "packed", "tma", "twopass",
-                                                               "fused2"])
+                                                               "fused2", "packed4"])
     ap.add_argument("--launch", default="", metavar="KERNEL,BX,BY,BUDGET",
                     help="pin one launch shape of the autotuner's list instead of tuning (profiling runs)")
     ap.add_argument("--workload", default="large8192", choices=sorted(WORKLOADS),
@@ -100,6 +100,9 @@ _FUSED2_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_pa
                    "k_fused2_launch.cuh", "k_fused2_inst.cuh", "k_step_fused2.cu", "k_fused2_f32.cu", "k_fused2_bf16.cu",
                    "k_fused2_f16.cu", "k_fused2_sub_f32.cu", "k_fused2_sub_bf16.cu", "k_fused2_sub_f16.cu",
                    "k_step_dfl.cu")
+_QUAD_SOURCES = ("rlbm_device.cuh", "packed.cuh", "k_step_vec.cuh", "k_step_pair.cuh", "k_step_quad.cuh",
+                 "k_quad_inst.cuh", "k_quad_f32.cu", "k_quad_bf16.cu", "k_quad_f16.cu", "k_quad_dfl_f32.cu",
+                 "k_quad_dfl_bf16.cu", "k_quad_dfl_f16.cu")
 
 
 def step_kernel_source_hash(kernel_id=4):
@@ -108,7 +111,7 @@ def step_kernel_source_hash(kernel_id=4):
     order: a stored DRAM-traffic figure counts only while it matches."""
     import hashlib
     src = os.path.join(ROOT, "paper_2101_06187_gb300", "csrc")
-    files = {5: _TMA_SOURCES, 7: _FUSED2_SOURCES}.get(kernel_id, _STEP_SOURCES)
+    files = {5: _TMA_SOURCES, 7: _FUSED2_SOURCES, 8: _QUAD_SOURCES}.get(kernel_id, _STEP_SOURCES)
     hsh = hashlib.sha256()
     for fn in sorted(files):
         with open(os.path.join(src, fn), "rb") as fh:

@@ -123,7 +123,12 @@ typedef enum { RLBM_LANDAU_FP64 = 0, RLBM_LANDAU_FP32 = 1 } rlbm_landau;
  * within one) and an odd remainder runs the packed single step; results
  * equal those of PACKED bit for bit.  block_x x block_y of the launch shape
  * is the output tile (64 x 16, 64 x 8, 32 x 16 or 128 x 8 nodes).
- * The vector, TMA and two-pass variants stream at CFL 1 only, the two-step
+ * PACKED4: the packed body for 4 nodes per thread (two node pairs): each
+ * class row around them is one aligned run of four values plus at most one
+ * side value, half the loads per node of PACKED; results equal PACKED's bit
+ * for bit.  Needs nx divisible by 4, CFL 1 and the one-layer lattice;
+ * FP32 or 16-bit storage, either Landau precision (as PACKED).
+ * The vector, TMA, two-pass and PACKED4 variants stream at CFL 1 only, the two-step
  * kernel at cfl <= 1 (halo 1), the packed kernel at any cfl (halo 2 above 1).
  * AUTO: the autotuned choice if one is cached for this lattice, else
  * GATHER. */
@@ -135,7 +140,8 @@ typedef enum {
     RLBM_KERNEL_PACKED = 4,
     RLBM_KERNEL_TMA = 5,
     RLBM_KERNEL_TWOPASS = 6,
-    RLBM_KERNEL_FUSED2 = 7
+    RLBM_KERNEL_FUSED2 = 7,
+    RLBM_KERNEL_PACKED4 = 8
 } rlbm_kernel;
 
 /* Stirring force (Sec. 5).  Modes are the integer wavevectors k with

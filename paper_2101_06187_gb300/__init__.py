@@ -31,7 +31,7 @@ STENCILS = {"sph26": RLBM_STENCIL_SPH26_SLAB, "ring8": RLBM_STENCIL_RING8_2D}
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 ROUNDING = {"default": 0, "nearest": 1, "stochastic": 2}
 LANDAU = {"fp64": 0, "fp32": 1}
-KERNELS = {"auto": 0, "gather": 1, "vec": 2, "vec2": 3, "packed": 4, "tma": 5, "twopass": 6, "fused2": 7}
+KERNELS = {"auto": 0, "gather": 1, "vec": 2, "vec2": 3, "packed": 4, "tma": 5, "twopass": 6, "fused2": 7, "packed4": 8}
 NCLASSES = 17
 
 # Symbols declared in include/rlbm.h (checked by the ABI test).

@@ -190,6 +190,20 @@ static cudaError_t launch_step_h(const rlbm_t *h, const LaunchCfg &cfg, const vo
     }
     if (cfg.kernel == RLBM_KERNEL_PACKED && dfl)
         return launch_step_pair_dfl(h->opts.dtype, cfg, h->forced, qin, qout, h->F, p, h->stream);
+    if (cfg.kernel == RLBM_KERNEL_PACKED4) {
+        switch (h->opts.dtype) {
+        case RLBM_F32:
+            return (dfl ? launch_step_quad_dfl_f32 : launch_step_quad_f32)(cfg, h->forced, qin, qout, h->F, p,
+                                                                          h->stream);
+        case RLBM_BF16:
+            return (dfl ? launch_step_quad_dfl_bf16 : launch_step_quad_bf16)(cfg, h->forced, qin, qout, h->F, p,
+                                                                            h->stream);
+        case RLBM_F16:
+            return (dfl ? launch_step_quad_dfl_f16 : launch_step_quad_f16)(cfg, h->forced, qin, qout, h->F, p,
+                                                                          h->stream);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (cfg.kernel == RLBM_KERNEL_TMA) {
         if (!h->tm_ready) return cudaErrorNotSupported;
         const CUtensorMap &mq = (qin == h->q[0]) ? h->tm_q[0] : h->tm_q[1];
@@ -333,6 +347,8 @@ static const LaunchCfg kCandidates[] = {
     {RLBM_KERNEL_GATHER, 256, 1}, {RLBM_KERNEL_GATHER, 32, 4}, {RLBM_KERNEL_GATHER, 128, 1},
     {RLBM_KERNEL_FUSED2, 64, 16, 2}, {RLBM_KERNEL_FUSED2, 64, 8, 4}, {RLBM_KERNEL_FUSED2, 32, 16, 4},
     {RLBM_KERNEL_FUSED2, 128, 8, 2},
+    {RLBM_KERNEL_PACKED4, 128, 1, 4}, {RLBM_KERNEL_PACKED4, 64, 2, 4}, {RLBM_KERNEL_PACKED4, 32, 4, 4},
+    {RLBM_KERNEL_PACKED4, 128, 1, 3}, {RLBM_KERNEL_PACKED4, 64, 2, 3}, {RLBM_KERNEL_PACKED4, 32, 4, 3},
 };
 // Whether launch shape c can run this lattice (the launchers reject the
 // remaining misfits: storage form, Landau precision, nx parity).
@@ -345,7 +361,8 @@ static bool candidate_applies(const rlbm_t *h, const LaunchCfg &c) {
         !(h->ring && c.kernel == RLBM_KERNEL_FUSED2))
         return false;
     if (c.kernel == RLBM_KERNEL_TMA && !h->tm_ready) return false;
-    if (h->opts.rounding == RLBM_ROUND_STOCHASTIC && c.kernel != RLBM_KERNEL_PACKED && c.kernel != RLBM_KERNEL_FUSED2)
+    if (h->opts.rounding == RLBM_ROUND_STOCHASTIC && c.kernel != RLBM_KERNEL_PACKED &&
+        c.kernel != RLBM_KERNEL_FUSED2 && c.kernel != RLBM_KERNEL_PACKED4)
         return false;  // the other kernels round to nearest
     return true;
 }
@@ -475,12 +492,15 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (opts) o = *opts;
     if (o.dtype < RLBM_F64 || o.dtype > RLBM_F16) return RLBM_ERR_ARG;
     if (o.landau != RLBM_LANDAU_FP64 && o.landau != RLBM_LANDAU_FP32) return RLBM_ERR_ARG;
-    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_FUSED2) return RLBM_ERR_ARG;
+    if (o.kernel < RLBM_KERNEL_AUTO || o.kernel > RLBM_KERNEL_PACKED4) return RLBM_ERR_ARG;
     if (o.kernel == RLBM_KERNEL_TMA && (nx % 2 != 0 || o.dtype != RLBM_F32 || o.landau != RLBM_LANDAU_FP32))
         return RLBM_ERR_ARG;
     if ((o.kernel == RLBM_KERNEL_PACKED || o.kernel == RLBM_KERNEL_TWOPASS || o.kernel == RLBM_KERNEL_FUSED2) &&
         (nx % 2 != 0 || o.dtype == RLBM_F64))
         return RLBM_ERR_ARG;
+    if (o.kernel == RLBM_KERNEL_PACKED4 && (nx % 4 != 0 || o.dtype == RLBM_F64 || ring || d3 ||
+                                            !(o.cfl == 0.0 || o.cfl == 1.0)))
+        return RLBM_ERR_ARG;  // four nodes per thread: aligned runs of four, CFL 1, the one-layer lattice
     // the FP64 Landau solve on the packed kernels is the frame refined on the FP32 lanes: one-layer lattice, CFL 1
     if (o.landau != RLBM_LANDAU_FP32 &&
         (o.kernel == RLBM_KERNEL_TWOPASS ||
@@ -507,7 +527,7 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
     if (o.rounding < RLBM_ROUND_DEFAULT || o.rounding > RLBM_ROUND_STOCHASTIC) return RLBM_ERR_ARG;
     const bool h16 = o.dtype == RLBM_BF16 || o.dtype == RLBM_F16;
     const bool sr_kernel = o.kernel == RLBM_KERNEL_AUTO || o.kernel == RLBM_KERNEL_PACKED ||
-                           o.kernel == RLBM_KERNEL_FUSED2;
+                           o.kernel == RLBM_KERNEL_FUSED2 || o.kernel == RLBM_KERNEL_PACKED4;
     if (o.rounding == RLBM_ROUND_DEFAULT)  // BF16: stochastic where the kernel can, else nearest
         o.rounding = (o.dtype == RLBM_BF16 && !ring && !d3 && sr_kernel && nx % 2 == 0) ? RLBM_ROUND_STOCHASTIC
                                                                                            : RLBM_ROUND_NEAREST;
@@ -589,6 +609,11 @@ static rlbm_status create_impl(int nx, int ny, int nz, bool d3, rlbm_stencil ste
             h->cfg.bx = 64;
             h->cfg.by = 2;
             h->cfg.minb = 3;
+        }
+        if (o.kernel == RLBM_KERNEL_PACKED4) {  // 128 threads per block, four blocks per SM
+            h->cfg.bx = 128;
+            h->cfg.by = 1;
+            h->cfg.minb = 4;
         }
         if (o.kernel == RLBM_KERNEL_FUSED2) {  // 64 x 16 output tiles, two CTAs per SM
             h->cfg.bx = 64;

@@ -71,6 +71,20 @@ cudaError_t launch_step_pair_dfl(int dtype, const LaunchCfg &cfg, bool forced, c
 cudaError_t fused2_dfl_prepare();
 cudaError_t launch_step_fused2_dfl(int dtype, const LaunchCfg &cfg, bool forced, const void *qin, void *qout,
                                    const void *F, const StepParams &p, cudaStream_t s);
+// Four nodes per thread (k_quad_*.cu, k_quad_dfl_*.cu): the packed body for
+// two node pairs per thread, FP32 / BF16 / FP16 storage, the FP32 Landau
+// frame or (_dfl_) the frame refined to FP64 accuracy on the FP32 lanes,
+// CFL 1, nx divisible by 4; cfg.bx x cfg.by <= 128 threads, cfg.minb 3 or 4.
+#define RLBM_QUAD_ENTRY(NAME)                                                                               \
+    cudaError_t NAME(const LaunchCfg &cfg, bool forced, const void *qin, void *qout, const void *F,         \
+                     const StepParams &p, cudaStream_t s);
+RLBM_QUAD_ENTRY(launch_step_quad_f32)
+RLBM_QUAD_ENTRY(launch_step_quad_bf16)
+RLBM_QUAD_ENTRY(launch_step_quad_f16)
+RLBM_QUAD_ENTRY(launch_step_quad_dfl_f32)
+RLBM_QUAD_ENTRY(launch_step_quad_dfl_bf16)
+RLBM_QUAD_ENTRY(launch_step_quad_dfl_f16)
+#undef RLBM_QUAD_ENTRY
 // Ensemble form over `runs` (BatchRun descriptors with TW x TH tiles, cfl 1
 // members): two steps per launch (two != 0) or one packed step.
 cudaError_t launch_batch_fused2(int dtype, int landau, const LaunchCfg &cfg, int grid, const void *runs, int nruns,

@@ -118,8 +118,20 @@ def test_create_rejects_invalid_arguments_without_touching_the_device(lib):
     o.dtype = rl.DTYPES["f32"]
     assert lib.rlbm_create3d(16, 16, 16, ctypes.c_double(0.8), None, ctypes.byref(o),
                              ctypes.byref(out)) == rl.RLBM_ERR_ARG   # not on the 3D lattice
-    o.kernel = 8
-    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # no kernel 8
+    o.kernel = 9
+    assert create(16, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG   # no kernel 9
+    # four nodes per thread: aligned runs of four, CFL 1, FP32 / 16-bit storage, the one-layer lattice
+    for field, value, nx in (("dtype", rl.DTYPES["f32"], 18), ("dtype", rl.DTYPES["f64"], 16),
+                             ("cfl", 0.625, 16), ("cfl", 1.25, 16)):
+        o = rl.rlbm_opts_default()
+        o.kernel = rl.KERNELS["packed4"]
+        setattr(o, field, value)
+        assert create(nx, 16, 0.8, opts=o) == rl.RLBM_ERR_ARG, (field, value, nx)
+    o = rl.rlbm_opts_default()
+    o.kernel = rl.KERNELS["packed4"]
+    assert create(16, 16, 0.8, opts=o, st=rl.RLBM_STENCIL_RING8_2D) == rl.RLBM_ERR_ARG
+    assert lib.rlbm_create3d(16, 16, 16, ctypes.c_double(0.8), None, ctypes.byref(o),
+                             ctypes.byref(out)) == rl.RLBM_ERR_ARG
     ring = rl.RLBM_STENCIL_RING8_2D   # the ring runs the gather kernel at CFL 1 with a fixed tau
     for field, value in (("kernel", rl.KERNELS["vec"]), ("kernel", rl.KERNELS["tma"]), ("cfl", 0.5),
                          ("eta_s", 0.1)):
