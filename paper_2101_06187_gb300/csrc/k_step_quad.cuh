@@ -33,34 +33,29 @@ __device__ __forceinline__ void store_quad(TS *p, float a0, float a1, float b0, 
     store_run<TS, float, 4>(p, out);
 }
 
-template <typename TS, bool FORCED, typename I, bool DFL, bool SR>
-__device__ __forceinline__ void step_quad(const TS *__restrict__ qin, TS *__restrict__ qout,
-                                          const float *__restrict__ F, const StepParams &p, int x0, int y) {
-    const int ym = (y == 0) ? p.ny - 1 : y - 1;
-    const int yp = (y == p.ny - 1) ? 0 : y + 1;
-    const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
-    const int xr = (x0 + 4 == p.nx) ? 0 : x0 + 4;
-    const I rowoff[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
-    const I plane = (I)p.plane;
+// Columns a class row of a run of four reads besides the run itself: x0 - 1
+// (a class pulling from the left) or x0 + 4 (from the right), at CFL 1.
+__host__ __device__ constexpr bool quad_left(int c) { return cls_ox(c) == -1; }
+__host__ __device__ constexpr bool quad_right(int c) {
+    return cls_ox(c) == 1 || (cls_ox(c) == 0 && cls_tx(c) != 0.0);
+}
 
-    pf2 qa[NC], qb[NC];
+// Bilinear pull at CFL 1 (Sec. 3.2) of the pairs (x0, x0 + 1) -> qa and
+// (x0 + 2, x0 + 3) -> qb.  row(C, r, a) fills the class row r around the
+// run: a[1..4] = columns x0 .. x0 + 3, a[0] = x0 - 1 if quad_left(c), a[5] =
+// x0 + 4 if quad_right(c) (pair j reads a[2j .. 2j + 3]); rows[k] is row
+// y - 1 + k in whatever offsets row() takes.  Taps, weights and operation
+// order per lane are those of step_pair.
+template <typename I, typename RowFn>
+__device__ __forceinline__ void pull_quad(RowFn &&row, const I (&rows)[3], pf2 (&qa)[NC], pf2 (&qb)[NC]) {
     static_for<0, NC>([&](auto C) {
         constexpr int c = decltype(C)::value;
         constexpr int ox = cls_ox(c), oy = cls_oy(c);
         constexpr double tx = cls_tx(c), ty = cls_ty(c);
-        // the class row around the four nodes: r[0] = column x0 - 1 (if the
-        // class pulls from the left), r[1..4] = x0 .. x0 + 3, r[5] = x0 + 4
-        // (if it pulls from the right); pair j reads r[2j .. 2j + 3]
-        auto row = [&](I r, float (&a)[6]) {
-            const I base = (I)c * plane + r;
-            load_run<TS, float, 4>(qin + (base + (I)x0), &a[1]);
-            if constexpr (ox == -1) a[0] = load_q<TS, float>(qin + (base + (I)xl));
-            if constexpr (ox == 1 || (ox == 0 && tx != 0.0)) a[5] = load_q<TS, float>(qin + (base + (I)xr));
-        };
         constexpr float w00 = (float)((1.0 - tx) * (1.0 - ty)), w10 = (float)(tx * (1.0 - ty));
         constexpr float w01 = (float)((1.0 - tx) * ty), w11 = (float)(tx * ty);
         float a[6];
-        row(rowoff[oy + 1], a);
+        row(C, rows[oy + 1], a);
         // a whole-cell shift (weight 1) needs no multiply: 1 * a is a exactly
         pf2 va, vb;
         if constexpr (tx == 0.0 && ty == 0.0) {
@@ -76,7 +71,7 @@ __device__ __forceinline__ void step_quad(const TS *__restrict__ qin, TS *__rest
         }
         if constexpr (ty != 0.0) {
             float b[6];
-            row(rowoff[oy + 2], b);
+            row(C, rows[oy + 2], b);
             va = fmadd(pf2(w01), pf2(b[ox + 1], b[ox + 2]), va);
             vb = fmadd(pf2(w01), pf2(b[ox + 3], b[ox + 4]), vb);
             if constexpr (tx != 0.0) {
@@ -87,6 +82,36 @@ __device__ __forceinline__ void step_quad(const TS *__restrict__ qin, TS *__rest
         qa[c] = va;
         qb[c] = vb;
     });
+}
+
+// A class row of a run of four from global memory: the aligned run at x0
+// and the side column xl or xr (the periodic neighbours x0 - 1, x0 + 4).
+template <typename TS, typename I>
+struct QuadRowGlobal {
+    const TS *__restrict__ q;
+    I plane, x0, xl, xr;
+    template <typename C>
+    __device__ __forceinline__ void operator()(C, I r, float (&a)[6]) const {
+        constexpr int c = C::value;
+        const I base = (I)c * plane + r;
+        load_run<TS, float, 4>(q + (base + x0), &a[1]);
+        if constexpr (quad_left(c)) a[0] = load_q<TS, float>(q + (base + xl));
+        if constexpr (quad_right(c)) a[5] = load_q<TS, float>(q + (base + xr));
+    }
+};
+
+template <typename TS, bool FORCED, typename I, bool DFL, bool SR>
+__device__ __forceinline__ void step_quad(const TS *__restrict__ qin, TS *__restrict__ qout,
+                                          const float *__restrict__ F, const StepParams &p, int x0, int y) {
+    const int ym = (y == 0) ? p.ny - 1 : y - 1;
+    const int yp = (y == p.ny - 1) ? 0 : y + 1;
+    const int xl = (x0 == 0) ? p.nx - 1 : x0 - 1;
+    const int xr = (x0 + 4 == p.nx) ? 0 : x0 + 4;
+    const I rowoff[3] = {(I)ym * (I)p.pitch, (I)y * (I)p.pitch, (I)yp * (I)p.pitch};
+    const I plane = (I)p.plane;
+
+    pf2 qa[NC], qb[NC];
+    pull_quad<I>(QuadRowGlobal<TS, I>{qin, plane, (I)x0, (I)xl, (I)xr}, rowoff, qa, qb);
 
     const I n0 = rowoff[1] + (I)x0;
     pf2 Fxa = 0.0f, Fya = 0.0f, Fxb = 0.0f, Fyb = 0.0f;
