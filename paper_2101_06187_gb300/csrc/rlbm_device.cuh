@@ -277,6 +277,34 @@ RLBM_HD inline void moments_add_pair(MomentSums<TC> &a, TC qp, TC qn) {
     }
 }
 
+// Opposite pairs k and k + 1 whose positive classes are (a, a) and (-a, a)
+// (the in-plane diagonals, a = 1/sqrt2, and the corners, a = 1/sqrt3), of
+// equal weight w.  With s_P, d_P and s_Q, d_Q the pairs' sums and
+// differences, S = s_P + s_Q, D = s_P - s_Q, U = d_P + d_Q, V = d_P - d_Q:
+//   E += w S,  S^xx, S^yy += w a^2 S,  S^xy += w a^2 D,
+//   M^x += w a V,  M^y += w a U,  Q^xxx, Q^xyy += w a^3 V,  Q^xxy, Q^yyy += w a^3 U
+// (the same sums as two moments_add_pair calls, in ten multiply-adds
+// instead of twenty).
+template <int k, typename TC>
+RLBM_HD inline void moments_add_diag(MomentSums<TC> &a, TC pp, TC pn, TC qp, TC qn) {
+    constexpr int cP = pair_pos(k), cQ = pair_pos(k + 1);
+    constexpr double w = cls_w(cP), c = cls_cx(cP);
+    static_assert(c > 0.0 && cls_cy(cP) == c && cls_cx(cQ) == -c && cls_cy(cQ) == c && cls_w(cQ) == w,
+                  "pairs k, k + 1 are the diagonal classes (a, a), (-a, a)");
+    const TC sP = pp + pn, dP = pp - pn, sQ = qp + qn, dQ = qp - qn;
+    const TC S = sP + sQ, D = sP - sQ, U = dP + dQ, V = dP - dQ;
+    a.e = fmadd((TC)w, S, a.e);
+    a.sxx = fmadd((TC)(w * c * c), S, a.sxx);
+    a.syy = fmadd((TC)(w * c * c), S, a.syy);
+    a.sxy = fmadd((TC)(w * c * c), D, a.sxy);
+    a.mx = fmadd((TC)(w * c), V, a.mx);
+    a.my = fmadd((TC)(w * c), U, a.my);
+    a.qxxx = fmadd((TC)(w * c * c * c), V, a.qxxx);
+    a.qxyy = fmadd((TC)(w * c * c * c), V, a.qxyy);
+    a.qxxy = fmadd((TC)(w * c * c * c), U, a.qxxy);
+    a.qyyy = fmadd((TC)(w * c * c * c), U, a.qyyy);
+}
+
 // UNIT: the deviation scale s is 1 (FP32 and FP64 storage), so the sums
 // are the moments and the multiplies are skipped (multiplying by 1 is exact:
 // the results are the same bits either way).
@@ -302,10 +330,13 @@ RLBM_HD inline NodeMoments<TC> moments_end(const MomentSums<TC> &a, TC s) {
 template <typename TC, bool UNIT = false>
 RLBM_HD inline NodeMoments<TC> node_moments(const TC (&q)[NC], TC s) {
     MomentSums<TC> a = moments_begin<TC>(q[0]);
-    static_for<0, NPAIR>([&](auto K) {
+    // the axis classes pair by pair, the diagonal and corner classes two pairs at a time
+    static_for<0, 4>([&](auto K) {
         constexpr int k = decltype(K)::value;
         moments_add_pair<k, TC>(a, q[pair_pos(k)], q[pair_neg(k)]);
     });
+    moments_add_diag<4, TC>(a, q[pair_pos(4)], q[pair_neg(4)], q[pair_pos(5)], q[pair_neg(5)]);
+    moments_add_diag<6, TC>(a, q[pair_pos(6)], q[pair_neg(6)], q[pair_pos(7)], q[pair_neg(7)]);
     return moments_end<TC, UNIT>(a, s);
 }
 
@@ -595,9 +626,12 @@ __device__ __forceinline__ void landau_refine_df(TL alpha_hi, TL alpha_lo, TL ep
 // and the odd part  xi [om (P1 - P0) - om P2 xi^2] + G1 (F.c)
 // lets each opposite pair (c, -c) share one evaluation.
 // Coefficients of the per-class update of one node (below).
+// vs = vx + vy, vd = vy - vx, KS = Kxx + Kyy, Gs = G1 (Fx + Fy), Gd =
+// G1 (Fy - Fx): the terms the diagonal classes (a, a), (-a, a) share.
 template <typename TC>
 struct CollideCoef {
     TC K0, Kxx, Kxy, Kyy, o1, no3, G1, om, nom, a0, vx, vy, Fx, Fy;
+    TC vs, vd, KS, Gs, Gd;
 };
 
 // Frame and update coefficients of a node from its moments.  DFL: refine
@@ -668,6 +702,15 @@ RLBM_HD inline Frame<TL> collide_coef(const NodeMoments<TC> &m, TC Fx, TC Fy, co
     k.vy = vy;
     k.Fx = Fx;
     k.Fy = Fy;
+    k.vs = vx + vy;
+    k.vd = vy - vx;
+    k.KS = Kxx + Kyy;
+    k.Gs = 0;
+    k.Gd = 0;
+    if constexpr (FORCED) {
+        k.Gs = G1 * (Fx + Fy);
+        k.Gd = G1 * (Fy - Fx);
+    }
     return fr;
 }
 
@@ -718,16 +761,46 @@ RLBM_HD inline void collide_pair(TC &qp, TC &qn, const CollideCoef<TC> &k) {
     qn = fmadd(n0, an, even - odd);
 }
 
+// Opposite pairs kp and kp + 1 with positive classes (a, a) and (-a, a)
+// (see moments_add_diag): xi = a vs and a vd, the even parts K0 + a^2 KS
+// +- a^2 Kxy, the forcing a Gs and a Gd -- collide_pair's update of the four
+// classes with the terms the two pairs share formed once.
+template <int kp, typename TC, bool FORCED>
+RLBM_HD inline void collide_diag(TC &pp, TC &pn, TC &qp, TC &qn, const CollideCoef<TC> &k) {
+    constexpr int cP = pair_pos(kp), cQ = pair_pos(kp + 1);
+    constexpr double c = cls_cx(cP);
+    static_assert(c > 0.0 && cls_cy(cP) == c && cls_cx(cQ) == -c && cls_cy(cQ) == c,
+                  "pairs kp, kp + 1 are the diagonal classes (a, a), (-a, a)");
+    const TC xiP = (TC)c * k.vs, xiQ = (TC)c * k.vd;
+    const TC base = fmadd((TC)(c * c), k.KS, k.K0);
+    const TC evenP = fmadd((TC)(c * c), k.Kxy, base), evenQ = fmadd((TC)(-c * c), k.Kxy, base);
+    TC oddP = xiP * fmadd(k.no3, xiP * xiP, k.o1);
+    TC oddQ = xiQ * fmadd(k.no3, xiQ * xiQ, k.o1);
+    if constexpr (FORCED) {
+        oddP = fmadd((TC)c, k.Gs, oddP);
+        oddQ = fmadd((TC)c, k.Gd, oddQ);
+    }
+    const TC aPp = fmadd(k.om, xiP, k.a0), aPn = fmadd(k.nom, xiP, k.a0);
+    const TC aQp = fmadd(k.om, xiQ, k.a0), aQn = fmadd(k.nom, xiQ, k.a0);
+    const TC p0 = pp, p1 = pn, q0 = qp, q1 = qn;
+    pp = fmadd(p0, aPp, evenP + oddP);
+    pn = fmadd(p1, aPn, evenP - oddP);
+    qp = fmadd(q0, aQp, evenQ + oddQ);
+    qn = fmadd(q1, aQn, evenQ - oddQ);
+}
+
 template <typename TC, typename TL, bool FORCED, bool DFL = false, bool UNIT = false>
 RLBM_HD inline Frame<TL> collide_node(TC (&q)[NC], TC Fx, TC Fy, const StepParams &p) {
     const NodeMoments<TC> m = node_moments<TC, UNIT>(q, par_scale<TC>(p));
     CollideCoef<TC> k;
     const Frame<TL> fr = collide_coef<TC, TL, FORCED, DFL, UNIT>(m, Fx, Fy, p, k);
     q[0] = collide_rest<TC>(q[0], k);
-    static_for<0, NPAIR>([&](auto K) {
+    static_for<0, 4>([&](auto K) {
         constexpr int kp = decltype(K)::value;
         collide_pair<kp, TC, FORCED>(q[pair_pos(kp)], q[pair_neg(kp)], k);
     });
+    collide_diag<4, TC, FORCED>(q[pair_pos(4)], q[pair_neg(4)], q[pair_pos(5)], q[pair_neg(5)], k);
+    collide_diag<6, TC, FORCED>(q[pair_pos(6)], q[pair_neg(6)], q[pair_pos(7)], q[pair_neg(7)], k);
     return fr;
 }
 
