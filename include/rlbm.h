@@ -230,8 +230,10 @@ typedef struct {
     size_t device_bytes;      /* device memory held by the handle */
     const void *populations;  /* device pointer of the current state, [nclasses][nz][ny][pitch] of the storage type */
     int nz;                   /* layers: 1, or nz of a 3D lattice */
-    int launch_budget;        /* register budget of the chosen launch: minimum resident 256-thread blocks
-                                 per SM asked of the compiler (packed variants), CTAs per SM (TMA), else 1 */
+    int launch_budget;        /* register budget of the chosen launch: minimum resident blocks per SM
+                                 asked of the compiler (256-thread blocks for the packed variants, except
+                                 budget 5: 128; the launch's own blocks of at most 128 threads for PACKED4,
+                                 3 or 4), CTAs per SM (TMA, FUSED2), else 1 */
     int steps_per_launch;     /* lattice steps one launch of the chosen kernel advances: 2 (FUSED2) or 1 */
 } rlbm_info_t;
 
