@@ -134,3 +134,13 @@ def test_autotuner_considers_four_node_runs():
     assert kernel == rl.KERNELS["packed4"] and bx * by <= 128
     lat.step(3)
     lat.close()
+
+
+def test_graphs_and_direct_launches_agree():
+    """Step chunks replayed as CUDA graphs equal the same launches issued
+    one by one (BF16, stochastic rounding, across forcing epochs)."""
+    nx, ny = 132, 50
+    fields = workloads.random_smooth(nx, ny, seed=6, deps=0.05, vmax=0.05)
+    a, _ = _run("packed4", nx, ny, "bf16", fields, steps=(6, 9, 1), rounding="stochastic", use_graphs=True)
+    b, _ = _run("packed4", nx, ny, "bf16", fields, steps=(6, 9, 1), rounding="stochastic", use_graphs=False)
+    np.testing.assert_array_equal(a, b)

@@ -225,18 +225,20 @@ def test_full_size_8192_spectrum_of_two_modes():
     assert np.max(others) < 1e-9 * E[k1], np.max(others)
 
 
-@pytest.mark.parametrize("kernel", ["packed", "fused2"])
-def test_lattice_beyond_32bit_offsets_stays_an_exact_tiling(tiled_reference, kernel):
-    """12032^2 FP32 (145 M nodes, 17 planes = 2.5 G elements: the 64-bit
-    offset path of the packed and two-step kernels), started on the device
-    from the tiled fields; sampled rows of the moments against the oracle's
-    64^2 tile."""
+@pytest.mark.parametrize("dtype,kernel", [("f32", "packed"), ("f32", "fused2"), ("f32", "packed4"),
+                                          ("bf16", "packed4")])
+def test_lattice_beyond_32bit_offsets_stays_an_exact_tiling(tiled_reference, dtype, kernel):
+    """12032^2 (145 M nodes, 17 planes = 2.5 G elements: the 64-bit offset
+    path of the packed, four-node and two-step kernels), started on the
+    device from the tiled fields; sampled rows of the moments against the
+    oracle's 64^2 tile (16-bit stores rounded to nearest, so every period of
+    the tiling evolves identically)."""
     period, tau, nsteps, ref = tiled_reference
     n = 12032
     rep = n // period
     e, a, b = workloads.random_smooth(period, period, seed=77, deps=0.02, vmax=0.02)
     dev = lambda g: torch.as_tensor(g, dtype=torch.float64, device="cuda").repeat(rep, rep).contiguous()
-    lat = rl.Lattice(n, n, tau, dtype="f32", kernel=kernel)
+    lat = rl.Lattice(n, n, tau, dtype=dtype, kernel=kernel, rounding="nearest")
     fe, fa, fb = dev(e), dev(a), dev(b)
     lat.init_fields_device(fe, fa, fb)
     lat.step(nsteps)
@@ -249,4 +251,4 @@ def test_lattice_beyond_32bit_offsets_stays_an_exact_tiling(tiled_reference, ker
     del fe, fa, fb, out
     want = [np.tile(r, (1, rep))[[y % period for y in rows]] for r in ref]
     err_e, err_v = _errs(want, got)
-    assert err_e < TILED_TOL["f32"] and err_v < TILED_TOL["f32"], (err_e, err_v)
+    assert err_e < TILED_TOL[dtype] and err_v < TILED_TOL[dtype], (err_e, err_v)
