@@ -144,3 +144,20 @@ def test_graphs_and_direct_launches_agree():
     a, _ = _run("packed4", nx, ny, "bf16", fields, steps=(6, 9, 1), rounding="stochastic", use_graphs=True)
     b, _ = _run("packed4", nx, ny, "bf16", fields, steps=(6, 9, 1), rounding="stochastic", use_graphs=False)
     np.testing.assert_array_equal(a, b)
+
+
+def test_autotuner_skips_four_node_runs_where_nx_is_not_divisible_by_4():
+    """On an automatic-kernel handle whose rows do not split into runs of
+    four, the four-node shapes are refused by their launcher and passed over;
+    pinning one fails and leaves the handle usable."""
+    nx, ny = 66, 40
+    fields = workloads.random_smooth(nx, ny, seed=8)
+    lat = rl.Lattice(nx, ny, 0.6, dtype="bf16", forcing=FORCING)
+    lat.init_fields(*fields)
+    kernel, _, _ = lat.autotune(reps=2)
+    assert kernel != rl.KERNELS["packed4"]
+    with pytest.raises(rl.RLBMError):
+        lat.set_launch("packed4", 128, 1, 4)
+    lat.step(4)
+    assert lat.info()["step"] == 4
+    lat.close()
