@@ -84,19 +84,24 @@ __device__ __forceinline__ void pull_quad(RowFn &&row, const I (&rows)[3], pf2 (
     });
 }
 
-// A class row of a run of four from global memory: the aligned run at x0
-// and the side column xl or xr (the periodic neighbours x0 - 1, x0 + 4).
-template <typename TS, typename I>
-struct QuadRowGlobal {
-    const TS *__restrict__ q;
-    I plane, x0, xl, xr;
+// A class row of a run of four from global memory, addressed from three
+// per-thread pointers to the run in rows y - 1, y, y + 1 of class 0 plus the
+// class's plane offset; the side columns lie at fixed distances dl = xl - x0
+// and dr = xr - x0 from the run (-1 and +4 away from the periodic edge).
+// (Measured against one 32-bit element offset per load, 10 fewer integer
+// instructions per node.)
+template <typename TS>
+struct QuadRowPtr {
+    const TS *rp[3];
+    long long plane;
+    int dl, dr;
     template <typename C>
-    __device__ __forceinline__ void operator()(C, I r, float (&a)[6]) const {
+    __device__ __forceinline__ void operator()(C, int k, float (&a)[6]) const {
         constexpr int c = C::value;
-        const I base = (I)c * plane + r;
-        load_run<TS, float, 4>(q + (base + x0), &a[1]);
-        if constexpr (quad_left(c)) a[0] = load_q<TS, float>(q + (base + xl));
-        if constexpr (quad_right(c)) a[5] = load_q<TS, float>(q + (base + xr));
+        const TS *p = rp[k] + (long long)c * plane;
+        load_run<TS, float, 4>(p, &a[1]);
+        if constexpr (quad_left(c)) a[0] = load_q<TS, float>(p + dl);
+        if constexpr (quad_right(c)) a[5] = load_q<TS, float>(p + dr);
     }
 };
 
@@ -111,7 +116,10 @@ __device__ __forceinline__ void step_quad(const TS *__restrict__ qin, TS *__rest
     const I plane = (I)p.plane;
 
     pf2 qa[NC], qb[NC];
-    pull_quad<I>(QuadRowGlobal<TS, I>{qin, plane, (I)x0, (I)xl, (I)xr}, rowoff, qa, qb);
+    const int rows[3] = {0, 1, 2};
+    pull_quad<int>(QuadRowPtr<TS>{{qin + (rowoff[0] + (I)x0), qin + (rowoff[1] + (I)x0), qin + (rowoff[2] + (I)x0)},
+                                  (long long)plane, xl - x0, xr - x0},
+                   rows, qa, qb);
 
     const I n0 = rowoff[1] + (I)x0;
     pf2 Fxa = 0.0f, Fya = 0.0f, Fxb = 0.0f, Fyb = 0.0f;
