@@ -379,9 +379,13 @@ def measure_ensemble(torch, rl, flush, steps=20, warmup=5, nruns=64, sides=None,
     peak, _ = load_peaks()
     step_ms = float(np.median(ms))
     side_set = "{256,384,512,768,1024}" if sides is None else "{%s}" % ",".join(str(x) for x in sides)
+    algo = ALGO_BYTES_PER_UPDATE["f32"]  # one read and one write of the 17 classes plus the force, per update
+    moved = info["bytes_per_step"] / info["nodes"]  # what the chosen body moves (half per update of a two-step launch)
     return {"workload": "%d stirred runs, sides %s, tau U[0.51,0.7], bands around U[4,12]" % (nruns, side_set),
             "nodes": int(info["nodes"]), "glups": info["nodes"] / (step_ms / 1e3) / 1e9,
-            "hbm_frac": info["bytes_per_step"] / (step_ms / 1e3) / 1e9 / peak,
+            "hbm_frac": algo * info["nodes"] / (step_ms / 1e3) / 1e9 / peak,
+            "bytes_per_update": algo, "moved_bytes_per_update": moved,
+            "frac_of_moved_bytes": info["bytes_per_step"] / (step_ms / 1e3) / 1e9 / peak,
             "glups_graph_100_steps": info["nodes"] * 100 / (graph_ms / 1e3) / 1e9,
             "block": [bx, by], "grid": grid, "tiles": int(info["ntiles"]), "launches_per_step": 1 / spl,
             "body": {v: k for k, v in rl.KERNELS.items()}[info["kernel"]]}
