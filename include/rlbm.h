@@ -171,7 +171,7 @@ typedef struct {
     int dtype;            /* rlbm_dtype (default RLBM_F32) */
     int landau;           /* rlbm_landau (default RLBM_LANDAU_FP32) */
     int kernel;           /* rlbm_kernel (default RLBM_KERNEL_AUTO) */
-    int use_graphs;       /* 1: replay the step loop as CUDA graphs (default 1) */
+    int use_graphs;       /* 1: replay chunks of two or more launches as CUDA graphs (default 1) */
     double eps0;          /* reference energy density of the deviation (default 1) */
     double scale;         /* s of the deviation; 0 = default: 1 (F64/F32, which accept only 1), 2^-6 (16-bit) */
     void *stream;         /* cudaStream_t the handle works on; NULL = legacy default stream */
@@ -480,7 +480,8 @@ RLBM_API rlbm_status rlbm_synchronize(rlbm_t *h);
  * Each member behaves exactly like an rlbm_t with the ensemble's options;
  * one step of the ensemble is a single launch over a flat list of tiles of
  * all members (a grid-stride loop, so the grid is sized to the GPU), and
- * chunks of steps inside a forcing epoch replay as CUDA graphs.  All members
+ * chunks of two or more launches inside a forcing epoch replay as CUDA
+ * graphs (a single launch goes directly).  All members
  * share one step counter, stream, storage form and the vector kernel (each
  * nx divisible by 4, or by 2 for F64). */
 typedef struct rlbm_batch rlbm_batch_t;

@@ -276,10 +276,14 @@ static rlbm_status launch_steps(rlbm_t *h, int n) {
 // Run `n` steps inside one epoch: replay a captured graph of the even part
 // of n (keyed by that count and the buffer it starts from; it leaves the
 // state in the buffer its launch count implies), then a last single step.
+// An even part of one launch (two steps of a two-step kernel) is launched
+// directly: a graph saves host work only over several launches, and a
+// one-node graph starts its kernel later on the GPU than a plain launch
+// (about 1.8 us at 1024^2, measured with CUDA events).
 static rlbm_status run_chunk(rlbm_t *h, int n) {
-    const bool graphs = h->opts.use_graphs && h->stream != nullptr && n >= 2;
-    if (!graphs) return launch_steps(h, n);
     const int even = n & ~1;
+    const bool graphs = h->opts.use_graphs && h->stream != nullptr && n >= 2 && launches_for(h->cfg, even) >= 2;
+    if (!graphs) return launch_steps(h, n);
     auto key = std::make_pair(even, h->cur);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
@@ -1504,10 +1508,11 @@ static rlbm_status batch_launch_steps(rlbm_batch_t *b, int n) {
     return RLBM_OK;
 }
 
+// As run_chunk: graphs for even parts of several launches only.
 static rlbm_status batch_run_chunk(rlbm_batch_t *b, int n) {
-    const bool graphs = b->opts.use_graphs && b->stream != nullptr && n >= 2;
-    if (!graphs) return batch_launch_steps(b, n);
     const int even = n & ~1;
+    const bool graphs = b->opts.use_graphs && b->stream != nullptr && n >= 2 && launches_for(b->cfg, even) >= 2;
+    if (!graphs) return batch_launch_steps(b, n);
     auto key = std::make_pair(even, b->cur);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
