@@ -145,11 +145,11 @@ struct C4 {
     TC ax, bx, ay, by;
 };
 
+// Mode m of epoch `epoch`: magnitude, phase and in-plane direction from two
+// Philox4x32-10 blocks keyed by the seed (Sec. 5's random stirring).
 template <typename TC>
-__global__ void k_draw_modes(Mode *modes, C4<TC> *coef, int nmodes, double amp, unsigned long long seed,
-                             unsigned long long epoch) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= nmodes) return;
+__device__ __forceinline__ void draw_mode(Mode *modes, C4<TC> *coef, int m, double amp, unsigned long long seed,
+                                          unsigned long long epoch) {
     const unsigned int k0 = (unsigned int)(seed & 0xffffffffull), k1 = (unsigned int)(seed >> 32);
     U4 c0 = {{(unsigned int)epoch, (unsigned int)m, 0u, 0u}};
     U4 c1 = {{(unsigned int)epoch, (unsigned int)m, 1u, 0u}};
@@ -168,6 +168,14 @@ __global__ void k_draw_modes(Mode *modes, C4<TC> *coef, int nmodes, double amp, 
     md.by = 2.0 * r * sth * sph;
     modes[m] = md;
     coef[m] = C4<TC>{(TC)md.ax, (TC)md.bx, (TC)md.ay, (TC)md.by};
+}
+
+template <typename TC>
+__global__ void k_draw_modes(Mode *modes, C4<TC> *coef, int nmodes, double amp, unsigned long long seed,
+                             unsigned long long epoch) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nmodes) return;
+    draw_mode<TC>(modes, coef, m, amp, seed, epoch);
 }
 
 cudaError_t launch_draw_modes(int dtype, Mode *modes, void *coef, int nmodes, double amp, unsigned long long seed,
@@ -251,11 +259,9 @@ cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, i
 // and per node F = Re sum_j G_j(x) Y_j(y)                   (k_synth_force):
 // 4 multiply-adds per run and node instead of 12 per mode and node.
 template <typename TC>
-__global__ void k_force_rows(C4<TC> *G, const C4<TC> *__restrict__ coef, const int *__restrict__ run_start,
-                             const C2<TC> *__restrict__ X, int nx) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (x >= nx) return;
+__device__ __forceinline__ void force_row(C4<TC> *G, const C4<TC> *__restrict__ coef,
+                                          const int *__restrict__ run_start, const C2<TC> *__restrict__ X, int nx,
+                                          int x, int j) {
     TC xr = 0, xi = 0, yr = 0, yi = 0;
     for (int m = run_start[j]; m < run_start[j + 1]; ++m) {
         const C4<TC> c = coef[m];
@@ -268,16 +274,22 @@ __global__ void k_force_rows(C4<TC> *G, const C4<TC> *__restrict__ coef, const i
     G[(long long)j * nx + x] = C4<TC>{xr, xi, yr, yi};
 }
 
+template <typename TC>
+__global__ void k_force_rows(C4<TC> *G, const C4<TC> *__restrict__ coef, const int *__restrict__ run_start,
+                             const C2<TC> *__restrict__ X, int nx) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    force_row<TC>(G, coef, run_start, X, nx, x, blockIdx.y);
+}
+
 // One thread per column x and SYNTH_ROWS consecutive rows: the row sums
 // G_j(x) are read once per run and reused for every row of the strip.
 constexpr int SYNTH_ROWS = 8;
 
 template <typename TC>
-__global__ void k_synth_force(TC *F, const C4<TC> *__restrict__ G, const int *__restrict__ run_start, int nruns,
-                              const C2<TC> *__restrict__ Y, StepParams p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * SYNTH_ROWS;
-    if (x >= p.nx || y0 >= p.ny) return;
+__device__ __forceinline__ void synth_strip(TC *F, const C4<TC> *__restrict__ G, const int *__restrict__ run_start,
+                                            int nruns, const C2<TC> *__restrict__ Y, const StepParams &p, int x,
+                                            int y0) {
     const int rows = min(SYNTH_ROWS, p.ny - y0);
     TC fx[SYNTH_ROWS], fy[SYNTH_ROWS];
 #pragma unroll
@@ -304,6 +316,15 @@ __global__ void k_synth_force(TC *F, const C4<TC> *__restrict__ G, const int *__
     }
 }
 
+template <typename TC>
+__global__ void k_synth_force(TC *F, const C4<TC> *__restrict__ G, const int *__restrict__ run_start, int nruns,
+                              const C2<TC> *__restrict__ Y, StepParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * SYNTH_ROWS;
+    if (x >= p.nx || y0 >= p.ny) return;
+    synth_strip<TC>(F, G, run_start, nruns, Y, p, x, y0);
+}
+
 cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const int *run_start, int nruns,
                                void *G, const void *X, const void *Y, const StepParams &p, cudaStream_t s) {
     if (nmodes <= 0 || nruns <= 0) return cudaSuccess;
@@ -320,6 +341,59 @@ cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes,
                                                run_start, static_cast<const C2<float> *>(X), p.nx);
         k_synth_force<float><<<grid, block, 0, s>>>(static_cast<float *>(F), static_cast<const C4<float> *>(G),
                                                     run_start, nruns, static_cast<const C2<float> *>(Y), p);
+    }
+    return cudaGetLastError();
+}
+
+// Ensemble-wide synthesis: the kernels above for every job whose redraw
+// period divides `step` (job = blockIdx.y for the draw, blockIdx.z for the
+// other two), each on its own lattice's sizes, so a member's force is the
+// one launch_draw_modes + launch_synth_force give it.
+__device__ __forceinline__ bool job_redraws(const ForceJob &j, long long step) { return step % j.period == 0; }
+
+template <typename TC>
+__global__ void k_draw_modes_jobs(const ForceJob *__restrict__ jobs, long long step) {
+    const ForceJob &j = jobs[blockIdx.y];
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= j.nmodes || !job_redraws(j, step)) return;
+    draw_mode<TC>(j.modes, static_cast<C4<TC> *>(j.coef), m, j.amp, j.seed, (unsigned long long)(step / j.period));
+}
+
+template <typename TC>
+__global__ void k_force_rows_jobs(const ForceJob *__restrict__ jobs, long long step) {
+    const ForceJob &j = jobs[blockIdx.z];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= j.p.nx || (int)blockIdx.y >= j.nruns || !job_redraws(j, step)) return;
+    force_row<TC>(static_cast<C4<TC> *>(j.G), static_cast<const C4<TC> *>(j.coef), j.run_start,
+                  static_cast<const C2<TC> *>(j.X), j.p.nx, x, blockIdx.y);
+}
+
+template <typename TC>
+__global__ void k_synth_force_jobs(const ForceJob *__restrict__ jobs, long long step) {
+    const ForceJob &j = jobs[blockIdx.z];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * SYNTH_ROWS;
+    if (x >= j.p.nx || y0 >= j.p.ny || !job_redraws(j, step)) return;
+    synth_strip<TC>(static_cast<TC *>(j.F), static_cast<const C4<TC> *>(j.G), j.run_start, j.nruns,
+                    static_cast<const C2<TC> *>(j.Y), j.p, x, y0);
+}
+
+cudaError_t launch_force_jobs(int dtype, const ForceJob *jobs, int njobs, int max_nmodes, int max_nruns, int max_nx,
+                              int max_ny, long long step, cudaStream_t s) {
+    if (njobs <= 0 || max_nmodes <= 0 || max_nruns <= 0) return cudaSuccess;
+    if (njobs > 65535 || max_nruns > 65535) return cudaErrorInvalidValue;
+    const dim3 gd((max_nmodes + 127) / 128, njobs, 1);
+    const dim3 gr((max_nx + 255) / 256, max_nruns, njobs);
+    const dim3 block(32, 8, 1);
+    const dim3 gs((max_nx + 31) / 32, (max_ny + 8 * SYNTH_ROWS - 1) / (8 * SYNTH_ROWS), njobs);
+    if (dtype == RLBM_F64) {
+        k_draw_modes_jobs<double><<<gd, 128, 0, s>>>(jobs, step);
+        k_force_rows_jobs<double><<<gr, 256, 0, s>>>(jobs, step);
+        k_synth_force_jobs<double><<<gs, block, 0, s>>>(jobs, step);
+    } else {
+        k_draw_modes_jobs<float><<<gd, 128, 0, s>>>(jobs, step);
+        k_force_rows_jobs<float><<<gr, 256, 0, s>>>(jobs, step);
+        k_synth_force_jobs<float><<<gs, block, 0, s>>>(jobs, step);
     }
     return cudaGetLastError();
 }

@@ -1408,6 +1408,8 @@ struct rlbm_batch {
     int grid = 0;          // blocks of the persistent launch
     int ntiles = 0;
     BatchRun *desc[2] = {nullptr, nullptr};  // device descriptors for parity 0 / 1
+    ForceJob *jobs = nullptr;  // device: the forced members' force synthesis, for epoch starts in three launches
+    int njobs = 0, job_nmodes = 0, job_nruns = 0, job_nx = 0, job_ny = 0;  // count and grid extents
     int cur = 0;
     long long step = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
@@ -1560,6 +1562,73 @@ static rlbm_status from_member(rlbm_batch_t *b, rlbm_t *h, rlbm_status st) {
     return st;
 }
 
+// The forced members' force synthesis as one job list on the device (what
+// ensure_force launches per member), built once at create.
+static rlbm_status batch_build_jobs(rlbm_batch_t *b) {
+    std::vector<ForceJob> jobs;
+    for (const rlbm_t *h : b->runs) {
+        if (!h->forced || h->nmodes <= 0) continue;
+        ForceJob j;
+        j.modes = h->modes;
+        j.coef = h->coef;
+        j.run_start = h->ky_start;
+        j.G = h->gtab;
+        j.X = h->tabx;
+        j.Y = h->taby;
+        j.F = h->F;
+        j.amp = h->forcing.amp;
+        j.seed = (unsigned long long)h->forcing.seed;
+        j.period = h->forcing.redraw_period;
+        j.nmodes = h->nmodes;
+        j.nruns = h->nky;
+        j.p = params_of(h);
+        jobs.push_back(j);
+        b->job_nmodes = std::max(b->job_nmodes, h->nmodes);
+        b->job_nruns = std::max(b->job_nruns, h->nky);
+        b->job_nx = std::max(b->job_nx, h->nx);
+        b->job_ny = std::max(b->job_ny, h->ny);
+    }
+    if (jobs.empty() || jobs.size() > 65535) return RLBM_OK;  // member by member (grid z limit)
+    b->jobs = static_cast<ForceJob *>(dev_alloc(b->runs[0], sizeof(ForceJob) * jobs.size()));
+    if (!b->jobs) return RLBM_ERR_ALLOC;
+    b->njobs = (int)jobs.size();
+    BCUDA_TRY(b, cudaMemcpy(b->jobs, jobs.data(), sizeof(ForceJob) * jobs.size(), cudaMemcpyHostToDevice));
+    return RLBM_OK;
+}
+
+// Bring every forced member's force to the epoch of the ensemble's step.
+// Where each member that needs a new force starts an epoch at this step (a
+// run stepped from its start), one ensemble-wide synthesis in three launches
+// redraws every member that starts an epoch here (a member already holding
+// that epoch's force gets the same values again); otherwise member by member
+// (192 launches for 64 members).
+static rlbm_status batch_ensure_forces(rlbm_batch_t *b) {
+    bool any = false, aligned = true;
+    for (rlbm_t *h : b->runs) {
+        if (!h->forced) continue;
+        batch_sync_member(b, h);
+        if (b->step / h->forcing.redraw_period == h->force_epoch) continue;
+        any = true;
+        if (b->step % h->forcing.redraw_period != 0) aligned = false;
+    }
+    if (!any) return RLBM_OK;
+    if (aligned && b->njobs > 0) {
+        NvtxRange range("rlbm_force_epoch");
+        BCUDA_TRY(b, launch_force_jobs(b->opts.dtype, b->jobs, b->njobs, b->job_nmodes, b->job_nruns, b->job_nx,
+                                       b->job_ny, b->step, b->stream));
+        for (rlbm_t *h : b->runs)
+            if (h->forced && h->nmodes > 0 && b->step % h->forcing.redraw_period == 0)
+                h->force_epoch = b->step / h->forcing.redraw_period;
+        return RLBM_OK;
+    }
+    for (rlbm_t *h : b->runs) {
+        if (!h->forced) continue;
+        rlbm_status st = from_member(b, h, ensure_force(h));
+        if (st != RLBM_OK) return st;
+    }
+    return RLBM_OK;
+}
+
 extern "C" {
 
 void rlbm_batch_destroy(rlbm_batch_t *b) {
@@ -1571,6 +1640,7 @@ void rlbm_batch_destroy(rlbm_batch_t *b) {
     if (!b->runs.empty()) {
         for (int par = 0; par < 2; ++par)
             dev_free(b->runs[0], b->desc[par], sizeof(BatchRun) * b->runs.size());
+        if (b->jobs) dev_free(b->runs[0], b->jobs, sizeof(ForceJob) * b->njobs);
     }
     for (rlbm_t *h : b->runs) rlbm_destroy(h);
     delete b;
@@ -1627,6 +1697,11 @@ rlbm_status rlbm_batch_create(int nruns, const rlbm_run_desc *runs, const rlbm_o
             return RLBM_ERR_ALLOC;
         }
     }
+    rlbm_status stj = batch_build_jobs(b);
+    if (stj != RLBM_OK) {
+        rlbm_batch_destroy(b);
+        return stj;
+    }
     if (bk == RLBM_KERNEL_PACKED) b->cfg = LaunchCfg{RLBM_KERNEL_PACKED, 64, 2, 1};
     else if (bk == RLBM_KERNEL_FUSED2) b->cfg = LaunchCfg{RLBM_KERNEL_FUSED2, 64, 8, 4};
     else b->cfg = LaunchCfg{RLBM_KERNEL_GATHER_VEC, 64, 2, 1};
@@ -1657,11 +1732,10 @@ rlbm_status rlbm_batch_step(rlbm_batch_t *b, int n) {
     if (n < 0) return bfail(b, RLBM_ERR_ARG, "negative step count");
     while (n > 0) {
         int chunk = n;
+        rlbm_status st0 = batch_ensure_forces(b);
+        if (st0 != RLBM_OK) return st0;
         for (rlbm_t *h : b->runs) {
             if (!h->forced) continue;
-            batch_sync_member(b, h);
-            rlbm_status st = from_member(b, h, ensure_force(h));
-            if (st != RLBM_OK) return st;
             const int left = h->forcing.redraw_period - (int)(b->step % h->forcing.redraw_period);
             chunk = std::min(chunk, left);
         }
@@ -1701,12 +1775,8 @@ rlbm_status rlbm_batch_get_populations(rlbm_batch_t *b, int run, double *f) {
 rlbm_status rlbm_batch_autotune(rlbm_batch_t *b, int reps, int *block_x, int *block_y, int *grid) {
     CHECK_BATCH(b);
     if (reps < 1) reps = 10;
-    for (rlbm_t *h : b->runs) {
-        if (!h->forced) continue;
-        batch_sync_member(b, h);
-        rlbm_status st = from_member(b, h, ensure_force(h));
-        if (st != RLBM_OK) return st;
-    }
+    rlbm_status st0 = batch_ensure_forces(b);
+    if (st0 != RLBM_OK) return st0;
     static const int shapes[][2] = {{32, 4}, {64, 2}, {128, 1}, {32, 8}, {64, 4}, {128, 2}, {32, 2}, {64, 1}};
     // two-step tiles (bx x by nodes) and their launch budgets
     static const int tiles2[][3] = {{64, 8, 4}, {64, 16, 2}, {32, 16, 4}, {128, 8, 2}};

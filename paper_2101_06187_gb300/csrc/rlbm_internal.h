@@ -23,6 +23,24 @@ struct Mode {
     double ax, bx, ay, by;
 };
 
+// One lattice's stirring force in an ensemble-wide synthesis: what
+// launch_draw_modes and launch_synth_force take for that lattice, plus its
+// redraw period (a lattice redraws at steps divisible by it, epoch = step /
+// period).  Device pointers; p is the lattice's step parameters.
+struct ForceJob {
+    Mode *modes;
+    void *coef;
+    const int *run_start;  // first mode of each run of equal ky, then nmodes [nruns + 1]
+    void *G;               // per-run row sums [nruns][nx] x 4
+    const void *X, *Y;     // per-mode phase tables [nmodes][nx], [nmodes][ny]
+    void *F;
+    double amp;
+    unsigned long long seed;
+    long long period;
+    int nmodes, nruns;
+    StepParams p;
+};
+
 // Launch shape of the fused step: kernel variant, thread-block shape and a
 // launch budget -- for the packed kernels the minimum resident blocks per SM
 // asked of the register allocator (1, 2, 3; 5 = five 128-thread blocks),
@@ -147,6 +165,13 @@ cudaError_t launch_mode_tables(int dtype, void *X, void *Y, const Mode *modes, i
 // runs with the run's y table (Y of its first mode); G is [nky][nx] x 4.
 cudaError_t launch_synth_force(int dtype, void *F, const void *coef, int nmodes, const int *ky_start, int nky,
                                void *G, const void *X, const void *Y, const StepParams &p, cudaStream_t s);
+// The force of every job in `jobs` (device array of njobs) whose period
+// divides `step`, in three launches for all of them; max_*: the largest
+// mode count, run count and sides among the jobs (the grid).  Per job the
+// arithmetic of launch_draw_modes + launch_synth_force, so the force is the
+// same bit for bit.
+cudaError_t launch_force_jobs(int dtype, const ForceJob *jobs, int njobs, int max_nmodes, int max_nruns, int max_nx,
+                              int max_ny, long long step, cudaStream_t s);
 cudaError_t launch_decode_class(int dtype, const void *q, int c, double W, const StepParams &p, double *out,
                                 cudaStream_t s);
 cudaError_t launch_encode_class(int dtype, void *q, int c, double W, const StepParams &p, const double *in,
