@@ -1588,7 +1588,7 @@ static rlbm_status batch_build_jobs(rlbm_batch_t *b) {
         b->job_nx = std::max(b->job_nx, h->nx);
         b->job_ny = std::max(b->job_ny, h->ny);
     }
-    if (jobs.empty() || jobs.size() > 65535) return RLBM_OK;  // member by member (grid z limit)
+    if (jobs.empty() || jobs.size() > 65535 || b->job_nruns > 65535) return RLBM_OK;  // member by member (grid limits)
     b->jobs = static_cast<ForceJob *>(dev_alloc(b->runs[0], sizeof(ForceJob) * jobs.size()));
     if (!b->jobs) return RLBM_ERR_ALLOC;
     b->njobs = (int)jobs.size();
