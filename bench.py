@@ -740,7 +740,9 @@ def main():
                      "kernel": kname, "launch_ms": launch_ms, "updates_per_launch": nodes * spl,
                      "epoch_launches_in_timed_region": n_epoch},
         "clocks": clocks.summary(),
-        "gpu_launches": int(info["timed_launches"] + 2 * n_epoch),
+        # an epoch start adds the force draw and synthesis: draw, row sums and synthesis (2D), draw and
+        # synthesis (3D lattice)
+        "gpu_launches": int(info["timed_launches"] + (2 if args.nz > 0 else 3) * n_epoch),
     }
     if ent:
         line["roofline"]["traffic_source"] = ent.get("from")
